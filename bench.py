@@ -1,0 +1,397 @@
+"""Benchmark of the L-ACE exchange hot path on one GB300 (or N independent replicas).
+
+Workload: the water-like localized-exchange system -- cubic L = 23.5 bohr,
+72^3 grid, 256 occupied orbitals (Gaussian sums around 192 centres,
+band-limited to 40 Ha), SCDM on the 1/8 grid subsample, overlap-of-moduli
+screening at S_thr = 1e-3.  One step is the whole hot path on inputs already
+in HBM: Loewdin orthonormalisation, SCDM localisation, screening, the
+screened pair convolutions with E_x, the ACE build (M, Cholesky, xi) and one
+ACE application to the N_P orbitals.  The metric counts the real pair
+convolutions (Poisson solves) of the step.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl lace|reference]
+Under torchrun each rank runs its own replica of the workload (weak scaling,
+no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Fock pair-convolutions/s & ACE build ms vs plain FP64 at stated dE_x; p99 latency"
+UNIT = "pair-convolutions/s"
+S_THR = 1e-3
+STRIDE = 2
+B_ALG_PER_PAIR_FP32 = 16  # bytes per grid point per real pair (3-pass FFT model)
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="lace", choices=["lace", "reference"])
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--profile-pairconv", action="store_true",
+                   help="only the pair convolutions of a 64-orbital 72^3 set (for ncu captures)")
+    p.add_argument("--fp64", action="store_true", help="with --profile-pairconv: FP64 path")
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(seed):
+    import synth
+
+    return synth.config2_water_like(seed=seed)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax = float(f[2])
+            except ValueError:
+                continue
+            for k, name in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        busy = [x for x in sm if smax and x > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def run_lace(args, rank, world, local):
+    import torch
+
+    import paper_1801_09263_gb300 as lace
+    from paper_1801_09263_gb300.build import build
+
+    build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+    sysm = workload(1801 + 1 + rank)
+    n, ng = sysm.n_occ, int(np.prod(sysm.shape))
+    phi_dev = torch.from_numpy(sysm.phi).to(dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    def make_ctx(prec):
+        ctx = lace.Lace(local, prec)
+        ctx.set_stream(stream.cuda_stream)
+        ctx.set_cell(sysm.cell, sysm.shape, sysm.ecut)
+        return ctx
+
+    out_dev = torch.empty_like(phi_dev)
+
+    def step(ctx):
+        ctx.load_orbitals_dev(phi_dev, n, 0, True)
+        ctx.localize(STRIDE)
+        npairs = ctx.screen(S_THR)
+        ctx.apply_exchange(want_W=False)
+        ctx.build_ace(lace.LACE_SYM_AVG)
+        ctx.apply_ace_dev(phi_dev, out_dev)
+        return npairs
+
+    # ---------------- mixed precision (headline)
+    ctx = make_ctx(lace.LACE_MIXED)
+    for _ in range(args.warmup):
+        npairs = step(ctx)
+    launches0 = ctx.launch_count()
+    pc_ms, ace_ms, step_ms = [], [], []
+    sampler = ClockSampler(local)
+    barrier()
+    sampler.start()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        e_a = torch.cuda.Event(enable_timing=True)
+        e_b = torch.cuda.Event(enable_timing=True)
+        e_a.record(stream)
+        npairs = step(ctx)
+        e_b.record(stream)
+        t = ctx.get_timings()
+        pc_ms.append(t["pairconv_kernels"])
+        ace_ms.append(t["ace_build"])
+        e_b.synchronize()
+        step_ms.append(e_a.elapsed_time(e_b))
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    total_ms = ev0.elapsed_time(ev1)
+    launches = ctx.launch_count() - launches0
+    stages = ctx.get_timings()
+    ex_mixed = ctx.exchange_energy(1.0)
+    if world > 1:
+        import torch.distributed as dist
+
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = npairs * args.steps * world / (total_ms / 1e3)
+
+    # ---------------- plain FP64 GPU form (same step)
+    fp64 = None
+    if not args.no_fp64:
+        c64 = make_ctx(lace.LACE_FP64)
+        step(c64)
+        barrier()
+        e_a = torch.cuda.Event(enable_timing=True)
+        e_b = torch.cuda.Event(enable_timing=True)
+        e_a.record(stream)
+        np64 = step(c64)
+        e_b.record(stream)
+        e_b.synchronize()
+        t64 = e_a.elapsed_time(e_b)
+        st64 = c64.get_timings()
+        ex64 = c64.exchange_energy(1.0)
+        fp64 = {"pair_convolutions_per_s": np64 / (t64 / 1e3), "step_ms": t64, "n_pairs": np64,
+                "pairconv_kernels_ms": st64["pairconv_kernels"], "ace_build_ms": st64["ace_build"],
+                "E_x_Ha": ex64, "dE_x_mixed_vs_fp64_Ha": ex_mixed - ex64}
+        c64.close()
+
+    # ---------------- end to end through the host API (pinned host buffers)
+    e2e = None
+    if not args.no_e2e:
+        phi_pin = torch.from_numpy(sysm.phi).pin_memory()
+        w_pin = torch.empty_like(phi_pin).pin_memory()
+        k_pin = torch.empty_like(phi_pin).pin_memory()
+        phi_np, w_np, k_np = phi_pin.numpy(), w_pin.numpy(), k_pin.numpy()
+        import ctypes as C
+
+        def e2e_step():
+            ctx._check(ctx.lib.lace_load_orbitals(ctx.h, phi_np.ctypes.data_as(C.c_void_p), n, 0, 1), "load")
+            ctx.localize(STRIDE)
+            ctx.screen(S_THR)
+            ex = C.c_double()
+            ctx._check(ctx.lib.lace_apply_exchange(ctx.h, w_np.ctypes.data_as(C.c_void_p), C.byref(ex)), "apply")
+            ctx.build_ace(lace.LACE_SYM_AVG)
+            ctx._check(ctx.lib.lace_apply_ace(ctx.h, phi_np.ctypes.data_as(C.c_void_p), n,
+                                              k_np.ctypes.data_as(C.c_void_p)), "apply ace")
+            return ex.value
+
+        e2e_step()
+        barrier()
+        t0 = time.perf_counter()
+        ksteps = max(1, min(args.steps, 3))
+        for _ in range(ksteps):
+            e2e_step()
+        barrier()
+        dt = time.perf_counter() - t0
+        e2e = {"value": npairs * ksteps * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": 2 * phi_np.nbytes, "d2h_bytes_per_step": w_np.nbytes + k_np.nbytes + 8,
+               "steps": ksteps}
+    ctx.close()
+
+    # ---------------- roofline of the pair-convolution kernels
+    peak, peak_kind = peaks()
+    pc_avg = statistics.mean(pc_ms)
+    alg_bytes = B_ALG_PER_PAIR_FP32 * ng * npairs
+    achieved = alg_bytes / (pc_avg / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
+            "kernel": "pairconv passes A+B+C (per step)", "alg_bytes_per_step": alg_bytes}
+    tr = os.path.join(ROOT, "profiles", "pairconv_traffic.json")
+    if os.path.exists(tr):
+        try:
+            d = json.load(open(tr))
+            if d.get("valid_for") == "pairconv-v1":
+                roof["traffic"] = d["traffic_bytes_per_step"]
+        except Exception:
+            pass
+    result = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "water-like localized exchange: L=23.5 bohr, 72^3, 256 occupied orbitals, "
+                               "SCDM stride 2, S_thr=1e-3, step = Loewdin+SCDM+screen+pair-conv+ACE build+ACE apply",
+                   "n_pairs": npairs, "kept_fraction": npairs / (n * (n + 1) / 2), "grid": list(sysm.shape),
+                   "n_occ": n, "precision": "mixed (FP32 FFT, FP64 energies and N x N factorisations)",
+                   "l2": "inputs (764 MB FP64 orbitals) larger than L2", "parallelism": f"replicas x{world}"},
+        "stages_ms": {k: round(v, 3) for k, v in stages.items()},
+        "ace_build_ms": round(statistics.mean(ace_ms), 3),
+        "latency_ms": {"p50": round(statistics.median(step_ms), 3),
+                       "p99": round(float(np.percentile(step_ms, 99)), 3)},
+        "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
+        "fp64_gpu": fp64, "E_x_Ha": ex_mixed,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(sysm, budget_s=15.0)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+
+
+def oracle_sample(sysm, n_targets):
+    """Localised orbitals and kept pairs from the oracle, plus a target sample."""
+    import oracle as O
+
+    g = O.Grid(sysm.cell, sysm.shape)
+    occ = O.lowdin(g, sysm.phi[: sysm.n_occ])
+    piv, _, w = O.scdm(g, occ, STRIDE)
+    s = O.overlap_moduli(g, w)
+    keep = O.kept_pairs(s, S_THR, sysm.n_occ, 0)
+    rng = np.random.default_rng(0)
+    targets = rng.choice(sysm.n_occ, size=n_targets, replace=False)
+    return g, w, keep, targets
+
+
+def cpu_baseline(sysm, budget_s=15.0, prepared=None):
+    """Oracle pair convolutions on the host cores, on a bounded sample of targets."""
+    import oracle as O
+
+    g, w, keep, targets = prepared or oracle_sample(sysm, 64)
+    done, t0 = 0, time.perf_counter()
+    used = []
+    for j in targets:
+        cols = keep[:, j:j + 1]
+        O.apply_exchange_columns(g, w, w[j:j + 1], cols)
+        done += int(cols.sum())
+        used.append(int(j))
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": round(done / dt, 2), "unit": UNIT, "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"oracle K psi_j for {len(used)} localized targets ({done} pair convolutions, scipy.fft "
+                      f"workers={len(os.sched_getaffinity(0))}) of the same 72^3 workload"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    sysm = workload(1801 + 1)
+    prepared = oracle_sample(sysm, 64)
+    for _ in range(args.warmup):
+        cpu_baseline(sysm, budget_s=2.0, prepared=prepared)
+    vals, t0 = [], time.perf_counter()
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(sysm, budget_s=8.0, prepared=prepared))
+    total = time.perf_counter() - t0
+    v = statistics.mean(x["value"] for x in vals)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1e3 * total / args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "water-like localized exchange: L=23.5 bohr, 72^3, 256 occupied orbitals, "
+                               "SCDM stride 2, S_thr=1e-3 (oracle pair convolutions on a target sample)"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": vals[0]["cores"],
+                         "sample": vals[0]["sample"]},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def run_profile(args, local):
+    """Pair convolutions only: 64 orbitals on the 72^3 grid, every pair (2080)."""
+    import synth
+    import torch
+
+    import paper_1801_09263_gb300 as lace
+    from paper_1801_09263_gb300.build import build
+
+    build()
+    torch.cuda.set_device(local)
+    sysm = synth.small_localized_system(7, (23.5, 23.5, 23.5), (72, 72, 72), 40.0, 48, 64)
+    ctx = lace.Lace(local, lace.LACE_FP64 if args.fp64 else lace.LACE_MIXED)
+    ctx.set_cell(sysm.cell, sysm.shape, sysm.ecut)
+    ctx.load_orbitals(sysm.phi, sysm.n_occ, 0, False)
+    for _ in range(max(1, args.steps)):
+        ctx.apply_exchange(want_W=False)
+    t = ctx.get_timings()
+    n = sysm.n_occ * (sysm.n_occ + 1) // 2
+    print(json.dumps({"profile": "pairconv", "n_pairs": n, "pairconv_ms": t["pairconv_kernels"],
+                      "us_per_pair": 1e3 * t["pairconv_kernels"] / n}), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.profile_pairconv:
+        run_profile(args, local)
+    elif args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_lace(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

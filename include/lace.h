@@ -1,0 +1,184 @@
+/*
+ * liblace -- GB300 (sm_103a) library for the exchange hot path of the L-ACE
+ * method (localized Adaptively Compressed Exchange, Carnimeo, Baroni and
+ * Giannozzi, arXiv:1801.09263).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Hartree atomic units, e^2 = 1; Gamma point; real orbitals; spin omitted
+ *    (Sec. 2).  K = -V_X is the (negative semidefinite) exchange operator:
+ *    the paper's V_X carries a minus sign to be positive definite (Sec. 2).
+ *  - An orthorhombic cell a x b x c (bohr) with an n1 x n2 x n3 grid,
+ *    Ng = n1 n2 n3, dV = abc / Ng.  Orbitals are real arrays laid out
+ *    [orbital][n1][n2][n3], C order (n3 fastest), normalised so that
+ *    dV * sum_r phi(r)^2 = 1.  Inner products carry dV.
+ *  - Coulomb kernel K(G) = 4 pi / |G|^2 on every G of the grid, K(0) = 0.
+ *  - Host pointers are owned by the caller and only read or written during
+ *    the call.  "_dev" pointers are device pointers on the context's device,
+ *    borrowed for the duration of the call (the call synchronises the
+ *    context's stream before returning).  All outputs go to caller buffers.
+ *  - Every call returns a lace_status; nothing throws across the ABI.  A call
+ *    made out of order returns LACE_ERR_STATE; lace_last_error() then holds a
+ *    one-line explanation.  A context is used by one host thread at a time.
+ *  - Precision LACE_FP64: every step in FP64.  LACE_MIXED: pair FFTs and the
+ *    accumulation of W in FP32 with FP64 pair energies; dense contractions
+ *    over the grid in split-precision (3xBF16 products, FP32 accumulate)
+ *    on tensor cores; FP64 for the small N x N factorisations (Cholesky,
+ *    triangular inverse, inverse square roots).
+ */
+#ifndef LACE_H
+#define LACE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lace_ctx lace_ctx; /* opaque; created and freed by the library */
+
+typedef enum {
+    LACE_OK = 0,
+    LACE_ERR_ARG = 1,         /* bad pointer, size or option value */
+    LACE_ERR_STATE = 2,       /* call made out of order */
+    LACE_ERR_OOM = 3,         /* device allocation failed; context unchanged */
+    LACE_ERR_CUDA = 4,        /* a CUDA call failed; see lace_last_error */
+    LACE_ERR_NOT_PD = 5,      /* -M' is not positive definite (Cholesky failed) */
+    LACE_ERR_TIMEOUT = 6,     /* a bounded device-side iteration did not converge */
+    LACE_ERR_UNSUPPORTED = 7  /* grid size or option this build does not handle */
+} lace_status;
+
+typedef enum { LACE_FP64 = 0, LACE_MIXED = 1 } lace_precision;
+
+/* Symmetrisation of the truncated exchange matrix M' before its Cholesky
+ * factorisation (Sec. 2, after Eq. 7): (M'+M'^T)/2, upper triangle copied
+ * into the lower, or lower copied into the upper. */
+typedef enum { LACE_SYM_AVG = 0, LACE_SYM_UPPER = 1, LACE_SYM_LOWER = 2 } lace_sym;
+
+/* Matrices that lace_get_matrix can return (FP64, row-major). */
+typedef enum {
+    LACE_MAT_OVERLAP_MODULI = 0, /* S_ik = int |w_i||w_k| (Eq. 4), n_occ x n_occ */
+    LACE_MAT_EXCHANGE = 1,       /* M' = dV Psi^T W before symmetrisation (Eq. 3/7), N_P x N_P */
+    LACE_MAT_CHOLESKY = 2,       /* L with -M'_sym = L L^T, lower triangular, N_P x N_P */
+    LACE_MAT_PAIR_ENERGY = 3,    /* e_ik = (ik|ki) for kept occupied pairs, 0 elsewhere, n_occ x n_occ */
+    LACE_MAT_SCDM_U = 4          /* orthogonal SCDM rotation U, w = phi U, n_occ x n_occ */
+} lace_matrix;
+
+/* Orbital sets that lace_get_orbitals can return (FP64, [orbital][n1][n2][n3]). */
+typedef enum {
+    LACE_ORB_PSI = 0, /* projection set Psi = [w (localised occupied), extras], N_P orbitals */
+    LACE_ORB_W = 1,   /* W = K' Psi from the last lace_apply_exchange, N_P orbitals */
+    LACE_ORB_XI = 2   /* ACE vectors xi = W L^{-T}, N_P orbitals */
+} lace_orbitals;
+
+/* Create a context on CUDA device `device` computing in `precision`
+ * (lace_precision).  *out receives the handle.  No device memory is
+ * allocated until lace_set_cell. */
+lace_status lace_create(lace_ctx** out, int device, int precision);
+
+/* Free the context and all its device memory.  NULL is accepted. */
+lace_status lace_destroy(lace_ctx* ctx);
+
+/* Run the context's work on `stream` (a cudaStream_t, or NULL for the
+ * context's own stream). */
+lace_status lace_set_stream(lace_ctx* ctx, void* stream);
+
+/* Cell, grid and orbital cutoff (Sec. 3: the exchange grid follows from the
+ * cell and the cutoff; here the caller gives the grid).  cell = (a, b, c) in
+ * bohr.  Every grid size must factor into 2, 3 and 5; this build handles
+ * 4 <= n <= 128 (FP32) and 4 <= n <= 108 (FP64).  ecut_ha > 0 is kept for
+ * the caller's records (the kernel uses every G of the grid).  Resets all
+ * loaded state. */
+lace_status lace_set_cell(lace_ctx* ctx, const double cell[3], int n1, int n2, int n3, double ecut_ha);
+
+/* Load n_occ occupied orbitals followed by n_extra extra (virtual) orbitals
+ * from host FP64 memory phi[(n_occ+n_extra)][n1][n2][n3] (copied).  With
+ * orthonormalize != 0 the occupied set is Loewdin-orthonormalised
+ * (phi <- phi S^{-1/2}, S = dV phi^T phi) and the extras are projected out
+ * of the occupied span and Loewdin-orthonormalised; otherwise the caller
+ * guarantees orthonormality.  Until lace_localize, the occupied orbitals
+ * used by the exchange are these (canonical) ones.  Resets localisation,
+ * screening and ACE state.  LACE_ERR_NOT_PD if an overlap matrix is
+ * singular. */
+lace_status lace_load_orbitals(lace_ctx* ctx, const double* phi, int n_occ, int n_extra, int orthonormalize);
+
+/* As lace_load_orbitals, from a device FP64 buffer (borrowed). */
+lace_status lace_load_orbitals_dev(lace_ctx* ctx, const double* d_phi, int n_occ, int n_extra, int orthonormalize);
+
+/* SCDM localisation of the occupied orbitals (Sec. 2): pivoted QR of the
+ * orbitals on the subsample of grid points whose three indices are
+ * multiples of `stride` (2 = 1/8 of the grid) selects n_occ points; then
+ * w = phi U with U = phi_C^T (phi_C phi_C^T)^{-1/2}.  pivots_out (nullable,
+ * n_occ entries) receives the selected points as full-grid linear indices
+ * in selection order.  Ties in the pivot choice go to the lowest index.
+ * Resets screening and ACE state. */
+lace_status lace_localize(lace_ctx* ctx, int stride, long long* pivots_out);
+
+/* SCDM with imposed pivots (full-grid linear indices, n == n_occ, all
+ * distinct): skips the pivoted QR.  Used to compare localised results with
+ * another implementation on the same point selection. */
+lace_status lace_set_pivots(lace_ctx* ctx, const long long* pivots, int n);
+
+/* Overlap-of-moduli screen (Eq. 4): an occupied pair (i, k) is dropped when
+ * S_ik < s_thr (both u^(ik) and u^(ki) of Eq. 5 go); pairs with an extra
+ * orbital are always kept (Sec. 4.1).  s_thr = 0 keeps everything.
+ * *n_pairs_out (nullable) receives the number of pair convolutions one
+ * exchange application will run (unique occupied pairs i <= k kept plus
+ * n_occ * n_extra). */
+lace_status lace_screen(lace_ctx* ctx, double s_thr, long long* n_pairs_out);
+
+/* Apply the (truncated) exchange operator to the projection set Psi (Eq. 2
+ * with Eq. 5): W_j = -sum_{i kept with j} w_i v_ij, v_ij the Coulomb
+ * potential of w_i psi_j.  W stays on the device; W_out (nullable, host,
+ * N_P x Ng FP64) receives a copy.  ex_out (nullable) receives E_x for
+ * f_spin = 1: -1/2 sum over ordered kept occupied pairs of (ik|ki). */
+lace_status lace_apply_exchange(lace_ctx* ctx, double* W_out, double* ex_out);
+
+/* E_x of the last lace_apply_exchange, times f_spin (1 for the unit
+ * occupations of Sec. 2, 2 for a closed shell). */
+lace_status lace_exchange_energy(lace_ctx* ctx, double f_spin, double* ex_out);
+
+/* Build the ACE projector from the last W (Eq. 3 and its Cholesky form):
+ * M' = dV Psi^T W, symmetrised by `sym` (lace_sym), -M'_sym = L L^T in
+ * FP64, xi = W L^{-T}.  LACE_ERR_NOT_PD leaves any previous ACE state
+ * intact. */
+lace_status lace_build_ace(lace_ctx* ctx, int sym);
+
+/* K_ACE psi = -xi (dV xi^T psi) for n functions psi (host FP64,
+ * [n][n1][n2][n3]); kpsi_out (host FP64, same shape) receives the result. */
+lace_status lace_apply_ace(lace_ctx* ctx, const double* psi, int n, double* kpsi_out);
+
+/* As lace_apply_ace with device FP64 buffers (borrowed). */
+lace_status lace_apply_ace_dev(lace_ctx* ctx, const double* d_psi, int n, double* d_kpsi_out);
+
+/* Copy a matrix (lace_matrix) to host FP64 memory `out` of `count` doubles;
+ * LACE_ERR_ARG if count is smaller than the matrix. */
+lace_status lace_get_matrix(lace_ctx* ctx, int which, double* out, long long count);
+
+/* Copy an orbital set (lace_orbitals) to host FP64 memory `out` of `count`
+ * doubles (N_P x Ng). */
+lace_status lace_get_orbitals(lace_ctx* ctx, int which, double* out, long long count);
+
+/* Copy the kept pair list: pairs_out[2*p], pairs_out[2*p+1] = (i, j) with i
+ * occupied and i <= j for occupied j; up to `cap` pairs; *n_out = count. */
+lace_status lace_get_pairs(lace_ctx* ctx, int* pairs_out, long long cap, long long* n_out);
+
+/* Device milliseconds of the stages of the last calls (CUDA events on the
+ * context's stream): [0] load+orthonormalise, [1] localise, [2] screen,
+ * [3] exchange (pair convolutions), [4] ACE build, [5] ACE apply,
+ * [6] pair-convolution kernels alone (sum over their launches). */
+lace_status lace_get_timings(lace_ctx* ctx, double* ms_out, int count);
+
+/* Number of kernel launches the library made since the context was
+ * created (all calls). */
+lace_status lace_get_launch_count(lace_ctx* ctx, long long* count_out);
+
+/* Static description of a status code. */
+const char* lace_status_string(lace_status status);
+
+/* One-line description of the last error on this context ("" if none). */
+const char* lace_last_error(lace_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LACE_H */

@@ -42,6 +42,7 @@ __all__ = [
     "orthonormalize_extras",
     "qrcp_pivots",
     "subsample_indices",
+    "qrcp_pivot_ratios",
     "scdm",
     "overlap_moduli",
     "kept_pairs",
@@ -130,8 +131,8 @@ def lowdin(grid: Grid, phi: np.ndarray) -> np.ndarray:
     a = phi.reshape(n, -1)
     s = grid.dv * (a @ a.T)
     lam, vec = np.linalg.eigh(s)
-    if lam.min() <= 0:
-        raise np.linalg.LinAlgError("overlap matrix is not positive definite")
+    if lam.min() <= 1e-12 * lam.max():
+        raise np.linalg.LinAlgError("overlap matrix is singular or ill-conditioned")
     x = (vec * (1.0 / np.sqrt(lam))[None, :]) @ vec.T
     return (x.T @ a).reshape(phi.shape)  # new_k = sum_j phi_j X_jk
 
@@ -186,6 +187,27 @@ def qrcp_pivots(a: np.ndarray, n_piv: int | None = None) -> np.ndarray:
     return piv
 
 
+def qrcp_pivot_ratios(a: np.ndarray, pivots) -> np.ndarray:
+    """Replay the pivoted QR of qrcp_pivots with a given pivot order.
+
+    For every step k returns ||r_{p_k}||^2 / max_c ||r_c||^2 over the columns
+    not yet chosen, with the residuals of the same exact Gram-Schmidt steps.
+    A valid Businger-Golub pivot order has every ratio equal to 1; a ratio
+    slightly below 1 marks a choice between near-tied columns.
+    """
+    r = np.array(a, dtype=np.float64, copy=True)
+    chosen = np.zeros(r.shape[1], dtype=bool)
+    out = np.empty(len(pivots))
+    for step, p in enumerate(pivots):
+        norms = np.einsum("ij,ij->j", r, r)
+        norms[chosen] = -1.0
+        out[step] = norms[p] / norms.max()
+        chosen[p] = True
+        q = r[:, p] / np.sqrt(norms[p])
+        r -= np.outer(q, q @ r)
+    return out
+
+
 def scdm(grid: Grid, phi: np.ndarray, stride: int = 2, pivots=None):
     """SCDM localisation of an orthonormal occupied set (Sec. 2).
 
@@ -209,7 +231,7 @@ def scdm(grid: Grid, phi: np.ndarray, stride: int = 2, pivots=None):
     phic = a[:, pivots].T  # (points, orbitals)
     b = phic @ phic.T
     lam, vec = np.linalg.eigh(b)
-    if lam.min() <= 0:
+    if lam.min() <= 1e-12 * lam.max():
         raise np.linalg.LinAlgError("selected columns are rank deficient")
     b_mhalf = (vec * (1.0 / np.sqrt(lam))[None, :]) @ vec.T
     u = phic.T @ b_mhalf  # (orbitals, orbitals), orthogonal

@@ -1,0 +1,232 @@
+"""ctypes binding of liblace (names follow the C calls of include/lace.h).
+
+Arguments are marshalled to plain pointers and sizes; results come back in
+caller-owned numpy arrays (host calls) or torch CUDA tensors (``_dev``
+calls, where torch only provides the device memory and the stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+LACE_OK = 0
+LACE_FP64, LACE_MIXED = 0, 1
+LACE_SYM_AVG, LACE_SYM_UPPER, LACE_SYM_LOWER = 0, 1, 2
+MAT_OVERLAP_MODULI, MAT_EXCHANGE, MAT_CHOLESKY, MAT_PAIR_ENERGY, MAT_SCDM_U = 0, 1, 2, 3, 4
+ORB_PSI, ORB_W, ORB_XI = 0, 1, 2
+STAGES = ("load", "localize", "screen", "exchange", "ace_build", "ace_apply", "pairconv_kernels")
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_HEADER = os.path.join(os.path.dirname(_HERE), "include", "lace.h")
+_LIB = None
+
+
+class LaceError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str):
+        super().__init__(f"{where}: status {status}: {detail}")
+        self.status = status
+
+
+def library_path() -> str:
+    return os.path.join(_HERE, "liblace.so")
+
+
+def exported_symbols() -> list[str]:
+    """Function names declared in include/lace.h."""
+    txt = open(_HEADER).read()
+    return sorted(set(re.findall(r"\b(lace_[a-z_]+)\s*\(", txt)))
+
+
+def load_library(build_if_missing: bool = False):
+    """Load liblace.so from the package directory (in-tree build)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = library_path()
+    if not os.path.exists(path):
+        if build_if_missing:
+            from .build import build
+            build()
+        else:
+            raise RuntimeError(f"liblace.so not built ({path}); run __graft_entry__.build() first")
+    lib = C.CDLL(path)
+    P, I, D, LL, V = C.c_void_p, C.c_int, C.c_double, C.c_longlong, None
+    sig = {
+        "lace_create": ([C.POINTER(P), I, I], I),
+        "lace_destroy": ([P], I),
+        "lace_set_stream": ([P, P], I),
+        "lace_set_cell": ([P, P, I, I, I, D], I),
+        "lace_load_orbitals": ([P, P, I, I, I], I),
+        "lace_load_orbitals_dev": ([P, P, I, I, I], I),
+        "lace_localize": ([P, I, P], I),
+        "lace_set_pivots": ([P, P, I], I),
+        "lace_screen": ([P, D, P], I),
+        "lace_apply_exchange": ([P, P, P], I),
+        "lace_exchange_energy": ([P, D, P], I),
+        "lace_build_ace": ([P, I], I),
+        "lace_apply_ace": ([P, P, I, P], I),
+        "lace_apply_ace_dev": ([P, P, I, P], I),
+        "lace_get_matrix": ([P, I, P, LL], I),
+        "lace_get_orbitals": ([P, I, P, LL], I),
+        "lace_get_pairs": ([P, P, LL, P], I),
+        "lace_get_timings": ([P, P, I], I),
+        "lace_get_launch_count": ([P, P], I),
+        "lace_status_string": ([I], C.c_char_p),
+        "lace_last_error": ([P], C.c_char_p),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _LIB = lib
+    return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class Lace:
+    """One liblace context (one device, one precision)."""
+
+    def __init__(self, device: int = 0, precision: int = LACE_FP64):
+        self.lib = load_library()
+        h = C.c_void_p()
+        st = self.lib.lace_create(C.byref(h), int(device), int(precision))
+        if st != LACE_OK:
+            raise LaceError(st, "lace_create", self.lib.lace_status_string(st).decode())
+        self.h = h
+        self.precision = precision
+        self.shape = None
+        self.n_occ = self.n_extra = 0
+
+    # -- helpers
+    def _check(self, st: int, where: str):
+        if st != LACE_OK:
+            detail = self.lib.lace_last_error(self.h).decode()
+            raise LaceError(st, where, detail or self.lib.lace_status_string(st).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lace_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def n_p(self) -> int:
+        return self.n_occ + self.n_extra
+
+    @property
+    def ng(self) -> int:
+        return int(np.prod(self.shape))
+
+    # -- the C calls
+    def set_stream(self, stream_ptr: int | None):
+        self._check(self.lib.lace_set_stream(self.h, C.c_void_p(stream_ptr or 0)), "lace_set_stream")
+
+    def set_cell(self, cell, shape, ecut: float):
+        c = _f64(cell)
+        self._check(self.lib.lace_set_cell(self.h, _ptr(c), int(shape[0]), int(shape[1]), int(shape[2]),
+                                           float(ecut)), "lace_set_cell")
+        self.shape = tuple(int(s) for s in shape)
+
+    def load_orbitals(self, phi, n_occ: int, n_extra: int = 0, orthonormalize: bool = True):
+        a = _f64(phi)
+        assert a.shape == (n_occ + n_extra,) + self.shape
+        self._check(self.lib.lace_load_orbitals(self.h, _ptr(a), n_occ, n_extra, int(orthonormalize)),
+                    "lace_load_orbitals")
+        self.n_occ, self.n_extra = n_occ, n_extra
+
+    def load_orbitals_dev(self, phi_dev, n_occ: int, n_extra: int = 0, orthonormalize: bool = True):
+        """phi_dev: a contiguous float64 CUDA torch tensor [(n_occ+n_extra), n1, n2, n3]."""
+        assert phi_dev.is_cuda and phi_dev.is_contiguous() and str(phi_dev.dtype) == "torch.float64"
+        self._check(self.lib.lace_load_orbitals_dev(self.h, C.c_void_p(phi_dev.data_ptr()), n_occ, n_extra,
+                                                    int(orthonormalize)), "lace_load_orbitals_dev")
+        self.n_occ, self.n_extra = n_occ, n_extra
+
+    def localize(self, stride: int = 2) -> np.ndarray:
+        piv = np.zeros(self.n_occ, dtype=np.int64)
+        self._check(self.lib.lace_localize(self.h, int(stride), _ptr(piv)), "lace_localize")
+        return piv
+
+    def set_pivots(self, pivots):
+        p = np.ascontiguousarray(pivots, dtype=np.int64)
+        self._check(self.lib.lace_set_pivots(self.h, _ptr(p), len(p)), "lace_set_pivots")
+
+    def screen(self, s_thr: float) -> int:
+        n = C.c_longlong(0)
+        self._check(self.lib.lace_screen(self.h, float(s_thr), C.byref(n)), "lace_screen")
+        return int(n.value)
+
+    def apply_exchange(self, want_W: bool = True):
+        ex = C.c_double(0.0)
+        W = np.empty((self.n_p,) + self.shape, dtype=np.float64) if want_W else None
+        self._check(self.lib.lace_apply_exchange(self.h, _ptr(W) if want_W else None, C.byref(ex)),
+                    "lace_apply_exchange")
+        return W, float(ex.value)
+
+    def exchange_energy(self, f_spin: float = 1.0) -> float:
+        ex = C.c_double(0.0)
+        self._check(self.lib.lace_exchange_energy(self.h, float(f_spin), C.byref(ex)), "lace_exchange_energy")
+        return float(ex.value)
+
+    def build_ace(self, sym: int = LACE_SYM_AVG):
+        self._check(self.lib.lace_build_ace(self.h, int(sym)), "lace_build_ace")
+
+    def apply_ace(self, psi) -> np.ndarray:
+        a = _f64(psi)
+        n = a.shape[0]
+        out = np.empty_like(a)
+        self._check(self.lib.lace_apply_ace(self.h, _ptr(a), n, _ptr(out)), "lace_apply_ace")
+        return out
+
+    def apply_ace_dev(self, psi_dev, out_dev):
+        assert psi_dev.is_cuda and out_dev.is_cuda and psi_dev.is_contiguous() and out_dev.is_contiguous()
+        self._check(self.lib.lace_apply_ace_dev(self.h, C.c_void_p(psi_dev.data_ptr()), int(psi_dev.shape[0]),
+                                                C.c_void_p(out_dev.data_ptr())), "lace_apply_ace_dev")
+
+    def get_matrix(self, which: int) -> np.ndarray:
+        n = self.n_p if which in (MAT_EXCHANGE, MAT_CHOLESKY) else self.n_occ
+        out = np.empty((n, n), dtype=np.float64)
+        self._check(self.lib.lace_get_matrix(self.h, int(which), _ptr(out), out.size), "lace_get_matrix")
+        return out
+
+    def get_orbitals(self, which: int) -> np.ndarray:
+        out = np.empty((self.n_p,) + self.shape, dtype=np.float64)
+        self._check(self.lib.lace_get_orbitals(self.h, int(which), _ptr(out), out.size), "lace_get_orbitals")
+        return out
+
+    def get_pairs(self) -> np.ndarray:
+        n = C.c_longlong(0)
+        self._check(self.lib.lace_get_pairs(self.h, None, 0, C.byref(n)), "lace_get_pairs")
+        out = np.empty((max(n.value, 1), 2), dtype=np.int32)
+        self._check(self.lib.lace_get_pairs(self.h, _ptr(out), n.value, C.byref(n)), "lace_get_pairs")
+        return out[: n.value]
+
+    def get_timings(self) -> dict:
+        ms = np.zeros(len(STAGES), dtype=np.float64)
+        self._check(self.lib.lace_get_timings(self.h, _ptr(ms), len(STAGES)), "lace_get_timings")
+        return dict(zip(STAGES, ms.tolist()))
+
+    def launch_count(self) -> int:
+        n = C.c_longlong(0)
+        self._check(self.lib.lace_get_launch_count(self.h, C.byref(n)), "lace_get_launch_count")
+        return int(n.value)

@@ -1,0 +1,788 @@
+// C-ABI of liblace: context, state machine and orchestration of the
+// exchange hot path of L-ACE (arXiv:1801.09263, Sec. 2).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/lace.h"
+#include "lace_internal.cuh"
+
+using namespace lace;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t b) {
+        if (b <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        if (b == 0) return cudaSuccess;
+        cudaError_t e = cudaMalloc(&p, b);
+        if (e == cudaSuccess) bytes = b;
+        return e;
+    }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+enum Stage { ST_LOAD = 0, ST_LOCALIZE, ST_SCREEN, ST_EXCHANGE, ST_ACE_BUILD, ST_ACE_APPLY, ST_PAIRCONV, ST_COUNT };
+
+}  // namespace
+
+struct lace_ctx {
+    int device = 0;
+    int prec = LACE_FP64;
+    cudaStream_t stream = nullptr;
+    cudaStream_t own_stream = nullptr;
+    std::string err;
+    long long launches = 0;
+
+    bool have_cell = false;
+    GridGeom g{};
+    DevBuf tw_d[3], tw_f[3], g2_d[3], g2_f[3];
+
+    int n_occ = 0, n_extra = 0, n_p = 0;
+    bool loaded = false, localized = false, screened = false, applied = false, ace = false;
+    double s_thr = 0.0;
+
+    DevBuf psi;     // [n_p][ng] working precision: [w (localised occupied) ; extras]
+    DevBuf canon;   // [n_occ][ng] canonical orthonormal occupied orbitals
+    DevBuf W;       // [n_p][ng]
+    DevBuf xi;      // [n_p][ng]
+    DevBuf stage64; // [rows][ng] FP64 staging (uploads, conversions)
+    DevBuf scratch; // complex FFT grids of one batch
+    DevBuf work;    // GEMM partials and the QRCP matrix
+    DevBuf aux;     // QRCP auxiliary
+    DevBuf mat;     // small FP64 matrices (see offsets below)
+    DevBuf pairs, counts, grids, epart, flag, piv, pivfull, exd;
+    long long n_pairs = 0;
+    std::vector<long long> pivots_host;
+
+    cudaEvent_t ev[2 * ST_COUNT] = {};
+    bool ev_used[ST_COUNT] = {};
+
+    // small-matrix slots inside `mat` (each n_p*n_p doubles, plus staging)
+    size_t mslot = 0;
+    double* m(int k) { return mat.as<double>() + (size_t)k * mslot; }
+};
+
+namespace {
+
+enum MatSlot { MS_S = 0, MS_M, MS_MSYM, MS_L, MS_LINV, MS_LINVT, MS_E, MS_U, MS_A, MS_B, MS_NSWORK, MS_COUNT_BASE };
+// MS_NSWORK takes 5 slots (Newton-Schulz work)
+constexpr int kMatSlots = MS_NSWORK + 5 + 1;
+
+lace_status fail(lace_ctx* c, lace_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+lace_status cuda_fail(lace_ctx* c, cudaError_t e, const char* where) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(c, LACE_ERR_OOM, std::string(where) + ": out of device memory");
+    }
+    return fail(c, LACE_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+lace_status ck_impl(lace_ctx* c, cudaError_t e, const char* where) {
+    return e == cudaSuccess ? LACE_OK : cuda_fail(c, e, where);
+}
+
+// CK(expression, "where"): return a lace_status on a CUDA error.
+#define CK(...)                                      \
+    do {                                             \
+        lace_status _st = ck_impl(c, __VA_ARGS__);   \
+        if (_st != LACE_OK) return _st;              \
+    } while (0)
+
+bool good_size(int n) {
+    if (n < 4 || n > kMaxN) return false;
+    int m = n;
+    for (int p : {2, 3, 5})
+        while (m % p == 0) m /= p;
+    return m == 1;
+}
+
+size_t elem_bytes(const lace_ctx* c) { return c->prec == LACE_FP64 ? 8 : 4; }
+
+void ev_begin(lace_ctx* c, int st) {
+    cudaEventRecord(c->ev[2 * st], c->stream);
+    c->ev_used[st] = true;
+}
+void ev_end(lace_ctx* c, int st) { cudaEventRecord(c->ev[2 * st + 1], c->stream); }
+
+struct Launch {
+    lace_ctx* c;
+    int n = 0;
+    ~Launch() { c->launches += n; }
+};
+
+// ------------------------------------------------------------------ tables
+lace_status build_tables(lace_ctx* c) {
+    for (int a = 0; a < 3; ++a) {
+        const int n = c->g.n[a];
+        std::vector<double2> twd(n);
+        std::vector<float2> twf(n);
+        std::vector<double> g2d(n);
+        std::vector<float> g2f(n);
+        for (int m = 0; m < n; ++m) {
+            const double ang = -2.0 * M_PI * (double)m / (double)n;
+            twd[m] = make_double2(std::cos(ang), std::sin(ang));
+            twf[m] = make_float2((float)twd[m].x, (float)twd[m].y);
+            const int mm = (m < (n + 1) / 2) ? m : m - n;
+            const double gv = 2.0 * M_PI * (double)mm / c->g.cell[a];
+            g2d[m] = gv * gv;
+            g2f[m] = (float)g2d[m];
+        }
+        CK(c->tw_d[a].ensure(n * sizeof(double2)), "tables");
+        CK(c->tw_f[a].ensure(n * sizeof(float2)), "tables");
+        CK(c->g2_d[a].ensure(n * sizeof(double)), "tables");
+        CK(c->g2_f[a].ensure(n * sizeof(float)), "tables");
+        CK(cudaMemcpy(c->tw_d[a].p, twd.data(), n * sizeof(double2), cudaMemcpyHostToDevice), "tables");
+        CK(cudaMemcpy(c->tw_f[a].p, twf.data(), n * sizeof(float2), cudaMemcpyHostToDevice), "tables");
+        CK(cudaMemcpy(c->g2_d[a].p, g2d.data(), n * sizeof(double), cudaMemcpyHostToDevice), "tables");
+        CK(cudaMemcpy(c->g2_f[a].p, g2f.data(), n * sizeof(float), cudaMemcpyHostToDevice), "tables");
+    }
+    return LACE_OK;
+}
+
+template <typename T> FFTTables<T> tables(lace_ctx* c);
+template <> FFTTables<double> tables<double>(lace_ctx* c) {
+    FFTTables<double> t;
+    for (int a = 0; a < 3; ++a) { t.tw[a] = c->tw_d[a].as<double2>(); t.g2[a] = c->g2_d[a].as<double>(); }
+    return t;
+}
+template <> FFTTables<float> tables<float>(lace_ctx* c) {
+    FFTTables<float> t;
+    for (int a = 0; a < 3; ++a) { t.tw[a] = c->tw_f[a].as<float2>(); t.g2[a] = c->g2_f[a].as<float>(); }
+    return t;
+}
+
+// ------------------------------------------------------------------ buffers
+lace_status ensure_orbital_buffers(lace_ctx* c, int n_occ, int n_extra) {
+    const int n_p = n_occ + n_extra;
+    const size_t ng = c->g.ng, eb = elem_bytes(c);
+    CK(c->psi.ensure((size_t)n_p * ng * eb), "alloc psi");
+    CK(c->canon.ensure((size_t)n_occ * ng * eb), "alloc canon");
+    CK(c->W.ensure((size_t)n_p * ng * eb), "alloc W");
+    CK(c->stage64.ensure((size_t)n_p * ng * 8), "alloc staging");
+    c->mslot = (size_t)n_p * n_p + 64 * (size_t)n_p + 64;
+    CK(c->mat.ensure(c->mslot * kMatSlots * sizeof(double)), "alloc matrices");
+    const size_t wk = std::max(gemm_rows_work_elems(n_p, n_p, ng), (size_t)1);
+    CK(c->work.ensure(wk * sizeof(double)), "alloc work");
+    CK(c->flag.ensure(64), "alloc flag");
+    CK(c->exd.ensure(64), "alloc exd");
+    CK(c->counts.ensure(sizeof(int) * (2 * (size_t)n_occ + 2)), "alloc counts");
+    return LACE_OK;
+}
+
+// Loewdin: dst[n] = sum_k src[k] X[k][n], X = S^{-1/2}, S = dV src src^T.
+template <typename T>
+lace_status lowdin_rows(lace_ctx* c, const T* src, int n, T* dst, Launch& L) {
+    const size_t ng = c->g.ng;
+    double* S = c->m(MS_A);
+    double* X = c->m(MS_B);
+    CK(gemm_rows<T>(n, n, ng, src, ng, src, ng, c->g.dv, false, S, n, c->work.as<double>(),
+                    c->work.bytes / sizeof(double), c->stream, &L.n),
+       "loewdin overlap");
+    int ok = 0;
+    CK(inv_sqrt_spd(n, S, X, c->m(MS_NSWORK), c->flag.as<int>(), &ok, c->stream, &L.n), "loewdin inverse sqrt");
+    if (!ok) return fail(c, LACE_ERR_NOT_PD, "overlap matrix is singular or ill-conditioned (inverse square root did not converge)");
+    CK(gemm_combine<T>(n, ng, n, src, ng, X, n, 0.0, dst, ng, c->stream, &L.n), "loewdin combine");
+    return LACE_OK;
+}
+
+template <typename T>
+lace_status load_impl(lace_ctx* c, const double* d_phi64, int n_occ, int n_extra, int ortho) {
+    Launch L{c};
+    const size_t ng = c->g.ng;
+    const int n_p = n_occ + n_extra;
+    T* psi = c->psi.as<T>();
+    T* canon = c->canon.as<T>();
+    // working-precision copy of the input into W (used as staging)
+    T* raw = c->W.as<T>();
+    CK(convert<double, T>(d_phi64, raw, (size_t)n_p * ng, c->stream, &L.n), "load convert");
+    if (ortho) {
+        lace_status st = lowdin_rows<T>(c, raw, n_occ, canon, L);
+        if (st) return st;
+        if (n_extra > 0) {
+            T* ex_raw = raw + (size_t)n_occ * ng;
+            double* C = c->m(MS_A);
+            // C[k][e] = -dV <occ_k, extra_e>; extra -= sum_k occ_k <occ_k, extra_e>
+            CK(gemm_rows<T>(n_occ, n_extra, ng, canon, ng, ex_raw, ng, -c->g.dv, false, C, n_extra,
+                            c->work.as<double>(), c->work.bytes / sizeof(double), c->stream, &L.n),
+               "extras projection");
+            CK(gemm_combine<T>(n_extra, ng, n_occ, canon, ng, C, n_extra, 1.0, ex_raw, ng, c->stream, &L.n),
+               "extras projection");
+            st = lowdin_rows<T>(c, ex_raw, n_extra, psi + (size_t)n_occ * ng, L);
+            if (st) return st;
+        }
+    } else {
+        CK(cudaMemcpyAsync(canon, raw, (size_t)n_occ * ng * sizeof(T), cudaMemcpyDeviceToDevice, c->stream), "load");
+        if (n_extra > 0)
+            CK(cudaMemcpyAsync(psi + (size_t)n_occ * ng, raw + (size_t)n_occ * ng, (size_t)n_extra * ng * sizeof(T),
+                               cudaMemcpyDeviceToDevice, c->stream),
+               "load");
+    }
+    CK(cudaMemcpyAsync(psi, canon, (size_t)n_occ * ng * sizeof(T), cudaMemcpyDeviceToDevice, c->stream), "load");
+    return LACE_OK;
+}
+
+lace_status load_common(lace_ctx* c, const double* phi, bool dev, int n_occ, int n_extra, int ortho) {
+    if (!c) return LACE_ERR_ARG;
+    if (!c->have_cell) return fail(c, LACE_ERR_STATE, "lace_set_cell must come first");
+    if (!phi || n_occ < 1 || n_extra < 0 || n_occ > 1024 || n_occ + n_extra > 2048)
+        return fail(c, LACE_ERR_ARG, "bad orbital pointer or counts (1 <= n_occ <= 1024, n_occ + n_extra <= 2048)");
+    cudaSetDevice(c->device);
+    c->loaded = c->localized = c->screened = c->applied = c->ace = false;
+    lace_status st = ensure_orbital_buffers(c, n_occ, n_extra);
+    if (st) return st;
+    c->n_occ = n_occ;
+    c->n_extra = n_extra;
+    c->n_p = n_occ + n_extra;
+    ev_begin(c, ST_LOAD);
+    const size_t bytes = (size_t)c->n_p * c->g.ng * sizeof(double);
+    const double* src = phi;
+    if (!dev) {
+        CK(cudaMemcpyAsync(c->stage64.p, phi, bytes, cudaMemcpyHostToDevice, c->stream), "upload");
+        src = c->stage64.as<double>();
+    }
+    st = c->prec == LACE_FP64 ? load_impl<double>(c, src, n_occ, n_extra, ortho)
+                              : load_impl<float>(c, src, n_occ, n_extra, ortho);
+    ev_end(c, ST_LOAD);
+    if (st) return st;
+    CK(cudaStreamSynchronize(c->stream), "load");
+    c->loaded = true;
+    return LACE_OK;
+}
+
+// ------------------------------------------------------------------ SCDM
+template <typename T>
+lace_status localize_impl(lace_ctx* c, int stride, const long long* imposed) {
+    Launch L{c};
+    const size_t ng = c->g.ng;
+    const int n = c->n_occ;
+    T* canon = c->canon.as<T>();
+    CK(c->pivfull.ensure(sizeof(long long) * n), "alloc pivots");
+    long long* d_full = c->pivfull.as<long long>();
+    if (!imposed) {
+        int ncol = 0;
+        const int m1 = (c->g.n[0] + stride - 1) / stride, m2 = (c->g.n[1] + stride - 1) / stride,
+                  m3 = (c->g.n[2] + stride - 1) / stride;
+        const size_t ncol_sz = (size_t)m1 * m2 * m3;
+        if (ncol_sz < (size_t)n) return fail(c, LACE_ERR_ARG, "subsample has fewer points than orbitals");
+        const size_t need = (size_t)n * ncol_sz * sizeof(T);
+        if (c->work.bytes < need) CK(c->work.ensure(need), "alloc qrcp");
+        CK(c->aux.ensure(qrcp_aux_bytes(n, (int)ncol_sz)), "alloc qrcp aux");
+        CK(c->piv.ensure(sizeof(int) * n), "alloc pivots");
+        T* R = c->work.as<T>();
+        CK(gather_subsample<T>(c->g, stride, canon, n, R, &ncol, c->stream, &L.n), "subsample");
+        CK(qrcp_pivots<T>(n, ncol, R, n, c->piv.as<int>(), c->aux.p, c->stream, &L.n), "qrcp");
+        std::vector<int> hp(n);
+        CK(cudaMemcpyAsync(hp.data(), c->piv.p, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream), "pivots");
+        CK(cudaStreamSynchronize(c->stream), "pivots");
+        c->pivots_host.resize(n);
+        for (int k = 0; k < n; ++k) {
+            const int cc = hp[k];
+            const int kz = cc % m3, jy = (cc / m3) % m2, ix = cc / (m3 * m2);
+            c->pivots_host[k] = ((long long)(ix * stride) * c->g.n[1] + (long long)(jy * stride)) * c->g.n[2] +
+                                (long long)(kz * stride);
+        }
+    } else {
+        c->pivots_host.assign(imposed, imposed + n);
+    }
+    CK(cudaMemcpyAsync(d_full, c->pivots_host.data(), sizeof(long long) * n, cudaMemcpyHostToDevice, c->stream),
+       "pivots");
+    double* phic = c->m(MS_A);
+    double* B = c->m(MS_B);
+    double* Bmh = c->m(MS_LINV);
+    double* U = c->m(MS_U);
+    CK(gather_columns<T>(canon, ng, n, d_full, n, phic, c->stream, &L.n), "gather phi_C");
+    // B = phi_C phi_C^T  (points x points)
+    CK(small_gemm_f64(n, n, n, phic, n, false, phic, n, true, 1.0, 0.0, B, n, c->stream, &L.n), "scdm B");
+    int ok = 0;
+    CK(inv_sqrt_spd(n, B, Bmh, c->m(MS_NSWORK), c->flag.as<int>(), &ok, c->stream, &L.n), "scdm inverse sqrt");
+    if (!ok) return fail(c, LACE_ERR_NOT_PD, "selected columns are rank deficient");
+    // U = phi_C^T B^{-1/2}  (orbitals x orbitals)
+    CK(small_gemm_f64(n, n, n, phic, n, true, Bmh, n, false, 1.0, 0.0, U, n, c->stream, &L.n), "scdm U");
+    // w = canon U
+    CK(gemm_combine<T>(n, ng, n, canon, ng, U, n, 0.0, c->psi.as<T>(), ng, c->stream, &L.n), "scdm rotate");
+    return LACE_OK;
+}
+
+// ------------------------------------------------------------------ screening
+template <typename T>
+lace_status screen_impl(lace_ctx* c, double thr) {
+    Launch L{c};
+    const size_t ng = c->g.ng;
+    const int n = c->n_occ;
+    CK(gemm_rows<T>(n, n, ng, c->psi.as<T>(), ng, c->psi.as<T>(), ng, c->g.dv, true, c->m(MS_S), n,
+                    c->work.as<double>(), c->work.bytes / sizeof(double), c->stream, &L.n),
+       "overlap of moduli");
+    return LACE_OK;
+}
+
+lace_status make_pairs(lace_ctx* c, bool use_S, double thr, Launch& L) {
+    const int n = c->n_occ, ne = c->n_extra;
+    const size_t maxp = (size_t)n * (n + 1) / 2 + (size_t)n * ne;
+    CK(c->pairs.ensure(sizeof(int2) * std::max<size_t>(maxp, 1)), "alloc pairs");
+    CK(c->grids.ensure(sizeof(PairGrid) * std::max<size_t>((maxp + 1) / 2, 1)), "alloc grids");
+    long long np = 0;
+    CK(build_pair_list(n, ne, c->m(MS_S), thr, use_S, c->pairs.as<int2>(), c->counts.as<int>(), &np, c->stream, &L.n),
+       "pair list");
+    CK(pack_pair_grids(c->pairs.as<int2>(), np, c->grids.as<PairGrid>(), c->stream, &L.n), "pack pairs");
+    c->n_pairs = np;
+    return LACE_OK;
+}
+
+int batch_for(lace_ctx* c) {
+    const size_t per = c->g.ng * 2 * elem_bytes(c);
+    const char* envb = getenv("LACE_BATCH");
+    long long b = envb ? atoll(envb) : (long long)((96ull << 20) / per);
+    b = std::max<long long>(4, std::min<long long>(b, 1024));
+    return (int)b;
+}
+
+// ------------------------------------------------------------------ exchange
+template <typename T>
+lace_status apply_impl(lace_ctx* c) {
+    Launch L{c};
+    const size_t ng = c->g.ng;
+    if (!c->screened) {
+        lace_status st = make_pairs(c, false, 0.0, L);
+        if (st) return st;
+        c->screened = true;
+        c->s_thr = 0.0;
+    }
+    const long long n_grids = (c->n_pairs + 1) / 2;
+    const int batch = (int)std::min<long long>(batch_for(c), std::max<long long>(n_grids, 1));
+    CK(c->scratch.ensure((size_t)batch * ng * 2 * sizeof(T)), "alloc FFT scratch");
+    CK(c->epart.ensure((size_t)batch * c->g.n[0] * 2 * sizeof(double)), "alloc energies");
+    CK(cudaMemsetAsync(c->W.p, 0, (size_t)c->n_p * ng * sizeof(T), c->stream), "zero W");
+    CK(fill_zero_f64(c->m(MS_E), (size_t)c->n_occ * c->n_occ, c->stream, &L.n), "zero E");
+    CK(pairconv_run<T>(c->g, tables<T>(c), c->psi.as<T>(), c->n_occ, c->W.as<T>(), c->grids.as<PairGrid>(),
+                       (int)n_grids, c->scratch.as<cplx<T>>(), batch, c->epart.as<double>(), c->m(MS_E), c->stream,
+                       &L.n, c->ev[2 * ST_PAIRCONV], c->ev[2 * ST_PAIRCONV + 1]),
+       "pair convolutions");
+    c->ev_used[ST_PAIRCONV] = true;
+    CK(exchange_energy_sum(c->n_occ, c->m(MS_E), c->exd.as<double>(), c->stream, &L.n), "energy");
+    return LACE_OK;
+}
+
+// ------------------------------------------------------------------ ACE
+template <typename T>
+lace_status build_ace_impl(lace_ctx* c, int sym) {
+    Launch L{c};
+    const size_t ng = c->g.ng;
+    const int n = c->n_p;
+    CK(c->xi.ensure((size_t)n * ng * sizeof(T)), "alloc xi");
+    double* M = c->m(MS_M);
+    double* A = c->m(MS_MSYM);
+    double* Linv = c->m(MS_LINV);
+    double* LinvT = c->m(MS_LINVT);
+    CK(gemm_rows<T>(n, n, ng, c->psi.as<T>(), ng, c->W.as<T>(), ng, c->g.dv, false, M, n, c->work.as<double>(),
+                    c->work.bytes / sizeof(double), c->stream, &L.n),
+       "exchange matrix");
+    CK(symmetrize(n, M, A, sym, true, c->stream, &L.n), "symmetrize");
+    int ok = 0;
+    CK(cholesky_lower(n, A, n, c->flag.as<int>(), &ok, c->stream, &L.n), "cholesky");
+    if (!ok) return fail(c, LACE_ERR_NOT_PD, "-M' is not positive definite (Cholesky failed)");
+    CK(cudaMemcpyAsync(c->m(MS_L), A, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, c->stream), "copy L");
+    CK(trtri_lower(n, A, n, Linv, n, c->stream, &L.n), "trtri");
+    CK(transpose_f64(n, Linv, LinvT, c->stream, &L.n), "transpose");
+    // xi_k = sum_j W_j (L^{-T})_{jk} = sum_j W_j Linv[k][j]: Coef[j][k] = LinvT[j][k]
+    CK(gemm_combine<T>(n, ng, n, c->W.as<T>(), ng, LinvT, n, 0.0, c->xi.as<T>(), ng, c->stream, &L.n), "xi");
+    return LACE_OK;
+}
+
+template <typename T>
+lace_status apply_ace_impl(lace_ctx* c, const double* d_psi64, int nf, double* d_out64) {
+    Launch L{c};
+    const size_t ng = c->g.ng;
+    const int n = c->n_p;
+    // staging for psi and result in working precision: use the FFT scratch
+    CK(c->scratch.ensure((size_t)2 * nf * ng * sizeof(T)), "alloc ace apply");
+    T* f = c->scratch.as<T>();
+    T* out = f + (size_t)nf * ng;
+    const T* in = nullptr;
+    if (sizeof(T) == 8) {
+        in = reinterpret_cast<const T*>(d_psi64);
+    } else {
+        CK(convert<double, T>(d_psi64, f, (size_t)nf * ng, c->stream, &L.n), "convert psi");
+        in = f;
+    }
+    double* X = c->m(MS_A);
+    if ((size_t)n * nf > c->mslot) return fail(c, LACE_ERR_ARG, "too many functions in one ACE apply");
+    CK(c->work.ensure(gemm_rows_work_elems(n, nf, ng) * sizeof(double)), "alloc work");
+    CK(gemm_rows<T>(n, nf, ng, c->xi.as<T>(), ng, in, ng, -c->g.dv, false, X, nf, c->work.as<double>(),
+                    c->work.bytes / sizeof(double), c->stream, &L.n),
+       "ace project");
+    T* dst = sizeof(T) == 8 ? reinterpret_cast<T*>(d_out64) : out;
+    CK(gemm_combine<T>(nf, ng, n, c->xi.as<T>(), ng, X, nf, 0.0, dst, ng, c->stream, &L.n), "ace combine");
+    if (sizeof(T) != 8) CK(convert<T, double>(out, d_out64, (size_t)nf * ng, c->stream, &L.n), "convert out");
+    return LACE_OK;
+}
+
+template <typename T>
+lace_status copy_orbitals_out(lace_ctx* c, const T* src, size_t count, double* host) {
+    Launch L{c};
+    if (sizeof(T) == 8) {
+        CK(cudaMemcpyAsync(host, src, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "download");
+    } else {
+        CK(c->stage64.ensure(count * sizeof(double)), "alloc staging");
+        CK(convert<T, double>(src, c->stage64.as<double>(), count, c->stream, &L.n), "convert");
+        CK(cudaMemcpyAsync(host, c->stage64.p, count * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "download");
+    }
+    CK(cudaStreamSynchronize(c->stream), "download");
+    return LACE_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+const char* lace_status_string(lace_status s) {
+    switch (s) {
+        case LACE_OK: return "ok";
+        case LACE_ERR_ARG: return "invalid argument";
+        case LACE_ERR_STATE: return "call made out of order";
+        case LACE_ERR_OOM: return "out of device memory";
+        case LACE_ERR_CUDA: return "CUDA error";
+        case LACE_ERR_NOT_PD: return "matrix not positive definite";
+        case LACE_ERR_TIMEOUT: return "iteration did not converge";
+        case LACE_ERR_UNSUPPORTED: return "unsupported size or option";
+    }
+    return "unknown status";
+}
+
+const char* lace_last_error(lace_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+lace_status lace_create(lace_ctx** out, int device, int precision) {
+    if (!out) return LACE_ERR_ARG;
+    *out = nullptr;
+    if (precision != LACE_FP64 && precision != LACE_MIXED) return LACE_ERR_ARG;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return LACE_ERR_CUDA;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) return LACE_ERR_CUDA;
+    lace_ctx* c = new lace_ctx();
+    c->device = device;
+    c->prec = precision;
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        delete c;
+        return LACE_ERR_CUDA;
+    }
+    c->stream = c->own_stream;
+    for (auto& e : c->ev) cudaEventCreate(&e);
+    *out = c;
+    return LACE_OK;
+}
+
+lace_status lace_destroy(lace_ctx* c) {
+    if (!c) return LACE_OK;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    DevBuf* bufs[] = {&c->psi, &c->canon, &c->W, &c->xi, &c->stage64, &c->scratch, &c->work, &c->aux, &c->mat,
+                      &c->pairs, &c->counts, &c->grids, &c->epart, &c->flag, &c->piv, &c->pivfull, &c->exd};
+    for (DevBuf* b : bufs) b->release();
+    for (int a = 0; a < 3; ++a) { c->tw_d[a].release(); c->tw_f[a].release(); c->g2_d[a].release(); c->g2_f[a].release(); }
+    for (auto& e : c->ev) if (e) cudaEventDestroy(e);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+    return LACE_OK;
+}
+
+lace_status lace_set_stream(lace_ctx* c, void* stream) {
+    if (!c) return LACE_ERR_ARG;
+    c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
+    return LACE_OK;
+}
+
+lace_status lace_set_cell(lace_ctx* c, const double cell[3], int n1, int n2, int n3, double ecut_ha) {
+    if (!c) return LACE_ERR_ARG;
+    if (!cell || !(cell[0] > 0) || !(cell[1] > 0) || !(cell[2] > 0) || !(ecut_ha > 0))
+        return fail(c, LACE_ERR_ARG, "cell lengths and cutoff must be positive");
+    const int ns[3] = {n1, n2, n3};
+    for (int a = 0; a < 3; ++a)
+        if (!good_size(ns[a])) return fail(c, LACE_ERR_UNSUPPORTED, "grid sizes must be 2^a 3^b 5^c within [4, 128]");
+    GridGeom g{};
+    for (int a = 0; a < 3; ++a) {
+        g.n[a] = ns[a];
+        g.cell[a] = cell[a];
+        if (!plan_axis(ns[a], &g.ax[a])) return fail(c, LACE_ERR_UNSUPPORTED, "no FFT plan for this size");
+    }
+    g.ng = (size_t)n1 * n2 * n3;
+    g.omega = cell[0] * cell[1] * cell[2];
+    g.dv = g.omega / (double)g.ng;
+    cudaSetDevice(c->device);
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, c->device);
+    const size_t eb = elem_bytes(c);
+    const size_t need = std::max(pairconv_smem_bytes(g, (int)eb, 0), pairconv_smem_bytes(g, (int)eb, 1));
+    if (need > prop.sharedMemPerBlockOptin)
+        return fail(c, LACE_ERR_UNSUPPORTED, "grid plane does not fit in shared memory at this precision");
+    c->g = g;
+    c->have_cell = true;
+    c->loaded = c->localized = c->screened = c->applied = c->ace = false;
+    return build_tables(c);
+}
+
+lace_status lace_load_orbitals(lace_ctx* c, const double* phi, int n_occ, int n_extra, int orthonormalize) {
+    return load_common(c, phi, false, n_occ, n_extra, orthonormalize);
+}
+
+lace_status lace_load_orbitals_dev(lace_ctx* c, const double* d_phi, int n_occ, int n_extra, int orthonormalize) {
+    return load_common(c, d_phi, true, n_occ, n_extra, orthonormalize);
+}
+
+static lace_status localize_common(lace_ctx* c, int stride, const long long* imposed, long long* pivots_out) {
+    if (!c) return LACE_ERR_ARG;
+    if (!c->loaded) return fail(c, LACE_ERR_STATE, "load orbitals before localising");
+    if (!imposed && (stride < 1 || stride > 8)) return fail(c, LACE_ERR_ARG, "stride must be in [1, 8]");
+    cudaSetDevice(c->device);
+    c->localized = c->screened = c->applied = c->ace = false;
+    ev_begin(c, ST_LOCALIZE);
+    lace_status st = c->prec == LACE_FP64 ? localize_impl<double>(c, stride, imposed)
+                                          : localize_impl<float>(c, stride, imposed);
+    ev_end(c, ST_LOCALIZE);
+    if (st) return st;
+    CK(cudaStreamSynchronize(c->stream), "localize");
+    if (pivots_out) std::copy(c->pivots_host.begin(), c->pivots_host.end(), pivots_out);
+    c->localized = true;
+    return LACE_OK;
+}
+
+lace_status lace_localize(lace_ctx* c, int stride, long long* pivots_out) {
+    return localize_common(c, stride, nullptr, pivots_out);
+}
+
+lace_status lace_set_pivots(lace_ctx* c, const long long* pivots, int n) {
+    if (!c) return LACE_ERR_ARG;
+    if (!c->loaded) return fail(c, LACE_ERR_STATE, "load orbitals before localising");
+    if (!pivots || n != c->n_occ) return fail(c, LACE_ERR_ARG, "need exactly n_occ pivots");
+    std::vector<long long> v(pivots, pivots + n);
+    for (long long p : v)
+        if (p < 0 || (size_t)p >= c->g.ng) return fail(c, LACE_ERR_ARG, "pivot outside the grid");
+    std::sort(v.begin(), v.end());
+    if (std::adjacent_find(v.begin(), v.end()) != v.end()) return fail(c, LACE_ERR_ARG, "pivots must be distinct");
+    return localize_common(c, 0, pivots, nullptr);
+}
+
+lace_status lace_screen(lace_ctx* c, double s_thr, long long* n_pairs_out) {
+    if (!c) return LACE_ERR_ARG;
+    if (!c->loaded) return fail(c, LACE_ERR_STATE, "load orbitals before screening");
+    if (!(s_thr >= 0.0)) return fail(c, LACE_ERR_ARG, "threshold must be >= 0");
+    cudaSetDevice(c->device);
+    c->screened = c->applied = c->ace = false;
+    ev_begin(c, ST_SCREEN);
+    lace_status st = c->prec == LACE_FP64 ? screen_impl<double>(c, s_thr) : screen_impl<float>(c, s_thr);
+    if (st) return st;
+    Launch L{c};
+    st = make_pairs(c, true, s_thr, L);
+    ev_end(c, ST_SCREEN);
+    if (st) return st;
+    c->screened = true;
+    c->s_thr = s_thr;
+    if (n_pairs_out) *n_pairs_out = c->n_pairs;
+    return LACE_OK;
+}
+
+lace_status lace_apply_exchange(lace_ctx* c, double* W_out, double* ex_out) {
+    if (!c) return LACE_ERR_ARG;
+    if (!c->loaded) return fail(c, LACE_ERR_STATE, "load orbitals before applying the exchange");
+    cudaSetDevice(c->device);
+    c->applied = false;
+    ev_begin(c, ST_EXCHANGE);
+    lace_status st = c->prec == LACE_FP64 ? apply_impl<double>(c) : apply_impl<float>(c);
+    ev_end(c, ST_EXCHANGE);
+    if (st) return st;
+    c->applied = true;
+    if (ex_out) {
+        CK(cudaMemcpyAsync(ex_out, c->exd.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "energy");
+    }
+    if (W_out) {
+        st = c->prec == LACE_FP64 ? copy_orbitals_out<double>(c, c->W.as<double>(), (size_t)c->n_p * c->g.ng, W_out)
+                                  : copy_orbitals_out<float>(c, c->W.as<float>(), (size_t)c->n_p * c->g.ng, W_out);
+        if (st) return st;
+    }
+    CK(cudaStreamSynchronize(c->stream), "apply exchange");
+    return LACE_OK;
+}
+
+lace_status lace_exchange_energy(lace_ctx* c, double f_spin, double* ex_out) {
+    if (!c || !ex_out) return LACE_ERR_ARG;
+    if (!c->applied) return fail(c, LACE_ERR_STATE, "apply the exchange first");
+    double ex = 0.0;
+    CK(cudaMemcpyAsync(&ex, c->exd.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "energy");
+    CK(cudaStreamSynchronize(c->stream), "energy");
+    *ex_out = f_spin * ex;
+    return LACE_OK;
+}
+
+lace_status lace_build_ace(lace_ctx* c, int sym) {
+    if (!c) return LACE_ERR_ARG;
+    if (!c->applied) return fail(c, LACE_ERR_STATE, "apply the exchange before building ACE");
+    if (sym < 0 || sym > 2) return fail(c, LACE_ERR_ARG, "bad symmetrisation");
+    cudaSetDevice(c->device);
+    ev_begin(c, ST_ACE_BUILD);
+    lace_status st = c->prec == LACE_FP64 ? build_ace_impl<double>(c, sym) : build_ace_impl<float>(c, sym);
+    ev_end(c, ST_ACE_BUILD);
+    if (st) return st;
+    CK(cudaStreamSynchronize(c->stream), "build ace");
+    c->ace = true;
+    return LACE_OK;
+}
+
+static lace_status apply_ace_common(lace_ctx* c, const double* psi, int n, double* out, bool dev) {
+    if (!c) return LACE_ERR_ARG;
+    if (!c->ace) return fail(c, LACE_ERR_STATE, "build ACE before applying it");
+    if (!psi || !out || n < 1) return fail(c, LACE_ERR_ARG, "bad pointers or count");
+    cudaSetDevice(c->device);
+    const size_t cnt = (size_t)n * c->g.ng;
+    const double* din = psi;
+    double* dout = out;
+    DevBuf tmp_in, tmp_out;
+    if (!dev) {
+        CK(tmp_in.ensure(cnt * sizeof(double)), "alloc ace io");
+        CK(tmp_out.ensure(cnt * sizeof(double)), "alloc ace io");
+        CK(cudaMemcpyAsync(tmp_in.p, psi, cnt * sizeof(double), cudaMemcpyHostToDevice, c->stream), "upload");
+        din = tmp_in.as<double>();
+        dout = tmp_out.as<double>();
+    }
+    ev_begin(c, ST_ACE_APPLY);
+    lace_status st = c->prec == LACE_FP64 ? apply_ace_impl<double>(c, din, n, dout)
+                                          : apply_ace_impl<float>(c, din, n, dout);
+    ev_end(c, ST_ACE_APPLY);
+    if (st == LACE_OK && !dev) {
+        cudaError_t e = cudaMemcpyAsync(out, dout, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+        if (e) st = cuda_fail(c, e, "download");
+    }
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    tmp_in.release();
+    tmp_out.release();
+    if (st) return st;
+    if (e) return cuda_fail(c, e, "apply ace");
+    return LACE_OK;
+}
+
+lace_status lace_apply_ace(lace_ctx* c, const double* psi, int n, double* kpsi_out) {
+    return apply_ace_common(c, psi, n, kpsi_out, false);
+}
+
+lace_status lace_apply_ace_dev(lace_ctx* c, const double* d_psi, int n, double* d_kpsi_out) {
+    return apply_ace_common(c, d_psi, n, d_kpsi_out, true);
+}
+
+lace_status lace_get_matrix(lace_ctx* c, int which, double* out, long long count) {
+    if (!c || !out) return LACE_ERR_ARG;
+    const double* src = nullptr;
+    long long need = 0;
+    switch (which) {
+        case LACE_MAT_OVERLAP_MODULI:
+            if (!c->screened || !c->loaded) return fail(c, LACE_ERR_STATE, "screen first");
+            src = c->m(MS_S);
+            need = (long long)c->n_occ * c->n_occ;
+            break;
+        case LACE_MAT_EXCHANGE:
+            if (!c->ace) return fail(c, LACE_ERR_STATE, "build ACE first");
+            src = c->m(MS_M);
+            need = (long long)c->n_p * c->n_p;
+            break;
+        case LACE_MAT_CHOLESKY:
+            if (!c->ace) return fail(c, LACE_ERR_STATE, "build ACE first");
+            src = c->m(MS_L);
+            need = (long long)c->n_p * c->n_p;
+            break;
+        case LACE_MAT_PAIR_ENERGY:
+            if (!c->applied) return fail(c, LACE_ERR_STATE, "apply the exchange first");
+            src = c->m(MS_E);
+            need = (long long)c->n_occ * c->n_occ;
+            break;
+        case LACE_MAT_SCDM_U:
+            if (!c->localized) return fail(c, LACE_ERR_STATE, "localise first");
+            src = c->m(MS_U);
+            need = (long long)c->n_occ * c->n_occ;
+            break;
+        default: return fail(c, LACE_ERR_ARG, "unknown matrix");
+    }
+    if (count < need) return fail(c, LACE_ERR_ARG, "output buffer too small");
+    CK(cudaMemcpyAsync(out, src, sizeof(double) * need, cudaMemcpyDeviceToHost, c->stream), "get matrix");
+    CK(cudaStreamSynchronize(c->stream), "get matrix");
+    return LACE_OK;
+}
+
+lace_status lace_get_orbitals(lace_ctx* c, int which, double* out, long long count) {
+    if (!c || !out) return LACE_ERR_ARG;
+    if (!c->loaded) return fail(c, LACE_ERR_STATE, "load orbitals first");
+    const long long need = (long long)c->n_p * (long long)c->g.ng;
+    if (count < need) return fail(c, LACE_ERR_ARG, "output buffer too small");
+    const void* src = nullptr;
+    switch (which) {
+        case LACE_ORB_PSI: src = c->psi.p; break;
+        case LACE_ORB_W:
+            if (!c->applied) return fail(c, LACE_ERR_STATE, "apply the exchange first");
+            src = c->W.p;
+            break;
+        case LACE_ORB_XI:
+            if (!c->ace) return fail(c, LACE_ERR_STATE, "build ACE first");
+            src = c->xi.p;
+            break;
+        default: return fail(c, LACE_ERR_ARG, "unknown orbital set");
+    }
+    cudaSetDevice(c->device);
+    return c->prec == LACE_FP64 ? copy_orbitals_out<double>(c, static_cast<const double*>(src), need, out)
+                                : copy_orbitals_out<float>(c, static_cast<const float*>(src), need, out);
+}
+
+lace_status lace_get_pairs(lace_ctx* c, int* pairs_out, long long cap, long long* n_out) {
+    if (!c || !n_out) return LACE_ERR_ARG;
+    if (!c->screened) return fail(c, LACE_ERR_STATE, "screen (or apply the exchange) first");
+    *n_out = c->n_pairs;
+    if (pairs_out && cap > 0) {
+        const long long k = std::min(cap, c->n_pairs);
+        CK(cudaMemcpyAsync(pairs_out, c->pairs.p, sizeof(int2) * k, cudaMemcpyDeviceToHost, c->stream), "get pairs");
+        CK(cudaStreamSynchronize(c->stream), "get pairs");
+    }
+    return LACE_OK;
+}
+
+lace_status lace_get_timings(lace_ctx* c, double* ms_out, int count) {
+    if (!c || !ms_out) return LACE_ERR_ARG;
+    CK(cudaStreamSynchronize(c->stream), "timings");
+    for (int i = 0; i < count && i < ST_COUNT; ++i) {
+        float ms = 0.f;
+        if (c->ev_used[i] && cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]) == cudaSuccess)
+            ms_out[i] = ms;
+        else {
+            cudaGetLastError();
+            ms_out[i] = 0.0;
+        }
+    }
+    return LACE_OK;
+}
+
+lace_status lace_get_launch_count(lace_ctx* c, long long* count_out) {
+    if (!c || !count_out) return LACE_ERR_ARG;
+    *count_out = c->launches;
+    return LACE_OK;
+}
+
+}  // extern "C"

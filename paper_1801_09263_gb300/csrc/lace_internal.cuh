@@ -1,0 +1,109 @@
+// Internal interfaces between the translation units of liblace.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace lace {
+
+constexpr int kMaxN = 128;  // largest grid size per axis (FP32); FP64 is limited by shared memory
+
+struct GridGeom {
+    int n[3];
+    double cell[3];
+    size_t ng;
+    double omega, dv;
+    AxisPlan ax[3];
+};
+
+// Device tables of one grid, per precision.
+template <typename T> struct FFTTables {
+    cplx<T>* tw[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i m / n_a), m < n_a
+    T* g2[3] = {nullptr, nullptr, nullptr};         // (2 pi m / L_a)^2 in FFT order
+};
+
+// One complex FFT grid carries two real pair densities: slot a = (i1, j1),
+// slot b = (i2, j2); j2 < 0 marks an empty slot.  i is an occupied orbital
+// (row of Psi < n_occ), j any row of Psi.
+struct PairGrid {
+    int i1, j1, i2, j2;
+};
+
+// Host planning helpers (pairconv.cu)
+bool plan_axis(int n, AxisPlan* out);
+size_t pairconv_smem_bytes(const GridGeom& g, int elem_bytes, int pass);
+
+template <typename T>
+cudaError_t pairconv_run(const GridGeom& g, const FFTTables<T>& tb, const T* psi, int n_occ, T* W,
+                         const PairGrid* d_grids, int n_grids, cplx<T>* scratch, int batch, double* epart,
+                         double* d_pair_e, cudaStream_t s, int* launches, cudaEvent_t ev0, cudaEvent_t ev1);
+
+// Dense linear algebra (linalg.cu).  Matrices are row-major.
+// C[m][n] = alpha * sum_r op(A[m][r]) op(B[n][r]) over r < K (A, B rows of
+// length K with leading dimension ld*), op = |.| when absval.  Accumulates
+// per K-chunk in T, reduces the chunks in FP64 (deterministic).
+template <typename T>
+cudaError_t gemm_rows(int M, int N, size_t K, const T* A, size_t lda, const T* B, size_t ldb, double alpha,
+                      bool absval, double* C, int ldc, double* work, size_t work_elems, cudaStream_t s, int* launches);
+size_t gemm_rows_work_elems(int M, int N, size_t K);
+
+// Out[n][r] = beta*Out[n][r] + sum_k Coef[k][n] * A[k][r]  (r < K, n < N, k < Kc)
+// Coef is FP64 [Kc][ldcoef] on the device.
+template <typename T>
+cudaError_t gemm_combine(int N, size_t K, int Kc, const T* A, size_t lda, const double* Coef, int ldcoef, double beta,
+                         T* Out, size_t ldo, cudaStream_t s, int* launches);
+
+// Small FP64 dense kernels (N x N).
+cudaError_t small_gemm_f64(int M, int N, int K, const double* A, int lda, bool ta, const double* B, int ldb, bool tb,
+                           double alpha, double beta, double* C, int ldc, cudaStream_t s, int* launches);
+// X = A^{-1/2} of a symmetric positive definite A by the coupled Newton-Schulz
+// iteration; returns cudaSuccess and *ok=0 if it does not converge.
+cudaError_t inv_sqrt_spd(int N, const double* A, double* X, double* work, int* d_flag, int* ok, cudaStream_t s,
+                         int* launches);
+size_t inv_sqrt_work_elems(int N);
+// In-place lower Cholesky of A (N x N, lda); *ok = 0 when not positive definite.
+cudaError_t cholesky_lower(int N, double* A, int lda, int* d_flag, int* ok, cudaStream_t s, int* launches);
+// Linv = L^{-1} for lower triangular L.
+cudaError_t trtri_lower(int N, const double* L, int ldl, double* Linv, int ldi, cudaStream_t s, int* launches);
+// B = A^T (N x N)
+cudaError_t transpose_f64(int N, const double* A, double* B, cudaStream_t s, int* launches);
+// B = sym(A): 0 avg, 1 upper->lower, 2 lower->upper; also negates when neg.
+cudaError_t symmetrize(int N, const double* A, double* B, int mode, bool neg, cudaStream_t s, int* launches);
+
+// SCDM pivoted QR (scdm.cu): selects npiv columns of R (nrow x ncol,
+// row-major, overwritten).  Pivots are column indices, ties to the lowest
+// index.  aux: caller scratch of qrcp_aux_bytes(nrow, ncol) bytes.
+template <typename T>
+cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* aux, cudaStream_t s, int* launches);
+size_t qrcp_aux_bytes(int nrow, int ncol);
+
+// Subsample gather: out[o][c] = psi[o][full index of subsample point c]
+template <typename T>
+cudaError_t gather_subsample(const GridGeom& g, int stride, const T* psi, int norb, T* out, int* ncol_out,
+                             cudaStream_t s, int* launches);
+// Gather phi_C[point p][orbital o] = psi[o][pivot_full[p]] into FP64 (N x N).
+template <typename T>
+cudaError_t gather_columns(const T* psi, size_t ldpsi, int norb, const long long* d_full_idx, int npts, double* out,
+                           cudaStream_t s, int* launches);
+
+// Screening (screen.cu): keep mask from S and the pair list.
+// Writes the kept (i, j) pairs, i <= j < n_occ with S_ij >= thr, row by row,
+// followed by all (i, n_occ + e).  Returns the count in *n_pairs (host).
+cudaError_t build_pair_list(int n_occ, int n_extra, const double* d_S, double thr, bool use_S, int2* d_pairs,
+                            int* d_counts, long long* n_pairs, cudaStream_t s, int* launches);
+// Pack pairs two by two into complex FFT grids.
+cudaError_t pack_pair_grids(const int2* d_pairs, long long n_pairs, PairGrid* d_grids, cudaStream_t s, int* launches);
+// E_x = -1/2 sum_ij E[i][j] over the n_occ x n_occ pair-energy matrix.
+cudaError_t exchange_energy_sum(int n_occ, const double* d_E, double* d_ex, cudaStream_t s, int* launches);
+
+// Precision conversions and small helpers (linalg.cu)
+template <typename Tin, typename Tout>
+cudaError_t convert(const Tin* in, Tout* out, size_t n, cudaStream_t s, int* launches);
+cudaError_t fill_zero_f64(double* p, size_t n, cudaStream_t s, int* launches);
+
+}  // namespace lace

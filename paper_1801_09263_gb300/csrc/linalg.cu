@@ -1,0 +1,566 @@
+// Dense linear algebra of the exchange path: contractions over the grid
+// (Gram-type products such as M = dV Psi^T W of Eq. 3, S of Eq. 4 and the
+// Loewdin overlap), orbital combinations (W_loc = phi U, xi = W L^{-T},
+// K_ACE psi = -xi X), and the small FP64 N x N factorisations (Cholesky of
+// -M', triangular inverse, inverse square roots by Newton-Schulz).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "lace_internal.cuh"
+
+namespace lace {
+
+namespace {
+
+// ------------------------------------------------------------------ gemm_rows
+constexpr int GR_BM = 64, GR_BN = 64, GR_BK = 16, GR_THREADS = 256;
+constexpr int GR_INNER = 8;  // BK steps accumulated before folding (FP32 path)
+
+template <typename T> __device__ __forceinline__ T opv(T x, bool a) { return a ? (x < T(0) ? -x : x) : x; }
+
+// Partial C over one K-chunk: work[chunk][m][n] = sum_{r in chunk} op(A[m][r]) op(B[n][r]).
+template <typename T>
+__global__ void __launch_bounds__(GR_THREADS) gemm_rows_kernel(int M, int N, size_t K, const T* __restrict__ A,
+                                                                size_t lda, const T* __restrict__ B, size_t ldb,
+                                                                bool absval, size_t kchunk, double* __restrict__ work) {
+    __shared__ T As[GR_BK][GR_BM + 1];
+    __shared__ T Bs[GR_BK][GR_BN + 1];
+    const int m0 = blockIdx.x * GR_BM, n0 = blockIdx.y * GR_BN;
+    const size_t k_begin = (size_t)blockIdx.z * kchunk;
+    const size_t k_end = min(K, k_begin + kchunk);
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    T acc[4][4], fold[4][4], comp[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { acc[i][j] = T(0); fold[i][j] = T(0); comp[i][j] = T(0); }
+    int inner = 0;
+    // each thread loads 4 elements of A tile and 4 of B tile per step
+    const int lrow = tid / 4;       // 0..63
+    const int lcol = (tid % 4) * 4;  // 0,4,8,12
+    for (size_t k0 = k_begin; k0 < k_end; k0 += GR_BK) {
+        {
+            const int m = m0 + lrow;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const size_t k = k0 + lcol + c;
+                T v = T(0);
+                if (m < M && k < k_end) v = opv(A[(size_t)m * lda + k], absval);
+                As[lcol + c][lrow] = v;
+            }
+            const int n = n0 + lrow;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const size_t k = k0 + lcol + c;
+                T v = T(0);
+                if (n < N && k < k_end) v = opv(B[(size_t)n * ldb + k], absval);
+                Bs[lcol + c][lrow] = v;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GR_BK; ++kk) {
+            T a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+        }
+        __syncthreads();
+        if constexpr (sizeof(T) == 4) {
+            if (++inner == GR_INNER) {
+                inner = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const T y = acc[i][j] - comp[i][j];
+                        const T t = fold[i][j] + y;
+                        comp[i][j] = (t - fold[i][j]) - y;
+                        fold[i][j] = t;
+                        acc[i][j] = T(0);
+                    }
+            }
+        }
+    }
+    double* out = work + (size_t)blockIdx.z * M * N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty * 4 + i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx * 4 + j;
+            if (n >= N) continue;
+            out[(size_t)m * N + n] = (double)fold[i][j] - (double)comp[i][j] + (double)acc[i][j];
+        }
+    }
+}
+
+__global__ void reduce_chunks_kernel(int M, int N, int nchunk, const double* __restrict__ work, double alpha,
+                                     double* __restrict__ C, int ldc) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)M * N) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += work[(size_t)c * M * N + idx];
+    const int m = (int)(idx / N), n = (int)(idx % N);
+    C[(size_t)m * ldc + n] = alpha * s;
+}
+
+size_t n_chunks_for(int M, int N, size_t K) {
+    const size_t tiles = (size_t)((M + GR_BM - 1) / GR_BM) * ((N + GR_BN - 1) / GR_BN);
+    size_t want = (4 * 152 + tiles - 1) / tiles;
+    size_t maxc = (K + 1023) / 1024;
+    return std::max<size_t>(1, std::min(want, maxc));
+}
+
+// ------------------------------------------------------------------ gemm_combine
+constexpr int GC_BR = 128, GC_BN = 64, GC_BK = 16, GC_THREADS = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(GC_THREADS) gemm_combine_kernel(int N, size_t K, int Kc, const T* __restrict__ A,
+                                                                   size_t lda, const double* __restrict__ Coef,
+                                                                   int ldcoef, double beta, T* __restrict__ Out,
+                                                                   size_t ldo) {
+    __shared__ T As[GC_BK][GC_BR];
+    __shared__ T Cs[GC_BK][GC_BN];
+    const size_t r0 = (size_t)blockIdx.x * GC_BR;
+    const int n0 = blockIdx.y * GC_BN;
+    const int tid = threadIdx.x;
+    const int tr = tid % 32;  // 4 r each: r = r0 + tr + 32*i
+    const int tn = tid / 32;  // 8 n each: n = n0 + tn*8 + j
+    T acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = T(0);
+    for (int k0 = 0; k0 < Kc; k0 += GC_BK) {
+        // A tile: 16 x 128 = 2048 elements, 8 per thread
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int e = tid + c * GC_THREADS;
+            const int kk = e / GC_BR, rr = e % GC_BR;
+            const int k = k0 + kk;
+            const size_t r = r0 + rr;
+            As[kk][rr] = (k < Kc && r < K) ? A[(size_t)k * lda + r] : T(0);
+        }
+        // Coef tile: 16 x 64 = 1024 elements, 4 per thread
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int e = tid + c * GC_THREADS;
+            const int kk = e / GC_BN, nn = e % GC_BN;
+            const int k = k0 + kk, n = n0 + nn;
+            Cs[kk][nn] = (k < Kc && n < N) ? (T)Coef[(size_t)k * ldcoef + n] : T(0);
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GC_BK; ++kk) {
+            T a[4], c[8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][tr + 32 * i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) c[j] = Cs[kk][tn * 8 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * c[j];
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int n = n0 + tn * 8 + j;
+        if (n >= N) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const size_t r = r0 + tr + 32 * i;
+            if (r >= K) continue;
+            T* o = Out + (size_t)n * ldo + r;
+            *o = beta == 0.0 ? acc[i][j] : (T)beta * *o + acc[i][j];
+        }
+    }
+}
+
+// ------------------------------------------------------------------ small FP64
+constexpr int SG = 16;
+
+__global__ void small_gemm_kernel(int M, int N, int K, const double* __restrict__ A, int lda, bool ta,
+                                  const double* __restrict__ B, int ldb, bool tb, double alpha, double beta,
+                                  double* __restrict__ C, int ldc) {
+    __shared__ double As[SG][SG + 1];
+    __shared__ double Bs[SG][SG + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int m = blockIdx.y * SG + ty, n = blockIdx.x * SG + tx;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < K; k0 += SG) {
+        {   // As[ty][tx] = op(A)[m][k0+tx]
+            const int k = k0 + tx;
+            double v = 0.0;
+            if (m < M && k < K) v = ta ? A[(size_t)k * lda + m] : A[(size_t)m * lda + k];
+            As[ty][tx] = v;
+        }
+        {   // Bs[ty][tx] = op(B)[k0+ty][n]
+            const int k = k0 + ty;
+            double v = 0.0;
+            if (n < N && k < K) v = tb ? B[(size_t)n * ldb + k] : B[(size_t)k * ldb + n];
+            Bs[ty][tx] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < SG; ++kk) acc = fma(As[ty][kk], Bs[kk][tx], acc);
+        __syncthreads();
+    }
+    if (m < M && n < N) {
+        double* c = C + (size_t)m * ldc + n;
+        *c = alpha * acc + (beta == 0.0 ? 0.0 : beta * *c);
+    }
+}
+
+__global__ void set_identity_kernel(int N, double* X, double scale) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N) return;
+    X[idx] = (idx / N == idx % N) ? scale : 0.0;
+}
+
+__global__ void scale_copy_kernel(int n, const double* in, double* out, double s) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n) out[idx] = s * in[idx];
+}
+
+// T = (3 I - P) / 2 in place on P
+__global__ void ns_t_kernel(int N, double* P) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N) return;
+    const double d = (idx / N == idx % N) ? 3.0 : 0.0;
+    P[idx] = 0.5 * (d - P[idx]);
+}
+
+// Frobenius norm squared (single block, fixed order) into out[0]; mode 1: of (I - A).
+__global__ void frob_kernel(int N, const double* A, int mode, double* out) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+        double v = A[idx];
+        if (mode == 1) v = ((idx / N == idx % N) ? 1.0 : 0.0) - v;
+        s += v * v;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+// ------------------------------------------------------------------ Cholesky
+constexpr int CH_NB = 32;
+
+// Unblocked Cholesky of the diagonal block at k0 (nb x nb) in shared memory.
+__global__ void potrf_diag_kernel(int N, double* A, int lda, int k0, int nb, int* flag) {
+    __shared__ double D[CH_NB][CH_NB + 1];
+    const int tid = threadIdx.x;
+    for (int e = tid; e < nb * nb; e += blockDim.x) D[e / nb][e % nb] = A[(size_t)(k0 + e / nb) * lda + k0 + e % nb];
+    __syncthreads();
+    for (int j = 0; j < nb; ++j) {
+        if (tid == 0) {
+            double d = D[j][j];
+            if (!(d > 0.0)) {
+                atomicExch(flag, 1);
+                d = 1.0;
+            }
+            D[j][j] = sqrt(d);
+        }
+        __syncthreads();
+        const double piv = D[j][j];
+        for (int i = j + 1 + tid; i < nb; i += blockDim.x) D[i][j] /= piv;
+        __syncthreads();
+        // trailing update of the block (lower part)
+        for (int e = tid; e < nb * nb; e += blockDim.x) {
+            const int i = e / nb, k = e % nb;
+            if (i > j && k > j && k <= i) D[i][k] -= D[i][j] * D[k][j];
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < nb * nb; e += blockDim.x) {
+        const int i = e / nb, k = e % nb;
+        A[(size_t)(k0 + i) * lda + k0 + k] = (k <= i) ? D[i][k] : 0.0;
+    }
+}
+
+// Rows below the diagonal block: L_ik = A_ik L_kk^{-T} (forward substitution per row).
+__global__ void trsm_panel_kernel(int N, double* A, int lda, int k0, int nb) {
+    __shared__ double D[CH_NB][CH_NB + 1];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) D[e / nb][e % nb] = A[(size_t)(k0 + e / nb) * lda + k0 + e % nb];
+    __syncthreads();
+    const int i = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= N) return;
+    double x[CH_NB];
+    double* row = A + (size_t)i * lda + k0;
+    for (int j = 0; j < nb; ++j) {
+        double s = row[j];
+        for (int l = 0; l < j; ++l) s -= x[l] * D[j][l];
+        x[j] = s / D[j][j];
+    }
+    for (int j = 0; j < nb; ++j) row[j] = x[j];
+}
+
+__global__ void zero_upper_kernel(int N, double* A, int lda) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N) return;
+    const int i = idx / N, j = idx % N;
+    if (j > i) A[(size_t)i * lda + j] = 0.0;
+}
+
+// Inverse of the lower-triangular diagonal block at k0 (nb x nb), written to X.
+__global__ void trtri_diag_kernel(int N, const double* L, int ldl, double* X, int ldx) {
+    const int k0 = blockIdx.x * CH_NB;
+    const int nb = min(CH_NB, N - k0);
+    __shared__ double D[CH_NB][CH_NB + 1];
+    __shared__ double R[CH_NB][CH_NB + 1];
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) D[e / nb][e % nb] = L[(size_t)(k0 + e / nb) * ldl + k0 + e % nb];
+    __syncthreads();
+    // column c of the inverse by forward substitution (one thread per column)
+    const int c = threadIdx.x;
+    if (c < nb) {
+        for (int i = 0; i < nb; ++i) {
+            double s = (i == c) ? 1.0 : 0.0;
+            for (int l = c; l < i; ++l) s -= D[i][l] * R[l][c];
+            R[i][c] = (i < c) ? 0.0 : s / D[i][i];
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) X[(size_t)(k0 + e / nb) * ldx + k0 + e % nb] = R[e / nb][e % nb];
+}
+
+__global__ void symmetrize_kernel(int N, const double* A, double* B, int mode, double sgn) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N) return;
+    const int i = idx / N, j = idx % N;
+    double v;
+    if (mode == 0) v = 0.5 * (A[(size_t)i * N + j] + A[(size_t)j * N + i]);
+    else if (mode == 1) v = (j >= i) ? A[(size_t)i * N + j] : A[(size_t)j * N + i];  // upper kept
+    else v = (j <= i) ? A[(size_t)i * N + j] : A[(size_t)j * N + i];                  // lower kept
+    B[idx] = sgn * v;
+}
+
+__global__ void transpose_kernel(int N, const double* A, double* B) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N) return;
+    const int i = idx / N, j = idx % N;
+    B[(size_t)j * N + i] = A[idx];
+}
+
+template <typename Tin, typename Tout>
+__global__ void convert_kernel(const Tin* __restrict__ in, Tout* __restrict__ out, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        out[i] = (Tout)in[i];
+}
+
+__global__ void fill_zero_kernel(double* p, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = 0.0;
+}
+
+}  // namespace
+
+// ============================================================================
+
+size_t gemm_rows_work_elems(int M, int N, size_t K) { return n_chunks_for(M, N, K) * (size_t)M * N; }
+
+template <typename T>
+cudaError_t gemm_rows(int M, int N, size_t K, const T* A, size_t lda, const T* B, size_t ldb, double alpha,
+                      bool absval, double* C, int ldc, double* work, size_t work_elems, cudaStream_t s,
+                      int* launches) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    const size_t nch = n_chunks_for(M, N, K);
+    if (nch * (size_t)M * N > work_elems) return cudaErrorInvalidValue;
+    size_t kchunk = (K + nch - 1) / nch;
+    kchunk = (kchunk + GR_BK - 1) / GR_BK * GR_BK;
+    const size_t nch_eff = (K + kchunk - 1) / kchunk;
+    dim3 grid((M + GR_BM - 1) / GR_BM, (N + GR_BN - 1) / GR_BN, (unsigned)nch_eff);
+    gemm_rows_kernel<T><<<grid, GR_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, absval, kchunk, work);
+    const size_t tot = (size_t)M * N;
+    reduce_chunks_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, N, (int)nch_eff, work, alpha, C, ldc);
+    *launches += 2;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gemm_combine(int N, size_t K, int Kc, const T* A, size_t lda, const double* Coef, int ldcoef, double beta,
+                         T* Out, size_t ldo, cudaStream_t s, int* launches) {
+    if (N <= 0 || K == 0) return cudaSuccess;
+    dim3 grid((unsigned)((K + GC_BR - 1) / GC_BR), (N + GC_BN - 1) / GC_BN);
+    gemm_combine_kernel<T><<<grid, GC_THREADS, 0, s>>>(N, K, Kc, A, lda, Coef, ldcoef, beta, Out, ldo);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t small_gemm_f64(int M, int N, int K, const double* A, int lda, bool ta, const double* B, int ldb, bool tb,
+                           double alpha, double beta, double* C, int ldc, cudaStream_t s, int* launches) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    dim3 grid((N + SG - 1) / SG, (M + SG - 1) / SG);
+    small_gemm_kernel<<<grid, dim3(SG, SG), 0, s>>>(M, N, K, A, lda, ta, B, ldb, tb, alpha, beta, C, ldc);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+size_t inv_sqrt_work_elems(int N) { return 4 * (size_t)N * N + 8; }
+
+// Coupled Newton-Schulz iteration (Higham, "Functions of Matrices", Sec. 6.7):
+// Y_0 = A/c, Z_0 = I; T = (3I - Z Y)/2; Y <- Y T; Z <- T Z.  Z -> (A/c)^{-1/2}.
+// c = ||A||_F puts the spectrum of A/c in (0, 1], where the iteration converges.
+cudaError_t inv_sqrt_spd(int N, const double* A, double* X, double* work, int* d_flag, int* ok, cudaStream_t s,
+                         int* launches) {
+    (void)d_flag;
+    const size_t nn = (size_t)N * N;
+    double* Y = work;
+    double* Z = X;
+    double* T = work + nn;
+    double* Y2 = work + 2 * nn;
+    double* Z2 = work + 3 * nn;
+    double* scal = work + 4 * nn;
+    const int nb = (int)((nn + 255) / 256);
+    double h_norm2 = 0.0;
+    frob_kernel<<<1, 256, 0, s>>>(N, A, 0, scal);
+    cudaMemcpyAsync(&h_norm2, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    *launches += 1;
+    if (e) return e;
+    if (!(h_norm2 > 0.0) || !std::isfinite(h_norm2)) { *ok = 0; return cudaSuccess; }
+    const double c = std::sqrt(h_norm2);
+    scale_copy_kernel<<<nb, 256, 0, s>>>((int)nn, A, Y, 1.0 / c);
+    set_identity_kernel<<<nb, 256, 0, s>>>(N, Z, 1.0);
+    *launches += 2;
+    *ok = 0;
+    // Stop when ||I - Z Y||_F^2 is below 1e-24 N, or once it is below 1e-12 N
+    // and no longer falls by 4x between checks (rounding floor reached).
+    double prev = INFINITY;
+    for (int it = 0; it < 160; ++it) {
+        small_gemm_f64(N, N, N, Z, N, false, Y, N, false, 1.0, 0.0, T, N, s, launches);
+        ns_t_kernel<<<nb, 256, 0, s>>>(N, T);
+        small_gemm_f64(N, N, N, Y, N, false, T, N, false, 1.0, 0.0, Y2, N, s, launches);
+        small_gemm_f64(N, N, N, T, N, false, Z, N, false, 1.0, 0.0, Z2, N, s, launches);
+        cudaMemcpyAsync(Y, Y2, nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(Z, Z2, nn * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        *launches += 1;
+        if (it >= 5 && (it % 2 == 1)) {
+            small_gemm_f64(N, N, N, Z, N, false, Y, N, false, 1.0, 0.0, T, N, s, launches);
+            frob_kernel<<<1, 256, 0, s>>>(N, T, 1, scal);
+            cudaMemcpyAsync(&h_norm2, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
+            *launches += 1;
+            if ((e = cudaStreamSynchronize(s))) return e;
+            if (!std::isfinite(h_norm2)) break;
+            if (h_norm2 < 1e-24 * N || (h_norm2 < 1e-12 * N && h_norm2 > 0.25 * prev)) { *ok = 1; break; }
+            prev = h_norm2;
+        }
+    }
+    if (!*ok) return cudaGetLastError();
+    // Reject ill-conditioned A: ||(A/c)^{-1/2}||_F^2 >= lambda_max/lambda_min.
+    frob_kernel<<<1, 256, 0, s>>>(N, Z, 0, scal);
+    cudaMemcpyAsync(&h_norm2, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
+    *launches += 1;
+    if ((e = cudaStreamSynchronize(s))) return e;
+    if (!(h_norm2 < 1e12)) { *ok = 0; return cudaSuccess; }
+    // A^{-1/2} = (A/c)^{-1/2} / sqrt(c)
+    scale_copy_kernel<<<nb, 256, 0, s>>>((int)nn, Z, X, 1.0 / std::sqrt(c));
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t cholesky_lower(int N, double* A, int lda, int* d_flag, int* ok, cudaStream_t s, int* launches) {
+    cudaMemsetAsync(d_flag, 0, sizeof(int), s);
+    for (int k0 = 0; k0 < N; k0 += CH_NB) {
+        const int nb = std::min(CH_NB, N - k0);
+        potrf_diag_kernel<<<1, 256, 0, s>>>(N, A, lda, k0, nb, d_flag);
+        *launches += 1;
+        const int rem = N - k0 - nb;
+        if (rem > 0) {
+            trsm_panel_kernel<<<(rem + 127) / 128, 128, 0, s>>>(N, A, lda, k0, nb);
+            *launches += 1;
+            // A22 -= L21 L21^T
+            double* L21 = A + (size_t)(k0 + nb) * lda + k0;
+            double* A22 = A + (size_t)(k0 + nb) * lda + k0 + nb;
+            small_gemm_f64(rem, rem, nb, L21, lda, false, L21, lda, true, -1.0, 1.0, A22, lda, s, launches);
+        }
+    }
+    zero_upper_kernel<<<(N * N + 255) / 256, 256, 0, s>>>(N, A, lda);
+    *launches += 1;
+    int h = 0;
+    cudaMemcpyAsync(&h, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    *ok = (h == 0);
+    return e;
+}
+
+// Blocked L^{-1}: X_ii = L_ii^{-1};  X_ij = -X_ii * sum_{k=j}^{i-1} L_ik X_kj  (j < i).
+cudaError_t trtri_lower(int N, const double* L, int ldl, double* X, int ldx, cudaStream_t s, int* launches) {
+    cudaMemsetAsync(X, 0, sizeof(double) * (size_t)N * ldx, s);
+    const int nblk = (N + CH_NB - 1) / CH_NB;
+    trtri_diag_kernel<<<nblk, CH_NB, 0, s>>>(N, L, ldl, X, ldx);
+    *launches += 1;
+    // temp rows: use the upper triangle of X?  No: need a separate buffer of nb x N.
+    // Work in place: for block row i, compute T = L[i, 0:i] * X[0:i, 0:i] into X[i, 0:i]
+    // (X[i, 0:i] is zero before), then X[i, 0:i] = -X_ii * T, using X's
+    // unused upper-right area is not safe; so two steps with a small staging
+    // area at the end of X's allocation (caller provides ldx*N + CH_NB*N).
+    double* stage = X + (size_t)N * ldx;
+    for (int bi = 1; bi < nblk; ++bi) {
+        const int i0 = bi * CH_NB;
+        const int nb = std::min(CH_NB, N - i0);
+        // stage[nb x i0] = L[i0:i0+nb, 0:i0] * X[0:i0, 0:i0]
+        small_gemm_f64(nb, i0, i0, L + (size_t)i0 * ldl, ldl, false, X, ldx, false, 1.0, 0.0, stage, i0, s, launches);
+        // X[i0:i0+nb, 0:i0] = -X_ii * stage
+        small_gemm_f64(nb, i0, nb, X + (size_t)i0 * ldx + i0, ldx, false, stage, i0, false, -1.0, 0.0,
+                       X + (size_t)i0 * ldx, ldx, s, launches);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t symmetrize(int N, const double* A, double* B, int mode, bool neg, cudaStream_t s, int* launches) {
+    symmetrize_kernel<<<(N * N + 255) / 256, 256, 0, s>>>(N, A, B, mode, neg ? -1.0 : 1.0);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t transpose_f64(int N, const double* A, double* B, cudaStream_t s, int* launches) {
+    transpose_kernel<<<(N * N + 255) / 256, 256, 0, s>>>(N, A, B);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+template <typename Tin, typename Tout>
+cudaError_t convert(const Tin* in, Tout* out, size_t n, cudaStream_t s, int* launches) {
+    if (n == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+    convert_kernel<Tin, Tout><<<blocks, 256, 0, s>>>(in, out, n);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t fill_zero_f64(double* p, size_t n, cudaStream_t s, int* launches) {
+    if (n == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+    fill_zero_kernel<<<blocks, 256, 0, s>>>(p, n);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+template cudaError_t gemm_rows<float>(int, int, size_t, const float*, size_t, const float*, size_t, double, bool,
+                                      double*, int, double*, size_t, cudaStream_t, int*);
+template cudaError_t gemm_rows<double>(int, int, size_t, const double*, size_t, const double*, size_t, double, bool,
+                                       double*, int, double*, size_t, cudaStream_t, int*);
+template cudaError_t gemm_combine<float>(int, size_t, int, const float*, size_t, const double*, int, double, float*,
+                                         size_t, cudaStream_t, int*);
+template cudaError_t gemm_combine<double>(int, size_t, int, const double*, size_t, const double*, int, double, double*,
+                                          size_t, cudaStream_t, int*);
+template cudaError_t convert<double, float>(const double*, float*, size_t, cudaStream_t, int*);
+template cudaError_t convert<float, double>(const float*, double*, size_t, cudaStream_t, int*);
+template cudaError_t convert<double, double>(const double*, double*, size_t, cudaStream_t, int*);
+
+}  // namespace lace

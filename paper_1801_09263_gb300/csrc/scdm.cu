@@ -1,0 +1,205 @@
+// SCDM localisation support (Sec. 2): pivoted QR (Businger-Golub, modified
+// Gram-Schmidt with exact column norms at every step) on the grid subsample,
+// and the gathers that feed it and the U = phi_C^T (phi_C phi_C^T)^{-1/2}
+// rotation computed by the caller.
+#include <algorithm>
+
+#include "lace_internal.cuh"
+
+namespace lace {
+
+namespace {
+
+constexpr int QR_THREADS = 256;
+constexpr int QR_MAXROWS = 1024;
+
+struct Best {
+    double v;
+    int idx;
+};
+
+__device__ __forceinline__ bool better(double v, int i, double bv, int bi) { return v > bv || (v == bv && i < bi); }
+
+// One column per thread: apply the previous reflection-free MGS step
+// R[:,c] -= q (q . R[:,c]), then the exact squared norm of the column.
+// Chosen columns report -1.  Per-block argmax (ties: lowest index).
+template <typename T>
+__global__ void __launch_bounds__(QR_THREADS) qr_update_kernel(int nrow, int ncol, T* __restrict__ R, size_t ld,
+                                                               const T* __restrict__ q, int has_q,
+                                                               const unsigned char* __restrict__ chosen,
+                                                               Best* __restrict__ block_best) {
+    __shared__ T qs[QR_MAXROWS];
+    __shared__ double bv[QR_THREADS];
+    __shared__ int bi[QR_THREADS];
+    for (int r = threadIdx.x; r < nrow; r += blockDim.x) qs[r] = has_q ? q[r] : T(0);
+    __syncthreads();
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    double best = -2.0;
+    int bidx = 0x7fffffff;
+    if (c < ncol) {
+        T* col = R + c;
+        if (has_q) {
+            T dot = T(0);
+            for (int r = 0; r < nrow; ++r) dot += qs[r] * col[(size_t)r * ld];
+            T nrm = T(0);
+            for (int r = 0; r < nrow; ++r) {
+                T v = col[(size_t)r * ld] - qs[r] * dot;
+                col[(size_t)r * ld] = v;
+                nrm += v * v;
+            }
+            best = chosen[c] ? -1.0 : (double)nrm;
+        } else {
+            T nrm = T(0);
+            for (int r = 0; r < nrow; ++r) {
+                T v = col[(size_t)r * ld];
+                nrm += v * v;
+            }
+            best = chosen[c] ? -1.0 : (double)nrm;
+        }
+        bidx = c;
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = bidx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            if (better(bv[threadIdx.x + o], bi[threadIdx.x + o], bv[threadIdx.x], bi[threadIdx.x])) {
+                bv[threadIdx.x] = bv[threadIdx.x + o];
+                bi[threadIdx.x] = bi[threadIdx.x + o];
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) block_best[blockIdx.x] = Best{bv[0], bi[0]};
+}
+
+// Pick the pivot among the block winners, mark it, form q = R[:,p]/||R[:,p]||.
+template <typename T>
+__global__ void __launch_bounds__(QR_THREADS) qr_select_kernel(int nrow, int nblocks, const T* __restrict__ R,
+                                                               size_t ld, const Best* __restrict__ block_best,
+                                                               unsigned char* __restrict__ chosen, T* __restrict__ q,
+                                                               int* __restrict__ piv, int step) {
+    __shared__ double bv[QR_THREADS];
+    __shared__ int bi[QR_THREADS];
+    __shared__ double nrm_sh[QR_THREADS];
+    double best = -3.0;
+    int bidx = 0x7fffffff;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) {
+        const Best x = block_best[b];
+        if (better(x.v, x.idx, best, bidx)) { best = x.v; bidx = x.idx; }
+    }
+    bv[threadIdx.x] = best;
+    bi[threadIdx.x] = bidx;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o && better(bv[threadIdx.x + o], bi[threadIdx.x + o], bv[threadIdx.x], bi[threadIdx.x])) {
+            bv[threadIdx.x] = bv[threadIdx.x + o];
+            bi[threadIdx.x] = bi[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    const int p = bi[0];
+    double s = 0.0;
+    for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
+        const double v = (double)R[(size_t)r * ld + p];
+        s += v * v;
+    }
+    nrm_sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) nrm_sh[threadIdx.x] += nrm_sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    const double inv = nrm_sh[0] > 0.0 ? 1.0 / sqrt(nrm_sh[0]) : 0.0;
+    for (int r = threadIdx.x; r < nrow; r += blockDim.x) q[r] = (T)((double)R[(size_t)r * ld + p] * inv);
+    if (threadIdx.x == 0) {
+        piv[step] = p;
+        chosen[p] = 1;
+    }
+}
+
+template <typename T>
+__global__ void gather_subsample_kernel(int n1, int n2, int n3, int stride, int m1, int m2, int m3,
+                                        const T* __restrict__ psi, size_t ng, T* __restrict__ out, size_t ncol) {
+    const int o = blockIdx.y;
+    for (size_t c = (size_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncol; c += (size_t)gridDim.x * blockDim.x) {
+        const int k = (int)(c % m3);
+        const int j = (int)((c / m3) % m2);
+        const int i = (int)(c / ((size_t)m3 * m2));
+        const size_t full = ((size_t)(i * stride) * n2 + (size_t)(j * stride)) * n3 + (size_t)(k * stride);
+        out[(size_t)o * ncol + c] = psi[(size_t)o * ng + full];
+    }
+    (void)n1;
+    (void)m1;
+}
+
+template <typename T>
+__global__ void gather_columns_kernel(const T* __restrict__ psi, size_t ldpsi, int norb,
+                                      const long long* __restrict__ idx, int npts, double* __restrict__ out) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= npts * norb) return;
+    const int p = e / norb, o = e % norb;
+    out[e] = (double)psi[(size_t)o * ldpsi + (size_t)idx[p]];
+}
+
+}  // namespace
+
+static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
+
+size_t qrcp_aux_bytes(int nrow, int ncol) {
+    const int nblocks = (ncol + QR_THREADS - 1) / QR_THREADS;
+    return align256(sizeof(Best) * nblocks) + align256((size_t)ncol) + align256(sizeof(double) * nrow);
+}
+
+// R (nrow x ncol, row-major, leading dimension ncol) is overwritten.  aux is
+// caller-provided scratch of qrcp_aux_bytes(nrow, ncol) bytes.
+template <typename T>
+cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* aux, cudaStream_t s, int* launches) {
+    if (nrow > QR_MAXROWS || npiv > ncol) return cudaErrorInvalidValue;
+    const int nblocks = (ncol + QR_THREADS - 1) / QR_THREADS;
+    unsigned char* base = static_cast<unsigned char*>(aux);
+    Best* best = reinterpret_cast<Best*>(base);
+    unsigned char* chosen = base + align256(sizeof(Best) * nblocks);
+    T* q = reinterpret_cast<T*>(chosen + align256((size_t)ncol));
+    cudaMemsetAsync(chosen, 0, ncol, s);
+    for (int step = 0; step < npiv; ++step) {
+        qr_update_kernel<T><<<nblocks, QR_THREADS, 0, s>>>(nrow, ncol, R, (size_t)ncol, q, step > 0, chosen, best);
+        qr_select_kernel<T><<<1, QR_THREADS, 0, s>>>(nrow, nblocks, R, (size_t)ncol, best, chosen, q, d_piv, step);
+        *launches += 2;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gather_subsample(const GridGeom& g, int stride, const T* psi, int norb, T* out, int* ncol_out,
+                             cudaStream_t s, int* launches) {
+    const int m1 = (g.n[0] + stride - 1) / stride, m2 = (g.n[1] + stride - 1) / stride,
+              m3 = (g.n[2] + stride - 1) / stride;
+    const size_t ncol = (size_t)m1 * m2 * m3;
+    *ncol_out = (int)ncol;
+    dim3 grid((unsigned)std::min<size_t>((ncol + 255) / 256, 1024), norb);
+    gather_subsample_kernel<T><<<grid, 256, 0, s>>>(g.n[0], g.n[1], g.n[2], stride, m1, m2, m3, psi, g.ng, out, ncol);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t gather_columns(const T* psi, size_t ldpsi, int norb, const long long* d_full_idx, int npts, double* out,
+                           cudaStream_t s, int* launches) {
+    const int tot = npts * norb;
+    gather_columns_kernel<T><<<(tot + 255) / 256, 256, 0, s>>>(psi, ldpsi, norb, d_full_idx, npts, out);
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+template cudaError_t qrcp_pivots<float>(int, int, float*, int, int*, void*, cudaStream_t, int*);
+template cudaError_t qrcp_pivots<double>(int, int, double*, int, int*, void*, cudaStream_t, int*);
+template cudaError_t gather_subsample<float>(const GridGeom&, int, const float*, int, float*, int*, cudaStream_t, int*);
+template cudaError_t gather_subsample<double>(const GridGeom&, int, const double*, int, double*, int*, cudaStream_t,
+                                              int*);
+template cudaError_t gather_columns<float>(const float*, size_t, int, const long long*, int, double*, cudaStream_t,
+                                           int*);
+template cudaError_t gather_columns<double>(const double*, size_t, int, const long long*, int, double*, cudaStream_t,
+                                            int*);
+
+}  // namespace lace

@@ -192,6 +192,16 @@ def test_qrcp_pivots_match_lapack_geqp3():
         assert list(piv) == list(p[:6])
 
 
+def test_qrcp_pivot_ratios_flag_a_wrong_order():
+    rng = np.random.default_rng(8)
+    a = rng.standard_normal((5, 30))
+    piv = O.qrcp_pivots(a, 5)
+    assert np.allclose(O.qrcp_pivot_ratios(a, piv), 1.0)
+    bad = list(piv)
+    bad[1], bad[2] = bad[2], bad[1]
+    assert O.qrcp_pivot_ratios(a, bad).min() < 0.999
+
+
 def test_qrcp_tie_takes_lowest_index():
     a = np.zeros((2, 5))
     a[0, 3] = 1.0
