@@ -178,6 +178,7 @@ class Lace:
 
     def apply_exchange(self, want_W: bool = True):
         ex = C.c_double(0.0)
+        want_W = want_W and self.shape is not None and self.n_p > 0
         W = np.empty((self.n_p,) + self.shape, dtype=np.float64) if want_W else None
         self._check(self.lib.lace_apply_exchange(self.h, _ptr(W) if want_W else None, C.byref(ex)),
                     "lace_apply_exchange")
