@@ -171,6 +171,43 @@ lace_status lace_get_timings(lace_ctx* ctx, double* ms_out, int count);
  * created (all calls). */
 lace_status lace_get_launch_count(lace_ctx* ctx, long long* count_out);
 
+/* Allocation-free exchange application (the paper has no counterpart: this
+ * call exists for callers that cannot allocate device memory where they need
+ * the exchange, e.g. a latency-critical loop where cudaMalloc/cudaFree would
+ * synchronise the device and stall other streams, or a program whose device
+ * memory is owned end to end by its own pool allocator).
+ *
+ * Computes, in FP64 and without a context, what lace_apply_exchange computes
+ * for a given pair list: W_j = -sum_i w_i v_ij over the pairs, with
+ * W_i -= w_j v_ij as well for an occupied j != i, and the pair energies.
+ *   cell      orthorhombic cell (a, b, c) in bohr (host, read during the call)
+ *   n1..n3    grid; each 2^a 3^b 5^c in [4, 128] and small enough for the FP64
+ *             passes' shared memory (n <= 108 on GB300)
+ *   d_psi     device FP64 [n_p][n1][n2][n3]; rows < n_occ are the occupied w_i
+ *   d_pairs   device int32 [n_pairs][2] of (i, j): i < n_occ, j < n_p, i <= j
+ *             when j < n_occ (the layout lace_get_pairs returns)
+ *   d_W       device FP64 [n_p][n1][n2][n3], overwritten (cleared first)
+ *   d_pair_e  device FP64 [n_occ][n_occ], overwritten: (ij|ji) of each pair,
+ *             both (i, j) and (j, i), zero elsewhere; E_x = -1/2 sum
+ *   stream    cudaStream_t the work is queued on (NULL = legacy default)
+ * Memory: every call uses one fixed 32 MiB device array inside the library
+ * (allocated when the library's device code is loaded, held until exit) and
+ * calls no cudaMalloc/cudaFree.  The array keeps the last call's contents;
+ * everything a call reads from it is rewritten by that call first.  Calls
+ * that overlap on the GPU (different streams, or different host threads on
+ * one device) share the array and race: serialise them.
+ * Set-up: the first call on a device looks up the array's device address
+ * (with that device current); make that first call before any stream
+ * capture.  Each call synchronises `stream` once, after checking the pair
+ * list on the device and before queueing the FFT passes.
+ * Returns LACE_ERR_ARG for null pointers, bad counts or a pair outside the
+ * ranges above; LACE_ERR_UNSUPPORTED for a grid size outside the list above
+ * or when one complex FFT grid plus the pair descriptors ((n_pairs+1)/2 x 16
+ * bytes) do not fit in the 32 MiB array; LACE_ERR_CUDA on a CUDA error. */
+lace_status lace_exchange_pairs_noalloc(const double cell[3], int n1, int n2, int n3, const double* d_psi,
+                                        int n_occ, int n_p, const int* d_pairs, long long n_pairs, double* d_W,
+                                        double* d_pair_e, void* stream);
+
 /* Static description of a status code. */
 const char* lace_status_string(lace_status status);
 

@@ -74,6 +74,7 @@ def load_library(build_if_missing: bool = False):
         "lace_get_pairs": ([P, P, LL, P], I),
         "lace_get_timings": ([P, P, I], I),
         "lace_get_launch_count": ([P, P], I),
+        "lace_exchange_pairs_noalloc": ([P, I, I, I, P, I, I, P, LL, P, P, P], I),
         "lace_status_string": ([I], C.c_char_p),
         "lace_last_error": ([P], C.c_char_p),
     }
