@@ -69,6 +69,21 @@ __host__ __device__ constexpr double ct_cos2pi(long m, long n) {
 }
 __host__ __device__ constexpr double ct_sin2pi(long m, long n) { return ct_cos2pi(m * 4 - n, 4 * n); }  // sin(x) = cos(x - pi/2)
 
+// x * c for a compile-time constant c.  In FP32 the constant is carried as
+// hi + lo (two floats) and the product rounded once: rounding the irrational
+// DFT constants (sqrt(1/2), sqrt(3)/2, cos/sin of 2 pi/5 ...) to a single
+// float scales every butterfly that uses them the same way, and the pair
+// energies inherit that bias (about -1e-7 relative per transform pair).
+template <typename T> __device__ __forceinline__ T mulk(T x, double c) {
+    if constexpr (sizeof(T) == 4) {
+        const float hi = (float)c;
+        const float lo = (float)(c - (double)hi);
+        return fmaf(x, hi, x * lo);
+    } else {
+        return x * (T)c;
+    }
+}
+
 // Multiply by exp(DIR * 2 pi i M / N), folding the trivial cases.
 template <int N, int M, int DIR, typename C>
 __device__ __forceinline__ C twiddle_ct(C a) {
@@ -85,7 +100,7 @@ __device__ __forceinline__ C twiddle_ct(C a) {
     } else {
         constexpr double c = ct_cos2pi(m, N);
         constexpr double s = DIR * ct_sin2pi(m, N);
-        return C{a.x * T(c) - a.y * T(s), a.x * T(s) + a.y * T(c)};
+        return C{mulk(a.x, c) - mulk(a.y, s), mulk(a.x, s) + mulk(a.y, c)};
     }
 }
 
@@ -109,7 +124,7 @@ template <int DIR> struct DFT<3, DIR> {
         C t1 = cadd(b, c);
         C t2 = C{a.x - T(0.5) * t1.x, a.y - T(0.5) * t1.y};
         C d = csub(b, c);
-        C t3 = cmul_i<DIR>(C{T(s3) * d.x, T(s3) * d.y});
+        C t3 = cmul_i<DIR>(C{mulk(d.x, s3), mulk(d.y, s3)});
         v[0] = cadd(a, t1);
         v[1] = cadd(t2, t3);
         v[2] = csub(t2, t3);
@@ -136,10 +151,10 @@ template <int DIR> struct DFT<5, DIR> {
         C a = v[0];
         C p1 = cadd(v[1], v[4]), m1 = csub(v[1], v[4]);
         C p2 = cadd(v[2], v[3]), m2 = csub(v[2], v[3]);
-        C r1 = C{a.x + T(c1) * p1.x + T(c2) * p2.x, a.y + T(c1) * p1.y + T(c2) * p2.y};
-        C r2 = C{a.x + T(c2) * p1.x + T(c1) * p2.x, a.y + T(c2) * p1.y + T(c1) * p2.y};
-        C i1 = cmul_i<DIR>(C{T(s1) * m1.x + T(s2) * m2.x, T(s1) * m1.y + T(s2) * m2.y});
-        C i2 = cmul_i<DIR>(C{T(s2) * m1.x - T(s1) * m2.x, T(s2) * m1.y - T(s1) * m2.y});
+        C r1 = C{a.x + mulk(p1.x, c1) + mulk(p2.x, c2), a.y + mulk(p1.y, c1) + mulk(p2.y, c2)};
+        C r2 = C{a.x + mulk(p1.x, c2) + mulk(p2.x, c1), a.y + mulk(p1.y, c2) + mulk(p2.y, c1)};
+        C i1 = cmul_i<DIR>(C{mulk(m1.x, s1) + mulk(m2.x, s2), mulk(m1.y, s1) + mulk(m2.y, s2)});
+        C i2 = cmul_i<DIR>(C{mulk(m1.x, s2) - mulk(m2.x, s1), mulk(m1.y, s2) - mulk(m2.y, s1)});
         v[0] = cadd(a, cadd(p1, p2));
         v[1] = cadd(r1, i1);
         v[4] = csub(r1, i1);

@@ -53,6 +53,7 @@ struct lace_ctx {
     bool have_cell = false;
     GridGeom g{};
     DevBuf tw_d[3], tw_f[3], g2_d[3], g2_f[3];
+    DevBuf ktab_f;  // K(G)/Ng rounded once from FP64 (FP32 path)
 
     int n_occ = 0, n_extra = 0, n_p = 0;
     bool loaded = false, localized = false, screened = false, applied = false, ace = false;
@@ -157,6 +158,30 @@ lace_status build_tables(lace_ctx* c) {
         CK(cudaMemcpy(c->g2_d[a].p, g2d.data(), n * sizeof(double), cudaMemcpyHostToDevice), "tables");
         CK(cudaMemcpy(c->g2_f[a].p, g2f.data(), n * sizeof(float), cudaMemcpyHostToDevice), "tables");
     }
+    // K(G)/Ng = 4 pi / (Ng |G|^2), K(0) = 0, evaluated in FP64 and rounded once:
+    // rounding 4 pi/Ng and |G|^2 separately in FP32 biases every pair energy alike.
+    const int n1 = c->g.n[0], n2 = c->g.n[1], n3 = c->g.n[2];
+    std::vector<double> gx(n1), gy(n2), gz(n3);
+    auto fill = [](std::vector<double>& v, int n, double len) {
+        for (int m = 0; m < n; ++m) {
+            const int mm = (m < (n + 1) / 2) ? m : m - n;
+            const double gv = 2.0 * M_PI * (double)mm / len;
+            v[m] = gv * gv;
+        }
+    };
+    fill(gx, n1, c->g.cell[0]);
+    fill(gy, n2, c->g.cell[1]);
+    fill(gz, n3, c->g.cell[2]);
+    std::vector<float> kt(c->g.ng);
+    const double scale = 4.0 * M_PI / (double)c->g.ng;
+    for (int x = 0; x < n1; ++x)
+        for (int y = 0; y < n2; ++y)
+            for (int z = 0; z < n3; ++z) {
+                const double gg = gx[x] + gy[y] + gz[z];
+                kt[((size_t)x * n2 + y) * n3 + z] = gg > 0.0 ? (float)(scale / gg) : 0.0f;
+            }
+    CK(c->ktab_f.ensure(c->g.ng * sizeof(float)), "tables");
+    CK(cudaMemcpy(c->ktab_f.p, kt.data(), c->g.ng * sizeof(float), cudaMemcpyHostToDevice), "tables");
     return LACE_OK;
 }
 
@@ -169,6 +194,7 @@ template <> FFTTables<double> tables<double>(lace_ctx* c) {
 template <> FFTTables<float> tables<float>(lace_ctx* c) {
     FFTTables<float> t;
     for (int a = 0; a < 3; ++a) { t.tw[a] = c->tw_f[a].as<float2>(); t.g2[a] = c->g2_f[a].as<float>(); }
+    t.ktab = c->ktab_f.as<float>();
     return t;
 }
 
@@ -200,7 +226,13 @@ lace_status lowdin_rows(lace_ctx* c, const T* src, int n, T* dst, Launch& L) {
                     c->work.bytes / sizeof(double), c->stream, &L.n),
        "loewdin overlap");
     int ok = 0;
-    CK(inv_sqrt_spd(n, S, X, c->m(MS_NSWORK), c->flag.as<int>(), &ok, c->stream, &L.n), "loewdin inverse sqrt");
+    if (c->prec == LACE_FP64) {
+        CK(inv_sqrt_spd(n, S, X, c->m(MS_NSWORK), c->flag.as<int>(), &ok, c->stream, &L.n), "loewdin inverse sqrt");
+    } else {
+        // FP32 Newton-Schulz, then one FP64 first-order Loewdin step on X^T S X
+        CK(inv_sqrt_spd_mixed(n, S, X, c->m(MS_NSWORK), &ok, c->stream, &L.n), "loewdin inverse sqrt");
+        if (ok) CK(lowdin_refine(n, X, S, c->m(MS_NSWORK), c->stream, &L.n), "loewdin refine");
+    }
     if (!ok) return fail(c, LACE_ERR_NOT_PD, "overlap matrix is singular or ill-conditioned (inverse square root did not converge)");
     CK(gemm_combine<T>(n, ng, n, src, ng, X, n, 0.0, dst, ng, c->stream, &L.n), "loewdin combine");
     return LACE_OK;
@@ -315,10 +347,16 @@ lace_status localize_impl(lace_ctx* c, int stride, const long long* imposed) {
     // B = phi_C phi_C^T  (points x points)
     CK(small_gemm_f64(n, n, n, phic, n, false, phic, n, true, 1.0, 0.0, B, n, c->stream, &L.n), "scdm B");
     int ok = 0;
-    CK(inv_sqrt_spd(n, B, Bmh, c->m(MS_NSWORK), c->flag.as<int>(), &ok, c->stream, &L.n), "scdm inverse sqrt");
+    if (c->prec == LACE_FP64) {
+        CK(inv_sqrt_spd(n, B, Bmh, c->m(MS_NSWORK), c->flag.as<int>(), &ok, c->stream, &L.n), "scdm inverse sqrt");
+    } else {
+        CK(inv_sqrt_spd_mixed(n, B, Bmh, c->m(MS_NSWORK), &ok, c->stream, &L.n), "scdm inverse sqrt");
+    }
     if (!ok) return fail(c, LACE_ERR_NOT_PD, "selected columns are rank deficient");
     // U = phi_C^T B^{-1/2}  (orbitals x orbitals)
     CK(small_gemm_f64(n, n, n, phic, n, true, Bmh, n, false, 1.0, 0.0, U, n, c->stream, &L.n), "scdm U");
+    // mixed path: restore exact orthogonality of U in FP64 (U <- U (I - (U^T U - I)/2))
+    if (c->prec != LACE_FP64) CK(lowdin_refine(n, U, nullptr, c->m(MS_NSWORK), c->stream, &L.n), "scdm refine");
     // w = canon U
     CK(gemm_combine<T>(n, ng, n, canon, ng, U, n, 0.0, c->psi.as<T>(), ng, c->stream, &L.n), "scdm rotate");
     return LACE_OK;
@@ -504,6 +542,7 @@ lace_status lace_destroy(lace_ctx* c) {
                       &c->pairs, &c->counts, &c->grids, &c->epart, &c->flag, &c->piv, &c->pivfull, &c->exd};
     for (DevBuf* b : bufs) b->release();
     for (int a = 0; a < 3; ++a) { c->tw_d[a].release(); c->tw_f[a].release(); c->g2_d[a].release(); c->g2_f[a].release(); }
+    c->ktab_f.release();
     for (auto& e : c->ev) if (e) cudaEventDestroy(e);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;

@@ -25,6 +25,7 @@ struct GridGeom {
 template <typename T> struct FFTTables {
     cplx<T>* tw[3] = {nullptr, nullptr, nullptr};  // exp(-2 pi i m / n_a), m < n_a
     T* g2[3] = {nullptr, nullptr, nullptr};         // (2 pi m / L_a)^2 in FFT order
+    T* ktab = nullptr;                              // optional K(G)/Ng table [n1][n2][n3]
 };
 
 // One complex FFT grid carries two real pair densities: slot a = (i1, j1),
@@ -33,6 +34,29 @@ template <typename T> struct FFTTables {
 struct PairGrid {
     int i1, j1, i2, j2;
 };
+
+// Kernel arguments of the three FFT passes.
+template <typename T> struct ConvArgs {
+    AxisPlan ax[3];
+    const cplx<T>* tw[3];
+    const T* g2[3];
+    T kscale;         // 4 pi / Ng
+    const T* ktab;    // K(G)/Ng per grid point, rounded once from FP64 (null: computed in T)
+    const T* psi;
+    int n_occ;
+    T* W;
+    const PairGrid* grids;
+    cplx<T>* scratch;
+    double* epart;  // [batch][n1][2]
+    size_t ng;
+    double dv;
+};
+
+// Size-specialised FP32 passes for cubic grids (pairconv_spec_*.cu): launch
+// pass 0/1/2 (A/B/C) for grid size n if a specialisation exists.
+bool spec_launch_s(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
+bool spec_launch_m(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
+bool spec_launch_l(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
 
 // Host planning helpers (pairconv.cu)
 bool plan_axis(int n, AxisPlan* out);
@@ -66,6 +90,13 @@ cudaError_t small_gemm_f64(int M, int N, int K, const double* A, int lda, bool t
 cudaError_t inv_sqrt_spd(int N, const double* A, double* X, double* work, int* d_flag, int* ok, cudaStream_t s,
                          int* launches);
 size_t inv_sqrt_work_elems(int N);
+// Mixed-precision variant: FP32 Newton-Schulz to ~1e-7, returns X0 ~ A^{-1/2}
+// (FP64, symmetric).  Pair it with lowdin_refine.
+cudaError_t inv_sqrt_spd_mixed(int N, const double* A, double* X, double* work, int* ok, cudaStream_t s,
+                               int* launches);
+size_t inv_sqrt_mixed_work_elems(int N);
+// F <- F (I - E/2), E = F^T G F - I (G = I when null): orthonormality to O(E^2).
+cudaError_t lowdin_refine(int N, double* F, const double* G, double* work, cudaStream_t s, int* launches);
 // In-place lower Cholesky of A (N x N, lda); *ok = 0 when not positive definite.
 cudaError_t cholesky_lower(int N, double* A, int lda, int* d_flag, int* ok, cudaStream_t s, int* launches);
 // Linv = L^{-1} for lower triangular L.

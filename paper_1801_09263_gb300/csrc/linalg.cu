@@ -15,7 +15,12 @@ namespace {
 
 // ------------------------------------------------------------------ gemm_rows
 constexpr int GR_BM = 64, GR_BN = 64, GR_BK = 16, GR_THREADS = 256;
-constexpr int GR_INNER = 8;  // BK steps accumulated before folding (FP32 path)
+// FP32 path: products of one BK step (16 neighbouring grid points) are summed
+// in FP32 and then folded into a compensated (Kahan) FP32 accumulator.  Folding
+// less often lets tiny tail products fall below half an ulp of a long running
+// sum and vanish, which biases Gram matrices of positive terms low (measured:
+// -3.6e-8 relative with 128-product runs on localised orbitals).
+constexpr int GR_INNER = 1;
 
 template <typename T> __device__ __forceinline__ T opv(T x, bool a) { return a ? (x < T(0) ? -x : x) : x; }
 
@@ -219,6 +224,79 @@ __global__ void small_gemm_kernel(int M, int N, int K, const double* __restrict_
         double* c = C + (size_t)m * ldc + n;
         *c = alpha * acc + (beta == 0.0 ? 0.0 : beta * *c);
     }
+}
+
+__global__ void small_gemm_f32_kernel(int N, const float* __restrict__ A, const float* __restrict__ B,
+                                      float* __restrict__ C) {
+    // C = A B for N x N row-major; 16 x 16 tiles, one output per thread
+    __shared__ float As[SG][SG + 1];
+    __shared__ float Bs[SG][SG + 1];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int m = blockIdx.y * SG + ty, n = blockIdx.x * SG + tx;
+    float acc = 0.f;
+    for (int k0 = 0; k0 < N; k0 += SG) {
+        As[ty][tx] = (m < N && k0 + tx < N) ? A[(size_t)m * N + k0 + tx] : 0.f;
+        Bs[ty][tx] = (n < N && k0 + ty < N) ? B[(size_t)(k0 + ty) * N + n] : 0.f;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < SG; ++kk) acc = fmaf(As[ty][kk], Bs[kk][tx], acc);
+        __syncthreads();
+    }
+    if (m < N && n < N) C[(size_t)m * N + n] = acc;
+}
+
+// T = (3 I - P) / 2 in place (FP32)
+__global__ void ns_t_f32_kernel(int N, float* P) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N) return;
+    const float d = (idx / N == idx % N) ? 3.f : 0.f;
+    P[idx] = 0.5f * (d - P[idx]);
+}
+
+// out[0] = || I - A ||_F^2 (FP32 input, FP64 sum, fixed order)
+__global__ void frob_res_f32_kernel(int N, const float* A, double* out) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
+        const double v = ((idx / N == idx % N) ? 1.0 : 0.0) - (double)A[idx];
+        s += v * v;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+__global__ void scale_to_f32_kernel(int n, const double* in, float* out, double s) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n) out[idx] = (float)(s * in[idx]);
+}
+
+__global__ void identity_f32_kernel(int N, float* X) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < N * N) X[idx] = (idx / N == idx % N) ? 1.f : 0.f;
+}
+
+// X = s * (Z + Z^T)/2 in FP64 from FP32 Z
+__global__ void sym_from_f32_kernel(int N, const float* Z, double* X, double s) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * N) return;
+    const int i = idx / N, j = idx % N;
+    X[idx] = s * 0.5 * ((double)Z[(size_t)i * N + j] + (double)Z[(size_t)j * N + i]);
+}
+
+// E := E - I (in place)
+__global__ void sub_identity_kernel(int N, double* E) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < N * N && idx / N == idx % N) E[idx] -= 1.0;
+}
+
+__global__ void axpy_kernel(int n, const double* x, double* y) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < n) y[idx] += x[idx];
 }
 
 __global__ void set_identity_kernel(int N, double* X, double scale) {
@@ -469,6 +547,93 @@ cudaError_t inv_sqrt_spd(int N, const double* A, double* X, double* work, int* d
     if (!(h_norm2 < 1e12)) { *ok = 0; return cudaSuccess; }
     // A^{-1/2} = (A/c)^{-1/2} / sqrt(c)
     scale_copy_kernel<<<nb, 256, 0, s>>>((int)nn, Z, X, 1.0 / std::sqrt(c));
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+size_t inv_sqrt_mixed_work_elems(int N) { return 4 * (size_t)N * N + 8; }
+
+// FP32 coupled Newton-Schulz to ~1e-7 (same iteration as inv_sqrt_spd), then
+// X0 = sym(Z)/sqrt(c) in FP64.  X0 A X0 = I + O(1e-7); callers restore exact
+// orthonormality with one FP64 first-order Loewdin step (lowdin_refine).
+cudaError_t inv_sqrt_spd_mixed(int N, const double* A, double* X, double* work, int* ok, cudaStream_t s,
+                               int* launches) {
+    const size_t nn = (size_t)N * N;
+    float* Y = reinterpret_cast<float*>(work);
+    float* Z = Y + nn;
+    float* T = Z + nn;
+    float* Y2 = T + nn;
+    float* Z2 = Y2 + nn;
+    double* scal = work + 3 * nn;  // past the five FP32 matrices (2.5 nn doubles)
+    const int nb = (int)((nn + 255) / 256);
+    const dim3 gg((N + SG - 1) / SG, (N + SG - 1) / SG), bb(SG, SG);
+    double h = 0.0;
+    frob_kernel<<<1, 256, 0, s>>>(N, A, 0, scal);
+    cudaMemcpyAsync(&h, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    *launches += 1;
+    if (e) return e;
+    *ok = 0;
+    if (!(h > 0.0) || !std::isfinite(h)) return cudaSuccess;
+    const double c = std::sqrt(h);
+    scale_to_f32_kernel<<<nb, 256, 0, s>>>((int)nn, A, Y, 1.0 / c);
+    identity_f32_kernel<<<nb, 256, 0, s>>>(N, Z);
+    *launches += 2;
+    double prev = INFINITY;
+    for (int it = 0; it < 160; ++it) {
+        small_gemm_f32_kernel<<<gg, bb, 0, s>>>(N, Z, Y, T);
+        ns_t_f32_kernel<<<nb, 256, 0, s>>>(N, T);
+        small_gemm_f32_kernel<<<gg, bb, 0, s>>>(N, Y, T, Y2);
+        small_gemm_f32_kernel<<<gg, bb, 0, s>>>(N, T, Z, Z2);
+        std::swap(Y, Y2);
+        std::swap(Z, Z2);
+        *launches += 4;
+        if (it >= 5 && (it % 3 == 2)) {
+            small_gemm_f32_kernel<<<gg, bb, 0, s>>>(N, Z, Y, T);
+            frob_res_f32_kernel<<<1, 256, 0, s>>>(N, T, scal);
+            cudaMemcpyAsync(&h, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
+            *launches += 2;
+            if ((e = cudaStreamSynchronize(s))) return e;
+            if (!std::isfinite(h)) break;
+            if (h < 1e-11 * N || (h < 1e-6 * N && h > 0.25 * prev)) { *ok = 1; break; }
+            prev = h;
+        }
+    }
+    if (!*ok) return cudaGetLastError();
+    // ||(A/c)^{-1/2}||_F^2 >= lambda_max / lambda_min: reject ill-conditioned A
+    sym_from_f32_kernel<<<nb, 256, 0, s>>>(N, Z, X, 1.0);
+    frob_kernel<<<1, 256, 0, s>>>(N, X, 0, scal);
+    cudaMemcpyAsync(&h, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
+    *launches += 2;
+    if ((e = cudaStreamSynchronize(s))) return e;
+    if (!(h < 1e12)) { *ok = 0; return cudaSuccess; }
+    scale_copy_kernel<<<nb, 256, 0, s>>>((int)nn, X, X, 1.0 / std::sqrt(c));
+    *launches += 1;
+    return cudaGetLastError();
+}
+
+// First-order Loewdin correction making F^T G F = I to second order:
+// E = F^T G F - I (G = identity when G == nullptr), F <- F (I - E/2).
+// F is N x N FP64 (in place); work holds 3 N x N.
+cudaError_t lowdin_refine(int N, double* F, const double* G, double* work, cudaStream_t s, int* launches) {
+    const size_t nn = (size_t)N * N;
+    double* GF = work;
+    double* E = work + nn;
+    double* F2 = work + 2 * nn;
+    const int nb = (int)((nn + 255) / 256);
+    const double* rhs = F;
+    if (G) {
+        small_gemm_f64(N, N, N, G, N, false, F, N, false, 1.0, 0.0, GF, N, s, launches);
+        rhs = GF;
+    }
+    small_gemm_f64(N, N, N, F, N, true, rhs, N, false, 1.0, 0.0, E, N, s, launches);
+    sub_identity_kernel<<<nb, 256, 0, s>>>(N, E);
+    *launches += 1;
+    small_gemm_f64(N, N, N, F, N, false, E, N, false, -0.5, 0.0, F2, N, s, launches);
+    // F += F2
+    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    axpy_kernel<<<nb, 256, 0, s>>>((int)nn, F2, F);
     *launches += 1;
     return cudaGetLastError();
 }

@@ -15,6 +15,8 @@
 //      adds) and the real-space pair energies dV sum rho v (FP64).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
+#include <type_traits>
 
 #include "lace_internal.cuh"
 
@@ -23,21 +25,6 @@ namespace lace {
 namespace {
 
 constexpr int kThreads = 256;
-
-template <typename T> struct ConvArgs {
-    AxisPlan ax[3];
-    const cplx<T>* tw[3];
-    const T* g2[3];
-    T kscale;  // 4 pi / Ng
-    const T* psi;
-    int n_occ;
-    T* W;
-    const PairGrid* grids;
-    cplx<T>* scratch;
-    double* epart;  // [batch][n1][2]
-    size_t ng;
-    double dv;
-};
 
 template <typename C>
 __device__ __forceinline__ void load_tw(C* dst, const C* src, int n) {
@@ -102,8 +89,13 @@ __global__ void __launch_bounds__(kThreads) pass_b_kernel(ConvArgs<T> P, int g0)
     const T gy2 = P.g2[1][ky];
     for (int e = threadIdx.x; e < n1 * n3; e += blockDim.x) {
         const int x = e / n3, z = e - x * n3;
-        const T gg = gx2[x] + gy2 + gz2[z];
-        const T k = gg > T(0) ? P.kscale / gg : T(0);
+        T k;
+        if (P.ktab) {
+            k = P.ktab[((size_t)x * n2 + ky) * n3 + z];
+        } else {
+            const T gg = gx2[x] + gy2 + gz2[z];
+            k = gg > T(0) ? P.kscale / gg : T(0);
+        }
         C v = slab[e];
         slab[e] = C{v.x * k, v.y * k};
     }
@@ -267,6 +259,7 @@ cudaError_t pairconv_run(const GridGeom& g, const FFTTables<T>& tb, const T* psi
         P.g2[a] = tb.g2[a];
     }
     P.kscale = (T)(4.0 * M_PI / (double)g.ng);
+    P.ktab = tb.ktab;
     P.psi = psi;
     P.n_occ = n_occ;
     P.W = W;
@@ -281,12 +274,25 @@ cudaError_t pairconv_run(const GridGeom& g, const FFTTables<T>& tb, const T* psi
     if ((e = cudaFuncSetAttribute(pass_a_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_plane))) return e;
     if ((e = cudaFuncSetAttribute(pass_c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_plane))) return e;
     if ((e = cudaFuncSetAttribute(pass_b_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_slab))) return e;
+    // size-specialised FP32 kernels for cubic grids with n % 4 == 0 (or LACE_GENERIC_FFT=1 to disable)
+    const char* gen = getenv("LACE_GENERIC_FFT");
+    const bool spec_ok = !(gen && gen[0] == '1') && g.n[0] == g.n[1] && g.n[1] == g.n[2] && g.n[0] % 4 == 0;
     if (ev0) cudaEventRecord(ev0, s);
     for (int g0 = 0; g0 < n_grids; g0 += batch) {
         const int nb = std::min(batch, n_grids - g0);
-        pass_a_kernel<T><<<dim3(g.n[0], nb), kThreads, sm_plane, s>>>(P, g0);
-        pass_b_kernel<T><<<dim3(g.n[1], nb), kThreads, sm_slab, s>>>(P, g0);
-        pass_c_kernel<T><<<dim3(g.n[0], nb), kThreads, sm_plane, s>>>(P, g0);
+        bool done = false;
+        if constexpr (std::is_same<T, float>::value) {
+            if (spec_ok) {
+                for (int pass = 0; pass < 3; ++pass)
+                    done = spec_launch_s(pass, g.n[0], nb, P, g0, s) || spec_launch_m(pass, g.n[0], nb, P, g0, s) ||
+                           spec_launch_l(pass, g.n[0], nb, P, g0, s);
+            }
+        }
+        if (!done) {
+            pass_a_kernel<T><<<dim3(g.n[0], nb), kThreads, sm_plane, s>>>(P, g0);
+            pass_b_kernel<T><<<dim3(g.n[1], nb), kThreads, sm_slab, s>>>(P, g0);
+            pass_c_kernel<T><<<dim3(g.n[0], nb), kThreads, sm_plane, s>>>(P, g0);
+        }
         energy_collect_kernel<<<(nb + 127) / 128, 128, 0, s>>>(epart, g.n[0], d_grids, g0, nb, n_occ, d_pair_e);
         *launches += 4;
         if ((e = cudaGetLastError())) return e;

@@ -2,9 +2,13 @@
 // Gram-Schmidt with exact column norms at every step) on the grid subsample,
 // and the gathers that feed it and the U = phi_C^T (phi_C phi_C^T)^{-1/2}
 // rotation computed by the caller.
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "lace_internal.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace lace {
 
@@ -118,6 +122,134 @@ __global__ void __launch_bounds__(QR_THREADS) qr_select_kernel(int nrow, int nbl
     }
 }
 
+// Persistent pivoted QR: one cooperative launch runs every step.  A CTA of
+// 512 threads (16 warps) walks tiles of 32 columns; lane = column, warp w
+// holds rows w, w+16, ... (RPT of them) in registers while it forms q.r
+// (reduced across the warps in shared memory), updates r -= q (q.r) and the
+// exact new norm.
+// One grid-wide barrier per step; the block winners are double-buffered by
+// step parity and a chosen column is never written again, so the pivot
+// column can be read by every CTA while the next step already runs.
+constexpr int QC_THREADS = 512, QC_WARPS = 16, QC_RPT = 32;  // rows <= 16 * RPT, RPT <= 32
+
+__device__ __forceinline__ void best_merge(double& v, int& i, double v2, int i2) {
+    if (better(v2, i2, v, i)) { v = v2; i = i2; }
+}
+
+template <typename T, int RPT>
+__global__ void __launch_bounds__(QC_THREADS) qr_persistent_kernel(int nrow, int ncol, T* __restrict__ R,
+                                                                   int npiv, Best* __restrict__ block_best,
+                                                                   unsigned char* __restrict__ chosen,
+                                                                   int* __restrict__ piv) {
+    cg::grid_group grid = cg::this_grid();
+    __shared__ T qs[QC_WARPS * QC_RPT];
+    __shared__ T part[QC_WARPS][32];
+    __shared__ double bv[QC_THREADS];
+    __shared__ int bi[QC_THREADS];
+    __shared__ int pivot_sh;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ntiles = (ncol + 31) / 32;
+    for (int r = threadIdx.x; r < QC_WARPS * QC_RPT; r += blockDim.x) qs[r] = T(0);
+    __syncthreads();
+    for (int step = 0; step < npiv; ++step) {
+        // (a) apply the previous step's q, exact norms, local argmax
+        double best = -2.0;
+        int bidx = 0x7fffffff;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int c = tile * 32 + lane;
+            const bool live = c < ncol && !chosen[c];
+            T v[RPT];
+            T dot = T(0);
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int r = warp + k * QC_WARPS;
+                v[k] = (r < nrow && live) ? R[(size_t)r * ncol + c] : T(0);
+                dot += qs[r] * v[k];
+            }
+            if (step > 0) {
+                part[warp][lane] = dot;
+                __syncthreads();
+                T d = T(0);
+#pragma unroll
+                for (int w = 0; w < QC_WARPS; ++w) d += part[w][lane];
+                __syncthreads();
+                dot = d;
+            }
+            T nrm = T(0);
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+                const int r = warp + k * QC_WARPS;
+                if (r < nrow) {
+                    if (step > 0) {
+                        v[k] -= qs[r] * dot;
+                        if (live) R[(size_t)r * ncol + c] = v[k];
+                    }
+                    nrm += v[k] * v[k];
+                }
+            }
+            part[warp][lane] = nrm;
+            __syncthreads();
+            if (warp == 0) {
+                T tot = T(0);
+#pragma unroll
+                for (int w = 0; w < QC_WARPS; ++w) tot += part[w][lane];
+                double cv = live ? (double)tot : (c < ncol ? -1.0 : -2.0);
+                int ci = c < ncol ? c : 0x7fffffff;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double ov = __shfl_xor_sync(0xffffffffu, cv, o);
+                    const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
+                    best_merge(cv, ci, ov, oi);
+                }
+                best_merge(best, bidx, cv, ci);
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) block_best[(step & 1) * gridDim.x + blockIdx.x] = Best{best, bidx};
+        grid.sync();
+        // (b) every CTA: global argmax, then q = R[:,p] / ||R[:,p]|| into shared memory
+        double gb = -3.0;
+        int gi = 0x7fffffff;
+        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+            const Best x = block_best[(step & 1) * gridDim.x + b];
+            best_merge(gb, gi, x.v, x.idx);
+        }
+        bv[threadIdx.x] = gb;
+        bi[threadIdx.x] = gi;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) {
+                double v2 = bv[threadIdx.x];
+                int i2 = bi[threadIdx.x];
+                best_merge(v2, i2, bv[threadIdx.x + o], bi[threadIdx.x + o]);
+                bv[threadIdx.x] = v2;
+                bi[threadIdx.x] = i2;
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) pivot_sh = bi[0];
+        __syncthreads();
+        const int p = pivot_sh;
+        double s2 = 0.0;
+        for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
+            const double x = (double)R[(size_t)r * ncol + p];
+            s2 += x * x;
+        }
+        bv[threadIdx.x] = s2;
+        __syncthreads();
+        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+            if (threadIdx.x < o) bv[threadIdx.x] += bv[threadIdx.x + o];
+            __syncthreads();
+        }
+        const double inv = bv[0] > 0.0 ? 1.0 / sqrt(bv[0]) : 0.0;
+        for (int r = threadIdx.x; r < nrow; r += blockDim.x) qs[r] = (T)((double)R[(size_t)r * ncol + p] * inv);
+        if (threadIdx.x == 0) {
+            chosen[p] = 1;
+            if (blockIdx.x == 0) piv[step] = p;
+        }
+        __syncthreads();
+    }
+}
+
 template <typename T>
 __global__ void gather_subsample_kernel(int n1, int n2, int n3, int stride, int m1, int m2, int m3,
                                         const T* __restrict__ psi, size_t ng, T* __restrict__ out, size_t ncol) {
@@ -146,8 +278,11 @@ __global__ void gather_columns_kernel(const T* __restrict__ psi, size_t ldpsi, i
 
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
+// Capacity (in Best entries) of the block-winner buffer of qrcp_aux_bytes.
+static int nblocks_cap(int ncol) { return std::max((ncol + QR_THREADS - 1) / QR_THREADS, 2 * 152 * 8); }
+
 size_t qrcp_aux_bytes(int nrow, int ncol) {
-    const int nblocks = (ncol + QR_THREADS - 1) / QR_THREADS;
+    const int nblocks = nblocks_cap(ncol);
     return align256(sizeof(Best) * nblocks) + align256((size_t)ncol) + align256(sizeof(double) * nrow);
 }
 
@@ -159,9 +294,29 @@ cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* au
     const int nblocks = (ncol + QR_THREADS - 1) / QR_THREADS;
     unsigned char* base = static_cast<unsigned char*>(aux);
     Best* best = reinterpret_cast<Best*>(base);
-    unsigned char* chosen = base + align256(sizeof(Best) * nblocks);
+    unsigned char* chosen = base + align256(sizeof(Best) * nblocks_cap(ncol));
     T* q = reinterpret_cast<T*>(chosen + align256((size_t)ncol));
     cudaMemsetAsync(chosen, 0, ncol, s);
+    // persistent cooperative version when the rows fit the per-thread registers
+    int dev = 0, sms = 0, per_sm = 0, coop = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    const int rpt = (nrow + QC_WARPS - 1) / QC_WARPS;
+    const void* fn = rpt <= 8 ? (const void*)qr_persistent_kernel<T, 8>
+                   : rpt <= 16 ? (const void*)qr_persistent_kernel<T, 16>
+                               : (const void*)qr_persistent_kernel<T, 32>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, QC_THREADS, 0);
+    const int ntiles = (ncol + 31) / 32;
+    const int gridn = std::min(ntiles, sms * per_sm);
+    if (coop && per_sm > 0 && rpt <= QC_RPT && 2 * gridn <= nblocks_cap(ncol)) {
+        Best* bb = best;
+        void* args[] = {(void*)&nrow, (void*)&ncol, (void*)&R, (void*)&npiv, (void*)&bb, (void*)&chosen,
+                        (void*)&d_piv};
+        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(gridn), dim3(QC_THREADS), args, 0, s);
+        *launches += 1;
+        return e;
+    }
     for (int step = 0; step < npiv; ++step) {
         qr_update_kernel<T><<<nblocks, QR_THREADS, 0, s>>>(nrow, ncol, R, (size_t)ncol, q, step > 0, chosen, best);
         qr_select_kernel<T><<<1, QR_THREADS, 0, s>>>(nrow, nblocks, R, (size_t)ncol, best, chosen, q, d_piv, step);

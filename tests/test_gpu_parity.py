@@ -266,3 +266,29 @@ def test_linearly_dependent_orbitals_are_rejected():
         ctx.load_orbitals(phi, 3, 0, True)
     assert e.value.status == 5
     ctx.close()
+
+
+# ------------------------------------------------------------------ size-specialised FP32 kernels
+
+
+@pytest.mark.parametrize("n", [48, 64, 72, 96, 128])
+def test_specialised_sizes_match_oracle(n):
+    # cubic grids with n % 4 == 0 run the compile-time-specialised passes in FP32
+    sysm = synth.small_localized_system(21 + n, (12.0, 12.0, 12.0), (n, n, n), 10.0, 3, 3)
+    g, occ, _ = oracle_orbitals(sysm)
+    W_ref, ex_ref, _ = O.apply_exchange(g, occ, None, np.ones((3, 3), dtype=bool))
+    with make_ctx(sysm, LACE_MIXED) as ctx:
+        W, ex = ctx.apply_exchange()
+    assert abs(ex - ex_ref) <= EX_TOL[LACE_MIXED]
+    assert relerr(W, W_ref) < REL_TOL[LACE_MIXED]
+
+
+def test_specialised_and_generic_fp32_passes_agree(small_loc, monkeypatch):
+    with make_ctx(small_loc, LACE_MIXED) as ctx:
+        ctx.localize(2)
+        ctx.screen(1e-3)
+        W_spec, ex_spec = ctx.apply_exchange()
+        monkeypatch.setenv("LACE_GENERIC_FFT", "1")
+        W_gen, ex_gen = ctx.apply_exchange()
+    assert abs(ex_spec - ex_gen) <= 1e-6
+    assert relerr(W_spec, W_gen) < 1e-5
