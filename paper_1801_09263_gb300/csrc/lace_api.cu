@@ -8,6 +8,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/lace.h"
@@ -382,6 +383,41 @@ lace_status make_pairs(lace_ctx* c, bool use_S, double thr, Launch& L) {
     long long np = 0;
     CK(build_pair_list(n, ne, c->m(MS_S), thr, use_S, c->pairs.as<int2>(), c->counts.as<int>(), &np, c->stream, &L.n),
        "pair list");
+    // Localised orbitals: order the pairs by the Z-order rank of their orbitals'
+    // SCDM points, so consecutive FFT grids touch nearby orbitals and their W
+    // and Psi planes stay in L2.  Each pair keeps (i, j) with i <= j.
+    const char* noord = getenv("LACE_NO_PAIR_ORDER");
+    if (c->localized && np > 1 && (int)c->pivots_host.size() == n && !(noord && noord[0] == '1')) {
+        std::vector<int2> hp(np);
+        CK(cudaMemcpyAsync(hp.data(), c->pairs.p, sizeof(int2) * np, cudaMemcpyDeviceToHost, c->stream), "pairs");
+        CK(cudaStreamSynchronize(c->stream), "pairs");
+        auto spread = [](uint64_t v) {  // interleave 21 bits with two zero bits
+            v &= 0x1fffff;
+            v = (v | v << 32) & 0x1f00000000ffffULL;
+            v = (v | v << 16) & 0x1f0000ff0000ffULL;
+            v = (v | v << 8) & 0x100f00f00f00f00fULL;
+            v = (v | v << 4) & 0x10c30c30c30c30c3ULL;
+            v = (v | v << 2) & 0x1249249249249249ULL;
+            return v;
+        };
+        std::vector<std::pair<uint64_t, int>> code(n);
+        for (int i = 0; i < n; ++i) {
+            const long long p = c->pivots_host[i];
+            const uint64_t z = p % c->g.n[2], y = (p / c->g.n[2]) % c->g.n[1], x = p / ((long long)c->g.n[2] * c->g.n[1]);
+            code[i] = {spread(x) << 2 | spread(y) << 1 | spread(z), i};
+        }
+        std::sort(code.begin(), code.end());
+        std::vector<int> rank(n + ne);
+        for (int r = 0; r < n; ++r) rank[code[r].second] = r;
+        for (int e = 0; e < ne; ++e) rank[n + e] = n + e;
+        std::stable_sort(hp.begin(), hp.end(), [&](const int2& a, const int2& b) {
+            const int a0 = std::min(rank[a.x], rank[a.y]), a1 = std::max(rank[a.x], rank[a.y]);
+            const int b0 = std::min(rank[b.x], rank[b.y]), b1 = std::max(rank[b.x], rank[b.y]);
+            return a0 != b0 ? a0 < b0 : a1 < b1;
+        });
+        CK(cudaMemcpyAsync(c->pairs.p, hp.data(), sizeof(int2) * np, cudaMemcpyHostToDevice, c->stream), "pairs");
+        CK(cudaStreamSynchronize(c->stream), "pairs");
+    }
     CK(pack_pair_grids(c->pairs.as<int2>(), np, c->grids.as<PairGrid>(), c->stream, &L.n), "pack pairs");
     c->n_pairs = np;
     return LACE_OK;
@@ -390,7 +426,7 @@ lace_status make_pairs(lace_ctx* c, bool use_S, double thr, Launch& L) {
 int batch_for(lace_ctx* c) {
     const size_t per = c->g.ng * 2 * elem_bytes(c);
     const char* envb = getenv("LACE_BATCH");
-    long long b = envb ? atoll(envb) : (long long)((96ull << 20) / per);
+    long long b = envb ? atoll(envb) : (long long)((192ull << 20) / per);
     b = std::max<long long>(4, std::min<long long>(b, 1024));
     return (int)b;
 }
@@ -422,6 +458,30 @@ lace_status apply_impl(lace_ctx* c) {
 }
 
 // ------------------------------------------------------------------ ACE
+// Dense contraction over the grid for the ACE matrices: tcgen05 3xBF16 on the
+// mixed path (LACE_NO_TC=1 selects the CUDA-core FP32 kernel), FP64 otherwise.
+template <typename T>
+lace_status ace_contract(lace_ctx* c, int M, int N, const T* A, const T* B, double alpha, double* C, Launch& L) {
+    const size_t ng = c->g.ng;
+    if constexpr (std::is_same<T, float>::value) {
+        const char* notc = getenv("LACE_NO_TC");
+        if (!(notc && notc[0] == '1')) {
+            CK(c->work.ensure(std::max(c->work.bytes, tc_gram_work_elems(M, N, ng) * sizeof(double))), "alloc work");
+            int herr = 0;
+            CK(tc_gram(M, N, ng, A, ng, B, ng, alpha, C, N, c->work.as<double>(), c->work.bytes / sizeof(double),
+                       c->flag.as<int>(), &herr, c->stream, &L.n),
+               "tensor-core contraction");
+            if (herr) return fail(c, LACE_ERR_TIMEOUT, "tensor-core contraction: an mbarrier wait timed out");
+            return LACE_OK;
+        }
+    }
+    CK(c->work.ensure(std::max(c->work.bytes, gemm_rows_work_elems(M, N, ng) * sizeof(double))), "alloc work");
+    CK(gemm_rows<T>(M, N, ng, A, ng, B, ng, alpha, false, C, N, c->work.as<double>(), c->work.bytes / sizeof(double),
+                    c->stream, &L.n),
+       "contraction");
+    return LACE_OK;
+}
+
 template <typename T>
 lace_status build_ace_impl(lace_ctx* c, int sym) {
     Launch L{c};
@@ -432,9 +492,10 @@ lace_status build_ace_impl(lace_ctx* c, int sym) {
     double* A = c->m(MS_MSYM);
     double* Linv = c->m(MS_LINV);
     double* LinvT = c->m(MS_LINVT);
-    CK(gemm_rows<T>(n, n, ng, c->psi.as<T>(), ng, c->W.as<T>(), ng, c->g.dv, false, M, n, c->work.as<double>(),
-                    c->work.bytes / sizeof(double), c->stream, &L.n),
-       "exchange matrix");
+    {
+        lace_status st = ace_contract<T>(c, n, n, c->psi.as<T>(), c->W.as<T>(), c->g.dv, M, L);
+        if (st) return st;
+    }
     CK(symmetrize(n, M, A, sym, true, c->stream, &L.n), "symmetrize");
     int ok = 0;
     CK(cholesky_lower(n, A, n, c->flag.as<int>(), &ok, c->stream, &L.n), "cholesky");
@@ -465,10 +526,10 @@ lace_status apply_ace_impl(lace_ctx* c, const double* d_psi64, int nf, double* d
     }
     double* X = c->m(MS_A);
     if ((size_t)n * nf > c->mslot) return fail(c, LACE_ERR_ARG, "too many functions in one ACE apply");
-    CK(c->work.ensure(gemm_rows_work_elems(n, nf, ng) * sizeof(double)), "alloc work");
-    CK(gemm_rows<T>(n, nf, ng, c->xi.as<T>(), ng, in, ng, -c->g.dv, false, X, nf, c->work.as<double>(),
-                    c->work.bytes / sizeof(double), c->stream, &L.n),
-       "ace project");
+    {
+        lace_status st = ace_contract<T>(c, n, nf, c->xi.as<T>(), in, -c->g.dv, X, L);
+        if (st) return st;
+    }
     T* dst = sizeof(T) == 8 ? reinterpret_cast<T*>(d_out64) : out;
     CK(gemm_combine<T>(nf, ng, n, c->xi.as<T>(), ng, X, nf, 0.0, dst, ng, c->stream, &L.n), "ace combine");
     if (sizeof(T) != 8) CK(convert<T, double>(out, d_out64, (size_t)nf * ng, c->stream, &L.n), "convert out");

@@ -82,6 +82,14 @@ template <typename T>
 cudaError_t gemm_combine(int N, size_t K, int Kc, const T* A, size_t lda, const double* Coef, int ldcoef, double beta,
                          T* Out, size_t ldo, cudaStream_t s, int* launches);
 
+// Tensor-core (tcgen05) 3xBF16 contraction C = alpha * sum_r A[m][r] B[n][r]
+// (FP32 operands, rows 16-byte aligned); h_err (nullable) receives 1 if a
+// bounded mbarrier wait gave up (the call then synchronises s).
+cudaError_t tc_gram(int M, int N, size_t K, const float* A, size_t lda, const float* B, size_t ldb, double alpha,
+                    double* C, int ldc, double* work, size_t work_elems, int* d_err, int* h_err, cudaStream_t s,
+                    int* launches);
+size_t tc_gram_work_elems(int M, int N, size_t K);
+
 // Small FP64 dense kernels (N x N).
 cudaError_t small_gemm_f64(int M, int N, int K, const double* A, int lda, bool ta, const double* B, int ldb, bool tb,
                            double alpha, double beta, double* C, int ldc, cudaStream_t s, int* launches);

@@ -28,9 +28,11 @@ template <typename T> __device__ __forceinline__ T opv(T x, bool a) { return a ?
 template <typename T>
 __global__ void __launch_bounds__(GR_THREADS) gemm_rows_kernel(int M, int N, size_t K, const T* __restrict__ A,
                                                                 size_t lda, const T* __restrict__ B, size_t ldb,
-                                                                bool absval, size_t kchunk, double* __restrict__ work) {
+                                                                bool absval, bool sym, size_t kchunk,
+                                                                double* __restrict__ work) {
     __shared__ T As[GR_BK][GR_BM + 1];
     __shared__ T Bs[GR_BK][GR_BN + 1];
+    if (sym && blockIdx.y < blockIdx.x) return;  // symmetric: upper tiles only
     const int m0 = blockIdx.x * GR_BM, n0 = blockIdx.y * GR_BN;
     const size_t k_begin = (size_t)blockIdx.z * kchunk;
     const size_t k_end = min(K, k_begin + kchunk);
@@ -108,12 +110,14 @@ __global__ void __launch_bounds__(GR_THREADS) gemm_rows_kernel(int M, int N, siz
 }
 
 __global__ void reduce_chunks_kernel(int M, int N, int nchunk, const double* __restrict__ work, double alpha,
-                                     double* __restrict__ C, int ldc) {
+                                     bool sym, double* __restrict__ C, int ldc) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)M * N) return;
-    double s = 0.0;
-    for (int c = 0; c < nchunk; ++c) s += work[(size_t)c * M * N + idx];
     const int m = (int)(idx / N), n = (int)(idx % N);
+    // symmetric products computed only the tiles above the diagonal: mirror the rest
+    const size_t src = (sym && n / GR_BN < m / GR_BM) ? (size_t)n * N + m : idx;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += work[(size_t)c * M * N + src];
     C[(size_t)m * ldc + n] = alpha * s;
 }
 
@@ -462,9 +466,11 @@ cudaError_t gemm_rows(int M, int N, size_t K, const T* A, size_t lda, const T* B
     kchunk = (kchunk + GR_BK - 1) / GR_BK * GR_BK;
     const size_t nch_eff = (K + kchunk - 1) / kchunk;
     dim3 grid((M + GR_BM - 1) / GR_BM, (N + GR_BN - 1) / GR_BN, (unsigned)nch_eff);
-    gemm_rows_kernel<T><<<grid, GR_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, absval, kchunk, work);
+    const bool sym = (A == B) && (lda == ldb) && (M == N);
+    gemm_rows_kernel<T><<<grid, GR_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, absval, sym, kchunk, work);
     const size_t tot = (size_t)M * N;
-    reduce_chunks_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, N, (int)nch_eff, work, alpha, C, ldc);
+    reduce_chunks_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, N, (int)nch_eff, work, alpha, sym, C,
+                                                                       ldc);
     *launches += 2;
     return cudaGetLastError();
 }

@@ -130,10 +130,11 @@ __global__ void __launch_bounds__(threads_for(N)) spec_pass_a(ConvArgs<float> P,
     const float4* a2 = reinterpret_cast<const float4*>(P.psi + (size_t)(two ? d.i2 : d.i1) * P.ng + off);
     const float4* b2 = reinterpret_cast<const float4*>(P.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off);
     float4* pl4 = reinterpret_cast<float4*>(plane);
+    const bool same_i = two && d.i1 == d.i2;
     for (int e = threadIdx.x; e < NP / 4; e += NT) {
         const float4 x1 = __ldg(a1 + e), y1 = __ldg(b1 + e);
         float4 x2 = make_float4(0.f, 0.f, 0.f, 0.f), y2 = x2;
-        if (two) { x2 = __ldg(a2 + e); y2 = __ldg(b2 + e); }
+        if (two) { x2 = same_i ? x1 : __ldg(a2 + e); y2 = __ldg(b2 + e); }
         pl4[2 * e] = make_float4(x1.x * y1.x, x2.x * y2.x, x1.y * y1.y, x2.y * y2.y);
         pl4[2 * e + 1] = make_float4(x1.z * y1.z, x2.z * y2.z, x1.w * y1.w, x2.w * y2.w);
     }
@@ -221,18 +222,27 @@ __global__ void __launch_bounds__(threads_for(N)) spec_pass_c(ConvArgs<float> P,
     const float4* pj2 = reinterpret_cast<const float4*>(P.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off);
     float4* Wj2 = reinterpret_cast<float4*>(P.W + (size_t)(two ? d.j2 : d.j1) * P.ng + off);
     float4* Wi2 = reinterpret_cast<float4*>(P.W + (size_t)(two ? d.i2 : d.i1) * P.ng + off);
+    // both slots symmetric with the same occupied i: one reduction into W_i
+    const bool merge_i = two && a_sym && b_sym && d.i1 == d.i2;
     float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
     for (int e = threadIdx.x; e < NP / 4; e += NT) {
         const float4 v01 = pl4[2 * e], v23 = pl4[2 * e + 1];  // (re0, im0, re1, im1), (re2, im2, re3, im3)
         const float4 x1 = __ldg(wi1 + e), y1 = __ldg(pj1 + e);
         atomicAdd(Wj1 + e, make_float4(-x1.x * v01.x, -x1.y * v01.z, -x1.z * v23.x, -x1.w * v23.z));
-        if (a_sym) atomicAdd(Wi1 + e, make_float4(-y1.x * v01.x, -y1.y * v01.z, -y1.z * v23.x, -y1.w * v23.z));
+        float4 wi_acc = make_float4(-y1.x * v01.x, -y1.y * v01.z, -y1.z * v23.x, -y1.w * v23.z);
+        if (a_sym && !merge_i) atomicAdd(Wi1 + e, wi_acc);
         if (a_occ)
             kahan(sa, ca, x1.x * y1.x * v01.x + x1.y * y1.y * v01.z + x1.z * y1.z * v23.x + x1.w * y1.w * v23.z);
         if (two) {
-            const float4 x2 = __ldg(wi2 + e), y2 = __ldg(pj2 + e);
+            const float4 x2 = merge_i ? x1 : __ldg(wi2 + e);
+            const float4 y2 = __ldg(pj2 + e);
             atomicAdd(Wj2 + e, make_float4(-x2.x * v01.y, -x2.y * v01.w, -x2.z * v23.y, -x2.w * v23.w));
-            if (b_sym) atomicAdd(Wi2 + e, make_float4(-y2.x * v01.y, -y2.y * v01.w, -y2.z * v23.y, -y2.w * v23.w));
+            const float4 w2 = make_float4(-y2.x * v01.y, -y2.y * v01.w, -y2.z * v23.y, -y2.w * v23.w);
+            if (merge_i) {
+                atomicAdd(Wi1 + e, make_float4(wi_acc.x + w2.x, wi_acc.y + w2.y, wi_acc.z + w2.z, wi_acc.w + w2.w));
+            } else if (b_sym) {
+                atomicAdd(Wi2 + e, w2);
+            }
             if (b_occ)
                 kahan(sb, cb, x2.x * y2.x * v01.y + x2.y * y2.y * v01.w + x2.z * y2.z * v23.y + x2.w * y2.w * v23.w);
         }

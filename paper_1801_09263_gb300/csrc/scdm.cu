@@ -122,126 +122,133 @@ __global__ void __launch_bounds__(QR_THREADS) qr_select_kernel(int nrow, int nbl
     }
 }
 
-// Persistent pivoted QR: one cooperative launch runs every step.  A CTA of
-// 512 threads (16 warps) walks tiles of 32 columns; lane = column, warp w
-// holds rows w, w+16, ... (RPT of them) in registers while it forms q.r
-// (reduced across the warps in shared memory), updates r -= q (q.r) and the
-// exact new norm.
-// One grid-wide barrier per step; the block winners are double-buffered by
-// step parity and a chosen column is never written again, so the pivot
-// column can be read by every CTA while the next step already runs.
-constexpr int QC_THREADS = 512, QC_WARPS = 16, QC_RPT = 32;  // rows <= 16 * RPT, RPT <= 32
+// Persistent pivoted QR: one cooperative launch runs every step.  One CTA
+// of 512 threads (16 warps) per SM.  A group of WPT warps owns a 32-column
+// tile (lane = column); warp g of the group holds rows g*RPW .. g*RPW+RPW-1
+// of the tile in registers, so a step loads each element once, forms q.r
+// (partial sums exchanged through shared memory behind a named barrier of
+// the group), updates the registers, stores them and forms the exact new
+// norm.  One grid-wide barrier per step; the block winners are
+// double-buffered by step parity and a chosen column is never written
+// again, so every CTA can read the pivot column while the next step runs.
+constexpr int QC_THREADS = 512, QC_WARPS = 16, QC_MAXROWS = 1024;
 
 __device__ __forceinline__ void best_merge(double& v, int& i, double v2, int i2) {
     if (better(v2, i2, v, i)) { v = v2; i = i2; }
 }
 
-template <typename T, int RPT>
+__device__ __forceinline__ void group_bar(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+template <typename T, int RPW>
 __global__ void __launch_bounds__(QC_THREADS) qr_persistent_kernel(int nrow, int ncol, T* __restrict__ R,
-                                                                   int npiv, Best* __restrict__ block_best,
+                                                                   int npiv, int wpt, Best* __restrict__ block_best,
                                                                    unsigned char* __restrict__ chosen,
                                                                    int* __restrict__ piv) {
     cg::grid_group grid = cg::this_grid();
-    __shared__ T qs[QC_WARPS * QC_RPT];
+    __shared__ T qs[QC_MAXROWS + RPW];
     __shared__ T part[QC_WARPS][32];
-    __shared__ double bv[QC_THREADS];
-    __shared__ int bi[QC_THREADS];
+    __shared__ double gv[QC_WARPS];
+    __shared__ int gi[QC_WARPS];
+    __shared__ double red[QC_WARPS];
     __shared__ int pivot_sh;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ngroups = QC_WARPS / wpt;
+    const int group = warp / wpt, wig = warp % wpt;
     const int ntiles = (ncol + 31) / 32;
-    for (int r = threadIdx.x; r < QC_WARPS * QC_RPT; r += blockDim.x) qs[r] = T(0);
+    const int ggroup = blockIdx.x * ngroups + group, total_groups = gridDim.x * ngroups;
+    const int rbase = wig * RPW;
+    for (int r = threadIdx.x; r < QC_MAXROWS + RPW; r += blockDim.x) qs[r] = T(0);
     __syncthreads();
     for (int step = 0; step < npiv; ++step) {
-        // (a) apply the previous step's q, exact norms, local argmax
         double best = -2.0;
         int bidx = 0x7fffffff;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            const int c = tile * 32 + lane;
-            const bool live = c < ncol && !chosen[c];
-            T v[RPT];
-            T dot = T(0);
+        if (group < ngroups) {
+            for (int tile = ggroup; tile < ntiles; tile += total_groups) {
+                const int c = tile * 32 + lane;
+                const bool live = c < ncol && !chosen[c];
+                T v[RPW];
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const int r = warp + k * QC_WARPS;
-                v[k] = (r < nrow && live) ? R[(size_t)r * ncol + c] : T(0);
-                dot += qs[r] * v[k];
-            }
-            if (step > 0) {
-                part[warp][lane] = dot;
-                __syncthreads();
-                T d = T(0);
+                for (int j = 0; j < RPW; ++j)
+                    v[j] = (live && rbase + j < nrow) ? R[(size_t)(rbase + j) * ncol + c] : T(0);
+                if (step > 0) {
+                    T pd = T(0);
 #pragma unroll
-                for (int w = 0; w < QC_WARPS; ++w) d += part[w][lane];
-                __syncthreads();
-                dot = d;
-            }
-            T nrm = T(0);
+                    for (int j = 0; j < RPW; ++j) pd += qs[rbase + j] * v[j];
+                    part[warp][lane] = pd;
+                    group_bar(1 + group, wpt * 32);
+                    T dot = T(0);
+                    for (int w = 0; w < wpt; ++w) dot += part[group * wpt + w][lane];
+                    group_bar(1 + group, wpt * 32);
 #pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-                const int r = warp + k * QC_WARPS;
-                if (r < nrow) {
-                    if (step > 0) {
-                        v[k] -= qs[r] * dot;
-                        if (live) R[(size_t)r * ncol + c] = v[k];
+                    for (int j = 0; j < RPW; ++j) {
+                        v[j] -= qs[rbase + j] * dot;
+                        if (live && rbase + j < nrow) R[(size_t)(rbase + j) * ncol + c] = v[j];
                     }
-                    nrm += v[k] * v[k];
                 }
-            }
-            part[warp][lane] = nrm;
-            __syncthreads();
-            if (warp == 0) {
-                T tot = T(0);
+                T pn = T(0);
 #pragma unroll
-                for (int w = 0; w < QC_WARPS; ++w) tot += part[w][lane];
-                double cv = live ? (double)tot : (c < ncol ? -1.0 : -2.0);
-                int ci = c < ncol ? c : 0x7fffffff;
-                for (int o = 16; o > 0; o >>= 1) {
-                    const double ov = __shfl_xor_sync(0xffffffffu, cv, o);
-                    const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
-                    best_merge(cv, ci, ov, oi);
+                for (int j = 0; j < RPW; ++j) pn += v[j] * v[j];
+                part[warp][lane] = pn;
+                group_bar(1 + group, wpt * 32);
+                if (wig == 0) {
+                    T tot = T(0);
+                    for (int w = 0; w < wpt; ++w) tot += part[group * wpt + w][lane];
+                    double cv = live ? (double)tot : (c < ncol ? -1.0 : -2.0);
+                    int ci = c < ncol ? c : 0x7fffffff;
+                    for (int o = 16; o > 0; o >>= 1) {
+                        const double ov = __shfl_xor_sync(0xffffffffu, cv, o);
+                        const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
+                        best_merge(cv, ci, ov, oi);
+                    }
+                    best_merge(best, bidx, cv, ci);
                 }
-                best_merge(best, bidx, cv, ci);
+                group_bar(1 + group, wpt * 32);
             }
-            __syncthreads();
         }
-        if (threadIdx.x == 0) block_best[(step & 1) * gridDim.x + blockIdx.x] = Best{best, bidx};
-        grid.sync();
-        // (b) every CTA: global argmax, then q = R[:,p] / ||R[:,p]|| into shared memory
-        double gb = -3.0;
-        int gi = 0x7fffffff;
-        for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-            const Best x = block_best[(step & 1) * gridDim.x + b];
-            best_merge(gb, gi, x.v, x.idx);
-        }
-        bv[threadIdx.x] = gb;
-        bi[threadIdx.x] = gi;
+        if (lane == 0 && wig == 0 && group < ngroups) { gv[group] = best; gi[group] = bidx; }
         __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) {
-                double v2 = bv[threadIdx.x];
-                int i2 = bi[threadIdx.x];
-                best_merge(v2, i2, bv[threadIdx.x + o], bi[threadIdx.x + o]);
-                bv[threadIdx.x] = v2;
-                bi[threadIdx.x] = i2;
-            }
-            __syncthreads();
+        if (threadIdx.x == 0) {
+            double b = gv[0];
+            int bi_ = gi[0];
+            for (int w = 1; w < ngroups; ++w) best_merge(b, bi_, gv[w], gi[w]);
+            block_best[(step & 1) * gridDim.x + blockIdx.x] = Best{b, bi_};
         }
-        if (threadIdx.x == 0) pivot_sh = bi[0];
+        grid.sync();
+        // every CTA: global argmax, then q = R[:,p] / ||R[:,p]|| into shared memory
+        if (warp == 0) {
+            double gb = -3.0;
+            int gbi = 0x7fffffff;
+            for (int b = lane; b < (int)gridDim.x; b += 32) {
+                const Best x = block_best[(step & 1) * gridDim.x + b];
+                best_merge(gb, gbi, x.v, x.idx);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const double ov = __shfl_xor_sync(0xffffffffu, gb, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, gbi, o);
+                best_merge(gb, gbi, ov, oi);
+            }
+            if (lane == 0) pivot_sh = gbi;
+        }
         __syncthreads();
         const int p = pivot_sh;
-        double s2 = 0.0;
-        for (int r = threadIdx.x; r < nrow; r += blockDim.x) {
-            const double x = (double)R[(size_t)r * ncol + p];
-            s2 += x * x;
-        }
-        bv[threadIdx.x] = s2;
+        const T xr = threadIdx.x < nrow ? R[(size_t)threadIdx.x * ncol + p] : T(0);
+        const int r2 = threadIdx.x + QC_THREADS;
+        const T xr2 = r2 < nrow ? R[(size_t)r2 * ncol + p] : T(0);
+        double s2 = (double)xr * (double)xr + (double)xr2 * (double)xr2;
+        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+        if (lane == 0) red[warp] = s2;
         __syncthreads();
-        for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-            if (threadIdx.x < o) bv[threadIdx.x] += bv[threadIdx.x + o];
-            __syncthreads();
+        if (warp == 0) {
+            double t = lane < QC_WARPS ? red[lane] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+            if (lane == 0) red[0] = t;
         }
-        const double inv = bv[0] > 0.0 ? 1.0 / sqrt(bv[0]) : 0.0;
-        for (int r = threadIdx.x; r < nrow; r += blockDim.x) qs[r] = (T)((double)R[(size_t)r * ncol + p] * inv);
+        __syncthreads();
+        const double inv = red[0] > 0.0 ? 1.0 / sqrt(red[0]) : 0.0;
+        if (threadIdx.x < nrow) qs[threadIdx.x] = (T)((double)xr * inv);
+        if (r2 < nrow) qs[r2] = (T)((double)xr2 * inv);
         if (threadIdx.x == 0) {
             chosen[p] = 1;
             if (blockIdx.x == 0) piv[step] = p;
@@ -302,17 +309,16 @@ cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* au
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    const int rpt = (nrow + QC_WARPS - 1) / QC_WARPS;
-    const void* fn = rpt <= 8 ? (const void*)qr_persistent_kernel<T, 8>
-                   : rpt <= 16 ? (const void*)qr_persistent_kernel<T, 16>
-                               : (const void*)qr_persistent_kernel<T, 32>;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, QC_THREADS, 0);
-    const int ntiles = (ncol + 31) / 32;
-    const int gridn = std::min(ntiles, sms * per_sm);
-    if (coop && per_sm > 0 && rpt <= QC_RPT && 2 * gridn <= nblocks_cap(ncol)) {
+    constexpr int RPW = sizeof(T) == 4 ? 64 : 32;  // rows per warp held in registers
+    int wpt = 2;  // >= 2 keeps the named-barrier ids (1 + group) within 1..8
+    while (wpt * RPW < nrow) wpt *= 2;
+    const void* fn = (const void*)qr_persistent_kernel<T, RPW>;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_persistent_kernel<T, RPW>, QC_THREADS, 0);
+    const int gridn = sms * std::min(per_sm, 1);
+    if (coop && per_sm > 0 && wpt <= QC_WARPS && nrow <= QC_MAXROWS && 2 * gridn <= nblocks_cap(ncol)) {
         Best* bb = best;
-        void* args[] = {(void*)&nrow, (void*)&ncol, (void*)&R, (void*)&npiv, (void*)&bb, (void*)&chosen,
-                        (void*)&d_piv};
+        void* args[] = {(void*)&nrow, (void*)&ncol, (void*)&R, (void*)&npiv, (void*)&wpt, (void*)&bb,
+                        (void*)&chosen, (void*)&d_piv};
         cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(gridn), dim3(QC_THREADS), args, 0, s);
         *launches += 1;
         return e;

@@ -1,0 +1,302 @@
+// Tensor-core (tcgen05, sm_103a) split-precision contraction over the grid:
+//   work[chunk][m][n] = sum_{r in chunk} A[m][r] * B[n][r]
+// for the dense ACE contractions (Eq. 3: M = dV Psi^T W; K_ACE psi needs
+// X = dV xi^T psi).  Each FP32 operand is split in registers into BF16
+// hi = bf16(x), lo = bf16(x - hi); the products hi.hi + hi.lo + lo.hi are
+// accumulated in FP32 in tensor memory (the lo.lo term, ~2^-16 relative, is
+// dropped).  Chunks of K are reduced in FP64 by the caller in a fixed order.
+//
+// CTA: 256 threads, one 128 x 128 output tile, one K chunk.  Per 64-wide K
+// step all threads load the FP32 rows (16-byte vectors), split them and
+// store four 128 x 64 BF16 tiles (A_hi, A_lo, B_hi, B_lo) in the 128-byte
+// swizzled K-major layout; thread 0 issues 3 x 4 tcgen05.mma (M128 N128 K16)
+// and commits them to the stage's mbarrier.  Two stages alternate so the
+// loads of one step overlap the MMAs of the previous one.  Every mbarrier
+// wait is bounded; on timeout the CTA records an error and stops issuing.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "lace_internal.cuh"
+
+namespace lace {
+
+namespace {
+
+constexpr int TC_M = 128, TC_N = 128, TC_BK = 64, TC_THREADS = 256;
+constexpr int TC_TILE_BYTES = TC_M * TC_BK * 2;      // 16 KB per BF16 tile
+constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;    // A_hi, A_lo, B_hi, B_lo
+constexpr int TC_SMEM_BYTES = 2 * TC_STAGE_BYTES + 1024;  // + alignment slack
+constexpr long long TC_WAIT_LIMIT = 1LL << 26;       // bounded mbarrier polls
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+// Bounded wait for the completion of the phase with the given parity.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 128-byte swizzled K-major shared-memory descriptor (SBO = 1024 B between
+// 8-row groups, version 1, layout type 2 = SWIZZLE_128B).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset
+    d |= (uint64_t)1 << 46;                  // descriptor version
+    d |= (uint64_t)2 << 61;                  // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M = 128, N = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(TC_N >> 3) << 17) |
+                            ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Byte offset of BF16 element (row r, k) in a 128-byte swizzled K-major tile of 64 columns.
+__device__ __forceinline__ uint32_t sw128_off(int r, int k) {
+    return (uint32_t)(r * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void split4(float4 v, uint2& hi, uint2& lo) {
+    const __nv_bfloat16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
+    const __nv_bfloat16 h2 = __float2bfloat16_rn(v.z), h3 = __float2bfloat16_rn(v.w);
+    const __nv_bfloat16 l0 = __float2bfloat16_rn(v.x - __bfloat162float(h0));
+    const __nv_bfloat16 l1 = __float2bfloat16_rn(v.y - __bfloat162float(h1));
+    const __nv_bfloat16 l2 = __float2bfloat16_rn(v.z - __bfloat162float(h2));
+    const __nv_bfloat16 l3 = __float2bfloat16_rn(v.w - __bfloat162float(h3));
+    hi.x = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
+    hi.y = (uint32_t)__bfloat16_as_ushort(h2) | ((uint32_t)__bfloat16_as_ushort(h3) << 16);
+    lo.x = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
+    lo.y = (uint32_t)__bfloat16_as_ushort(l2) | ((uint32_t)__bfloat16_as_ushort(l3) << 16);
+}
+
+// Load a 128 x 64 FP32 tile (rows row0.., columns k0..) and store its BF16 hi/lo
+// split into the two swizzled tiles.  Rows >= nrows and columns >= kend are zero.
+__device__ __forceinline__ void stage_tile(const float* __restrict__ src, size_t ld, int row0, int nrows, size_t k0,
+                                           size_t kend, unsigned char* hi_tile, unsigned char* lo_tile) {
+    // 128 rows x 16 float4 = 2048 vectors, 8 per thread
+#pragma unroll
+    for (int j = 0; j < (TC_M * TC_BK / 4) / TC_THREADS; ++j) {
+        const int e = threadIdx.x + j * TC_THREADS;
+        const int r = e >> 4, kv = (e & 15) * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int row = row0 + r;
+        const size_t k = k0 + kv;
+        if (row < nrows) {
+            const float* p = src + (size_t)row * ld + k;
+            if (k + 4 <= kend) {
+                v = __ldg(reinterpret_cast<const float4*>(p));
+            } else {
+                if (k + 0 < kend) v.x = p[0];
+                if (k + 1 < kend) v.y = p[1];
+                if (k + 2 < kend) v.z = p[2];
+            }
+        }
+        uint2 h, l;
+        split4(v, h, l);
+        const uint32_t off = sw128_off(r, kv);
+        *reinterpret_cast<uint2*>(hi_tile + off) = h;
+        *reinterpret_cast<uint2*>(lo_tile + off) = l;
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gram_kernel(int M, int N, size_t K, const float* __restrict__ A, size_t lda, const float* __restrict__ B,
+                   size_t ldb, size_t kchunk, double* __restrict__ work, int* __restrict__ err) {
+    extern __shared__ unsigned char tc_smem_raw[];
+    __shared__ uint64_t bars[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * TC_N;
+    const size_t k_begin = (size_t)blockIdx.z * kchunk;
+    const size_t k_end = min(K, k_begin + kchunk);
+    const int nsteps = (int)((k_end - k_begin + TC_BK - 1) / TC_BK);
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        // 128 TMEM columns x 128 lanes of FP32 accumulators
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+
+    uint32_t uses[2] = {0u, 0u};
+    for (int step = 0; step < nsteps; ++step) {
+        const int s = step & 1;
+        unsigned char* st = smem + s * TC_STAGE_BYTES;
+        if (uses[s] > 0) {
+            // the MMAs that read this stage two steps ago must be done
+            if (threadIdx.x == 0 && !mbar_wait(&bars[s], (uses[s] - 1) & 1)) abort_sh = 1;
+            __syncthreads();
+            if (abort_sh) break;
+        }
+        const size_t k0 = k_begin + (size_t)step * TC_BK;
+        stage_tile(A, lda, m0, M, k0, k_end, st, st + TC_TILE_BYTES);
+        stage_tile(B, ldb, n0, N, k0, k_end, st + 2 * TC_TILE_BYTES, st + 3 * TC_TILE_BYTES);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_hi = smem_u32(st), a_lo = a_hi + TC_TILE_BYTES;
+            const uint32_t b_hi = a_hi + 2 * TC_TILE_BYTES, b_lo = a_hi + 3 * TC_TILE_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                const uint32_t ko = kk * 32;  // 16 BF16 = 32 bytes along K inside the swizzle atom
+                const uint32_t first = (step == 0 && kk == 0) ? 0u : 1u;
+                mma_bf16(tmem, sw128_desc(a_hi + ko), sw128_desc(b_hi + ko), first);
+                mma_bf16(tmem, sw128_desc(a_hi + ko), sw128_desc(b_lo + ko), 1u);
+                mma_bf16(tmem, sw128_desc(a_lo + ko), sw128_desc(b_hi + ko), 1u);
+            }
+            mma_commit(&bars[s]);
+        }
+        uses[s] += 1;
+    }
+    // wait for the last MMAs (commits complete in issue order)
+    if (nsteps > 0 && !abort_sh) {
+        const int s = (nsteps - 1) & 1;
+        if (threadIdx.x == 0 && !mbar_wait(&bars[s], (uses[s] - 1) & 1)) abort_sh = 1;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (abort_sh) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+    } else if (warp < 4 && nsteps > 0) {
+        // warp w reads TMEM lanes 32w..32w+31 = output rows m0 + 32w + lane
+        const int row = m0 + warp * 32 + (threadIdx.x & 31);
+        double* out = work + (size_t)blockIdx.z * M * N;
+#pragma unroll 1
+        for (int c0 = 0; c0 < TC_N; c0 += 16) {
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + c0 + j;
+                    if (col < N) out[(size_t)row * N + col] = (double)__uint_as_float(v[j]);
+                }
+            }
+        }
+    } else if (nsteps == 0 && warp < 4) {
+        const int row = m0 + warp * 32 + (threadIdx.x & 31);
+        double* out = work + (size_t)blockIdx.z * M * N;
+        if (row < M)
+            for (int j = 0; j < TC_N; ++j)
+                if (n0 + j < N) out[(size_t)row * N + n0 + j] = 0.0;
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+    }
+}
+
+__global__ void tc_reduce_kernel(int M, int N, int nchunk, const double* __restrict__ work, double alpha,
+                                 double* __restrict__ C, int ldc) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (size_t)M * N) return;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += work[(size_t)c * M * N + idx];
+    const int m = (int)(idx / N), n = (int)(idx % N);
+    C[(size_t)m * ldc + n] = alpha * s;
+}
+
+}  // namespace
+
+size_t tc_gram_work_elems(int M, int N, size_t K) {
+    const size_t tiles = (size_t)((M + TC_M - 1) / TC_M) * ((N + TC_N - 1) / TC_N);
+    size_t want = (152 + tiles - 1) / tiles;
+    const size_t maxc = (K + 4095) / 4096;
+    want = std::max<size_t>(1, std::min(want, maxc));
+    return want * (size_t)M * N;
+}
+
+cudaError_t tc_gram(int M, int N, size_t K, const float* A, size_t lda, const float* B, size_t ldb, double alpha,
+                    double* C, int ldc, double* work, size_t work_elems, int* d_err, int* h_err, cudaStream_t s,
+                    int* launches) {
+    if (M <= 0 || N <= 0) return cudaSuccess;
+    // 16-byte row alignment for the vector loads
+    if ((lda % 4) || (ldb % 4) || ((uintptr_t)A % 16) || ((uintptr_t)B % 16)) return cudaErrorInvalidValue;
+    const size_t tiles = (size_t)((M + TC_M - 1) / TC_M) * ((N + TC_N - 1) / TC_N);
+    const size_t nch = tc_gram_work_elems(M, N, K) / ((size_t)M * N);
+    if (nch * (size_t)M * N > work_elems) return cudaErrorInvalidValue;
+    size_t kchunk = (K + nch - 1) / nch;
+    kchunk = (kchunk + TC_BK - 1) / TC_BK * TC_BK;
+    const size_t nch_eff = (K + kchunk - 1) / kchunk;
+    static unsigned long long attr_done = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !(attr_done & (1ull << dev))) {
+        cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+        if (e) return e;
+        attr_done |= 1ull << dev;
+    }
+    cudaMemsetAsync(d_err, 0, sizeof(int), s);
+    dim3 grid((M + TC_M - 1) / TC_M, (N + TC_N - 1) / TC_N, (unsigned)nch_eff);
+    tc_gram_kernel<<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(M, N, K, A, lda, B, ldb, kchunk, work, d_err);
+    const size_t tot = (size_t)M * N;
+    tc_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, N, (int)nch_eff, work, alpha, C, ldc);
+    *launches += 2;
+    (void)tiles;
+    if (h_err) {
+        cudaMemcpyAsync(h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e) return e;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace lace

@@ -292,3 +292,21 @@ def test_specialised_and_generic_fp32_passes_agree(small_loc, monkeypatch):
         W_gen, ex_gen = ctx.apply_exchange()
     assert abs(ex_spec - ex_gen) <= 1e-6
     assert relerr(W_spec, W_gen) < 1e-5
+
+
+def test_tensor_core_ace_contraction_matches_fp32_cuda_cores(small_loc, monkeypatch):
+    # mixed path: M = dV Psi^T W on tcgen05 (3xBF16 products, FP32 accumulate) vs the FP32 CUDA-core kernel
+    mats = {}
+    for notc in ("0", "1"):
+        monkeypatch.setenv("LACE_NO_TC", notc)
+        with make_ctx(small_loc, LACE_MIXED) as ctx:
+            ctx.localize(2)
+            ctx.screen(1e-3)
+            ctx.apply_exchange(want_W=False)
+            ctx.build_ace()
+            probe = np.random.default_rng(4).standard_normal((2,) + small_loc.shape)
+            mats[notc] = (ctx.get_matrix(B.MAT_EXCHANGE), ctx.apply_ace(probe))
+    m_tc, k_tc = mats["0"]
+    m_cc, k_cc = mats["1"]
+    assert relerr(m_tc, m_cc) < 2e-5
+    assert relerr(k_tc, k_cc) < 5e-5
