@@ -426,7 +426,7 @@ lace_status make_pairs(lace_ctx* c, bool use_S, double thr, Launch& L) {
 int batch_for(lace_ctx* c) {
     const size_t per = c->g.ng * 2 * elem_bytes(c);
     const char* envb = getenv("LACE_BATCH");
-    long long b = envb ? atoll(envb) : (long long)((192ull << 20) / per);
+    long long b = envb ? atoll(envb) : (long long)((768ull << 20) / per);
     b = std::max<long long>(4, std::min<long long>(b, 1024));
     return (int)b;
 }
@@ -482,6 +482,27 @@ lace_status ace_contract(lace_ctx* c, int M, int N, const T* A, const T* B, doub
     return LACE_OK;
 }
 
+// Out[n] = sum_k Coef[k][n] A[k] over the grid for the ACE vectors: tcgen05
+// 3xBF16 on the mixed path (LACE_NO_TC=1: CUDA-core FP32), FP64 otherwise.
+template <typename T>
+lace_status ace_combine(lace_ctx* c, int N, int Kc, const T* A, const double* Coef, T* Out, Launch& L) {
+    const size_t ng = c->g.ng;
+    if constexpr (std::is_same<T, float>::value) {
+        const char* notc = getenv("LACE_NO_TC");
+        if (!(notc && notc[0] == '1')) {
+            CK(c->work.ensure(std::max(c->work.bytes, tc_combine_scratch_bytes(N, Kc))), "alloc work");
+            int herr = 0;
+            CK(tc_combine(N, ng, Kc, A, ng, Coef, N, 0.0, Out, ng, c->work.p, c->flag.as<int>(), &herr, c->stream,
+                          &L.n),
+               "tensor-core combination");
+            if (herr) return fail(c, LACE_ERR_TIMEOUT, "tensor-core combination: an mbarrier wait timed out");
+            return LACE_OK;
+        }
+    }
+    CK(gemm_combine<T>(N, ng, Kc, A, ng, Coef, N, 0.0, Out, ng, c->stream, &L.n), "combination");
+    return LACE_OK;
+}
+
 template <typename T>
 lace_status build_ace_impl(lace_ctx* c, int sym) {
     Launch L{c};
@@ -504,7 +525,10 @@ lace_status build_ace_impl(lace_ctx* c, int sym) {
     CK(trtri_lower(n, A, n, Linv, n, c->stream, &L.n), "trtri");
     CK(transpose_f64(n, Linv, LinvT, c->stream, &L.n), "transpose");
     // xi_k = sum_j W_j (L^{-T})_{jk} = sum_j W_j Linv[k][j]: Coef[j][k] = LinvT[j][k]
-    CK(gemm_combine<T>(n, ng, n, c->W.as<T>(), ng, LinvT, n, 0.0, c->xi.as<T>(), ng, c->stream, &L.n), "xi");
+    {
+        lace_status st = ace_combine<T>(c, n, n, c->W.as<T>(), LinvT, c->xi.as<T>(), L);
+        if (st) return st;
+    }
     return LACE_OK;
 }
 
@@ -531,7 +555,10 @@ lace_status apply_ace_impl(lace_ctx* c, const double* d_psi64, int nf, double* d
         if (st) return st;
     }
     T* dst = sizeof(T) == 8 ? reinterpret_cast<T*>(d_out64) : out;
-    CK(gemm_combine<T>(nf, ng, n, c->xi.as<T>(), ng, X, nf, 0.0, dst, ng, c->stream, &L.n), "ace combine");
+    {
+        lace_status st = ace_combine<T>(c, nf, n, c->xi.as<T>(), X, dst, L);
+        if (st) return st;
+    }
     if (sizeof(T) != 8) CK(convert<T, double>(out, d_out64, (size_t)nf * ng, c->stream, &L.n), "convert out");
     return LACE_OK;
 }

@@ -89,6 +89,12 @@ cudaError_t tc_gram(int M, int N, size_t K, const float* A, size_t lda, const fl
                     double* C, int ldc, double* work, size_t work_elems, int* d_err, int* h_err, cudaStream_t s,
                     int* launches);
 size_t tc_gram_work_elems(int M, int N, size_t K);
+// Tensor-core combination Out[n][r] = beta Out + sum_k Coef[k][n] A[k][r]
+// (FP32 A and Out, FP64 Coef, split 3xBF16); scratch of tc_combine_scratch_bytes.
+cudaError_t tc_combine(int N, size_t K, int Kc, const float* A, size_t lda, const double* Coef, int ldcoef,
+                       double beta, float* Out, size_t ldo, void* scratch, int* d_err, int* h_err, cudaStream_t s,
+                       int* launches);
+size_t tc_combine_scratch_bytes(int N, int Kc);
 
 // Small FP64 dense kernels (N x N).
 cudaError_t small_gemm_f64(int M, int N, int K, const double* A, int lda, bool ta, const double* B, int ldb, bool tb,

@@ -6,8 +6,9 @@
 // accumulated in FP32 in tensor memory (the lo.lo term, ~2^-16 relative, is
 // dropped).  Chunks of K are reduced in FP64 by the caller in a fixed order.
 //
-// CTA: 256 threads, one 128 x 128 output tile, one K chunk.  Per 64-wide K
-// step all threads load the FP32 rows (16-byte vectors), split them and
+// CTA: 512 threads, one 128 x 128 output tile, one K chunk.  Per 64-wide K
+// step all threads load the FP32 rows (16-byte vectors, one step ahead in
+// registers), split them and
 // store four 128 x 64 BF16 tiles (A_hi, A_lo, B_hi, B_lo) in the 128-byte
 // swizzled K-major layout; thread 0 issues 3 x 4 tcgen05.mma (M128 N128 K16)
 // and commits them to the stage's mbarrier.  Two stages alternate so the
@@ -25,7 +26,8 @@ namespace lace {
 
 namespace {
 
-constexpr int TC_M = 128, TC_N = 128, TC_BK = 64, TC_THREADS = 256;
+constexpr int TC_M = 128, TC_N = 128, TC_BK = 64, TC_THREADS = 512;
+constexpr int TC_VPT = (TC_M * TC_BK / 4) / TC_THREADS;  // float4 vectors per thread per tile
 constexpr int TC_TILE_BYTES = TC_M * TC_BK * 2;      // 16 KB per BF16 tile
 constexpr int TC_STAGE_BYTES = 4 * TC_TILE_BYTES;    // A_hi, A_lo, B_hi, B_lo
 constexpr int TC_SMEM_BYTES = 2 * TC_STAGE_BYTES + 1024;  // + alignment slack
@@ -103,30 +105,39 @@ __device__ __forceinline__ void split4(float4 v, uint2& hi, uint2& lo) {
     lo.y = (uint32_t)__bfloat16_as_ushort(l2) | ((uint32_t)__bfloat16_as_ushort(l3) << 16);
 }
 
-// Load a 128 x 64 FP32 tile (rows row0.., columns k0..) and store its BF16 hi/lo
-// split into the two swizzled tiles.  Rows >= nrows and columns >= kend are zero.
-__device__ __forceinline__ void stage_tile(const float* __restrict__ src, size_t ld, int row0, int nrows, size_t k0,
-                                           size_t kend, unsigned char* hi_tile, unsigned char* lo_tile) {
-    // 128 rows x 16 float4 = 2048 vectors, 8 per thread
+// Load this thread's share of a 128 x 64 FP32 tile (rows row0.., columns
+// k0..) into registers.  Rows >= nrows and columns >= kend read as zero.
+__device__ __forceinline__ void load_tile(const float* __restrict__ src, size_t ld, int row0, int nrows, size_t k0,
+                                          size_t kend, float4* v) {
 #pragma unroll
-    for (int j = 0; j < (TC_M * TC_BK / 4) / TC_THREADS; ++j) {
+    for (int j = 0; j < TC_VPT; ++j) {
         const int e = threadIdx.x + j * TC_THREADS;
         const int r = e >> 4, kv = (e & 15) * 4;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
         const int row = row0 + r;
         const size_t k = k0 + kv;
-        if (row < nrows) {
+        if (row < nrows && k < kend) {
             const float* p = src + (size_t)row * ld + k;
             if (k + 4 <= kend) {
-                v = __ldg(reinterpret_cast<const float4*>(p));
+                x = __ldg(reinterpret_cast<const float4*>(p));
             } else {
-                if (k + 0 < kend) v.x = p[0];
-                if (k + 1 < kend) v.y = p[1];
-                if (k + 2 < kend) v.z = p[2];
+                x.x = p[0];
+                if (k + 1 < kend) x.y = p[1];
+                if (k + 2 < kend) x.z = p[2];
             }
         }
+        v[j] = x;
+    }
+}
+
+// Split the registers into BF16 hi/lo and store them in the swizzled tiles.
+__device__ __forceinline__ void store_tile(const float4* v, unsigned char* hi_tile, unsigned char* lo_tile) {
+#pragma unroll
+    for (int j = 0; j < TC_VPT; ++j) {
+        const int e = threadIdx.x + j * TC_THREADS;
+        const int r = e >> 4, kv = (e & 15) * 4;
         uint2 h, l;
-        split4(v, h, l);
+        split4(v[j], h, l);
         const uint32_t off = sw128_off(r, kv);
         *reinterpret_cast<uint2*>(hi_tile + off) = h;
         *reinterpret_cast<uint2*>(lo_tile + off) = l;
@@ -167,6 +178,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     const uint32_t tmem = tmem_base_sh;
 
     uint32_t uses[2] = {0u, 0u};
+    // one step of register prefetch: the rows of step t+1 are in flight while
+    // step t is split, stored and handed to the tensor cores
+    float4 va[TC_VPT], vb[TC_VPT];
+    if (nsteps > 0) {
+        load_tile(A, lda, m0, M, k_begin, k_end, va);
+        load_tile(B, ldb, n0, N, k_begin, k_end, vb);
+    }
     for (int step = 0; step < nsteps; ++step) {
         const int s = step & 1;
         unsigned char* st = smem + s * TC_STAGE_BYTES;
@@ -176,9 +194,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             __syncthreads();
             if (abort_sh) break;
         }
-        const size_t k0 = k_begin + (size_t)step * TC_BK;
-        stage_tile(A, lda, m0, M, k0, k_end, st, st + TC_TILE_BYTES);
-        stage_tile(B, ldb, n0, N, k0, k_end, st + 2 * TC_TILE_BYTES, st + 3 * TC_TILE_BYTES);
+        store_tile(va, st, st + TC_TILE_BYTES);
+        store_tile(vb, st + 2 * TC_TILE_BYTES, st + 3 * TC_TILE_BYTES);
+        if (step + 1 < nsteps) {
+            const size_t k1 = k_begin + (size_t)(step + 1) * TC_BK;
+            load_tile(A, lda, m0, M, k1, k_end, va);
+            load_tile(B, ldb, n0, N, k1, k_end, vb);
+        }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
         if (threadIdx.x == 0) {
@@ -254,7 +276,219 @@ __global__ void tc_reduce_kernel(int M, int N, int nchunk, const double* __restr
     C[(size_t)m * ldc + n] = alpha * s;
 }
 
+// ---------------------------------------------------------------------------
+// Combination over orbitals: Out[n][r] = beta Out[n][r] + sum_k Coef[k][n] A[k][r]
+// (xi = W L^{-T}; K_ACE psi = -xi X).  As an MMA: D[r][n] = sum_k A^T[r][k]
+// Coef[k][n], M = 128 grid points per CTA, N = 256 target orbitals, K = the
+// orbitals being combined (64 per step).  The A tile is transposed while it is
+// staged (each thread loads 4 consecutive k of one r and stores one 8-byte
+// chunk of the K-major row r); Coef is pre-split into BF16 hi/lo rows
+// CoefT[n][k] once per call.
+constexpr int CB_N = 256;
+constexpr int CB_A_BYTES = TC_M * TC_BK * 2;   // 16 KB
+constexpr int CB_B_BYTES = CB_N * TC_BK * 2;   // 32 KB
+constexpr int CB_STAGE_BYTES = 2 * CB_A_BYTES + 2 * CB_B_BYTES;
+constexpr int CB_SMEM_BYTES = 2 * CB_STAGE_BYTES + 1024;
+constexpr uint32_t kIdescN256 = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(CB_N >> 3) << 17) |
+                                ((uint32_t)(TC_M >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16_n256(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\n"
+        "setp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(kIdescN256), "r"(accumulate));
+}
+
+// hiT[n][k], loT[n][k] (BF16, rows of kpad, zero padded) from Coef[k][n] (FP64)
+__global__ void coef_split_kernel(int Kc, int N, const double* __restrict__ coef, int ldcoef, int kpad, int npad,
+                                  __nv_bfloat16* __restrict__ hiT, __nv_bfloat16* __restrict__ loT) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= npad * kpad) return;
+    const int n = idx / kpad, k = idx % kpad;
+    const float x = (n < N && k < Kc) ? (float)coef[(size_t)k * ldcoef + n] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    hiT[idx] = h;
+    loT[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_combine_kernel(int N, size_t K, int Kc, int kpad, const float* __restrict__ A, size_t lda,
+                      const __nv_bfloat16* __restrict__ hiT, const __nv_bfloat16* __restrict__ loT, float beta,
+                      float* __restrict__ Out, size_t ldo, int* __restrict__ err) {
+    extern __shared__ unsigned char tc_smem_raw[];
+    __shared__ uint64_t bars[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5;
+    const size_t r0 = (size_t)blockIdx.x * TC_M;
+    const int n0 = blockIdx.y * CB_N;
+    const int nsteps = kpad / TC_BK;
+    if (threadIdx.x == 0) {
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(CB_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+    // this thread stages grid point r = tid % 128 and k-quads q = tid / 128 + 4j
+    const int ar = threadIdx.x & (TC_M - 1), aq = threadIdx.x >> 7;
+    const bool rvalid = r0 + ar < K;
+    uint32_t uses[2] = {0u, 0u};
+    for (int step = 0; step < nsteps; ++step) {
+        const int s = step & 1;
+        unsigned char* st = smem + s * CB_STAGE_BYTES;
+        if (uses[s] > 0) {
+            if (threadIdx.x == 0 && !mbar_wait(&bars[s], (uses[s] - 1) & 1)) abort_sh = 1;
+            __syncthreads();
+            if (abort_sh) break;
+        }
+        const int k0 = step * TC_BK;
+        // A^T tile: 128 r x 64 k, 16 quads of 4 k per row, 4 per thread
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int kq = (aq + 4 * j) * 4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rvalid) {
+                const int k = k0 + kq;
+                const float* p = A + (size_t)k * lda + r0 + ar;
+                if (k + 0 < Kc) v.x = __ldg(p);
+                if (k + 1 < Kc) v.y = __ldg(p + lda);
+                if (k + 2 < Kc) v.z = __ldg(p + 2 * lda);
+                if (k + 3 < Kc) v.w = __ldg(p + 3 * lda);
+            }
+            uint2 h, l;
+            split4(v, h, l);
+            const uint32_t off = sw128_off(ar, kq);
+            *reinterpret_cast<uint2*>(st + off) = h;
+            *reinterpret_cast<uint2*>(st + CB_A_BYTES + off) = l;
+        }
+        // B tiles: rows n0.., 64 k of the pre-split CoefT (16-byte chunks)
+        {
+            unsigned char* bh = st + 2 * CB_A_BYTES;
+            unsigned char* bl = bh + CB_B_BYTES;
+#pragma unroll
+            for (int j = 0; j < (CB_N * 8) / TC_THREADS; ++j) {
+                const int e = threadIdx.x + j * TC_THREADS;
+                const int n = e >> 3, c = e & 7;
+                const size_t g = (size_t)(n0 + n) * kpad + k0 + c * 8;
+                const uint4 hv = *reinterpret_cast<const uint4*>(hiT + g);
+                const uint4 lv = *reinterpret_cast<const uint4*>(loT + g);
+                const uint32_t off = (uint32_t)(n * 128 + (((c ^ (n & 7)) & 7) << 4));
+                *reinterpret_cast<uint4*>(bh + off) = hv;
+                *reinterpret_cast<uint4*>(bl + off) = lv;
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_hi = smem_u32(st), a_lo = a_hi + CB_A_BYTES;
+            const uint32_t b_hi = a_hi + 2 * CB_A_BYTES, b_lo = b_hi + CB_B_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                const uint32_t ko = kk * 32;
+                const uint32_t first = (step == 0 && kk == 0) ? 0u : 1u;
+                mma_bf16_n256(tmem, sw128_desc(a_hi + ko), sw128_desc(b_hi + ko), first);
+                mma_bf16_n256(tmem, sw128_desc(a_hi + ko), sw128_desc(b_lo + ko), 1u);
+                mma_bf16_n256(tmem, sw128_desc(a_lo + ko), sw128_desc(b_hi + ko), 1u);
+            }
+            mma_commit(&bars[s]);
+        }
+        uses[s] += 1;
+    }
+    if (nsteps > 0 && !abort_sh) {
+        const int s = (nsteps - 1) & 1;
+        if (threadIdx.x == 0 && !mbar_wait(&bars[s], (uses[s] - 1) & 1)) abort_sh = 1;
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (abort_sh) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+    } else if (warp < 4) {
+        const size_t r = r0 + warp * 32 + (threadIdx.x & 31);
+#pragma unroll 1
+        for (int c0 = 0; c0 < CB_N; c0 += 16) {
+            if (n0 + c0 >= N) break;
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (r < K) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n < N) {
+                        float* o = Out + (size_t)n * ldo + r;
+                        *o = beta == 0.f ? __uint_as_float(v[j]) : beta * *o + __uint_as_float(v[j]);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CB_N) : "memory");
+    }
+}
+
 }  // namespace
+
+size_t tc_combine_scratch_bytes(int N, int Kc) {
+    const size_t kpad = ((size_t)Kc + TC_BK - 1) / TC_BK * TC_BK;
+    const size_t npad = ((size_t)N + CB_N - 1) / CB_N * CB_N;
+    return 2 * kpad * npad * sizeof(__nv_bfloat16);
+}
+
+cudaError_t tc_combine(int N, size_t K, int Kc, const float* A, size_t lda, const double* Coef, int ldcoef,
+                       double beta, float* Out, size_t ldo, void* scratch, int* d_err, int* h_err, cudaStream_t s,
+                       int* launches) {
+    if (N <= 0 || K == 0) return cudaSuccess;
+    const int kpad = (Kc + TC_BK - 1) / TC_BK * TC_BK;
+    const int npad = (N + CB_N - 1) / CB_N * CB_N;
+    __nv_bfloat16* hiT = static_cast<__nv_bfloat16*>(scratch);
+    __nv_bfloat16* loT = hiT + (size_t)kpad * npad;
+    static unsigned long long attr_done = 0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !(attr_done & (1ull << dev))) {
+        cudaError_t e =
+            cudaFuncSetAttribute(tc_combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB_SMEM_BYTES);
+        if (e) return e;
+        attr_done |= 1ull << dev;
+    }
+    cudaMemsetAsync(d_err, 0, sizeof(int), s);
+    const int tot = kpad * npad;
+    coef_split_kernel<<<(tot + 255) / 256, 256, 0, s>>>(Kc, N, Coef, ldcoef, kpad, npad, hiT, loT);
+    dim3 grid((unsigned)((K + TC_M - 1) / TC_M), npad / CB_N);
+    tc_combine_kernel<<<grid, TC_THREADS, CB_SMEM_BYTES, s>>>(N, K, Kc, kpad, A, lda, hiT, loT, (float)beta, Out,
+                                                              ldo, d_err);
+    *launches += 2;
+    if (h_err) {
+        cudaMemcpyAsync(h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+        cudaError_t e = cudaStreamSynchronize(s);
+        if (e) return e;
+    }
+    return cudaGetLastError();
+}
 
 size_t tc_gram_work_elems(int M, int N, size_t K) {
     const size_t tiles = (size_t)((M + TC_M - 1) / TC_M) * ((N + TC_N - 1) / TC_N);
