@@ -137,6 +137,19 @@ __device__ __forceinline__ void best_merge(double& v, int& i, double v2, int i2)
     if (better(v2, i2, v, i)) { v = v2; i = i2; }
 }
 
+template <typename T> struct Vec4 {
+    T a, b, c, d;
+};
+// four consecutive shared-memory values as 16-byte loads (16-byte aligned p)
+__device__ __forceinline__ Vec4<float> load4(const float* p) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    return {v.x, v.y, v.z, v.w};
+}
+__device__ __forceinline__ Vec4<double> load4(const double* p) {
+    const double2 v0 = *reinterpret_cast<const double2*>(p), v1 = *reinterpret_cast<const double2*>(p + 2);
+    return {v0.x, v0.y, v1.x, v1.y};
+}
+
 __device__ __forceinline__ void group_bar(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
@@ -147,7 +160,7 @@ __global__ void __launch_bounds__(QC_THREADS) qr_persistent_kernel(int nrow, int
                                                                    unsigned char* __restrict__ chosen,
                                                                    int* __restrict__ piv) {
     cg::grid_group grid = cg::this_grid();
-    __shared__ T qs[QC_MAXROWS + RPW];
+    __shared__ __align__(16) T qs[QC_MAXROWS + RPW];
     __shared__ T part[QC_WARPS][32];
     __shared__ double gv[QC_WARPS];
     __shared__ int gi[QC_WARPS];
@@ -169,22 +182,45 @@ __global__ void __launch_bounds__(QC_THREADS) qr_persistent_kernel(int nrow, int
                 const int c = tile * 32 + lane;
                 const bool live = c < ncol && !chosen[c];
                 T v[RPW];
+                // all RPW rows of this warp exist: no per-row guard (the common case)
+                const bool full = rbase + RPW <= nrow;
+                if (full) {
 #pragma unroll
-                for (int j = 0; j < RPW; ++j)
-                    v[j] = (live && rbase + j < nrow) ? R[(size_t)(rbase + j) * ncol + c] : T(0);
+                    for (int j = 0; j < RPW; ++j) v[j] = live ? R[(size_t)(rbase + j) * ncol + c] : T(0);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < RPW; ++j)
+                        v[j] = (live && rbase + j < nrow) ? R[(size_t)(rbase + j) * ncol + c] : T(0);
+                }
                 if (step > 0) {
                     T pd = T(0);
 #pragma unroll
-                    for (int j = 0; j < RPW; ++j) pd += qs[rbase + j] * v[j];
+                    for (int j = 0; j < RPW; j += 4) {
+                        const Vec4<T> q4 = load4(qs + rbase + j);
+                        pd += q4.a * v[j] + q4.b * v[j + 1] + q4.c * v[j + 2] + q4.d * v[j + 3];
+                    }
                     part[warp][lane] = pd;
                     group_bar(1 + group, wpt * 32);
                     T dot = T(0);
                     for (int w = 0; w < wpt; ++w) dot += part[group * wpt + w][lane];
                     group_bar(1 + group, wpt * 32);
 #pragma unroll
-                    for (int j = 0; j < RPW; ++j) {
-                        v[j] -= qs[rbase + j] * dot;
-                        if (live && rbase + j < nrow) R[(size_t)(rbase + j) * ncol + c] = v[j];
+                    for (int j = 0; j < RPW; j += 4) {
+                        const Vec4<T> q4 = load4(qs + rbase + j);
+                        v[j] -= q4.a * dot;
+                        v[j + 1] -= q4.b * dot;
+                        v[j + 2] -= q4.c * dot;
+                        v[j + 3] -= q4.d * dot;
+                    }
+                    if (live) {
+                        if (full) {
+#pragma unroll
+                            for (int j = 0; j < RPW; ++j) R[(size_t)(rbase + j) * ncol + c] = v[j];
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < RPW; ++j)
+                                if (rbase + j < nrow) R[(size_t)(rbase + j) * ncol + c] = v[j];
+                        }
                     }
                 }
                 T pn = T(0);
