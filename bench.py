@@ -34,6 +34,7 @@ UNIT = "pair-convolutions/s"
 S_THR = 1e-3
 STRIDE = 2
 B_ALG_PER_PAIR_FP32 = 16  # bytes per grid point per real pair (3-pass FFT model)
+TRAFFIC_TAG = "pairconv-spec-v2"  # kernels the committed DRAM-traffic measurement belongs to
 
 
 def parse():
@@ -262,7 +263,9 @@ def run_lace(args, rank, world, local):
     # ---------------- roofline of the pair-convolution kernels
     peak, peak_kind = peaks()
     pc_avg = statistics.mean(pc_ms)
-    alg_bytes = B_ALG_PER_PAIR_FP32 * ng * npairs
+    # 16 Ng bytes per real pair, plus once per application: read the occupied and
+    # target orbitals ((N_occ + N_P) Ng 4 bytes) and write W (N_P Ng 4 bytes)
+    alg_bytes = B_ALG_PER_PAIR_FP32 * ng * npairs + (n + n) * ng * 4 + n * ng * 4
     achieved = alg_bytes / (pc_avg / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
@@ -271,7 +274,7 @@ def run_lace(args, rank, world, local):
     if os.path.exists(tr):
         try:
             d = json.load(open(tr))
-            if d.get("valid_for") == "pairconv-v1":
+            if d.get("valid_for") == TRAFFIC_TAG:
                 roof["traffic"] = d["traffic_bytes_per_step"]
         except Exception:
             pass
