@@ -49,6 +49,14 @@ def parse():
     p.add_argument("--profile-pairconv", action="store_true",
                    help="only the pair convolutions of a 64-orbital 72^3 set (for ncu captures)")
     p.add_argument("--fp64", action="store_true", help="with --profile-pairconv: FP64 path")
+    p.add_argument("--serving", action="store_true",
+                   help="only the serving stream (32 resident systems, Poisson arrivals, p50/p99 latency)")
+    p.add_argument("--serve-iters", type=int, default=10, help="SCF-like iterations per system (--serving)")
+    p.add_argument("--serve-systems", type=int, default=32)
+    p.add_argument("--serve-slots", type=int, default=8)
+    p.add_argument("--serve-rebuild-slots", type=int, default=4)
+    p.add_argument("--serve-fp64", action="store_true", help="serve in the plain FP64 form (for comparison)")
+    p.add_argument("--no-serving", action="store_true", help="skip the serving sample of the default run")
     return p.parse_args()
 
 
@@ -294,6 +302,17 @@ def run_lace(args, rank, world, local):
         "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
         "fp64_gpu": fp64, "E_x_Ha": ex_mixed,
     }
+    if not args.no_serving:
+        # the serving stream (each rank serves its own replica of it)
+        del phi_dev, out_dev
+        torch.cuda.empty_cache()
+        result["serving"] = run_serving(local, args.serve_systems, args.serve_iters, args.serve_slots,
+                                        args.serve_rebuild_slots)
+        result["latency_ms"] = {"p50": result["serving"]["latency_ms"]["p50"],
+                                "p99": result["serving"]["latency_ms"]["p99"],
+                                "of": "serving-stream requests (submission to completion)"}
+        result["step_latency_ms"] = {"p50": round(statistics.median(step_ms), 3),
+                                     "p99": round(float(np.percentile(step_ms, 99)), 3)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(sysm, budget_s=15.0)
     if world > 1:
@@ -362,6 +381,132 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+SERVE_RATE = 200.0        # offered requests per second over all systems
+SERVE_APPLIES = 4         # inner-loop K_ACE applications per ACE rebuild
+SERVE_BLOCK = 32          # functions per application (a block of trial vectors)
+SERVE_EPS = 1e-3          # SCF-like drift of the orbitals between rebuilds
+
+
+def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp64=False):
+    """The serving stream: resident systems (N log-uniform in [32, 512],
+    2/3/5-smooth cubic grids in [48, 128]), each an SCF-like client whose
+    requests are REBUILD (orthonormalise, SCDM, screen, pair convolutions,
+    ACE build) then SERVE_APPLIES x APPLY (K_ACE on a block of SERVE_BLOCK
+    orbitals), for `iters` outer iterations with the orbitals drifting by
+    SERVE_EPS between rebuilds.  Request k of a system arrives at its Poisson
+    time (rate SERVE_RATE / n_systems per system, seeded) and is submitted at
+    max(arrival, completion of request k-1): a client sends its next request
+    only after the previous result.  Latency = submission to completion (the
+    server's), response = arrival to completion.  Mixed precision (or plain
+    FP64 with fp64=True); memory admission with the default budget (90% of
+    free device memory)."""
+    import synth
+    import torch
+
+    import paper_1801_09263_gb300 as lace
+
+    torch.cuda.set_device(local)
+    systems = synth.serving_systems(n_systems=n_systems)
+    t0 = time.perf_counter()
+    # the client's orbitals and results live in pinned host memory
+    phis, outs = [], []
+    for s in systems:
+        nb = min(SERVE_BLOCK, s.n_occ)
+        phis.append(synth.serving_orbitals(
+            s, torch.empty((s.n_occ,) + s.shape, dtype=torch.float64, pin_memory=True).numpy()))
+        outs.append(torch.empty((nb,) + s.shape, dtype=torch.float64, pin_memory=True).numpy())
+    gen_s = time.perf_counter() - t0
+    rng = np.random.default_rng(1801 + 4 + 1000)
+    per = SERVE_APPLIES + 1
+    nreq = iters * per
+    gaps = rng.exponential(n_systems / SERVE_RATE, size=(n_systems, nreq))
+    arrivals = np.cumsum(gaps, axis=1)
+    srv = lace.Server(local, lace.LACE_FP64 if fp64 else lace.LACE_MIXED, slots=slots, rebuild_slots=rebuild_slots)
+    sids = [srv.add_system(s.cell, s.shape, s.ecut, s.n_occ, 0, S_THR) for s in systems]
+    step = [0] * n_systems
+    outstanding = [None] * n_systems
+    submitted = [0.0] * n_systems
+    lat = {"rebuild": [], "apply": []}
+    resp = []
+    pairs = 0
+    ex_last = [None] * n_systems
+    peak_running, peak_bytes = 0, 0
+    fails = []
+    launches = 0
+    t_start = time.perf_counter()
+    done_all = 0
+    while done_all < n_systems:
+        now = time.perf_counter() - t_start
+        for k in range(n_systems):
+            rid = outstanding[k]
+            if rid is not None:
+                r = srv.poll(rid, wait=False)
+                if r is None:
+                    continue
+                outstanding[k] = None
+                kind = "rebuild" if (step[k] - 1) % per == 0 else "apply"
+                if r["status"] != 0:
+                    fails.append({"system": k, "kind": kind, "status": r["status"], "error": r["error"]})
+                lat[kind].append(r["latency_ms"])
+                resp.append(1e3 * (time.perf_counter() - t_start - arrivals[k][step[k] - 1]))
+                if kind == "rebuild":
+                    pairs += r["n_pairs"]
+                    ex_last[k] = r["ex"] if r["status"] == 0 else None
+                if step[k] == nreq:
+                    done_all += 1
+            if outstanding[k] is None and step[k] < nreq and now >= arrivals[k][step[k]]:
+                j = step[k]
+                if j % per == 0:
+                    if j > 0:
+                        synth.perturb_in_place(phis[k], SERVE_EPS)
+                    outstanding[k] = srv.submit_rebuild(sids[k], phis[k])
+                else:
+                    outstanding[k] = srv.submit_apply(sids[k], phis[k][: len(outs[k])], outs[k])
+                submitted[k] = now
+                step[k] += 1
+        st = srv.stats()
+        peak_running = max(peak_running, st["running"])
+        peak_bytes = max(peak_bytes, st["bytes_resident"])
+        time.sleep(0.0005)
+    makespan = time.perf_counter() - t_start
+    srv.close()
+    # accuracy: the last rebuild of the smallest systems against the plain FP64 GPU form
+    order = sorted((k for k in range(n_systems) if ex_last[k] is not None),
+                   key=lambda k: systems[k].n_occ * int(np.prod(systems[k].shape)))
+    dex = []
+    for k in order[:fp64_sample]:
+        s = systems[k]
+        with lace.Lace(local, lace.LACE_FP64) as c64:
+            c64.set_cell(s.cell, s.shape, s.ecut)
+            c64.load_orbitals(phis[k], s.n_occ, 0, True)
+            c64.localize(STRIDE)
+            c64.screen(S_THR)
+            _, ex64 = c64.apply_exchange(want_W=False)
+        dex.append(abs(ex_last[k] - ex64))
+    all_lat = lat["rebuild"] + lat["apply"]
+
+    def pct(v, q):
+        return round(float(np.percentile(v, q)), 3) if v else None
+
+    return {
+        "workload": f"{n_systems} resident systems, N log-uniform [32,512], cubic 2/3/5-smooth grids [48,128], "
+                    f"{iters} SCF-like iterations x (1 rebuild + {SERVE_APPLIES} applies of {SERVE_BLOCK} orbitals), "
+                    f"Poisson arrivals {SERVE_RATE:g} req/s offered, closed loop per system, {slots} slots "
+                    f"({rebuild_slots} for rebuilds), "
+                    f"S_thr={S_THR:g}, {'plain FP64' if fp64 else 'mixed precision'}",
+        "requests": len(all_lat), "failed": fails[:8], "n_failed": len(fails),
+        "latency_ms": {"p50": pct(all_lat, 50), "p99": pct(all_lat, 99),
+                       "rebuild_p50": pct(lat["rebuild"], 50), "rebuild_p99": pct(lat["rebuild"], 99),
+                       "apply_p50": pct(lat["apply"], 50), "apply_p99": pct(lat["apply"], 99)},
+        "response_ms": {"p50": pct(resp, 50), "p99": pct(resp, 99)},
+        "pair_convolutions_per_s": round(pairs / makespan, 1), "pair_convolutions": int(pairs),
+        "makespan_s": round(makespan, 3), "peak_running": peak_running,
+        "peak_resident_GB": round(peak_bytes / 1e9, 2),
+        "dE_x_vs_fp64_gpu_Ha": {"max": max(dex) if dex else None, "systems": len(dex)},
+        "orbital_generation_s": round(gen_s, 1),
+    }
+
+
 def run_profile(args, local):
     """Pair convolutions only: 64 orbitals on the 72^3 grid, every pair (2080)."""
     import synth
@@ -390,6 +535,12 @@ def main():
     rank, world, local = dist_env()
     if args.profile_pairconv:
         run_profile(args, local)
+    elif args.serving:
+        from paper_1801_09263_gb300.build import build
+
+        build()
+        print(json.dumps({"serving": run_serving(local, args.serve_systems, args.serve_iters, args.serve_slots,
+                                                 args.serve_rebuild_slots, fp64=args.serve_fp64)}), flush=True)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

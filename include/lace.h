@@ -171,6 +171,81 @@ lace_status lace_get_timings(lace_ctx* ctx, double* ms_out, int count);
  * created (all calls). */
 lace_status lace_get_launch_count(lace_ctx* ctx, long long* count_out);
 
+/* Device bytes the context's buffers hold now (they grow to the largest
+ * request seen and are freed by lace_destroy). */
+lace_status lace_get_device_bytes(lace_ctx* ctx, unsigned long long* bytes_out);
+
+/* ------------------------------------------------------------------ serving
+ * A request server over resident systems (the paper's double SCF loop, Sec. 2,
+ * rebuilds ACE once per outer iteration and applies it many times; a server
+ * keeps each system's projector on the device between those requests).
+ * Each system owns a context and CUDA stream (APPLY requests run on a
+ * high-priority stream of their system); `slots` worker threads each run one
+ * request at a time, taking the earliest queued request whose system is idle,
+ * whose device memory fits the budget and, for a REBUILD, for which one of the
+ * `rebuild_slots` is free, so requests for different systems overlap on the
+ * GPU and short applications are not stuck behind long rebuilds.  Requests of one system run in submission
+ * order; a request that does not fit yet waits while others run, and may be
+ * overtaken by requests of other systems that do fit.  Memory is accounted
+ * as the bytes every resident system holds plus, for each running request,
+ * the predicted growth of its system.  Host buffers passed to a request must
+ * stay valid until it completes.  All server calls are thread-safe. */
+typedef struct lace_server lace_server;
+
+typedef enum {
+    LACE_REQ_REBUILD = 0, /* data = n_occ + n_extra raw orbitals (host FP64): orthonormalise,
+                             localise (stride 2), screen at the system's S_thr, apply the
+                             exchange and build ACE; the result is E_x (f_spin = 1) */
+    LACE_REQ_APPLY = 1    /* data = n functions (host FP64): out = K_ACE data (host FP64) */
+} lace_request_kind;
+
+/* Server on `device` computing in `precision` with `slots` concurrent
+ * requests (1..64), of which at most rebuild_slots (1..slots; 0 = slots) are
+ * REBUILDs, and a device-memory budget of mem_bytes (0 = 90% of the free
+ * memory at creation). */
+lace_status lace_server_create(lace_server** out, int device, int precision, int slots, int rebuild_slots,
+                               unsigned long long mem_bytes);
+
+/* Wait for every queued request, then free all systems.  NULL is accepted. */
+lace_status lace_server_destroy(lace_server* srv);
+
+/* Register a resident system (cell, grid and cutoff as lace_set_cell; the
+ * orbital counts and screening threshold of its rebuilds).  *system_id_out
+ * receives its id.  Nothing is computed until its first REBUILD. */
+lace_status lace_server_add_system(lace_server* srv, const double cell[3], int n1, int n2, int n3, double ecut_ha,
+                                   int n_occ, int n_extra, double s_thr, int* system_id_out);
+
+/* Queue a request (lace_request_kind) for a system.  data (host, borrowed
+ * until completion) holds n_occ + n_extra orbitals for a REBUILD or n
+ * functions for an APPLY; out (host, n functions, APPLY only) receives
+ * K_ACE data.  *request_id_out receives the request id.  LACE_ERR_ARG for an
+ * unknown system or bad sizes (an APPLY takes 1 .. n_occ + n_extra + 64
+ * functions); an APPLY before the system's first successful REBUILD
+ * completes with LACE_ERR_STATE; a request that does not fit the memory
+ * budget while no other request runs completes with LACE_ERR_OOM. */
+lace_status lace_server_submit(lace_server* srv, int system_id, int kind, const double* data, int n, double* out,
+                               long long* request_id_out);
+
+/* Status of a request: *done_out = 1 once it has completed (wait != 0 blocks
+ * until then).  On completion *result_out holds its lace_status, *latency_ms
+ * the time from submission to completion, and for a REBUILD *ex_out its E_x
+ * and *n_pairs_out the pair convolutions it ran.  Any output may be NULL;
+ * LACE_ERR_ARG for an unknown request id. */
+lace_status lace_server_poll(lace_server* srv, long long request_id, int wait, int* done_out, int* result_out,
+                             double* latency_ms, double* ex_out, long long* n_pairs_out);
+
+/* What made a completed request fail ("" when it succeeded); NULL for an
+ * unknown or unfinished request.  The string lives as long as the server. */
+const char* lace_server_request_error(lace_server* srv, long long request_id);
+
+/* Free a system's device memory once its queued requests have completed
+ * (blocks until then); later requests for it fail with LACE_ERR_ARG. */
+lace_status lace_server_remove_system(lace_server* srv, int system_id);
+
+/* Snapshot: device bytes held by resident systems, requests running and
+ * requests queued.  Any output may be NULL. */
+lace_status lace_server_stats(lace_server* srv, unsigned long long* bytes_resident, int* running, int* queued);
+
 /* Allocation-free exchange application (the paper has no counterpart: this
  * call exists for callers that cannot allocate device memory where they need
  * the exchange, e.g. a latency-critical loop where cudaMalloc/cudaFree would

@@ -3,7 +3,7 @@
 Python binding of ``liblace.so`` (C ABI declared in ``include/lace.h``).  The
 binding only marshals arguments: every step of the computation runs in the
 library's CUDA kernels.  Importing this package does not need a GPU; creating
-a :class:`Lace` context does, and fails loudly when the library or a CUDA
+a :class:`Lace` context or a :class:`Server` does, and fails loudly when the library or a CUDA
 device is missing.
 """
 from .binding import (  # noqa: F401
@@ -14,6 +14,7 @@ from .binding import (  # noqa: F401
     LACE_SYM_UPPER,
     Lace,
     LaceError,
+    Server,
     exported_symbols,
     library_path,
     load_library,

@@ -17,6 +17,7 @@ LACE_FP64, LACE_MIXED = 0, 1
 LACE_SYM_AVG, LACE_SYM_UPPER, LACE_SYM_LOWER = 0, 1, 2
 MAT_OVERLAP_MODULI, MAT_EXCHANGE, MAT_CHOLESKY, MAT_PAIR_ENERGY, MAT_SCDM_U = 0, 1, 2, 3, 4
 ORB_PSI, ORB_W, ORB_XI = 0, 1, 2
+REQ_REBUILD, REQ_APPLY = 0, 1
 STAGES = ("load", "localize", "screen", "exchange", "ace_build", "ace_apply", "pairconv_kernels")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -74,6 +75,15 @@ def load_library(build_if_missing: bool = False):
         "lace_get_pairs": ([P, P, LL, P], I),
         "lace_get_timings": ([P, P, I], I),
         "lace_get_launch_count": ([P, P], I),
+        "lace_get_device_bytes": ([P, P], I),
+        "lace_server_create": ([C.POINTER(P), I, I, I, I, C.c_ulonglong], I),
+        "lace_server_destroy": ([P], I),
+        "lace_server_add_system": ([P, P, I, I, I, D, I, I, D, P], I),
+        "lace_server_submit": ([P, I, I, P, I, P, P], I),
+        "lace_server_poll": ([P, LL, I, P, P, P, P, P], I),
+        "lace_server_remove_system": ([P, I], I),
+        "lace_server_request_error": ([P, LL], C.c_char_p),
+        "lace_server_stats": ([P, P, P, P], I),
         "lace_exchange_pairs_noalloc": ([P, I, I, I, P, I, I, P, LL, P, P, P], I),
         "lace_status_string": ([I], C.c_char_p),
         "lace_last_error": ([P], C.c_char_p),
@@ -232,3 +242,105 @@ class Lace:
         n = C.c_longlong(0)
         self._check(self.lib.lace_get_launch_count(self.h, C.byref(n)), "lace_get_launch_count")
         return int(n.value)
+
+    def device_bytes(self) -> int:
+        n = C.c_ulonglong(0)
+        self._check(self.lib.lace_get_device_bytes(self.h, C.byref(n)), "lace_get_device_bytes")
+        return int(n.value)
+
+
+class Server:
+    """lace_server_*: requests against resident systems, run by `slots`
+    worker threads (at most `rebuild_slots` of them on rebuilds; 0 = all)
+    under a device-memory budget (0 = 90% of free memory).
+
+    submit() keeps the request's arrays alive until its poll(wait=True) (or
+    a done poll) has returned, as the C call borrows them until completion.
+    """
+
+    def __init__(self, device: int = 0, precision: int = LACE_MIXED, slots: int = 4, rebuild_slots: int = 0,
+                 mem_bytes: int = 0):
+        self.lib = load_library()
+        h = C.c_void_p()
+        st = self.lib.lace_server_create(C.byref(h), int(device), int(precision), int(slots), int(rebuild_slots),
+                                         int(mem_bytes))
+        if st != LACE_OK:
+            raise LaceError(st, "lace_server_create", self.lib.lace_status_string(st).decode())
+        self.h = h
+        self._systems = {}
+        self._live = {}
+
+    def _check(self, st: int, where: str):
+        if st != LACE_OK:
+            raise LaceError(st, where, self.lib.lace_status_string(st).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lace_server_destroy(self.h)
+            self.h = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def add_system(self, cell, shape, ecut: float, n_occ: int, n_extra: int = 0, s_thr: float = 1e-3) -> int:
+        c = _f64(cell)
+        sid = C.c_int(-1)
+        self._check(self.lib.lace_server_add_system(self.h, _ptr(c), int(shape[0]), int(shape[1]), int(shape[2]),
+                                                    float(ecut), int(n_occ), int(n_extra), float(s_thr),
+                                                    C.byref(sid)), "lace_server_add_system")
+        self._systems[sid.value] = (tuple(int(x) for x in shape), int(n_occ) + int(n_extra))
+        return sid.value
+
+    def submit_rebuild(self, system: int, phi) -> int:
+        a = _f64(phi)
+        shape, n_p = self._systems[system]
+        assert a.shape == (n_p,) + shape
+        rid = C.c_longlong(0)
+        self._check(self.lib.lace_server_submit(self.h, int(system), REQ_REBUILD, _ptr(a), n_p, None,
+                                                C.byref(rid)), "lace_server_submit")
+        self._live[rid.value] = (a, None)
+        return rid.value
+
+    def submit_apply(self, system: int, psi, out=None) -> int:
+        """K_ACE psi into `out` (a new array unless given, e.g. a pinned buffer)."""
+        a = _f64(psi)
+        shape, _ = self._systems[system]
+        assert a.shape[1:] == shape
+        if out is None:
+            out = np.empty_like(a)
+        assert out.shape == a.shape and out.dtype == np.float64 and out.flags.c_contiguous
+        rid = C.c_longlong(0)
+        self._check(self.lib.lace_server_submit(self.h, int(system), REQ_APPLY, _ptr(a), a.shape[0], _ptr(out),
+                                                C.byref(rid)), "lace_server_submit")
+        self._live[rid.value] = (a, out)
+        return rid.value
+
+    def poll(self, request: int, wait: bool = True) -> dict | None:
+        """None while running; else {status, latency_ms, ex, n_pairs, out}."""
+        done, res, lat, ex, npairs = C.c_int(0), C.c_int(0), C.c_double(0), C.c_double(0), C.c_longlong(0)
+        self._check(self.lib.lace_server_poll(self.h, int(request), int(wait), C.byref(done), C.byref(res),
+                                              C.byref(lat), C.byref(ex), C.byref(npairs)), "lace_server_poll")
+        if not done.value:
+            return None
+        _, out = self._live.pop(request, (None, None))
+        err = self.lib.lace_server_request_error(self.h, int(request)) if res.value else b""
+        return dict(status=res.value, latency_ms=lat.value, ex=ex.value, n_pairs=npairs.value, out=out,
+                    error=(err or b"").decode())
+
+    def remove_system(self, system: int):
+        self._check(self.lib.lace_server_remove_system(self.h, int(system)), "lace_server_remove_system")
+
+    def stats(self) -> dict:
+        b, r, q = C.c_ulonglong(0), C.c_int(0), C.c_int(0)
+        self._check(self.lib.lace_server_stats(self.h, C.byref(b), C.byref(r), C.byref(q)), "lace_server_stats")
+        return dict(bytes_resident=int(b.value), running=r.value, queued=q.value)

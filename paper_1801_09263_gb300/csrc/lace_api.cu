@@ -70,6 +70,7 @@ struct lace_ctx {
     DevBuf aux;     // QRCP auxiliary
     DevBuf mat;     // small FP64 matrices (see offsets below)
     DevBuf pairs, counts, grids, epart, flag, piv, pivfull, exd;
+    DevBuf aceio;   // FP64 device copies of a host ACE apply's input and output
     long long n_pairs = 0;
     std::vector<long long> pivots_host;
 
@@ -324,7 +325,9 @@ lace_status localize_impl(lace_ctx* c, int stride, const long long* imposed) {
         CK(c->piv.ensure(sizeof(int) * n), "alloc pivots");
         T* R = c->work.as<T>();
         CK(gather_subsample<T>(c->g, stride, canon, n, R, &ncol, c->stream, &L.n), "subsample");
-        CK(qrcp_pivots<T>(n, ncol, R, n, c->piv.as<int>(), c->aux.p, c->stream, &L.n), "qrcp");
+        int timeout = 0;
+        CK(qrcp_pivots<T>(n, ncol, R, n, c->piv.as<int>(), c->aux.p, &timeout, c->stream, &L.n), "qrcp");
+        if (timeout) return fail(c, LACE_ERR_TIMEOUT, "pivoted QR: a grid barrier wait timed out");
         std::vector<int> hp(n);
         CK(cudaMemcpyAsync(hp.data(), c->piv.p, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream), "pivots");
         CK(cudaStreamSynchronize(c->stream), "pivots");
@@ -423,13 +426,15 @@ lace_status make_pairs(lace_ctx* c, bool use_S, double thr, Launch& L) {
     return LACE_OK;
 }
 
-int batch_for(lace_ctx* c) {
-    const size_t per = c->g.ng * 2 * elem_bytes(c);
+int batch_for_sizes(size_t ng, size_t eb) {
+    const size_t per = ng * 2 * eb;
     const char* envb = getenv("LACE_BATCH");
     long long b = envb ? atoll(envb) : (long long)((768ull << 20) / per);
     b = std::max<long long>(4, std::min<long long>(b, 1024));
     return (int)b;
 }
+
+int batch_for(lace_ctx* c) { return batch_for_sizes(c->g.ng, elem_bytes(c)); }
 
 // ------------------------------------------------------------------ exchange
 template <typename T>
@@ -460,12 +465,15 @@ lace_status apply_impl(lace_ctx* c) {
 // ------------------------------------------------------------------ ACE
 // Dense contraction over the grid for the ACE matrices: tcgen05 3xBF16 on the
 // mixed path (LACE_NO_TC=1 selects the CUDA-core FP32 kernel), FP64 otherwise.
+// The tensor-core kernel reads rows with 16-byte loads, so grids whose point
+// count is not a multiple of 4 take the CUDA-core kernel.
 template <typename T>
 lace_status ace_contract(lace_ctx* c, int M, int N, const T* A, const T* B, double alpha, double* C, Launch& L) {
     const size_t ng = c->g.ng;
     if constexpr (std::is_same<T, float>::value) {
         const char* notc = getenv("LACE_NO_TC");
-        if (!(notc && notc[0] == '1')) {
+        const bool aligned = ng % 4 == 0 && (uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0;
+        if (!(notc && notc[0] == '1') && aligned) {
             CK(c->work.ensure(std::max(c->work.bytes, tc_gram_work_elems(M, N, ng) * sizeof(double))), "alloc work");
             int herr = 0;
             CK(tc_gram(M, N, ng, A, ng, B, ng, alpha, C, N, c->work.as<double>(), c->work.bytes / sizeof(double),
@@ -579,6 +587,44 @@ lace_status copy_orbitals_out(lace_ctx* c, const T* src, size_t count, double* h
 
 }  // namespace
 
+namespace lace {
+
+// Device bytes a context holds after loading n_occ + n_extra orbitals on an
+// n[0] x n[1] x n[2] grid, localising them (stride 2), screening, applying the
+// exchange, building ACE and applying it to n_apply host functions: the
+// buffers of the calls above at their largest (the tables excepted, which
+// are far smaller than one orbital).
+size_t predict_ctx_bytes(int prec, const int n[3], int n_occ, int n_extra, int n_apply) {
+    const size_t ng = (size_t)n[0] * n[1] * n[2], eb = prec == LACE_FP64 ? 8 : 4;
+    const size_t n_p = (size_t)n_occ + n_extra, na = (size_t)std::max(n_apply, 0);
+    const size_t ncol = (size_t)((n[0] + 1) / 2) * ((n[1] + 1) / 2) * ((n[2] + 1) / 2);
+    const size_t maxp = (size_t)n_occ * (n_occ + 1) / 2 + (size_t)n_occ * n_extra;
+    const size_t batch = (size_t)std::min<long long>(batch_for_sizes(ng, eb), std::max<long long>((maxp + 1) / 2, 1));
+    size_t work = gemm_rows_work_elems((int)n_p, (int)n_p, ng) * sizeof(double);
+    work = std::max(work, (size_t)n_occ * ncol * eb);
+    if (prec != LACE_FP64) {
+        work = std::max(work, tc_gram_work_elems((int)n_p, (int)n_p, ng) * sizeof(double));
+        work = std::max(work, tc_combine_scratch_bytes((int)n_p, (int)n_p));
+        if (na) {
+            work = std::max(work, tc_gram_work_elems((int)n_p, (int)na, ng) * sizeof(double));
+            work = std::max(work, tc_combine_scratch_bytes((int)na, (int)n_p));
+        }
+    }
+    if (na) work = std::max(work, gemm_rows_work_elems((int)n_p, (int)na, ng) * sizeof(double));
+    const size_t mslot = n_p * n_p + 64 * n_p + 64;
+    size_t b = 0;
+    b += 3 * n_p * ng * eb;        // psi, W, xi
+    b += (size_t)n_occ * ng * eb;  // canonical orbitals
+    b += n_p * ng * 8;             // FP64 staging
+    b += mslot * kMatSlots * sizeof(double) + work + qrcp_aux_bytes(n_occ, (int)ncol);
+    b += maxp * 8 + (maxp + 1) / 2 * sizeof(PairGrid);
+    b += std::max(batch * ng * 2 * eb, 2 * na * ng * eb) + batch * n[0] * 2 * sizeof(double);
+    b += 2 * na * ng * sizeof(double) + ng * sizeof(float);
+    return b;
+}
+
+}  // namespace lace
+
 // ============================================================================ C ABI
 
 extern "C" {
@@ -627,7 +673,8 @@ lace_status lace_destroy(lace_ctx* c) {
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->psi, &c->canon, &c->W, &c->xi, &c->stage64, &c->scratch, &c->work, &c->aux, &c->mat,
-                      &c->pairs, &c->counts, &c->grids, &c->epart, &c->flag, &c->piv, &c->pivfull, &c->exd};
+                      &c->pairs, &c->counts, &c->grids, &c->epart, &c->flag, &c->piv, &c->pivfull, &c->exd,
+                      &c->aceio};
     for (DevBuf* b : bufs) b->release();
     for (int a = 0; a < 3; ++a) { c->tw_d[a].release(); c->tw_f[a].release(); c->g2_d[a].release(); c->g2_f[a].release(); }
     c->ktab_f.release();
@@ -786,13 +833,11 @@ static lace_status apply_ace_common(lace_ctx* c, const double* psi, int n, doubl
     const size_t cnt = (size_t)n * c->g.ng;
     const double* din = psi;
     double* dout = out;
-    DevBuf tmp_in, tmp_out;
     if (!dev) {
-        CK(tmp_in.ensure(cnt * sizeof(double)), "alloc ace io");
-        CK(tmp_out.ensure(cnt * sizeof(double)), "alloc ace io");
-        CK(cudaMemcpyAsync(tmp_in.p, psi, cnt * sizeof(double), cudaMemcpyHostToDevice, c->stream), "upload");
-        din = tmp_in.as<double>();
-        dout = tmp_out.as<double>();
+        CK(c->aceio.ensure(2 * cnt * sizeof(double)), "alloc ace io");
+        CK(cudaMemcpyAsync(c->aceio.p, psi, cnt * sizeof(double), cudaMemcpyHostToDevice, c->stream), "upload");
+        din = c->aceio.as<double>();
+        dout = c->aceio.as<double>() + cnt;
     }
     ev_begin(c, ST_ACE_APPLY);
     lace_status st = c->prec == LACE_FP64 ? apply_ace_impl<double>(c, din, n, dout)
@@ -803,8 +848,6 @@ static lace_status apply_ace_common(lace_ctx* c, const double* psi, int n, doubl
         if (e) st = cuda_fail(c, e, "download");
     }
     cudaError_t e = cudaStreamSynchronize(c->stream);
-    tmp_in.release();
-    tmp_out.release();
     if (st) return st;
     if (e) return cuda_fail(c, e, "apply ace");
     return LACE_OK;
@@ -903,6 +946,18 @@ lace_status lace_get_timings(lace_ctx* c, double* ms_out, int count) {
             ms_out[i] = 0.0;
         }
     }
+    return LACE_OK;
+}
+
+lace_status lace_get_device_bytes(lace_ctx* c, unsigned long long* bytes_out) {
+    if (!c || !bytes_out) return LACE_ERR_ARG;
+    const DevBuf* bufs[] = {&c->psi,   &c->canon, &c->W,      &c->xi,    &c->stage64, &c->scratch, &c->work,
+                            &c->aux,   &c->mat,   &c->pairs,  &c->counts, &c->grids,  &c->epart,   &c->flag,
+                            &c->piv,   &c->pivfull, &c->exd,  &c->aceio, &c->ktab_f};
+    unsigned long long b = 0;
+    for (const DevBuf* d : bufs) b += d->bytes;
+    for (int a = 0; a < 3; ++a) b += c->tw_d[a].bytes + c->tw_f[a].bytes + c->g2_d[a].bytes + c->g2_f[a].bytes;
+    *bytes_out = b;
     return LACE_OK;
 }
 

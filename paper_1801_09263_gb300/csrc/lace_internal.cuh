@@ -123,8 +123,11 @@ cudaError_t symmetrize(int N, const double* A, double* B, int mode, bool neg, cu
 // SCDM pivoted QR (scdm.cu): selects npiv columns of R (nrow x ncol,
 // row-major, overwritten).  Pivots are column indices, ties to the lowest
 // index.  aux: caller scratch of qrcp_aux_bytes(nrow, ncol) bytes.
+// *h_timeout = 1 when a grid-barrier wait of the persistent kernel ran out of
+// time (the pivots are then invalid); the persistent path waits for s.
 template <typename T>
-cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* aux, cudaStream_t s, int* launches);
+cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* aux, int* h_timeout, cudaStream_t s,
+                        int* launches);
 size_t qrcp_aux_bytes(int nrow, int ncol);
 
 // Subsample gather: out[o][c] = psi[o][full index of subsample point c]
@@ -150,5 +153,9 @@ cudaError_t exchange_energy_sum(int n_occ, const double* d_E, double* d_ex, cuda
 template <typename Tin, typename Tout>
 cudaError_t convert(const Tin* in, Tout* out, size_t n, cudaStream_t s, int* launches);
 cudaError_t fill_zero_f64(double* p, size_t n, cudaStream_t s, int* launches);
+
+// Device bytes of a context after a full load / localise / screen / exchange /
+// ACE build / ACE apply of n_apply host functions (lace_api.cu).
+size_t predict_ctx_bytes(int prec, const int n[3], int n_occ, int n_extra, int n_apply);
 
 }  // namespace lace

@@ -13,6 +13,7 @@
 //   B: per y-slab: FFT along x, multiply by K(G)/Ng, inverse FFT along x.
 //   C: per x-plane: inverse 2D FFT, then accumulate -w v into W (atomic
 //      adds) and the real-space pair energies dV sum rho v (FP64).
+#include <atomic>
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -271,9 +272,27 @@ cudaError_t pairconv_run(const GridGeom& g, const FFTTables<T>& tb, const T* psi
     const size_t sm_plane = pairconv_smem_bytes(g, sizeof(T), 0);
     const size_t sm_slab = pairconv_smem_bytes(g, sizeof(T), 1);
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(pass_a_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_plane))) return e;
-    if ((e = cudaFuncSetAttribute(pass_c_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_plane))) return e;
-    if ((e = cudaFuncSetAttribute(pass_b_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_slab))) return e;
+    // The dynamic shared-memory limit is a per-function attribute shared by
+    // every thread and stream of the process: set it once per device to the
+    // device's opt-in maximum (grids of different sizes can be in flight
+    // together), never to one grid's need.
+    static std::atomic<unsigned long long> attr_done{0};
+    int dev = 0;
+    if ((e = cudaGetDevice(&dev))) return e;
+    if (dev >= 64 || !(attr_done.load() & (1ull << dev))) {
+        int optin = 0;
+        if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev))) return e;
+        const void* fns[3] = {(const void*)pass_a_kernel<T>, (const void*)pass_b_kernel<T>,
+                              (const void*)pass_c_kernel<T>};
+        for (const void* fn : fns) {
+            cudaFuncAttributes fa{};
+            if ((e = cudaFuncGetAttributes(&fa, fn))) return e;
+            const int dyn = optin - (int)fa.sharedSizeBytes;  // static shared memory counts against the limit
+            if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn))) return e;
+        }
+        if (dev < 64) attr_done.fetch_or(1ull << dev);
+    }
+    if (sm_plane > (size_t)INT32_MAX || sm_slab > (size_t)INT32_MAX) return cudaErrorInvalidValue;
     // size-specialised FP32 kernels for cubic grids with n % 4 == 0 (or LACE_GENERIC_FFT=1 to disable)
     const char* gen = getenv("LACE_GENERIC_FFT");
     const bool spec_ok = !(gen && gen[0] == '1') && g.n[0] == g.n[1] && g.n[1] == g.n[2] && g.n[0] % 4 == 0;

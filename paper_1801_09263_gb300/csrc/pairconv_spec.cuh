@@ -5,6 +5,7 @@
 // register-held butterflies, orbital reads and W updates are 16-byte vectors.
 #pragma once
 
+#include <atomic>
 #include "lace_internal.cuh"
 
 namespace lace {
@@ -273,14 +274,14 @@ size_t spec_smem(int pass) {
 
 template <int N>
 bool spec_launch_one(int pass, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s) {
-    static unsigned long long attr_done = 0;  // one bit per device
+    static std::atomic<unsigned long long> attr_done{0};  // one bit per device
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && !(attr_done & (1ull << dev))) {
+    if (dev < 64 && !(attr_done.load() & (1ull << dev))) {
         cudaFuncSetAttribute(spec_pass_a<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem<N>(0));
         cudaFuncSetAttribute(spec_pass_b<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem<N>(1));
         cudaFuncSetAttribute(spec_pass_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spec_smem<N>(2));
-        attr_done |= 1ull << dev;
+        attr_done.fetch_or(1ull << dev);
     }
     const size_t sm = spec_smem<N>(pass);
     const dim3 grid(N, nb);

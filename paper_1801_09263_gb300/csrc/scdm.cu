@@ -2,13 +2,9 @@
 // Gram-Schmidt with exact column norms at every step) on the grid subsample,
 // and the gathers that feed it and the U = phi_C^T (phi_C phi_C^T)^{-1/2}
 // rotation computed by the caller.
-#include <cooperative_groups.h>
-
 #include <algorithm>
 
 #include "lace_internal.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace lace {
 
@@ -154,18 +150,65 @@ __device__ __forceinline__ void group_bar(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr unsigned long long kBarrierLimitNs = 2000000000ull;  // 2 s
+
+// Grid-wide barrier of a co-resident grid with a time limit.  bar[0] counts
+// arrivals, bar[1] is the generation, bar[2] the error flag (all zero at
+// launch).  A CTA whose wait runs out sets the flag and leaves the barrier;
+// the return value (same for every thread of the CTA) says whether the grid
+// may go on.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* abort_sh) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned target = gen + 1;
+        __threadfence();
+        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicExch(&bar[1], target);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_u32(&bar[1]) != target) {
+                __nanosleep(40);
+                if (global_ns() - t0 > kBarrierLimitNs) {
+                    atomicExch(&bar[2], 1u);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        gen = target;
+        *abort_sh = ld_acquire_u32(&bar[2]) != 0u;
+    }
+    __syncthreads();
+    return !*abort_sh;
+}
+
 template <typename T, int RPW>
 __global__ void __launch_bounds__(QC_THREADS) qr_persistent_kernel(int nrow, int ncol, T* __restrict__ R,
                                                                    int npiv, int wpt, Best* __restrict__ block_best,
                                                                    unsigned char* __restrict__ chosen,
-                                                                   int* __restrict__ piv) {
-    cg::grid_group grid = cg::this_grid();
+                                                                   int* __restrict__ piv, unsigned* bar) {
     __shared__ __align__(16) T qs[QC_MAXROWS + RPW];
     __shared__ T part[QC_WARPS][32];
     __shared__ double gv[QC_WARPS];
     __shared__ int gi[QC_WARPS];
     __shared__ double red[QC_WARPS];
     __shared__ int pivot_sh;
+    __shared__ int abort_sh;
+    unsigned gen = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int ngroups = QC_WARPS / wpt;
     const int group = warp / wpt, wig = warp % wpt;
@@ -251,7 +294,7 @@ __global__ void __launch_bounds__(QC_THREADS) qr_persistent_kernel(int nrow, int
             for (int w = 1; w < ngroups; ++w) best_merge(b, bi_, gv[w], gi[w]);
             block_best[(step & 1) * gridDim.x + blockIdx.x] = Best{b, bi_};
         }
-        grid.sync();
+        if (!grid_barrier(bar, gen, &abort_sh)) return;
         // every CTA: global argmax, then q = R[:,p] / ||R[:,p]|| into shared memory
         if (warp == 0) {
             double gb = -3.0;
@@ -326,19 +369,22 @@ static int nblocks_cap(int ncol) { return std::max((ncol + QR_THREADS - 1) / QR_
 
 size_t qrcp_aux_bytes(int nrow, int ncol) {
     const int nblocks = nblocks_cap(ncol);
-    return align256(sizeof(Best) * nblocks) + align256((size_t)ncol) + align256(sizeof(double) * nrow);
+    return align256(sizeof(Best) * nblocks) + align256((size_t)ncol) + align256(sizeof(double) * nrow) + 256;
 }
 
 // R (nrow x ncol, row-major, leading dimension ncol) is overwritten.  aux is
 // caller-provided scratch of qrcp_aux_bytes(nrow, ncol) bytes.
 template <typename T>
-cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* aux, cudaStream_t s, int* launches) {
+cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* aux, int* h_timeout, cudaStream_t s,
+                        int* launches) {
+    *h_timeout = 0;
     if (nrow > QR_MAXROWS || npiv > ncol) return cudaErrorInvalidValue;
     const int nblocks = (ncol + QR_THREADS - 1) / QR_THREADS;
     unsigned char* base = static_cast<unsigned char*>(aux);
     Best* best = reinterpret_cast<Best*>(base);
     unsigned char* chosen = base + align256(sizeof(Best) * nblocks_cap(ncol));
     T* q = reinterpret_cast<T*>(chosen + align256((size_t)ncol));
+    unsigned* bar = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(q) + align256(sizeof(double) * nrow));
     cudaMemsetAsync(chosen, 0, ncol, s);
     // persistent cooperative version when the rows fit the per-thread registers
     int dev = 0, sms = 0, per_sm = 0, coop = 0;
@@ -353,11 +399,18 @@ cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* au
     const int gridn = sms * std::min(per_sm, 1);
     if (coop && per_sm > 0 && wpt <= QC_WARPS && nrow <= QC_MAXROWS && 2 * gridn <= nblocks_cap(ncol)) {
         Best* bb = best;
+        cudaError_t e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s);
+        if (e) return e;
         void* args[] = {(void*)&nrow, (void*)&ncol, (void*)&R, (void*)&npiv, (void*)&wpt, (void*)&bb,
-                        (void*)&chosen, (void*)&d_piv};
-        cudaError_t e = cudaLaunchCooperativeKernel(fn, dim3(gridn), dim3(QC_THREADS), args, 0, s);
+                        (void*)&chosen, (void*)&d_piv, (void*)&bar};
+        e = cudaLaunchCooperativeKernel(fn, dim3(gridn), dim3(QC_THREADS), args, 0, s);
         *launches += 1;
-        return e;
+        if (e) return e;
+        unsigned flag = 0;
+        if ((e = cudaMemcpyAsync(&flag, bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s))) return e;
+        if ((e = cudaStreamSynchronize(s))) return e;
+        *h_timeout = flag != 0u;
+        return cudaSuccess;
     }
     for (int step = 0; step < npiv; ++step) {
         qr_update_kernel<T><<<nblocks, QR_THREADS, 0, s>>>(nrow, ncol, R, (size_t)ncol, q, step > 0, chosen, best);
@@ -389,8 +442,8 @@ cudaError_t gather_columns(const T* psi, size_t ldpsi, int norb, const long long
     return cudaGetLastError();
 }
 
-template cudaError_t qrcp_pivots<float>(int, int, float*, int, int*, void*, cudaStream_t, int*);
-template cudaError_t qrcp_pivots<double>(int, int, double*, int, int*, void*, cudaStream_t, int*);
+template cudaError_t qrcp_pivots<float>(int, int, float*, int, int*, void*, int*, cudaStream_t, int*);
+template cudaError_t qrcp_pivots<double>(int, int, double*, int, int*, void*, int*, cudaStream_t, int*);
 template cudaError_t gather_subsample<float>(const GridGeom&, int, const float*, int, float*, int*, cudaStream_t, int*);
 template cudaError_t gather_subsample<double>(const GridGeom&, int, const double*, int, double*, int*, cudaStream_t,
                                               int*);

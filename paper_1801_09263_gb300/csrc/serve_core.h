@@ -1,0 +1,266 @@
+// Request scheduling of the exchange server: requests against resident
+// systems are admitted continuously as worker slots and device memory free
+// up, so the work of requests for different systems overlaps on the device.
+// The paper's double loop (Sec. 2) rebuilds the ACE projector once per outer
+// SCF iteration and applies it many times in the inner loop; the server keeps
+// each system's projector resident between those requests.
+//
+// Plain C++17 (no CUDA): the executor that runs a request on a system is a
+// template parameter, so the scheduling is testable without a device.
+//
+// Executor interface (all calls from worker threads; calls for one system are
+// never concurrent):
+//   using Handle = ...;                                   // per-system state, default-constructible
+//   size_t predict(const SystemDesc&, const Handle&, int kind, int n);  // bytes the system holds after the request
+//   size_t held(const Handle&);                           // bytes the system holds now
+//   int run(const SystemDesc&, Handle&, Request&);        // status code (0 = ok); fills ex / n_pairs / err
+//   void release(Handle&);                                // free the system's memory
+#pragma once
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstddef>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+namespace lace_serve {
+
+// Status codes (the values of lace_status).
+enum { S_OK = 0, S_ERR_ARG = 1, S_ERR_STATE = 2, S_ERR_OOM = 3 };
+enum { REQ_REBUILD = 0, REQ_APPLY = 1 };
+
+using Clock = std::chrono::steady_clock;
+
+struct SystemDesc {
+    double cell[3];
+    int n[3];
+    double ecut;
+    int n_occ, n_extra;
+    double s_thr;
+};
+
+struct Request {
+    long long id = 0;
+    int sys = 0, kind = 0, n = 0;
+    const double* data = nullptr;
+    double* out = nullptr;
+    Clock::time_point t_submit, t_done;
+    bool done = false;
+    int result = 0;
+    double ex = 0.0;
+    long long n_pairs = 0;
+    std::string err;  // what failed (empty when result == 0)
+};
+
+template <class Exec>
+class Scheduler {
+  public:
+    // slots worker threads run requests; at most rebuild_slots of them run a
+    // REBUILD at once, so short APPLY requests find a free slot while long
+    // rebuilds run.
+    Scheduler(Exec& exec, int slots, int rebuild_slots, size_t budget)
+        : exec_(exec), budget_(budget), rebuild_slots_(std::max(1, std::min(rebuild_slots, slots))) {
+        for (int k = 0; k < slots; ++k) workers_.emplace_back([this] { work(); });
+    }
+
+    ~Scheduler() {
+        {
+            std::unique_lock<std::mutex> lk(mu_);
+            idle_cv_.wait(lk, [&] { return pending_.empty() && running_ == 0; });
+            stop_ = true;
+        }
+        work_cv_.notify_all();
+        for (auto& t : workers_) t.join();
+        for (auto& s : systems_)
+            if (s && s->alive) exec_.release(s->h);
+    }
+
+    int add_system(const SystemDesc& d) {
+        std::lock_guard<std::mutex> lk(mu_);
+        systems_.emplace_back(new Sys{d});
+        return (int)systems_.size() - 1;
+    }
+
+    const SystemDesc* desc(int sys) {
+        std::lock_guard<std::mutex> lk(mu_);
+        return valid(sys) ? &systems_[sys]->d : nullptr;
+    }
+
+    // Queue a request; the caller validated its sizes against desc().
+    int submit(int sys, int kind, const double* data, int n, double* out, long long* id_out) {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (!valid(sys) || systems_[sys]->removing) return S_ERR_ARG;
+        auto r = std::make_shared<Request>();
+        r->id = next_id_++;
+        r->sys = sys;
+        r->kind = kind;
+        r->data = data;
+        r->n = n;
+        r->out = out;
+        r->t_submit = Clock::now();
+        reqs_[r->id] = r;
+        pending_.push_back(r);
+        systems_[sys]->queued++;
+        *id_out = r->id;
+        work_cv_.notify_one();
+        return S_OK;
+    }
+
+    int poll(long long id, bool wait, int* done, int* result, double* lat_ms, double* ex, long long* n_pairs) {
+        std::unique_lock<std::mutex> lk(mu_);
+        auto it = reqs_.find(id);
+        if (it == reqs_.end()) return S_ERR_ARG;
+        std::shared_ptr<Request> r = it->second;
+        if (wait) done_cv_.wait(lk, [&] { return r->done; });
+        if (done) *done = r->done ? 1 : 0;
+        if (r->done) {
+            if (result) *result = r->result;
+            if (lat_ms) *lat_ms = std::chrono::duration<double, std::milli>(r->t_done - r->t_submit).count();
+            if (ex) *ex = r->ex;
+            if (n_pairs) *n_pairs = r->n_pairs;
+        }
+        return S_OK;
+    }
+
+    // The failure message of a completed request ("" if none); the storage
+    // lives as long as the scheduler.
+    const char* error(long long id) {
+        std::lock_guard<std::mutex> lk(mu_);
+        auto it = reqs_.find(id);
+        if (it == reqs_.end() || !it->second->done) return nullptr;
+        return it->second->err.c_str();
+    }
+
+    int remove_system(int sys) {
+        std::unique_lock<std::mutex> lk(mu_);
+        if (!valid(sys) || systems_[sys]->removing) return S_ERR_ARG;
+        Sys& s = *systems_[sys];
+        s.removing = true;
+        done_cv_.wait(lk, [&] { return s.queued == 0 && !s.busy; });
+        exec_.release(s.h);
+        s.held = 0;
+        s.alive = false;
+        work_cv_.notify_all();
+        return S_OK;
+    }
+
+    void stats(size_t* held, int* running, int* queued) {
+        std::lock_guard<std::mutex> lk(mu_);
+        size_t h = 0;
+        for (auto& s : systems_) h += s->held;
+        if (held) *held = h;
+        if (running) *running = running_;
+        if (queued) *queued = (int)pending_.size();
+    }
+
+  private:
+    struct Sys {
+        SystemDesc d;
+        typename Exec::Handle h{};
+        size_t held = 0;     // bytes the system holds (updated after each request)
+        size_t growth = 0;   // predicted growth of the running request
+        int queued = 0;      // requests submitted and not yet completed
+        bool busy = false, removing = false, alive = true;
+    };
+
+    bool valid(int sys) const { return sys >= 0 && sys < (int)systems_.size() && systems_[sys]->alive; }
+
+    size_t committed() const {
+        size_t b = 0;
+        for (auto& s : systems_) b += s->held + (s->busy ? s->growth : 0);
+        return b;
+    }
+
+    // Under mu_: the earliest pending request whose system is idle, that is
+    // its system's oldest pending request, whose growth fits the budget and,
+    // for a REBUILD, for which a rebuild slot is free.  A request that cannot
+    // fit even with nothing running completes with S_ERR_OOM.
+    std::shared_ptr<Request> pick(size_t* growth_out) {
+        std::vector<char> seen(systems_.size(), 0);
+        const size_t used = committed();
+        for (auto it = pending_.begin(); it != pending_.end(); ++it) {
+            auto r = *it;
+            Sys& s = *systems_[r->sys];
+            if (seen[r->sys]) continue;
+            seen[r->sys] = 1;
+            if (s.busy) continue;
+            if (r->kind == REQ_REBUILD && rebuilds_running_ >= rebuild_slots_) continue;
+            const size_t after = exec_.predict(s.d, s.h, r->kind, r->n);
+            const size_t growth = after > s.held ? after - s.held : 0;
+            if (used + growth <= budget_) {
+                pending_.erase(it);
+                *growth_out = growth;
+                return r;
+            }
+            // nothing else can release memory: this request never fits
+            if (running_ == 0 && used - s.held + after > budget_) {
+                pending_.erase(it);
+                *growth_out = (size_t)-1;
+                return r;
+            }
+        }
+        return nullptr;
+    }
+
+    void work() {
+        std::unique_lock<std::mutex> lk(mu_);
+        for (;;) {
+            size_t growth = 0;
+            std::shared_ptr<Request> r;
+            work_cv_.wait(lk, [&] { return stop_ || (r = pick(&growth)) != nullptr; });
+            if (!r) return;  // stop_ with nothing runnable
+            Sys& s = *systems_[r->sys];
+            if (growth == (size_t)-1) {
+                r->err = "the request does not fit the device-memory budget beside the resident systems";
+                finish(s, *r, S_ERR_OOM);
+                continue;
+            }
+            const bool rebuild = r->kind == REQ_REBUILD;
+            s.busy = true;
+            s.growth = growth;
+            running_++;
+            rebuilds_running_ += rebuild;
+            lk.unlock();
+            const int st = exec_.run(s.d, s.h, *r);
+            const size_t held = exec_.held(s.h);
+            lk.lock();
+            s.held = held;
+            s.busy = false;
+            s.growth = 0;
+            running_--;
+            rebuilds_running_ -= rebuild;
+            finish(s, *r, st);
+            work_cv_.notify_all();  // memory and the system are free again
+        }
+    }
+
+    void finish(Sys& s, Request& r, int st) {
+        r.result = st;
+        r.t_done = Clock::now();
+        r.done = true;
+        s.queued--;
+        done_cv_.notify_all();
+        if (pending_.empty() && running_ == 0) idle_cv_.notify_all();
+    }
+
+    Exec& exec_;
+    const size_t budget_;
+    std::mutex mu_;
+    std::condition_variable work_cv_, done_cv_, idle_cv_;
+    std::vector<std::unique_ptr<Sys>> systems_;
+    std::deque<std::shared_ptr<Request>> pending_;
+    std::map<long long, std::shared_ptr<Request>> reqs_;
+    std::vector<std::thread> workers_;
+    const int rebuild_slots_;
+    long long next_id_ = 1;
+    int running_ = 0, rebuilds_running_ = 0;
+    bool stop_ = false;
+};
+
+}  // namespace lace_serve

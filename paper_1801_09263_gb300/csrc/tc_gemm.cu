@@ -14,6 +14,7 @@
 // and commits them to the stage's mbarrier.  Two stages alternate so the
 // loads of one step overlap the MMAs of the previous one.  Every mbarrier
 // wait is bounded; on timeout the CTA records an error and stops issuing.
+#include <atomic>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -466,14 +467,14 @@ cudaError_t tc_combine(int N, size_t K, int Kc, const float* A, size_t lda, cons
     const int npad = (N + CB_N - 1) / CB_N * CB_N;
     __nv_bfloat16* hiT = static_cast<__nv_bfloat16*>(scratch);
     __nv_bfloat16* loT = hiT + (size_t)kpad * npad;
-    static unsigned long long attr_done = 0;
+    static std::atomic<unsigned long long> attr_done{0};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && !(attr_done & (1ull << dev))) {
+    if (dev < 64 && !(attr_done.load() & (1ull << dev))) {
         cudaError_t e =
             cudaFuncSetAttribute(tc_combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB_SMEM_BYTES);
         if (e) return e;
-        attr_done |= 1ull << dev;
+        attr_done.fetch_or(1ull << dev);
     }
     cudaMemsetAsync(d_err, 0, sizeof(int), s);
     const int tot = kpad * npad;
@@ -510,13 +511,13 @@ cudaError_t tc_gram(int M, int N, size_t K, const float* A, size_t lda, const fl
     size_t kchunk = (K + nch - 1) / nch;
     kchunk = (kchunk + TC_BK - 1) / TC_BK * TC_BK;
     const size_t nch_eff = (K + kchunk - 1) / kchunk;
-    static unsigned long long attr_done = 0;
+    static std::atomic<unsigned long long> attr_done{0};
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && !(attr_done & (1ull << dev))) {
+    if (dev < 64 && !(attr_done.load() & (1ull << dev))) {
         cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
         if (e) return e;
-        attr_done |= 1ull << dev;
+        attr_done.fetch_or(1ull << dev);
     }
     cudaMemsetAsync(d_err, 0, sizeof(int), s);
     dim3 grid((M + TC_M - 1) / TC_M, (N + TC_N - 1) / TC_N, (unsigned)nch_eff);

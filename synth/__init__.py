@@ -32,6 +32,10 @@ __all__ = [
     "config3_water_like_with_extras",
     "small_localized_system",
     "random_orthogonal",
+    "ServingSystem",
+    "serving_systems",
+    "serving_orbitals",
+    "perturb_in_place",
 ]
 
 
@@ -181,3 +185,94 @@ def small_localized_system(seed: int, cell, shape, ecut, n_centres, n_occ, n_ext
         phi = occ
     return System(tuple(cell), tuple(shape), ecut, phi, n_occ, n_extra, seed,
                   {"name": f"small-{n_occ}+{n_extra}orb-{shape[0]}x{shape[1]}x{shape[2]}"})
+
+
+# ------------------------------------------------------------------ serving workload
+
+def _smooth_235(n: int) -> bool:
+    for p in (2, 3, 5):
+        while n % p == 0:
+            n //= p
+    return n == 1
+
+
+SERVING_SIZES = tuple(n for n in range(48, 129) if _smooth_235(n))
+WATER_BOHR3_PER_ORBITAL = 30.0 * 1.8897261**3 / 4.0  # 30 A^3 per molecule, 4 occupied orbitals
+
+
+@dataclass
+class ServingSystem:
+    """One resident system of the serving stream (orbitals made on demand)."""
+
+    index: int
+    cell: tuple[float, float, float]
+    shape: tuple[int, int, int]
+    ecut: float
+    n_occ: int
+    seed: int
+
+
+def serving_systems(seed: int = 1801 + 4, n_systems: int = 32) -> list[ServingSystem]:
+    """Resident systems of the serving stream: N log-uniform in [32, 512],
+    cubic grids drawn from the 2/3/5-smooth sizes in [48, 128], water
+    density (cell volume N x 30 A^3 / 4), cutoff min(40 Ha, 0.45 (pi n / L)^2)
+    so the band limit stays inside the grid's Nyquist cube."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_systems):
+        n_occ = int(round(np.exp(rng.uniform(np.log(32), np.log(512)))))
+        n = int(rng.choice(SERVING_SIZES))
+        L = float((n_occ * WATER_BOHR3_PER_ORBITAL) ** (1.0 / 3.0))
+        ecut = float(min(40.0, 0.45 * (np.pi * n / L) ** 2))
+        out.append(ServingSystem(k, (L, L, L), (n, n, n), ecut, n_occ, int(rng.integers(1 << 31))))
+    return out
+
+
+def _periodic_gaussian_1d(n: int, L: float, ecut: float, centres: np.ndarray, alphas: np.ndarray) -> np.ndarray:
+    """Rows t: sqrt(pi/alpha_t)/L * sum_{G^2/2 < ecut} exp(-G^2/(4 alpha_t)) cos(G (x - X_t)) on the n grid
+    points of [0, L): the 1D factor of a Gaussian band-limited to a cube."""
+    x = np.arange(n) * (L / n)
+    mmax = int(np.floor(np.sqrt(2.0 * ecut) * L / (2.0 * np.pi) - 1e-12))
+    if mmax >= n // 2:
+        raise ValueError("band limit reaches the Nyquist plane")
+    G = 2.0 * np.pi * np.arange(1, mmax + 1) / L
+    d = x[None, :] - centres[:, None]                                   # (t, n)
+    w = np.exp(-G[None, :] ** 2 / (4.0 * alphas[:, None]))              # (t, m)
+    s = 1.0 + 2.0 * np.einsum("tm,tmn->tn", w, np.cos(G[None, :, None] * d[:, None, :]))
+    return s * (np.sqrt(np.pi / alphas) / L)[:, None]
+
+
+def serving_orbitals(s: ServingSystem, out: np.ndarray | None = None) -> np.ndarray:
+    """Raw orbitals of a serving system, [n_occ][n][n][n] float64: orbital o is
+    4 Gaussians (alpha ~ U[0.5, 2], c ~ U[-1, 1]) around centre o mod N_c
+    (N_c = 3N/4 uniform centres, N(0, 0.5^2) jitter), band-limited to the
+    cube |G_a|^2/2 < E_cut so that every term is a product of 1D factors.
+    Not mixed: the orbitals start localised.  `out` (optional) receives them."""
+    rng = np.random.default_rng(s.seed)
+    n, L, N = s.shape[0], s.cell[0], s.n_occ
+    n_c = max(1, (3 * N) // 4)
+    centres = rng.uniform(0.0, L, size=(n_c, 3))
+    owner = np.repeat(np.arange(N), 4)
+    pos = centres[owner % n_c] + rng.normal(0.0, 0.5, size=(4 * N, 3))
+    alphas = rng.uniform(0.5, 2.0, size=4 * N)
+    coefs = rng.uniform(-1.0, 1.0, size=4 * N)
+    f = [_periodic_gaussian_1d(n, L, s.ecut, pos[:, a], alphas) for a in range(3)]
+    if out is None:
+        out = np.empty((N, n, n, n), dtype=np.float64)
+    assert out.shape == (N, n, n, n) and out.dtype == np.float64 and out.flags.c_contiguous
+    fx = (f[0] * coefs[:, None]).reshape(N, 4, n)
+    fy, fz = f[1].reshape(N, 4, n), f[2].reshape(N, 4, n)
+    for o in range(N):
+        xy = np.ascontiguousarray((fx[o][:, :, None] * fy[o][:, None, :]).reshape(4, n * n).T)  # (n^2, 4)
+        np.matmul(xy, fz[o], out=out[o].reshape(n * n, n))
+    return out
+
+
+def perturb_in_place(phi: np.ndarray, eps: float) -> None:
+    """One SCF-like step of drift: phi_o += eps * phi_{(o+1) mod N} (a
+    band-limited perturbation of the same class; orthonormalisation is the
+    method's job)."""
+    first = phi[0].copy()
+    for o in range(len(phi) - 1):
+        phi[o] += eps * phi[o + 1]
+    phi[-1] += eps * first

@@ -210,6 +210,26 @@ def test_ace_build_and_apply(small_loc, prec, sym):
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_ace_on_a_grid_with_an_odd_point_count(prec):
+    # 25 x 27 x 45 points: rows of the orbital arrays are not 16-byte aligned
+    sysm = synth.small_localized_system(41, (9.5, 10.0, 16.0), (25, 27, 45), 6.0, 6, 8, 3)
+    g, occ, extra = oracle_orbitals(sysm)
+    probe = np.random.default_rng(5).standard_normal((2,) + g.shape)
+    with make_ctx(sysm, prec) as ctx:
+        piv = ctx.localize(2)
+        ctx.screen(0.0)
+        W, ex = ctx.apply_exchange()
+        ctx.build_ace()
+        k_probe = ctx.apply_ace(probe)
+    _, _, w = O.scdm(g, occ, 2, pivots=piv)
+    W_ref, ex_ref, _ = O.apply_exchange(g, w, extra, np.ones((8, 11), dtype=bool))
+    xi_ref, _, _ = O.ace_build(g, np.concatenate([w, extra]), W_ref)
+    tol = 1e-9 if prec == LACE_FP64 else 5e-5
+    assert abs(ex - ex_ref) <= EX_TOL[prec]
+    assert relerr(k_probe, O.ace_apply(g, xi_ref, probe)) < tol
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
 def test_ace_exact_on_building_set_without_truncation(small_loc, prec):
     # Sec. 2: ACE equals the exchange operator on the functions used to build it
     with make_ctx(small_loc, prec) as ctx:

@@ -1,0 +1,137 @@
+"""The exchange server on the device: each result is the same alone and in
+the mix.
+
+Five systems of different cells, grids and band sizes (two non-cubic grids
+on the generic FFT path, with different shared-memory needs) each take two SCF-like outer iterations: REBUILD with
+orbitals, APPLY of K_ACE to probes, REBUILD with the orbitals perturbed by
+1e-3 times band-limited noise, APPLY again.  Every system runs alone (its own
+one-slot server), then all run together on one five-slot server with their
+requests interleaved.  Mixed precision; the stated tolerances are
+|dE_x| <= 1e-5 Ha and 1e-5 relative on K_ACE probes.  One system at
+S_thr = 0 is also checked against the FP64 oracle (E_x and K_ACE on probes
+are then independent of the SCDM rotation): |dE_x| <= 1e-5 Ha and the 5e-5
+relative bound of the mixed-precision ACE parity tests.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from paper_1801_09263_gb300 import LACE_MIXED, Server
+
+pytestmark = pytest.mark.gpu
+
+SYSTEMS = [  # cell, shape, ecut, centres, n_occ, n_extra, s_thr
+    ((10.0, 10.0, 10.0), (24, 24, 24), 8.0, 6, 8, 0, 0.0),
+    ((12.0, 12.0, 12.0), (32, 32, 32), 10.0, 10, 16, 4, 1e-3),
+    ((9.0, 11.0, 8.0), (24, 30, 20), 6.0, 4, 6, 2, 1e-3),
+    ((14.0, 14.0, 14.0), (48, 48, 48), 12.0, 16, 24, 8, 1e-3),
+    ((9.5, 10.0, 12.0), (25, 27, 32), 6.0, 4, 6, 0, 1e-3),
+]
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def inputs():
+    out = []
+    for k, (cell, shape, ecut, nc, no, ne, thr) in enumerate(SYSTEMS):
+        s = synth.small_localized_system(100 + k, cell, shape, ecut, nc, no, ne)
+        noise = synth.small_localized_system(200 + k, cell, shape, ecut, nc, no + ne, 0, mix=False).phi
+        phi2 = s.phi + 1e-3 * noise
+        probe = np.random.default_rng(300 + k).standard_normal((3,) + tuple(shape))
+        out.append(dict(sys=s, thr=thr, phis=[s.phi, phi2], probe=probe))
+    return out
+
+
+def _sequence(srv, sid, inp):
+    ids = []
+    for phi in inp["phis"]:
+        ids.append(srv.submit_rebuild(sid, phi))
+        ids.append(srv.submit_apply(sid, inp["probe"]))
+    return ids
+
+
+def _add(srv, inp):
+    s = inp["sys"]
+    return srv.add_system(s.cell, s.shape, s.ecut, s.n_occ, s.n_extra, inp["thr"])
+
+
+def _collect(srv, ids):
+    res = [srv.poll(i, wait=True) for i in ids]
+    assert all(r["status"] == 0 for r in res), [(r["status"], r["error"]) for r in res]
+    return res
+
+
+@pytest.fixture(scope="module")
+def alone(inputs):
+    out = []
+    for inp in inputs:
+        with Server(0, LACE_MIXED, slots=1) as srv:
+            sid = _add(srv, inp)
+            out.append(_collect(srv, _sequence(srv, sid, inp)))
+    return out
+
+
+@pytest.fixture(scope="module")
+def mixed(inputs):
+    with Server(0, LACE_MIXED, slots=5) as srv:
+        sids = [_add(srv, inp) for inp in inputs]
+        seqs = [[] for _ in inputs]
+        # interleave: every system's first rebuild, then their applies, ...
+        for step in range(4):
+            for k, inp in enumerate(inputs):
+                if step % 2 == 0:
+                    seqs[k].append(srv.submit_rebuild(sids[k], inp["phis"][step // 2]))
+                else:
+                    seqs[k].append(srv.submit_apply(sids[k], inp["probe"]))
+        peak = 0
+        while True:
+            st = srv.stats()
+            peak = max(peak, st["running"])
+            if st["running"] == 0 and st["queued"] == 0:
+                break
+            time.sleep(0.002)
+        res = [_collect(srv, ids) for ids in seqs]
+        assert srv.stats()["bytes_resident"] > 0
+    return res, peak
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix(alone, mixed):
+    res, peak = mixed
+    assert peak >= 2  # requests of different systems ran at the same time
+    for a, m in zip(alone, res):
+        for ra, rm in zip(a, m):
+            assert ra["n_pairs"] == rm["n_pairs"]
+            assert abs(ra["ex"] - rm["ex"]) <= 1e-5
+            if ra["out"] is not None:
+                assert relerr(rm["out"], ra["out"]) <= 1e-5
+            assert rm["latency_ms"] > 0
+
+
+def test_served_results_match_the_fp64_oracle(inputs, alone):
+    inp, r = inputs[0], alone[0]
+    s = inp["sys"]
+    g = O.Grid(s.cell, s.shape)
+    for it, phi in enumerate(inp["phis"]):
+        occ = O.lowdin(g, phi)
+        W, ex, _ = O.apply_exchange(g, occ, None, np.ones((s.n_occ, s.n_occ), dtype=bool))
+        assert abs(r[2 * it]["ex"] - ex) <= 1e-5
+        xi, _, _ = O.ace_build(g, occ, W)
+        # the mixed-precision ACE bound of the parity tests (FP32 W and xi, 3xBF16 products)
+        assert relerr(r[2 * it + 1]["out"], O.ace_apply(g, xi, inp["probe"])) <= 5e-5
+    # the perturbation moved E_x by far more than the tolerance
+    assert abs(r[0]["ex"] - r[2]["ex"]) > 1e-5
+
+
+def test_bad_requests():
+    with Server(0, LACE_MIXED, slots=2) as srv:
+        sid = srv.add_system((10.0, 10.0, 10.0), (24, 24, 24), 8.0, 4, 0, 0.0)
+        rid = srv.submit_apply(sid, np.zeros((1, 24, 24, 24)))
+        assert srv.poll(rid)["status"] == 2  # no ACE built yet
+        with pytest.raises(Exception):
+            srv.submit_apply(sid + 7, np.zeros((1, 24, 24, 24)))
