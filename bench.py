@@ -57,6 +57,9 @@ def parse():
     p.add_argument("--serve-rebuild-slots", type=int, default=4)
     p.add_argument("--serve-fp64", action="store_true", help="serve in the plain FP64 form (for comparison)")
     p.add_argument("--no-serving", action="store_true", help="skip the serving sample of the default run")
+    p.add_argument("--batched", action="store_true",
+                   help="only the batched uneven instances (48 systems, persistent launch in a CUDA graph)")
+    p.add_argument("--no-batched", action="store_true", help="skip the batched sample of the default run")
     return p.parse_args()
 
 
@@ -313,6 +316,8 @@ def run_lace(args, rank, world, local):
                                 "of": "serving-stream requests (submission to completion)"}
         result["step_latency_ms"] = {"p50": round(statistics.median(step_ms), 3),
                                      "p99": round(float(np.percentile(step_ms, 99)), 3)}
+    if not args.no_batched:
+        result["batched"] = run_batched(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(sysm, budget_s=15.0)
     if world > 1:
@@ -507,6 +512,58 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
     }
 
 
+def run_batched(local, steps=5, n_instances=48):
+    """Batched uneven instances: 48 cubic cells (L ~ U[10, 20] bohr, 2/3/5-smooth
+    grids in [32, 64], N log-uniform in [16, 128], S_thr = 1e-3), localised
+    exchange + ACE build for all of them per step through one lace_batch:
+    run 1 eager (with the launch-shape autotuning), run 2 captures the CUDA
+    graph, then `steps` timed runs replay it (host wall clock per run; the
+    device time of the pair convolutions and of the whole graph from the
+    library's events)."""
+    import synth
+    import torch
+
+    import paper_1801_09263_gb300 as lace
+
+    torch.cuda.set_device(local)
+    inst = synth.batch_instances(n_instances=n_instances)
+    phis = [synth.serving_orbitals(s) for s in inst]
+    with lace.Batch([(s.cell, s.shape, s.ecut, s.n_occ, S_THR) for s in inst], device=local) as b:
+        for q, p in enumerate(phis):
+            b.set_orbitals(q, p)
+        t0 = time.perf_counter()
+        ex, st = b.run()
+        first_s = time.perf_counter() - t0
+        b.run()
+        walls, pcs, hots, setups = [], [], [], []
+        for _ in range(steps):
+            t0 = time.perf_counter()
+            ex, st = b.run()
+            walls.append(1e3 * (time.perf_counter() - t0))
+            inf = b.info()
+            pcs.append(inf["pairconv_ms"])
+            hots.append(inf["hot_ms"])
+            setups.append(inf["setup_ms"])
+        npairs = sum(len(b.context(q).get_pairs()) for q in range(len(inst)))
+        inf = b.info()
+    wall = statistics.median(walls)
+    return {
+        "workload": f"{n_instances} cubic cells, L~U[10,20] bohr, 2/3/5-smooth grids [32,64], N log-uniform [16,128], "
+                    f"S_thr={S_THR:g}, localised exchange + ACE build per instance, mixed precision",
+        "instances": n_instances, "failed": int((st != 0).sum()), "pair_convolutions": int(npairs),
+        "step_ms": round(wall, 3), "instances_per_s": round(n_instances / (wall / 1e3), 1),
+        "pair_convolutions_per_s": round(npairs / (wall / 1e3), 1),
+        "setup_ms": round(statistics.median(setups), 3),
+        "pairconv_device_ms": round(statistics.median(pcs), 3),
+        "graph_device_ms": round(statistics.median(hots), 3),
+        "pair_convolutions_per_s_device": round(npairs / (statistics.median(pcs) / 1e3), 1),
+        "launch_shape": {"threads": inf["threads"], "ctas_per_sm": inf["ctas_per_sm"], "chunks": inf["chunks"],
+                         "tuned_ms": inf["tune_ms"]},
+        "graph_replays": inf["graph_replays"], "first_run_s": round(first_s, 3),
+        "E_x_Ha_sum": float(np.sum(ex)),
+    }
+
+
 def run_profile(args, local):
     """Pair convolutions only: 64 orbitals on the 72^3 grid, every pair (2080)."""
     import synth
@@ -535,6 +592,11 @@ def main():
     rank, world, local = dist_env()
     if args.profile_pairconv:
         run_profile(args, local)
+    elif args.batched:
+        from paper_1801_09263_gb300.build import build
+
+        build()
+        print(json.dumps({"batched": run_batched(local, steps=max(1, args.steps))}), flush=True)
     elif args.serving:
         from paper_1801_09263_gb300.build import build
 

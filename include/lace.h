@@ -246,6 +246,64 @@ lace_status lace_server_remove_system(lace_server* srv, int system_id);
  * requests queued.  Any output may be NULL. */
 lace_status lace_server_stats(lace_server* srv, unsigned long long* bytes_resident, int* running, int* queued);
 
+/* ------------------------------------------------------------------ batches
+ * Batched uneven instances: many independent systems (each its own cell,
+ * grid, cutoff, orbital count and threshold) run the localised exchange and
+ * the ACE build of Sec. 2 together, in the mixed precision of LACE_MIXED:
+ * per instance orthonormalisation, SCDM (stride 2) and screening on host
+ * worker threads; then the pair convolutions of every instance in one
+ * persistent cooperative launch (one per scratch chunk of 16 GiB), E_x, and
+ * the ACE builds on forked streams.  That second part runs eagerly on the
+ * first lace_batch_run and is captured into a CUDA graph on the second;
+ * later runs replay it.  The launch shape of the persistent kernel (threads
+ * per CTA, CTAs per SM) is chosen by timing every candidate on the first
+ * run. */
+typedef struct lace_batch lace_batch;
+
+typedef struct {
+    double cell[3];     /* orthorhombic a, b, c (bohr) */
+    int n1, n2, n3;     /* grid, 2^a 3^b 5^c, 4 .. 128 */
+    double ecut_ha;     /* orbital cutoff, as lace_set_cell */
+    int n_occ;          /* occupied orbitals, 1 .. 1024 */
+    double s_thr;       /* screening threshold (Eq. 5) */
+} lace_instance;
+
+/* A batch of n_inst (1 .. 4096) instances on `device`.  LACE_ERR_UNSUPPORTED
+ * for a grid as lace_set_cell rejects it. */
+lace_status lace_batch_create(lace_batch** out, int device, int n_inst, const lace_instance* inst);
+
+/* Free the batch and its instances' contexts.  NULL is accepted. */
+lace_status lace_batch_destroy(lace_batch* batch);
+
+/* Raw orbitals of instance `inst` (host FP64 [n_occ][n1][n2][n3], borrowed:
+ * read by every later lace_batch_run, so they must stay valid and may be
+ * changed between runs). */
+lace_status lace_batch_set_orbitals(lace_batch* batch, int inst, const double* phi);
+
+/* Run every instance.  ex_out[q] (nullable) receives E_x of instance q
+ * (f_spin = 1), status_out[q] (nullable) its status: LACE_ERR_NOT_PD for
+ * a failed Cholesky, LACE_ERR_TIMEOUT for a bounded wait that gave up, or
+ * the status of its setup.  The call returns LACE_OK when it ran, even if
+ * some instances failed. */
+lace_status lace_batch_run(lace_batch* batch, double* ex_out, int* status_out);
+
+/* The context of instance `inst` (owned by the batch): after a run the
+ * getters lace_get_matrix / lace_get_orbitals / lace_get_pairs and the ACE
+ * applications work on it.  NULL for a bad index. */
+lace_ctx* lace_batch_context(lace_batch* batch, int inst);
+
+/* The chosen launch shape, the scratch chunks (launches of the persistent
+ * kernel), graph replays so far, kernel launches so far (all instances),
+ * milliseconds of the last run ([0] setup, host; [1] pair convolutions,
+ * device, of the last eager run or of the autotuned shape; [2] pair
+ * convolutions + energies + ACE builds, device; [3] the whole call, host) and the timed candidates (-1: did not fit).  Any output
+ * may be NULL. */
+lace_status lace_batch_info(lace_batch* batch, int* threads, int* ctas_per_sm, int* chunks, long long* graph_replays,
+                            long long* launches, double* ms_out, double* tune_ms_out, int tune_count);
+
+/* Message of the last failed batch call. */
+const char* lace_batch_last_error(lace_batch* batch);
+
 /* Allocation-free exchange application (the paper has no counterpart: this
  * call exists for callers that cannot allocate device memory where they need
  * the exchange, e.g. a latency-critical loop where cudaMalloc/cudaFree would

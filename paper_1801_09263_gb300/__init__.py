@@ -7,6 +7,7 @@ a :class:`Lace` context or a :class:`Server` does, and fails loudly when the lib
 device is missing.
 """
 from .binding import (  # noqa: F401
+    Batch,
     LACE_FP64,
     LACE_MIXED,
     LACE_SYM_AVG,

@@ -83,6 +83,13 @@ def load_library(build_if_missing: bool = False):
         "lace_server_poll": ([P, LL, I, P, P, P, P, P], I),
         "lace_server_remove_system": ([P, I], I),
         "lace_server_request_error": ([P, LL], C.c_char_p),
+        "lace_batch_create": ([C.POINTER(P), I, I, P], I),
+        "lace_batch_destroy": ([P], I),
+        "lace_batch_set_orbitals": ([P, I, P], I),
+        "lace_batch_run": ([P, P, P], I),
+        "lace_batch_context": ([P, I], P),
+        "lace_batch_info": ([P, P, P, P, P, P, P, P, I], I),
+        "lace_batch_last_error": ([P], C.c_char_p),
         "lace_server_stats": ([P, P, P, P], I),
         "lace_exchange_pairs_noalloc": ([P, I, I, I, P, I, I, P, LL, P, P, P], I),
         "lace_status_string": ([I], C.c_char_p),
@@ -344,3 +351,94 @@ class Server:
         b, r, q = C.c_ulonglong(0), C.c_int(0), C.c_int(0)
         self._check(self.lib.lace_server_stats(self.h, C.byref(b), C.byref(r), C.byref(q)), "lace_server_stats")
         return dict(bytes_resident=int(b.value), running=r.value, queued=q.value)
+
+
+class _Instance(C.Structure):
+    _fields_ = [("cell", C.c_double * 3), ("n1", C.c_int), ("n2", C.c_int), ("n3", C.c_int),
+                ("ecut_ha", C.c_double), ("n_occ", C.c_int), ("s_thr", C.c_double)]
+
+
+TUNE_SHAPES = ((128, 1), (128, 2), (128, 3), (128, 4), (256, 1), (256, 2), (512, 1))
+
+
+class Batch:
+    """lace_batch_*: independent systems run together (mixed precision).
+
+    instances: sequence of (cell, shape, ecut, n_occ, s_thr).  set_orbitals()
+    keeps the arrays alive: the library reads them on every run().
+    """
+
+    def __init__(self, instances, device: int = 0):
+        self.lib = load_library()
+        arr = (_Instance * len(instances))()
+        self.shapes = []
+        for k, (cell, shape, ecut, n_occ, s_thr) in enumerate(instances):
+            arr[k].cell[:] = [float(x) for x in cell]
+            arr[k].n1, arr[k].n2, arr[k].n3 = (int(x) for x in shape)
+            arr[k].ecut_ha, arr[k].n_occ, arr[k].s_thr = float(ecut), int(n_occ), float(s_thr)
+            self.shapes.append(((int(n_occ),) + tuple(int(x) for x in shape)))
+        h = C.c_void_p()
+        st = self.lib.lace_batch_create(C.byref(h), int(device), len(instances), C.cast(arr, C.c_void_p))
+        if st != LACE_OK:
+            raise LaceError(st, "lace_batch_create", self.lib.lace_status_string(st).decode())
+        self.h = h
+        self.n = len(instances)
+        self._phi = [None] * self.n
+
+    def _check(self, st: int, where: str):
+        if st != LACE_OK:
+            detail = self.lib.lace_batch_last_error(self.h).decode() if self.h else ""
+            raise LaceError(st, where, detail or self.lib.lace_status_string(st).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.lace_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_orbitals(self, inst: int, phi):
+        a = _f64(phi)
+        assert a.shape == self.shapes[inst]
+        self._phi[inst] = a
+        self._check(self.lib.lace_batch_set_orbitals(self.h, int(inst), _ptr(a)), "lace_batch_set_orbitals")
+
+    def run(self):
+        """(E_x per instance, status per instance)."""
+        ex = np.zeros(self.n, dtype=np.float64)
+        st = np.zeros(self.n, dtype=np.int32)
+        self._check(self.lib.lace_batch_run(self.h, _ptr(ex), _ptr(st)), "lace_batch_run")
+        return ex, st
+
+    def context(self, inst: int) -> "Lace":
+        """A non-owning Lace view of an instance's context (for the getters)."""
+        h = self.lib.lace_batch_context(self.h, int(inst))
+        if not h:
+            raise LaceError(1, "lace_batch_context", "bad instance")
+        view = Lace.__new__(Lace)
+        view.lib, view.h, view.precision = self.lib, C.c_void_p(h), LACE_MIXED
+        n_occ = self.shapes[inst][0]
+        view.shape, view.n_occ, view.n_extra = self.shapes[inst][1:], n_occ, 0
+        view.close = lambda: None  # owned by the batch
+        return view
+
+    def info(self) -> dict:
+        th, ct, ch = C.c_int(0), C.c_int(0), C.c_int(0)
+        rp, ln = C.c_longlong(0), C.c_longlong(0)
+        ms = np.zeros(4, dtype=np.float64)
+        tune = np.zeros(len(TUNE_SHAPES), dtype=np.float64)
+        self._check(self.lib.lace_batch_info(self.h, C.byref(th), C.byref(ct), C.byref(ch), C.byref(rp), C.byref(ln),
+                                             _ptr(ms), _ptr(tune), len(TUNE_SHAPES)), "lace_batch_info")
+        return dict(threads=th.value, ctas_per_sm=ct.value, chunks=ch.value, graph_replays=rp.value,
+                    launches=ln.value, setup_ms=ms[0], pairconv_ms=ms[1], hot_ms=ms[2], call_ms=ms[3],
+                    tune_ms={f"{a}x{b}": round(float(t), 3) for (a, b), t in zip(TUNE_SHAPES, tune)})

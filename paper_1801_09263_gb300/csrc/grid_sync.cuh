@@ -1,0 +1,54 @@
+// Grid-wide barrier with a time limit for persistent kernels launched
+// cooperatively (all CTAs co-resident).
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace lace {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+constexpr unsigned long long kBarrierLimitNs = 2000000000ull;  // 2 s
+
+// bar[0] counts arrivals, bar[1] is the generation, bar[2] the error flag
+// (all zero at launch).  A CTA whose wait runs out sets the flag and leaves
+// the barrier; the return value (the same for every thread of the CTA) says
+// whether the grid may go on.  gen is the caller's per-CTA generation count.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* abort_sh) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned target = gen + 1;
+        __threadfence();
+        if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
+            atomicExch(&bar[0], 0u);
+            __threadfence();
+            atomicExch(&bar[1], target);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (ld_acquire_u32(&bar[1]) != target) {
+                __nanosleep(40);
+                if (global_ns() - t0 > kBarrierLimitNs) {
+                    atomicExch(&bar[2], 1u);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        gen = target;
+        *abort_sh = ld_acquire_u32(&bar[2]) != 0u;
+    }
+    __syncthreads();
+    return !*abort_sh;
+}
+
+}  // namespace lace

@@ -13,80 +13,11 @@
 
 #include "../../include/lace.h"
 #include "lace_internal.cuh"
+#include "lace_ctx.cuh"
 
 using namespace lace;
 
 namespace {
-
-struct DevBuf {
-    void* p = nullptr;
-    size_t bytes = 0;
-    cudaError_t ensure(size_t b) {
-        if (b <= bytes) return cudaSuccess;
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-        if (b == 0) return cudaSuccess;
-        cudaError_t e = cudaMalloc(&p, b);
-        if (e == cudaSuccess) bytes = b;
-        return e;
-    }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
-    template <typename T> T* as() const { return static_cast<T*>(p); }
-};
-
-enum Stage { ST_LOAD = 0, ST_LOCALIZE, ST_SCREEN, ST_EXCHANGE, ST_ACE_BUILD, ST_ACE_APPLY, ST_PAIRCONV, ST_COUNT };
-
-}  // namespace
-
-struct lace_ctx {
-    int device = 0;
-    int prec = LACE_FP64;
-    cudaStream_t stream = nullptr;
-    cudaStream_t own_stream = nullptr;
-    std::string err;
-    long long launches = 0;
-
-    bool have_cell = false;
-    GridGeom g{};
-    DevBuf tw_d[3], tw_f[3], g2_d[3], g2_f[3];
-    DevBuf ktab_f;  // K(G)/Ng rounded once from FP64 (FP32 path)
-
-    int n_occ = 0, n_extra = 0, n_p = 0;
-    bool loaded = false, localized = false, screened = false, applied = false, ace = false;
-    double s_thr = 0.0;
-
-    DevBuf psi;     // [n_p][ng] working precision: [w (localised occupied) ; extras]
-    DevBuf canon;   // [n_occ][ng] canonical orthonormal occupied orbitals
-    DevBuf W;       // [n_p][ng]
-    DevBuf xi;      // [n_p][ng]
-    DevBuf stage64; // [rows][ng] FP64 staging (uploads, conversions)
-    DevBuf scratch; // complex FFT grids of one batch
-    DevBuf work;    // GEMM partials and the QRCP matrix
-    DevBuf aux;     // QRCP auxiliary
-    DevBuf mat;     // small FP64 matrices (see offsets below)
-    DevBuf pairs, counts, grids, epart, flag, piv, pivfull, exd;
-    DevBuf aceio;   // FP64 device copies of a host ACE apply's input and output
-    long long n_pairs = 0;
-    std::vector<long long> pivots_host;
-
-    cudaEvent_t ev[2 * ST_COUNT] = {};
-    bool ev_used[ST_COUNT] = {};
-
-    // small-matrix slots inside `mat` (each n_p*n_p doubles, plus staging)
-    size_t mslot = 0;
-    double* m(int k) { return mat.as<double>() + (size_t)k * mslot; }
-};
-
-namespace {
-
-enum MatSlot { MS_S = 0, MS_M, MS_MSYM, MS_L, MS_LINV, MS_LINVT, MS_E, MS_U, MS_A, MS_B, MS_NSWORK, MS_COUNT_BASE };
-// MS_NSWORK takes 5 slots (Newton-Schulz work)
-constexpr int kMatSlots = MS_NSWORK + 5 + 1;
 
 lace_status fail(lace_ctx* c, lace_status st, const std::string& msg) {
     if (c) c->err = msg;

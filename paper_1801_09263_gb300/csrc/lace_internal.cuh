@@ -58,6 +58,32 @@ bool spec_launch_s(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cu
 bool spec_launch_m(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
 bool spec_launch_l(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
 
+// Persistent multi-instance pair convolutions (pairconv_multi.cu): the kept
+// pairs of many independent systems in one cooperative launch.
+struct MultiInst {
+    ConvArgs<float> P;  // per-instance arguments (P.scratch, P.epart unused)
+    double* E;          // pair-energy matrix [n_occ][n_occ]
+    int n1, n2;         // planes of passes A/C, slabs of pass B
+};
+struct MultiArgs {
+    const MultiInst* inst;  // device array [n_inst]
+    int n_inst;
+    const int* n_grids;     // device: complex grids per instance, read at run time
+    cplx<float>* pool;      // complex scratch of pool_elems elements (>= the largest grid)
+    size_t pool_elems;
+    double* epart;          // plane energies, epart_elems doubles (>= 2 n1 of any instance)
+    size_t epart_elems;
+    unsigned* bar;          // 4 unsigned: barrier counters and the timeout flag bar[2]
+};
+size_t pairconv_multi_smem(int n1, int n2, int n3);
+int pairconv_multi_occupancy(int threads, size_t smem);  // CTAs per SM (0: unsupported)
+// n_chunks cooperative launches (chunk c in launch c; see pairconv_multi_chunks).
+cudaError_t pairconv_multi_run(const MultiArgs& A, int n_chunks, size_t smem, int threads, int ctas_per_sm,
+                               cudaStream_t s, int* launches);
+// Host copy of the kernel's chunking: chunks needed for these grid counts.
+int pairconv_multi_chunks(const std::vector<int>& n_grids, const std::vector<size_t>& ng, const std::vector<int>& n1,
+                          size_t pool_elems, size_t epart_elems);
+
 // Host planning helpers (pairconv.cu)
 bool plan_axis(int n, AxisPlan* out);
 size_t pairconv_smem_bytes(const GridGeom& g, int elem_bytes, int pass);
@@ -112,6 +138,8 @@ size_t inv_sqrt_mixed_work_elems(int N);
 // F <- F (I - E/2), E = F^T G F - I (G = I when null): orthonormality to O(E^2).
 cudaError_t lowdin_refine(int N, double* F, const double* G, double* work, cudaStream_t s, int* launches);
 // In-place lower Cholesky of A (N x N, lda); *ok = 0 when not positive definite.
+// With ok == nullptr nothing is read back (stream-capturable): d_flag != 0
+// then marks failure.
 cudaError_t cholesky_lower(int N, double* A, int lda, int* d_flag, int* ok, cudaStream_t s, int* launches);
 // Linv = L^{-1} for lower triangular L.
 cudaError_t trtri_lower(int N, const double* L, int ldl, double* Linv, int ldi, cudaStream_t s, int* launches);

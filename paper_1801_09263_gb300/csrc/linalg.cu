@@ -662,6 +662,7 @@ cudaError_t cholesky_lower(int N, double* A, int lda, int* d_flag, int* ok, cuda
     }
     zero_upper_kernel<<<(N * N + 255) / 256, 256, 0, s>>>(N, A, lda);
     *launches += 1;
+    if (!ok) return cudaGetLastError();  // deferred: the caller reads d_flag (0 = positive definite)
     int h = 0;
     cudaMemcpyAsync(&h, d_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);

@@ -20,6 +20,7 @@
 #include <type_traits>
 
 #include "lace_internal.cuh"
+#include "pairconv_generic.cuh"
 
 namespace lace {
 
@@ -27,162 +28,31 @@ namespace {
 
 constexpr int kThreads = 256;
 
-template <typename C>
-__device__ __forceinline__ void load_tw(C* dst, const C* src, int n) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
-}
-
 // Pass A: rho for plane x of complex grid g, forward FFT over z then y.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) pass_a_kernel(ConvArgs<T> P, int g0) {
-    using C = cplx<T>;
     extern __shared__ unsigned char smem_raw[];
-    C* plane = reinterpret_cast<C*>(smem_raw);
-    const int n1 = P.ax[0].n, n2 = P.ax[1].n, n3 = P.ax[2].n;
-    const int np = n2 * n3;
-    C* tw2 = plane + np;
-    C* tw3 = tw2 + n2;
-    const int g = blockIdx.y, x = blockIdx.x;
-    const PairGrid d = P.grids[g0 + g];
-    load_tw(tw2, P.tw[1], n2);
-    load_tw(tw3, P.tw[2], n3);
-    const size_t off = (size_t)x * np;
-    const T* a1 = P.psi + (size_t)d.i1 * P.ng + off;
-    const T* b1 = P.psi + (size_t)d.j1 * P.ng + off;
-    const bool two = d.j2 >= 0;
-    const T* a2 = P.psi + (size_t)(two ? d.i2 : d.i1) * P.ng + off;
-    const T* b2 = P.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off;
-    for (int e = threadIdx.x; e < np; e += blockDim.x) {
-        T ra = a1[e] * b1[e];
-        T rb = two ? a2[e] * b2[e] : T(0);
-        plane[e] = C{ra, rb};
-    }
-    __syncthreads();
-    fft_lines<T, -1>(plane, P.ax[2], n2, n3, 1, false, tw3);  // z lines
-    fft_lines<T, -1>(plane, P.ax[1], n3, 1, n3, true, tw2);   // y lines
-    C* out = P.scratch + (size_t)g * P.ng + off;
-    for (int e = threadIdx.x; e < np; e += blockDim.x) out[e] = plane[e];
-    (void)n1;
+    const int g = blockIdx.y;
+    gen::pass_a_plane<T>(P, P.grids[g0 + g], P.scratch + (size_t)g * P.ng, blockIdx.x,
+                         reinterpret_cast<cplx<T>*>(smem_raw));
 }
 
 // Pass B: slab ky of complex grid g: FFT along x, * K/Ng, inverse FFT along x.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) pass_b_kernel(ConvArgs<T> P, int g0) {
-    using C = cplx<T>;
     extern __shared__ unsigned char smem_raw[];
-    C* slab = reinterpret_cast<C*>(smem_raw);
-    const int n1 = P.ax[0].n, n2 = P.ax[1].n, n3 = P.ax[2].n;
-    C* tw1 = slab + n1 * n3;
-    T* gz2 = reinterpret_cast<T*>(tw1 + n1);
-    T* gx2 = gz2 + n3;
-    const int g = blockIdx.y, ky = blockIdx.x;
-    load_tw(tw1, P.tw[0], n1);
-    for (int i = threadIdx.x; i < n3; i += blockDim.x) gz2[i] = P.g2[2][i];
-    for (int i = threadIdx.x; i < n1; i += blockDim.x) gx2[i] = P.g2[0][i];
-    C* base = P.scratch + (size_t)g * P.ng + (size_t)ky * n3;
-    const size_t xs = (size_t)n2 * n3;
-    for (int e = threadIdx.x; e < n1 * n3; e += blockDim.x) {
-        const int x = e / n3, z = e - x * n3;
-        slab[e] = base[(size_t)x * xs + z];
-    }
-    __syncthreads();
-    fft_lines<T, -1>(slab, P.ax[0], n3, 1, n3, true, tw1);
-    const T gy2 = P.g2[1][ky];
-    for (int e = threadIdx.x; e < n1 * n3; e += blockDim.x) {
-        const int x = e / n3, z = e - x * n3;
-        T k;
-        if (P.ktab) {
-            k = P.ktab[((size_t)x * n2 + ky) * n3 + z];
-        } else {
-            const T gg = gx2[x] + gy2 + gz2[z];
-            k = gg > T(0) ? P.kscale / gg : T(0);
-        }
-        C v = slab[e];
-        slab[e] = C{v.x * k, v.y * k};
-    }
-    __syncthreads();
-    fft_lines<T, +1>(slab, P.ax[0], n3, 1, n3, true, tw1);
-    for (int e = threadIdx.x; e < n1 * n3; e += blockDim.x) {
-        const int x = e / n3, z = e - x * n3;
-        base[(size_t)x * xs + z] = slab[e];
-    }
+    gen::pass_b_slab<T>(P, P.scratch + (size_t)blockIdx.y * P.ng, blockIdx.x, reinterpret_cast<cplx<T>*>(smem_raw));
     (void)g0;
-}
-
-template <typename T> __device__ __forceinline__ void red_add(T* p, T v) { atomicAdd(p, v); }
-
-template <typename T> __device__ __forceinline__ void kahan_add(T& s, T& c, T v) {
-    const T y = v - c;
-    const T t = s + y;
-    c = (t - s) - y;
-    s = t;
 }
 
 // Pass C: inverse 2D FFT of plane x, accumulate into W and pair energies.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) pass_c_kernel(ConvArgs<T> P, int g0) {
-    using C = cplx<T>;
     extern __shared__ unsigned char smem_raw[];
-    C* plane = reinterpret_cast<C*>(smem_raw);
-    const int n2 = P.ax[1].n, n3 = P.ax[2].n;
-    const int np = n2 * n3;
-    C* tw2 = plane + np;
-    C* tw3 = tw2 + n2;
-    __shared__ double red[2][kThreads / 32];
+    __shared__ double red[2 * 32];
     const int g = blockIdx.y, x = blockIdx.x;
-    const PairGrid d = P.grids[g0 + g];
-    load_tw(tw2, P.tw[1], n2);
-    load_tw(tw3, P.tw[2], n3);
-    const size_t off = (size_t)x * np;
-    const C* in = P.scratch + (size_t)g * P.ng + off;
-    for (int e = threadIdx.x; e < np; e += blockDim.x) plane[e] = in[e];
-    __syncthreads();
-    fft_lines<T, +1>(plane, P.ax[1], n3, 1, n3, true, tw2);
-    fft_lines<T, +1>(plane, P.ax[2], n2, n3, 1, false, tw3);
-    const bool two = d.j2 >= 0;
-    const bool a_occ = d.j1 < P.n_occ, a_sym = a_occ && d.j1 != d.i1;
-    const bool b_occ = two && d.j2 < P.n_occ, b_sym = b_occ && d.j2 != d.i2;
-    const T* wi1 = P.psi + (size_t)d.i1 * P.ng + off;
-    const T* pj1 = P.psi + (size_t)d.j1 * P.ng + off;
-    T* Wj1 = P.W + (size_t)d.j1 * P.ng + off;
-    T* Wi1 = P.W + (size_t)d.i1 * P.ng + off;
-    const T* wi2 = P.psi + (size_t)(two ? d.i2 : d.i1) * P.ng + off;
-    const T* pj2 = P.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off;
-    T* Wj2 = P.W + (size_t)(two ? d.j2 : d.j1) * P.ng + off;
-    T* Wi2 = P.W + (size_t)(two ? d.i2 : d.i1) * P.ng + off;
-    // Per-thread energy sums in T with compensated (Kahan) addition; the
-    // warp sums stay in T and only the per-warp totals go to FP64, so the
-    // FP32 path issues no FP64 arithmetic per grid point.
-    T sa = T(0), ca = T(0), sb = T(0), cb = T(0);
-    for (int e = threadIdx.x; e < np; e += blockDim.x) {
-        const C v = plane[e];
-        const T x1 = wi1[e], y1 = pj1[e];
-        red_add(Wj1 + e, -x1 * v.x);
-        if (a_sym) red_add(Wi1 + e, -y1 * v.x);
-        if (a_occ) kahan_add(sa, ca, x1 * y1 * v.x);
-        if (two) {
-            const T x2 = wi2[e], y2 = pj2[e];
-            red_add(Wj2 + e, -x2 * v.y);
-            if (b_sym) red_add(Wi2 + e, -y2 * v.y);
-            if (b_occ) kahan_add(sb, cb, x2 * y2 * v.y);
-        }
-    }
-    sa -= ca;
-    sb -= cb;
-    for (int o = 16; o > 0; o >>= 1) {
-        sa += __shfl_xor_sync(0xffffffffu, sa, o);
-        sb += __shfl_xor_sync(0xffffffffu, sb, o);
-    }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { red[0][warp] = (double)sa; red[1][warp] = (double)sb; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double ta = 0.0, tbb = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { ta += red[0][w]; tbb += red[1][w]; }
-        double* ep = P.epart + ((size_t)g * gridDim.x + x) * 2;
-        ep[0] = ta * P.dv;
-        ep[1] = tbb * P.dv;
-    }
+    gen::pass_c_plane<T>(P, P.grids[g0 + g], P.scratch + (size_t)g * P.ng, x, reinterpret_cast<cplx<T>*>(smem_raw),
+                         red, P.epart + ((size_t)g * gridDim.x + x) * 2);
 }
 
 // Sum the per-plane energies of each grid (fixed order) into the pair-energy

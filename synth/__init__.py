@@ -36,6 +36,7 @@ __all__ = [
     "serving_systems",
     "serving_orbitals",
     "perturb_in_place",
+    "batch_instances",
 ]
 
 
@@ -269,10 +270,31 @@ def serving_orbitals(s: ServingSystem, out: np.ndarray | None = None) -> np.ndar
 
 
 def perturb_in_place(phi: np.ndarray, eps: float) -> None:
-    """One SCF-like step of drift: phi_o += eps * phi_{(o+1) mod N} (a
-    band-limited perturbation of the same class; orthonormalisation is the
-    method's job)."""
-    first = phi[0].copy()
+    """One SCF-like step of drift: phi_o += eps * T phi_{(o+1) mod N}, T a
+    shift by one grid point along x (band-limited, and out of the current
+    span, so E_x moves; orthonormalisation is the method's job)."""
+    first = np.roll(phi[0], 1, axis=0)
     for o in range(len(phi) - 1):
-        phi[o] += eps * phi[o + 1]
+        phi[o] += eps * np.roll(phi[o + 1], 1, axis=0)
     phi[-1] += eps * first
+
+
+# ------------------------------------------------------------------ batched uneven instances
+
+BATCH_SIZES = tuple(n for n in range(32, 65) if _smooth_235(n))
+
+
+def batch_instances(seed: int = 1801 + 3, n_instances: int = 48) -> list[ServingSystem]:
+    """Independent cubic cells for the batched workload: L ~ U[10, 20] bohr,
+    grids drawn from the 2/3/5-smooth sizes in [32, 64], N log-uniform in
+    [16, 128], cutoff min(40 Ha, 0.45 (pi n / L)^2) (band limit inside the
+    Nyquist cube).  Orbitals: serving_orbitals (cube band limit, localised)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n_instances):
+        L = float(rng.uniform(10.0, 20.0))
+        n = int(rng.choice(BATCH_SIZES))
+        n_occ = int(round(np.exp(rng.uniform(np.log(16), np.log(128)))))
+        ecut = float(min(40.0, 0.45 * (np.pi * n / L) ** 2))
+        out.append(ServingSystem(k, (L, L, L), (n, n, n), ecut, n_occ, int(rng.integers(1 << 31))))
+    return out
