@@ -21,13 +21,15 @@ __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
 constexpr unsigned long long kBarrierLimitNs = 2000000000ull;  // 2 s
 
 // bar[0] counts arrivals, bar[1] is the generation, bar[2] the error flag
-// (all zero at launch).  A CTA whose wait runs out sets the flag and leaves
-// the barrier; the return value (the same for every thread of the CTA) says
-// whether the grid may go on.  gen is the caller's per-CTA generation count.
+// (all zero at launch).  A CTA whose wait runs out sets the flag and returns
+// false (the same for every thread of the CTA); it then leaves the kernel,
+// so the other CTAs run out of time at their next barrier and leave too.
+// gen is the caller's per-CTA generation count.
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* abort_sh) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned target = gen + 1;
+        int timed_out = 0;
         __threadfence();
         if (atomicAdd(&bar[0], 1u) == gridDim.x - 1) {
             atomicExch(&bar[0], 0u);
@@ -36,16 +38,17 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* 
         } else {
             const unsigned long long t0 = global_ns();
             while (ld_acquire_u32(&bar[1]) != target) {
-                __nanosleep(40);
+                __nanosleep(32);
                 if (global_ns() - t0 > kBarrierLimitNs) {
                     atomicExch(&bar[2], 1u);
+                    timed_out = 1;
                     break;
                 }
             }
         }
         __threadfence();
         gen = target;
-        *abort_sh = ld_acquire_u32(&bar[2]) != 0u;
+        *abort_sh = timed_out;
     }
     __syncthreads();
     return !*abort_sh;

@@ -258,22 +258,6 @@ __global__ void ns_t_f32_kernel(int N, float* P) {
 }
 
 // out[0] = || I - A ||_F^2 (FP32 input, FP64 sum, fixed order)
-__global__ void frob_res_f32_kernel(int N, const float* A, double* out) {
-    __shared__ double sh[256];
-    double s = 0.0;
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-        const double v = ((idx / N == idx % N) ? 1.0 : 0.0) - (double)A[idx];
-        s += v * v;
-    }
-    sh[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[0] = sh[0];
-}
-
 __global__ void scale_to_f32_kernel(int n, const double* in, float* out, double s) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
     if (idx < n) out[idx] = (float)(s * in[idx]);
@@ -323,14 +307,33 @@ __global__ void ns_t_kernel(int N, double* P) {
 }
 
 // Frobenius norm squared (single block, fixed order) into out[0]; mode 1: of (I - A).
-__global__ void frob_kernel(int N, const double* A, int mode, double* out) {
-    __shared__ double sh[256];
+// ||A||_F^2 (mode 0) or ||I - A||_F^2 (mode 1) of an N x N matrix: one block
+// per row (FP64 sums), then a fixed-order sum of the rows (deterministic).
+// part holds N doubles past out.
+template <typename TA>
+__global__ void frob_rows_kernel(int N, const TA* __restrict__ A, int mode, double* __restrict__ part) {
+    __shared__ double sh[32];
+    const int r = blockIdx.x;
     double s = 0.0;
-    for (int idx = threadIdx.x; idx < N * N; idx += blockDim.x) {
-        double v = A[idx];
-        if (mode == 1) v = ((idx / N == idx % N) ? 1.0 : 0.0) - v;
+    for (int c = threadIdx.x; c < N; c += blockDim.x) {
+        double v = (double)A[(size_t)r * N + c];
+        if (mode == 1) v = (r == c ? 1.0 : 0.0) - v;
         s += v * v;
     }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sh[w];
+        part[r] = t;
+    }
+}
+
+__global__ void sum_rows_kernel(int N, const double* __restrict__ part, double* __restrict__ out) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) s += part[r];
     sh[threadIdx.x] = s;
     __syncthreads();
     for (int o = blockDim.x / 2; o > 0; o >>= 1) {
@@ -338,6 +341,13 @@ __global__ void frob_kernel(int N, const double* A, int mode, double* out) {
         __syncthreads();
     }
     if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+template <typename TA>
+void frob(int N, const TA* A, int mode, double* scal, cudaStream_t s, int* launches) {
+    frob_rows_kernel<TA><<<N, 128, 0, s>>>(N, A, mode, scal + 8);
+    sum_rows_kernel<<<1, 256, 0, s>>>(N, scal + 8, scal);
+    *launches += 2;
 }
 
 // ------------------------------------------------------------------ Cholesky
@@ -511,10 +521,9 @@ cudaError_t inv_sqrt_spd(int N, const double* A, double* X, double* work, int* d
     double* scal = work + 4 * nn;
     const int nb = (int)((nn + 255) / 256);
     double h_norm2 = 0.0;
-    frob_kernel<<<1, 256, 0, s>>>(N, A, 0, scal);
+    frob<double>(N, A, 0, scal, s, launches);
     cudaMemcpyAsync(&h_norm2, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
-    *launches += 1;
     if (e) return e;
     if (!(h_norm2 > 0.0) || !std::isfinite(h_norm2)) { *ok = 0; return cudaSuccess; }
     const double c = std::sqrt(h_norm2);
@@ -535,9 +544,8 @@ cudaError_t inv_sqrt_spd(int N, const double* A, double* X, double* work, int* d
         *launches += 1;
         if (it >= 5 && (it % 2 == 1)) {
             small_gemm_f64(N, N, N, Z, N, false, Y, N, false, 1.0, 0.0, T, N, s, launches);
-            frob_kernel<<<1, 256, 0, s>>>(N, T, 1, scal);
+            frob<double>(N, T, 1, scal, s, launches);
             cudaMemcpyAsync(&h_norm2, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
-            *launches += 1;
             if ((e = cudaStreamSynchronize(s))) return e;
             if (!std::isfinite(h_norm2)) break;
             if (h_norm2 < 1e-24 * N || (h_norm2 < 1e-12 * N && h_norm2 > 0.25 * prev)) { *ok = 1; break; }
@@ -546,9 +554,8 @@ cudaError_t inv_sqrt_spd(int N, const double* A, double* X, double* work, int* d
     }
     if (!*ok) return cudaGetLastError();
     // Reject ill-conditioned A: ||(A/c)^{-1/2}||_F^2 >= lambda_max/lambda_min.
-    frob_kernel<<<1, 256, 0, s>>>(N, Z, 0, scal);
+    frob<double>(N, Z, 0, scal, s, launches);
     cudaMemcpyAsync(&h_norm2, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
-    *launches += 1;
     if ((e = cudaStreamSynchronize(s))) return e;
     if (!(h_norm2 < 1e12)) { *ok = 0; return cudaSuccess; }
     // A^{-1/2} = (A/c)^{-1/2} / sqrt(c)
@@ -574,10 +581,9 @@ cudaError_t inv_sqrt_spd_mixed(int N, const double* A, double* X, double* work, 
     const int nb = (int)((nn + 255) / 256);
     const dim3 gg((N + SG - 1) / SG, (N + SG - 1) / SG), bb(SG, SG);
     double h = 0.0;
-    frob_kernel<<<1, 256, 0, s>>>(N, A, 0, scal);
+    frob<double>(N, A, 0, scal, s, launches);
     cudaMemcpyAsync(&h, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
-    *launches += 1;
     if (e) return e;
     *ok = 0;
     if (!(h > 0.0) || !std::isfinite(h)) return cudaSuccess;
@@ -596,9 +602,9 @@ cudaError_t inv_sqrt_spd_mixed(int N, const double* A, double* X, double* work, 
         *launches += 4;
         if (it >= 5 && (it % 3 == 2)) {
             small_gemm_f32_kernel<<<gg, bb, 0, s>>>(N, Z, Y, T);
-            frob_res_f32_kernel<<<1, 256, 0, s>>>(N, T, scal);
+            frob<float>(N, T, 1, scal, s, launches);
             cudaMemcpyAsync(&h, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
-            *launches += 2;
+            *launches += 1;
             if ((e = cudaStreamSynchronize(s))) return e;
             if (!std::isfinite(h)) break;
             if (h < 1e-11 * N || (h < 1e-6 * N && h > 0.25 * prev)) { *ok = 1; break; }
@@ -608,9 +614,9 @@ cudaError_t inv_sqrt_spd_mixed(int N, const double* A, double* X, double* work, 
     if (!*ok) return cudaGetLastError();
     // ||(A/c)^{-1/2}||_F^2 >= lambda_max / lambda_min: reject ill-conditioned A
     sym_from_f32_kernel<<<nb, 256, 0, s>>>(N, Z, X, 1.0);
-    frob_kernel<<<1, 256, 0, s>>>(N, X, 0, scal);
+    frob<double>(N, X, 0, scal, s, launches);
     cudaMemcpyAsync(&h, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
-    *launches += 2;
+    *launches += 1;
     if ((e = cudaStreamSynchronize(s))) return e;
     if (!(h < 1e12)) { *ok = 0; return cudaSuccess; }
     scale_copy_kernel<<<nb, 256, 0, s>>>((int)nn, X, X, 1.0 / std::sqrt(c));

@@ -119,15 +119,19 @@ __global__ void __launch_bounds__(QR_THREADS) qr_select_kernel(int nrow, int nbl
     }
 }
 
-// Persistent pivoted QR: one cooperative launch runs every step.  One CTA
-// of 512 threads (16 warps) per SM.  A group of WPT warps owns a 32-column
-// tile (lane = column); warp g of the group holds rows g*RPW .. g*RPW+RPW-1
-// of the tile in registers, so a step loads each element once, forms q.r
-// (partial sums exchanged through shared memory behind a named barrier of
-// the group), updates the registers, stores them and forms the exact new
-// norm.  One grid-wide barrier per step; the block winners are
-// double-buffered by step parity and a chosen column is never written
-// again, so every CTA can read the pivot column while the next step runs.
+// Persistent pivoted QR: one cooperative launch runs every step, one CTA of
+// 512 threads (16 warps) per SM.  A group of wpt warps owns 32-column tiles
+// (lane = column); warp w of the group holds rows w*RPW .. w*RPW+RPW-1 of a
+// tile.  The matrix stays on chip across the steps where it fits: the first
+// NREG tiles of a group live in registers, the next nsm tiles in shared
+// memory, and only the rest is streamed from and back to global memory
+// every step.  A step forms q.r (partial sums exchanged through shared
+// memory behind the group's named barrier), updates the column, forms its
+// exact new norm and the group's argmax; each CTA then publishes its best
+// column's values, so one grid-wide barrier per step suffices: after it,
+// every CTA picks the global winner and reads the winner's published column
+// as the next q.  Block winners and published columns are double-buffered by
+// step parity.
 constexpr int QC_THREADS = 512, QC_WARPS = 16, QC_MAXROWS = 1024;
 
 __device__ __forceinline__ void best_merge(double& v, int& i, double v2, int i2) {
@@ -151,141 +155,313 @@ __device__ __forceinline__ void group_bar(int id, int nthreads) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
 }
 
+// q . v over this warp's RPW rows, four independent partial sums
 template <typename T, int RPW>
-__global__ void __launch_bounds__(QC_THREADS) qr_persistent_kernel(int nrow, int ncol, T* __restrict__ R,
-                                                                   int npiv, int wpt, Best* __restrict__ block_best,
-                                                                   unsigned char* __restrict__ chosen,
-                                                                   int* __restrict__ piv, unsigned* bar) {
+__device__ __forceinline__ T dot_rows(const T* v, const T* qs, int rbase) {
+    T p0 = T(0), p1 = T(0), p2 = T(0), p3 = T(0);
+#pragma unroll
+    for (int j = 0; j < RPW; j += 4) {
+        const Vec4<T> q4 = load4(qs + rbase + j);
+        p0 += q4.a * v[j];
+        p1 += q4.b * v[j + 1];
+        p2 += q4.c * v[j + 2];
+        p3 += q4.d * v[j + 3];
+    }
+    return (p0 + p1) + (p2 + p3);
+}
+
+// v -= q dot over the warp's rows, and the new squared norm of v
+template <typename T, int RPW>
+__device__ __forceinline__ T update_rows(T* v, const T* qs, int rbase, T dot) {
+    T n0 = T(0), n1 = T(0), n2 = T(0), n3 = T(0);
+#pragma unroll
+    for (int j = 0; j < RPW; j += 4) {
+        const Vec4<T> q4 = load4(qs + rbase + j);
+        v[j] -= q4.a * dot;
+        v[j + 1] -= q4.b * dot;
+        v[j + 2] -= q4.c * dot;
+        v[j + 3] -= q4.d * dot;
+        n0 += v[j] * v[j];
+        n1 += v[j + 1] * v[j + 1];
+        n2 += v[j + 2] * v[j + 2];
+        n3 += v[j + 3] * v[j + 3];
+    }
+    return (n0 + n1) + (n2 + n3);
+}
+
+template <typename T, int RPW>
+__device__ __forceinline__ T norm_rows(const T* v) {
+    T n0 = T(0), n1 = T(0), n2 = T(0), n3 = T(0);
+#pragma unroll
+    for (int j = 0; j < RPW; j += 4) {
+        n0 += v[j] * v[j];
+        n1 += v[j + 1] * v[j + 1];
+        n2 += v[j + 2] * v[j + 2];
+        n3 += v[j + 3] * v[j + 3];
+    }
+    return (n0 + n1) + (n2 + n3);
+}
+
+// Warp argmax of the 32 columns of a tile (lane = column), merged into (best, bidx).
+__device__ __forceinline__ void tile_argmax(double cv, int ci, double& best, int& bidx) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_xor_sync(0xffffffffu, cv, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
+        best_merge(cv, ci, ov, oi);
+    }
+    best_merge(best, bidx, cv, ci);
+}
+
+template <typename T, int RPW, int NREG>
+__global__ void __launch_bounds__(QC_THREADS, 1)
+    qr_persistent_kernel(int nrow, int ncol, T* __restrict__ R, int npiv, int wpt, int nsm,
+                         Best* __restrict__ block_best, T* __restrict__ pub, unsigned char* __restrict__ chosen,
+                         int* __restrict__ piv, unsigned* bar) {
+    extern __shared__ __align__(16) unsigned char qr_smem_raw[];
+    const int ngroups = QC_WARPS / wpt;
+    const int kres_max = NREG + nsm;                 // resident tiles per group at most
+    T* stiles = reinterpret_cast<T*>(qr_smem_raw);  // [ngroups][nsm][wpt][RPW][32]
+    T* pdot = stiles + (size_t)ngroups * nsm * wpt * RPW * 32;  // [kres_max][QC_WARPS][32]
+    T* pnrm = pdot + (size_t)kres_max * QC_WARPS * 32;            // [kres_max][QC_WARPS][32]
     __shared__ __align__(16) T qs[QC_MAXROWS + RPW];
-    __shared__ T part[QC_WARPS][32];
+    __shared__ T part[QC_WARPS * 32];
     __shared__ double gv[QC_WARPS];
     __shared__ int gi[QC_WARPS];
+    __shared__ int wsel[QC_WARPS];
     __shared__ double red[QC_WARPS];
-    __shared__ int pivot_sh;
+    __shared__ int pivot_sh, winner_sh, mybest_sh;
     __shared__ int abort_sh;
     unsigned gen = 0;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int ngroups = QC_WARPS / wpt;
     const int group = warp / wpt, wig = warp % wpt;
     const int ntiles = (ncol + 31) / 32;
     const int ggroup = blockIdx.x * ngroups + group, total_groups = gridDim.x * ngroups;
+    const int ktot = ggroup < ntiles ? (ntiles - ggroup + total_groups - 1) / total_groups : 0;
+    const int kres = min(ktot, kres_max);  // this group's resident tiles
     const int rbase = wig * RPW;
+    const int rows_pad = wpt * RPW;
+    T vr[NREG > 0 ? NREG : 1][RPW];
+    // chosen columns among this lane's resident tiles (bit k: resident tile k),
+    // kept in a register so that a step reads no global flag for them
+    unsigned cmask = 0u;
     for (int r = threadIdx.x; r < QC_MAXROWS + RPW; r += blockDim.x) qs[r] = T(0);
     __syncthreads();
     for (int step = 0; step < npiv; ++step) {
         double best = -2.0;
         int bidx = 0x7fffffff;
-        if (group < ngroups) {
-            for (int tile = ggroup; tile < ntiles; tile += total_groups) {
-                const int c = tile * 32 + lane;
-                const bool live = c < ncol && !chosen[c];
-                T v[RPW];
-                // all RPW rows of this warp exist: no per-row guard (the common case)
-                const bool full = rbase + RPW <= nrow;
-                if (full) {
+        // resident tiles: all dot partials, one barrier, all updates and norm
+        // partials, one barrier, then the argmax over the tiles
+        if (step == 0) {
 #pragma unroll
-                    for (int j = 0; j < RPW; ++j) v[j] = live ? R[(size_t)(rbase + j) * ncol + c] : T(0);
-                } else {
+            for (int k = 0; k < NREG; ++k) {
+                if (k < kres) {
+                    const int c = (ggroup + k * total_groups) * 32 + lane;
 #pragma unroll
                     for (int j = 0; j < RPW; ++j)
-                        v[j] = (live && rbase + j < nrow) ? R[(size_t)(rbase + j) * ncol + c] : T(0);
+                        vr[k][j] = (c < ncol && rbase + j < nrow) ? R[(size_t)(rbase + j) * ncol + c] : T(0);
+                    pnrm[(k * QC_WARPS + warp) * 32 + lane] = norm_rows<T, RPW>(vr[k]);
                 }
-                if (step > 0) {
-                    T pd = T(0);
+            }
+            for (int k = NREG; k < kres; ++k) {
+                const int c = (ggroup + k * total_groups) * 32 + lane;
+                T* st = stiles + ((((size_t)group * nsm + (k - NREG)) * wpt + wig) * RPW) * 32 + lane;
+                T v[RPW];
 #pragma unroll
-                    for (int j = 0; j < RPW; j += 4) {
-                        const Vec4<T> q4 = load4(qs + rbase + j);
-                        pd += q4.a * v[j] + q4.b * v[j + 1] + q4.c * v[j + 2] + q4.d * v[j + 3];
-                    }
-                    part[warp][lane] = pd;
-                    group_bar(1 + group, wpt * 32);
+                for (int j = 0; j < RPW; ++j) {
+                    v[j] = (c < ncol && rbase + j < nrow) ? R[(size_t)(rbase + j) * ncol + c] : T(0);
+                    st[j * 32] = v[j];
+                }
+                pnrm[(k * QC_WARPS + warp) * 32 + lane] = norm_rows<T, RPW>(v);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < NREG; ++k)
+                if (k < kres) pdot[(k * QC_WARPS + warp) * 32 + lane] = dot_rows<T, RPW>(vr[k], qs, rbase);
+            for (int k = NREG; k < kres; ++k) {
+                const T* st = stiles + ((((size_t)group * nsm + (k - NREG)) * wpt + wig) * RPW) * 32 + lane;
+                T v[RPW];
+#pragma unroll
+                for (int j = 0; j < RPW; ++j) v[j] = st[j * 32];
+                pdot[(k * QC_WARPS + warp) * 32 + lane] = dot_rows<T, RPW>(v, qs, rbase);
+            }
+            if (kres > 0) group_bar(1 + group, wpt * 32);
+#pragma unroll
+            for (int k = 0; k < NREG; ++k) {
+                if (k < kres) {
                     T dot = T(0);
-                    for (int w = 0; w < wpt; ++w) dot += part[group * wpt + w][lane];
-                    group_bar(1 + group, wpt * 32);
-#pragma unroll
-                    for (int j = 0; j < RPW; j += 4) {
-                        const Vec4<T> q4 = load4(qs + rbase + j);
-                        v[j] -= q4.a * dot;
-                        v[j + 1] -= q4.b * dot;
-                        v[j + 2] -= q4.c * dot;
-                        v[j + 3] -= q4.d * dot;
-                    }
-                    if (live) {
-                        if (full) {
-#pragma unroll
-                            for (int j = 0; j < RPW; ++j) R[(size_t)(rbase + j) * ncol + c] = v[j];
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < RPW; ++j)
-                                if (rbase + j < nrow) R[(size_t)(rbase + j) * ncol + c] = v[j];
-                        }
-                    }
+                    for (int w = 0; w < wpt; ++w) dot += pdot[(k * QC_WARPS + group * wpt + w) * 32 + lane];
+                    pnrm[(k * QC_WARPS + warp) * 32 + lane] = update_rows<T, RPW>(vr[k], qs, rbase, dot);
                 }
-                T pn = T(0);
+            }
+            for (int k = NREG; k < kres; ++k) {
+                T* st = stiles + ((((size_t)group * nsm + (k - NREG)) * wpt + wig) * RPW) * 32 + lane;
+                T dot = T(0);
+                for (int w = 0; w < wpt; ++w) dot += pdot[(k * QC_WARPS + group * wpt + w) * 32 + lane];
+                T v[RPW];
 #pragma unroll
-                for (int j = 0; j < RPW; ++j) pn += v[j] * v[j];
-                part[warp][lane] = pn;
-                group_bar(1 + group, wpt * 32);
-                if (wig == 0) {
-                    T tot = T(0);
-                    for (int w = 0; w < wpt; ++w) tot += part[group * wpt + w][lane];
-                    double cv = live ? (double)tot : (c < ncol ? -1.0 : -2.0);
-                    int ci = c < ncol ? c : 0x7fffffff;
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const double ov = __shfl_xor_sync(0xffffffffu, cv, o);
-                        const int oi = __shfl_xor_sync(0xffffffffu, ci, o);
-                        best_merge(cv, ci, ov, oi);
-                    }
-                    best_merge(best, bidx, cv, ci);
-                }
-                group_bar(1 + group, wpt * 32);
+                for (int j = 0; j < RPW; ++j) v[j] = st[j * 32];
+                pnrm[(k * QC_WARPS + warp) * 32 + lane] = update_rows<T, RPW>(v, qs, rbase, dot);
+#pragma unroll
+                for (int j = 0; j < RPW; ++j) st[j * 32] = v[j];
             }
         }
-        if (lane == 0 && wig == 0 && group < ngroups) { gv[group] = best; gi[group] = bidx; }
+        if (kres > 0) group_bar(1 + group, wpt * 32);
+        if (wig == 0) {
+            for (int k = 0; k < kres; ++k) {
+                T tot = T(0);
+                for (int w = 0; w < wpt; ++w) tot += pnrm[(k * QC_WARPS + group * wpt + w) * 32 + lane];
+                const int c = (ggroup + k * total_groups) * 32 + lane;
+                const bool live = c < ncol && !((cmask >> k) & 1u);
+                tile_argmax(live ? (double)tot : (c < ncol ? -1.0 : -2.0), c < ncol ? c : 0x7fffffff, best, bidx);
+            }
+        }
+        // the rest: streamed from and back to global memory, one tile at a time
+        for (int tile = ggroup + kres_max * total_groups; tile < ntiles; tile += total_groups) {
+            const int c = tile * 32 + lane;
+            const bool live = c < ncol && !chosen[c];
+            T v[RPW];
+            const bool full = rbase + RPW <= nrow;
+            if (full) {
+#pragma unroll
+                for (int j = 0; j < RPW; ++j) v[j] = live ? R[(size_t)(rbase + j) * ncol + c] : T(0);
+            } else {
+#pragma unroll
+                for (int j = 0; j < RPW; ++j)
+                    v[j] = (live && rbase + j < nrow) ? R[(size_t)(rbase + j) * ncol + c] : T(0);
+            }
+            if (step > 0) {
+                part[warp * 32 + lane] = dot_rows<T, RPW>(v, qs, rbase);
+                group_bar(1 + group, wpt * 32);
+                T dot = T(0);
+                for (int w = 0; w < wpt; ++w) dot += part[(group * wpt + w) * 32 + lane];
+                group_bar(1 + group, wpt * 32);
+                part[warp * 32 + lane] = update_rows<T, RPW>(v, qs, rbase, dot);
+                if (live) {
+                    if (full) {
+#pragma unroll
+                        for (int j = 0; j < RPW; ++j) R[(size_t)(rbase + j) * ncol + c] = v[j];
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < RPW; ++j)
+                            if (rbase + j < nrow) R[(size_t)(rbase + j) * ncol + c] = v[j];
+                    }
+                }
+            } else {
+                part[warp * 32 + lane] = norm_rows<T, RPW>(v);
+            }
+            group_bar(1 + group, wpt * 32);
+            if (wig == 0) {
+                T tot = T(0);
+                for (int w = 0; w < wpt; ++w) tot += part[(group * wpt + w) * 32 + lane];
+                tile_argmax(live ? (double)tot : (c < ncol ? -1.0 : -2.0), c < ncol ? c : 0x7fffffff, best, bidx);
+            }
+            group_bar(1 + group, wpt * 32);
+        }
+        if (lane == 0 && wig == 0) { gv[group] = best; gi[group] = bidx; }
         __syncthreads();
         if (threadIdx.x == 0) {
             double b = gv[0];
             int bi_ = gi[0];
             for (int w = 1; w < ngroups; ++w) best_merge(b, bi_, gv[w], gi[w]);
             block_best[(step & 1) * gridDim.x + blockIdx.x] = Best{b, bi_};
+            mybest_sh = (b >= 0.0 && bi_ < ncol) ? bi_ : -1;
+        }
+        __syncthreads();
+        // publish this CTA's candidate column (its current residual values) and,
+        // in slot rows_pad, the inverse of its FP64 norm
+        {
+            T* out = pub + ((size_t)(step & 1) * gridDim.x + blockIdx.x) * (rows_pad + 4);
+            const int cb = mybest_sh;
+            if (cb >= 0) {
+                const int tile = cb / 32, cl = cb % 32;
+                const int kk = tile / total_groups, gg = tile % total_groups - blockIdx.x * ngroups;
+                T x = T(0);
+                if (kk < NREG) {
+                    // the lane holding the column, in each warp of its group
+                    if (group == gg && lane == cl) {
+#pragma unroll
+                        for (int k = 0; k < NREG; ++k)
+                            if (k == kk) {
+#pragma unroll
+                                for (int j = 0; j < RPW; ++j) out[rbase + j] = vr[k][j];
+                            }
+                    }
+                    __syncthreads();
+                    if (threadIdx.x < rows_pad) x = out[threadIdx.x];
+                } else if (kk < kres_max) {
+                    const T* st = stiles + (((size_t)gg * nsm + (kk - NREG)) * wpt) * RPW * 32 + cl;
+                    if (threadIdx.x < rows_pad) {
+                        x = st[(size_t)threadIdx.x * 32];
+                        out[threadIdx.x] = x;
+                    }
+                } else {
+                    if (threadIdx.x < rows_pad) {
+                        x = threadIdx.x < nrow ? R[(size_t)threadIdx.x * ncol + cb] : T(0);
+                        out[threadIdx.x] = x;
+                    }
+                }
+                const int r2 = threadIdx.x + QC_THREADS;
+                T x2 = T(0);
+                if (r2 < rows_pad) {
+                    if (kk < NREG) x2 = out[r2];
+                    else if (kk < kres_max)
+                        x2 = stiles[((((size_t)gg * nsm + (kk - NREG)) * wpt) * RPW + r2) * 32 + cl];
+                    else x2 = r2 < nrow ? R[(size_t)r2 * ncol + cb] : T(0);
+                    if (kk >= NREG) out[r2] = x2;
+                }
+                double s2 = (double)x * (double)x + (double)x2 * (double)x2;
+                for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+                if (lane == 0) red[warp] = s2;
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    double t = 0.0;
+                    for (int w = 0; w < QC_WARPS; ++w) t += red[w];
+                    out[rows_pad] = (T)(t > 0.0 ? 1.0 / sqrt(t) : 0.0);
+                }
+            }
         }
         if (!grid_barrier(bar, gen, &abort_sh)) return;
-        // every CTA: global argmax, then q = R[:,p] / ||R[:,p]|| into shared memory
-        if (warp == 0) {
+        // every CTA: global argmax (one block winner per thread: a single round
+        // of loads), then q = (winner's column) x (its inverse norm)
+        {
             double gb = -3.0;
-            int gbi = 0x7fffffff;
-            for (int b = lane; b < (int)gridDim.x; b += 32) {
-                const Best x = block_best[(step & 1) * gridDim.x + b];
-                best_merge(gb, gbi, x.v, x.idx);
+            int gbi = 0x7fffffff, gw = 0;
+            if (threadIdx.x < gridDim.x) {
+                const Best x = block_best[(step & 1) * gridDim.x + threadIdx.x];
+                gb = x.v;
+                gbi = x.idx;
+                gw = threadIdx.x;
             }
             for (int o = 16; o > 0; o >>= 1) {
                 const double ov = __shfl_xor_sync(0xffffffffu, gb, o);
                 const int oi = __shfl_xor_sync(0xffffffffu, gbi, o);
-                best_merge(gb, gbi, ov, oi);
+                const int ow = __shfl_xor_sync(0xffffffffu, gw, o);
+                if (better(ov, oi, gb, gbi)) { gb = ov; gbi = oi; gw = ow; }
             }
-            if (lane == 0) pivot_sh = gbi;
+            if (lane == 0) { gv[warp] = gb; gi[warp] = gbi; wsel[warp] = gw; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int w = 1; w < QC_WARPS; ++w)
+                    if (better(gv[w], gi[w], gb, gbi)) { gb = gv[w]; gbi = gi[w]; gw = wsel[w]; }
+                pivot_sh = gbi;
+                winner_sh = gw;
+            }
         }
         __syncthreads();
         const int p = pivot_sh;
-        const T xr = threadIdx.x < nrow ? R[(size_t)threadIdx.x * ncol + p] : T(0);
-        const int r2 = threadIdx.x + QC_THREADS;
-        const T xr2 = r2 < nrow ? R[(size_t)r2 * ncol + p] : T(0);
-        double s2 = (double)xr * (double)xr + (double)xr2 * (double)xr2;
-        for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
-        if (lane == 0) red[warp] = s2;
-        __syncthreads();
-        if (warp == 0) {
-            double t = lane < QC_WARPS ? red[lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-            if (lane == 0) red[0] = t;
+        {
+            const T* col = pub + ((size_t)(step & 1) * gridDim.x + winner_sh) * (rows_pad + 4);
+            const double inv = (double)col[rows_pad];
+            for (int r = threadIdx.x; r < nrow; r += blockDim.x) qs[r] = (T)((double)col[r] * inv);
         }
-        __syncthreads();
-        const double inv = red[0] > 0.0 ? 1.0 / sqrt(red[0]) : 0.0;
-        if (threadIdx.x < nrow) qs[threadIdx.x] = (T)((double)xr * inv);
-        if (r2 < nrow) qs[r2] = (T)((double)xr2 * inv);
         if (threadIdx.x == 0) {
             chosen[p] = 1;
             if (blockIdx.x == 0) piv[step] = p;
+        }
+        {
+            const int tile = p / 32, gg = tile % total_groups, kk = tile / total_groups;
+            if (gg / ngroups == (int)blockIdx.x && group == gg % ngroups && lane == p % 32 && kk < kres_max)
+                cmask |= 1u << kk;
         }
         __syncthreads();
     }
@@ -322,9 +498,61 @@ static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 // Capacity (in Best entries) of the block-winner buffer of qrcp_aux_bytes.
 static int nblocks_cap(int ncol) { return std::max((ncol + QR_THREADS - 1) / QR_THREADS, 2 * 152 * 8); }
 
+// Published candidate columns of the persistent kernel: 2 (step parity) x
+// CTAs (up to 304) x padded rows (< 2 nrow + 64), FP64 at most.
+static size_t pub_bytes(int nrow) { return align256((size_t)2 * 304 * (2 * (size_t)nrow + 64) * sizeof(double)); }
+
 size_t qrcp_aux_bytes(int nrow, int ncol) {
     const int nblocks = nblocks_cap(ncol);
-    return align256(sizeof(Best) * nblocks) + align256((size_t)ncol) + align256(sizeof(double) * nrow) + 256;
+    return align256(sizeof(Best) * nblocks) + align256((size_t)ncol) + align256(sizeof(double) * nrow) + 256 +
+           pub_bytes(nrow);
+}
+
+// The persistent kernel for one (T, RPW, NREG); *ran = false when the rows
+// do not fit its warp layout or the device cannot co-schedule it.
+template <typename T, int RPW, int NREG>
+static cudaError_t qr_persistent_launch(int nrow, int ncol, T* R, int npiv, Best* best, T* pub,
+                                        unsigned char* chosen, int* d_piv, unsigned* bar, cudaStream_t s,
+                                        int* launches, bool* ran) {
+    *ran = false;
+    int dev = 0, sms = 0, coop = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int wpt = 2;  // >= 2 keeps the named-barrier ids (1 + group) within 1..8
+    while (wpt * RPW < nrow) wpt *= 2;
+    if (!coop || wpt > QC_WARPS || nrow > QC_MAXROWS || sms > 304 || 2 * sms > nblocks_cap(ncol) ||
+        (size_t)2 * sms * (wpt * RPW + 4) * sizeof(T) > pub_bytes(nrow))
+        return cudaSuccess;
+    const void* fn = (const void*)qr_persistent_kernel<T, RPW, NREG>;
+    cudaFuncAttributes fa{};
+    cudaError_t e;
+    if ((e = cudaFuncGetAttributes(&fa, fn))) return e;
+    // one limit for every caller of this kernel: the opt-in maximum
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes)))
+        return e;
+    const int ngroups = QC_WARPS / wpt;
+    const int ntiles = (ncol + 31) / 32, total_groups = sms * ngroups;
+    const int max_k = (ntiles + total_groups - 1) / total_groups;
+    const size_t tile_bytes = (size_t)wpt * RPW * 32 * sizeof(T);  // one tile slot of one group
+    const size_t red_bytes = (size_t)2 * QC_WARPS * 32 * sizeof(T);  // dot and norm partials of one tile slot
+    const size_t budget = (size_t)std::max(0, optin - (int)fa.sharedSizeBytes - 1024);
+    if (budget < NREG * red_bytes) return cudaSuccess;
+    int nsm = std::max(0, max_k - NREG);
+    nsm = (int)std::min<size_t>((size_t)nsm, (budget - NREG * red_bytes) / (ngroups * tile_bytes + red_bytes));
+    nsm = std::min(nsm, 30 - NREG);  // the per-lane chosen mask has 32 bits
+    const size_t dyn = (size_t)ngroups * nsm * tile_bytes + (size_t)(NREG + nsm) * red_bytes;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, QC_THREADS, dyn))) return e;
+    if (per_sm < 1) return cudaSuccess;
+    if ((e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s))) return e;
+    void* args[] = {(void*)&nrow, (void*)&ncol, (void*)&R,   (void*)&npiv,   (void*)&wpt,  (void*)&nsm,
+                    (void*)&best, (void*)&pub,  (void*)&chosen, (void*)&d_piv, (void*)&bar};
+    if ((e = cudaLaunchCooperativeKernel(fn, dim3(sms), dim3(QC_THREADS), args, dyn, s))) return e;
+    *launches += 1;
+    *ran = true;
+    return cudaSuccess;
 }
 
 // R (nrow x ncol, row-major, leading dimension ncol) is overwritten.  aux is
@@ -340,27 +568,22 @@ cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* au
     unsigned char* chosen = base + align256(sizeof(Best) * nblocks_cap(ncol));
     T* q = reinterpret_cast<T*>(chosen + align256((size_t)ncol));
     unsigned* bar = reinterpret_cast<unsigned*>(reinterpret_cast<unsigned char*>(q) + align256(sizeof(double) * nrow));
+    T* pub = reinterpret_cast<T*>(reinterpret_cast<unsigned char*>(bar) + 256);
     cudaMemsetAsync(chosen, 0, ncol, s);
-    // persistent cooperative version when the rows fit the per-thread registers
-    int dev = 0, sms = 0, per_sm = 0, coop = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-    constexpr int RPW = sizeof(T) == 4 ? 64 : 32;  // rows per warp held in registers
-    int wpt = 2;  // >= 2 keeps the named-barrier ids (1 + group) within 1..8
-    while (wpt * RPW < nrow) wpt *= 2;
-    const void* fn = (const void*)qr_persistent_kernel<T, RPW>;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, qr_persistent_kernel<T, RPW>, QC_THREADS, 0);
-    const int gridn = sms * std::min(per_sm, 1);
-    if (coop && per_sm > 0 && wpt <= QC_WARPS && nrow <= QC_MAXROWS && 2 * gridn <= nblocks_cap(ncol)) {
-        Best* bb = best;
-        cudaError_t e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s);
-        if (e) return e;
-        void* args[] = {(void*)&nrow, (void*)&ncol, (void*)&R, (void*)&npiv, (void*)&wpt, (void*)&bb,
-                        (void*)&chosen, (void*)&d_piv, (void*)&bar};
-        e = cudaLaunchCooperativeKernel(fn, dim3(gridn), dim3(QC_THREADS), args, 0, s);
-        *launches += 1;
-        if (e) return e;
+    // persistent cooperative version: float rows <= 512 keep two tiles per group
+    // in registers (32 rows per warp); otherwise shared memory and streaming only
+    bool ran = false;
+    cudaError_t e;
+    if constexpr (sizeof(T) == 4) {
+        if (nrow <= 512)
+            e = qr_persistent_launch<T, 32, 2>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, s, launches, &ran);
+        else
+            e = qr_persistent_launch<T, 64, 0>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, s, launches, &ran);
+    } else {
+        e = qr_persistent_launch<T, 32, 0>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, s, launches, &ran);
+    }
+    if (e) return e;
+    if (ran) {
         unsigned flag = 0;
         if ((e = cudaMemcpyAsync(&flag, bar + 2, sizeof(unsigned), cudaMemcpyDeviceToHost, s))) return e;
         if ((e = cudaStreamSynchronize(s))) return e;

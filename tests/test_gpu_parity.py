@@ -134,6 +134,20 @@ def test_scdm_pivots_are_a_valid_qrcp_order(small_loc, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_scdm_pivots_are_deterministic(prec):
+    # the persistent QR runs on every SM with a grid barrier per step; repeated
+    # runs (and a second context) must select the same pivots
+    # 200 rows x 46,656 columns: tiles in registers and in shared memory
+    sysm = synth.small_localized_system(13, (23.5, 23.5, 23.5), (72, 72, 72), 40.0, 150, 200)
+    out = []
+    for _ in range(2):
+        with make_ctx(sysm, prec) as ctx:
+            out.append([ctx.localize(2) for _ in range(2)])
+    ref = out[0][0]
+    assert all((p == ref).all() for run in out for p in run)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
 def test_scdm_rotation_with_imposed_pivots(small_loc, prec):
     g, occ, _ = oracle_orbitals(small_loc)
     piv, u_ref, w_ref = O.scdm(g, occ, 2)
