@@ -149,12 +149,12 @@ lace_status ensure_orbital_buffers(lace_ctx* c, int n_occ, int n_extra) {
     return LACE_OK;
 }
 
-// Loewdin: dst[n] = sum_k src[k] X[k][n], X = S^{-1/2}, S = dV src src^T.
+// Loewdin coefficients: X = S^{-1/2}, S = dV src src^T (FP64 Newton-Schulz;
+// mixed path: FP32 Newton-Schulz and one FP64 first-order refinement).
 template <typename T>
-lace_status lowdin_rows(lace_ctx* c, const T* src, int n, T* dst, Launch& L) {
+lace_status lowdin_coeffs(lace_ctx* c, const T* src, int n, double* X, Launch& L) {
     const size_t ng = c->g.ng;
     double* S = c->m(MS_A);
-    double* X = c->m(MS_B);
     CK(gemm_rows<T>(n, n, ng, src, ng, src, ng, c->g.dv, false, S, n, c->work.as<double>(),
                     c->work.bytes / sizeof(double), c->stream, &L.n),
        "loewdin overlap");
@@ -167,44 +167,89 @@ lace_status lowdin_rows(lace_ctx* c, const T* src, int n, T* dst, Launch& L) {
         if (ok) CK(lowdin_refine(n, X, S, c->m(MS_NSWORK), c->stream, &L.n), "loewdin refine");
     }
     if (!ok) return fail(c, LACE_ERR_NOT_PD, "overlap matrix is singular or ill-conditioned (inverse square root did not converge)");
-    CK(gemm_combine<T>(n, ng, n, src, ng, X, n, 0.0, dst, ng, c->stream, &L.n), "loewdin combine");
     return LACE_OK;
 }
 
+// Loewdin: dst[n] = sum_k src[k] X[k][n], X = S^{-1/2}, S = dV src src^T.
+template <typename T>
+lace_status lowdin_rows(lace_ctx* c, const T* src, int n, T* dst, Launch& L) {
+    double* X = c->m(MS_B);
+    lace_status st = lowdin_coeffs<T>(c, src, n, X, L);
+    if (st) return st;
+    CK(gemm_combine<T>(n, c->g.ng, n, src, c->g.ng, X, n, 0.0, dst, c->g.ng, c->stream, &L.n), "loewdin combine");
+    return LACE_OK;
+}
+
+// The occupied orbitals stay raw (canon buffer) with their Loewdin
+// coefficients X: localisation folds X into its rotation (one combination
+// over the grid instead of two), and psi is formed only when needed.
 template <typename T>
 lace_status load_impl(lace_ctx* c, const double* d_phi64, int n_occ, int n_extra, int ortho) {
     Launch L{c};
     const size_t ng = c->g.ng;
-    const int n_p = n_occ + n_extra;
     T* psi = c->psi.as<T>();
-    T* canon = c->canon.as<T>();
-    // working-precision copy of the input into W (used as staging)
-    T* raw = c->W.as<T>();
-    CK(convert<double, T>(d_phi64, raw, (size_t)n_p * ng, c->stream, &L.n), "load convert");
+    T* raw = c->canon.as<T>();
+    double* X = c->m(MS_X);
+    CK(convert<double, T>(d_phi64, raw, (size_t)n_occ * ng, c->stream, &L.n), "load convert");
+    c->x_identity = !ortho;
+    c->psi_occ_ready = false;
     if (ortho) {
-        lace_status st = lowdin_rows<T>(c, raw, n_occ, canon, L);
+        lace_status st = lowdin_coeffs<T>(c, raw, n_occ, X, L);
         if (st) return st;
-        if (n_extra > 0) {
-            T* ex_raw = raw + (size_t)n_occ * ng;
-            double* C = c->m(MS_A);
-            // C[k][e] = -dV <occ_k, extra_e>; extra -= sum_k occ_k <occ_k, extra_e>
-            CK(gemm_rows<T>(n_occ, n_extra, ng, canon, ng, ex_raw, ng, -c->g.dv, false, C, n_extra,
-                            c->work.as<double>(), c->work.bytes / sizeof(double), c->stream, &L.n),
+    }
+    if (n_extra > 0) {
+        T* ex_raw = c->W.as<T>();  // staging
+        CK(convert<double, T>(d_phi64 + (size_t)n_occ * ng, ex_raw, (size_t)n_extra * ng, c->stream, &L.n),
+           "load convert");
+        if (ortho) {
+            // extra -= canon (dV canon^T extra), canon = raw X:  coefficients -X X^T G,
+            // G = dV raw^T extra
+            double* G = c->m(MS_A);
+            double* T1 = c->m(MS_B);
+            double* D = c->m(MS_LINV);
+            CK(gemm_rows<T>(n_occ, n_extra, ng, raw, ng, ex_raw, ng, c->g.dv, false, G, n_extra, c->work.as<double>(),
+                            c->work.bytes / sizeof(double), c->stream, &L.n),
                "extras projection");
-            CK(gemm_combine<T>(n_extra, ng, n_occ, canon, ng, C, n_extra, 1.0, ex_raw, ng, c->stream, &L.n),
+            CK(small_gemm_f64(n_occ, n_extra, n_occ, X, n_occ, true, G, n_extra, false, 1.0, 0.0, T1, n_extra,
+                              c->stream, &L.n),
                "extras projection");
-            st = lowdin_rows<T>(c, ex_raw, n_extra, psi + (size_t)n_occ * ng, L);
+            CK(small_gemm_f64(n_occ, n_extra, n_occ, X, n_occ, false, T1, n_extra, false, -1.0, 0.0, D, n_extra,
+                              c->stream, &L.n),
+               "extras projection");
+            CK(gemm_combine<T>(n_extra, ng, n_occ, raw, ng, D, n_extra, 1.0, ex_raw, ng, c->stream, &L.n),
+               "extras projection");
+            lace_status st = lowdin_rows<T>(c, ex_raw, n_extra, psi + (size_t)n_occ * ng, L);
             if (st) return st;
-        }
-    } else {
-        CK(cudaMemcpyAsync(canon, raw, (size_t)n_occ * ng * sizeof(T), cudaMemcpyDeviceToDevice, c->stream), "load");
-        if (n_extra > 0)
-            CK(cudaMemcpyAsync(psi + (size_t)n_occ * ng, raw + (size_t)n_occ * ng, (size_t)n_extra * ng * sizeof(T),
+        } else {
+            CK(cudaMemcpyAsync(psi + (size_t)n_occ * ng, ex_raw, (size_t)n_extra * ng * sizeof(T),
                                cudaMemcpyDeviceToDevice, c->stream),
                "load");
+        }
     }
-    CK(cudaMemcpyAsync(psi, canon, (size_t)n_occ * ng * sizeof(T), cudaMemcpyDeviceToDevice, c->stream), "load");
     return LACE_OK;
+}
+
+// psi[0 .. n_occ) = canon X, the canonical orbitals (when not localised).
+template <typename T>
+lace_status materialize_impl(lace_ctx* c) {
+    Launch L{c};
+    const size_t ng = c->g.ng;
+    const int n = c->n_occ;
+    if (c->x_identity) {
+        CK(cudaMemcpyAsync(c->psi.p, c->canon.p, (size_t)n * ng * sizeof(T), cudaMemcpyDeviceToDevice, c->stream),
+           "orbitals");
+    } else {
+        CK(gemm_combine<T>(n, ng, n, c->canon.as<T>(), ng, c->m(MS_X), n, 0.0, c->psi.as<T>(), ng, c->stream, &L.n),
+           "loewdin combine");
+    }
+    return LACE_OK;
+}
+
+lace_status materialize_psi(lace_ctx* c) {
+    if (c->psi_occ_ready) return LACE_OK;
+    lace_status st = c->prec == LACE_FP64 ? materialize_impl<double>(c) : materialize_impl<float>(c);
+    if (st == LACE_OK) c->psi_occ_ready = true;
+    return st;
 }
 
 lace_status load_common(lace_ctx* c, const double* phi, bool dev, int n_occ, int n_extra, int ortho) {
@@ -241,7 +286,8 @@ lace_status localize_impl(lace_ctx* c, int stride, const long long* imposed) {
     Launch L{c};
     const size_t ng = c->g.ng;
     const int n = c->n_occ;
-    T* canon = c->canon.as<T>();
+    T* raw = c->canon.as<T>();
+    const double* X = c->m(MS_X);
     CK(c->pivfull.ensure(sizeof(long long) * n), "alloc pivots");
     long long* d_full = c->pivfull.as<long long>();
     if (!imposed) {
@@ -255,7 +301,15 @@ lace_status localize_impl(lace_ctx* c, int stride, const long long* imposed) {
         CK(c->aux.ensure(qrcp_aux_bytes(n, (int)ncol_sz)), "alloc qrcp aux");
         CK(c->piv.ensure(sizeof(int) * n), "alloc pivots");
         T* R = c->work.as<T>();
-        CK(gather_subsample<T>(c->g, stride, canon, n, R, &ncol, c->stream, &L.n), "subsample");
+        // the canonical orbitals on the subsample: (raw on the subsample) X
+        if (c->x_identity) {
+            CK(gather_subsample<T>(c->g, stride, raw, n, R, &ncol, c->stream, &L.n), "subsample");
+        } else {
+            T* tmp = c->W.as<T>();
+            CK(gather_subsample<T>(c->g, stride, raw, n, tmp, &ncol, c->stream, &L.n), "subsample");
+            CK(gemm_combine<T>(n, (size_t)ncol, n, tmp, (size_t)ncol, X, n, 0.0, R, (size_t)ncol, c->stream, &L.n),
+               "subsample");
+        }
         int timeout = 0;
         CK(qrcp_pivots<T>(n, ncol, R, n, c->piv.as<int>(), c->aux.p, &timeout, c->stream, &L.n), "qrcp");
         if (timeout) return fail(c, LACE_ERR_TIMEOUT, "pivoted QR: a grid barrier wait timed out");
@@ -278,7 +332,14 @@ lace_status localize_impl(lace_ctx* c, int stride, const long long* imposed) {
     double* B = c->m(MS_B);
     double* Bmh = c->m(MS_LINV);
     double* U = c->m(MS_U);
-    CK(gather_columns<T>(canon, ng, n, d_full, n, phic, c->stream, &L.n), "gather phi_C");
+    // phi_C = canonical orbitals at the pivot points = (raw at the points) X
+    if (c->x_identity) {
+        CK(gather_columns<T>(raw, ng, n, d_full, n, phic, c->stream, &L.n), "gather phi_C");
+    } else {
+        double* phir = c->m(MS_E);
+        CK(gather_columns<T>(raw, ng, n, d_full, n, phir, c->stream, &L.n), "gather phi_C");
+        CK(small_gemm_f64(n, n, n, phir, n, false, X, n, false, 1.0, 0.0, phic, n, c->stream, &L.n), "gather phi_C");
+    }
     // B = phi_C phi_C^T  (points x points)
     CK(small_gemm_f64(n, n, n, phic, n, false, phic, n, true, 1.0, 0.0, B, n, c->stream, &L.n), "scdm B");
     int ok = 0;
@@ -292,8 +353,15 @@ lace_status localize_impl(lace_ctx* c, int stride, const long long* imposed) {
     CK(small_gemm_f64(n, n, n, phic, n, true, Bmh, n, false, 1.0, 0.0, U, n, c->stream, &L.n), "scdm U");
     // mixed path: restore exact orthogonality of U in FP64 (U <- U (I - (U^T U - I)/2))
     if (c->prec != LACE_FP64) CK(lowdin_refine(n, U, nullptr, c->m(MS_NSWORK), c->stream, &L.n), "scdm refine");
-    // w = canon U
-    CK(gemm_combine<T>(n, ng, n, canon, ng, U, n, 0.0, c->psi.as<T>(), ng, c->stream, &L.n), "scdm rotate");
+    // w = canon U = raw (X U): one combination over the grid
+    const double* Cf = U;
+    if (!c->x_identity) {
+        double* XU = c->m(MS_LINVT);
+        CK(small_gemm_f64(n, n, n, X, n, false, U, n, false, 1.0, 0.0, XU, n, c->stream, &L.n), "scdm rotate");
+        Cf = XU;
+    }
+    CK(gemm_combine<T>(n, ng, n, raw, ng, Cf, n, 0.0, c->psi.as<T>(), ng, c->stream, &L.n), "scdm rotate");
+    c->psi_occ_ready = true;
     return LACE_OK;
 }
 
@@ -697,6 +765,10 @@ lace_status lace_screen(lace_ctx* c, double s_thr, long long* n_pairs_out) {
     if (!(s_thr >= 0.0)) return fail(c, LACE_ERR_ARG, "threshold must be >= 0");
     cudaSetDevice(c->device);
     c->screened = c->applied = c->ace = false;
+    {
+        lace_status st = materialize_psi(c);
+        if (st) return st;
+    }
     ev_begin(c, ST_SCREEN);
     lace_status st = c->prec == LACE_FP64 ? screen_impl<double>(c, s_thr) : screen_impl<float>(c, s_thr);
     if (st) return st;
@@ -715,6 +787,10 @@ lace_status lace_apply_exchange(lace_ctx* c, double* W_out, double* ex_out) {
     if (!c->loaded) return fail(c, LACE_ERR_STATE, "load orbitals before applying the exchange");
     cudaSetDevice(c->device);
     c->applied = false;
+    {
+        lace_status st = materialize_psi(c);
+        if (st) return st;
+    }
     ev_begin(c, ST_EXCHANGE);
     lace_status st = c->prec == LACE_FP64 ? apply_impl<double>(c) : apply_impl<float>(c);
     ev_end(c, ST_EXCHANGE);
@@ -837,7 +913,13 @@ lace_status lace_get_orbitals(lace_ctx* c, int which, double* out, long long cou
     if (count < need) return fail(c, LACE_ERR_ARG, "output buffer too small");
     const void* src = nullptr;
     switch (which) {
-        case LACE_ORB_PSI: src = c->psi.p; break;
+        case LACE_ORB_PSI: {
+            cudaSetDevice(c->device);
+            lace_status st = materialize_psi(c);
+            if (st) return st;
+            src = c->psi.p;
+            break;
+        }
         case LACE_ORB_W:
             if (!c->applied) return fail(c, LACE_ERR_STATE, "apply the exchange first");
             src = c->W.p;

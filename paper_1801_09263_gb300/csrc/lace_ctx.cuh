@@ -36,7 +36,7 @@ struct DevBuf {
 enum Stage { ST_LOAD = 0, ST_LOCALIZE, ST_SCREEN, ST_EXCHANGE, ST_ACE_BUILD, ST_ACE_APPLY, ST_PAIRCONV, ST_COUNT };
 
 // Small-matrix slots inside lace_ctx::mat (each mslot doubles).
-enum MatSlot { MS_S = 0, MS_M, MS_MSYM, MS_L, MS_LINV, MS_LINVT, MS_E, MS_U, MS_A, MS_B, MS_NSWORK, MS_COUNT_BASE };
+enum MatSlot { MS_S = 0, MS_M, MS_MSYM, MS_L, MS_LINV, MS_LINVT, MS_E, MS_U, MS_A, MS_B, MS_X, MS_NSWORK, MS_COUNT_BASE };
 // MS_NSWORK takes 5 slots (Newton-Schulz work)
 constexpr int kMatSlots = MS_NSWORK + 5 + 1;
 
@@ -60,10 +60,12 @@ struct lace_ctx {
 
     int n_occ = 0, n_extra = 0, n_p = 0;
     bool loaded = false, localized = false, screened = false, applied = false, ace = false;
+    bool x_identity = false;     // X = I (loaded without orthonormalisation)
+    bool psi_occ_ready = false;  // psi[0 .. n_occ) holds canon X (or its SCDM rotation)
     double s_thr = 0.0;
 
     DevBuf psi;     // [n_p][ng] working precision: [w (localised occupied) ; extras]
-    DevBuf canon;   // [n_occ][ng] canonical orthonormal occupied orbitals
+    DevBuf canon;   // [n_occ][ng] the raw occupied orbitals; the canonical (Loewdin) ones are canon X, X in MS_X
     DevBuf W;       // [n_p][ng]
     DevBuf xi;      // [n_p][ng]
     DevBuf stage64; // [rows][ng] FP64 staging (uploads, conversions)
