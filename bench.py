@@ -60,6 +60,7 @@ def parse():
     p.add_argument("--batched", action="store_true",
                    help="only the batched uneven instances (48 systems, persistent launch in a CUDA graph)")
     p.add_argument("--no-batched", action="store_true", help="skip the batched sample of the default run")
+    p.add_argument("--batch-instances", type=int, default=48, help="instances of --batched (fewer for ncu captures)")
     return p.parse_args()
 
 
@@ -596,7 +597,8 @@ def main():
         from paper_1801_09263_gb300.build import build
 
         build()
-        print(json.dumps({"batched": run_batched(local, steps=max(1, args.steps))}), flush=True)
+        print(json.dumps({"batched": run_batched(local, steps=max(1, args.steps), n_instances=args.batch_instances)}),
+              flush=True)
     elif args.serving:
         from paper_1801_09263_gb300.build import build
 
