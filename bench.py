@@ -61,6 +61,8 @@ def parse():
                    help="only the batched uneven instances (48 systems, persistent launch in a CUDA graph)")
     p.add_argument("--no-batched", action="store_true", help="skip the batched sample of the default run")
     p.add_argument("--batch-instances", type=int, default=48, help="instances of --batched (fewer for ncu captures)")
+    p.add_argument("--no-ace96", action="store_true", help="skip the 96^3 ACE build comparison of the default run")
+    p.add_argument("--ace96", action="store_true", help="only the 96^3 ACE build comparison")
     return p.parse_args()
 
 
@@ -319,6 +321,8 @@ def run_lace(args, rank, world, local):
                                      "p99": round(float(np.percentile(step_ms, 99)), 3)}
     if not args.no_batched:
         result["batched"] = run_batched(local)
+    if not args.no_ace96:
+        result["ace_96"] = run_ace96(local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(sysm, budget_s=15.0)
     if world > 1:
@@ -513,6 +517,57 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
     }
 
 
+def run_ace96(local, reps=3):
+    """ACE build and apply on the 96^3 workload: 256 water-like occupied + 128
+    extra orbitals (N_P = 384), S_thr = 1e-3.  Mixed precision (tcgen05 3xBF16
+    M' and xi, FP64 Cholesky) against the plain FP64 GPU form on the same
+    pivots: ACE build ms (CUDA events), E_x, and the relative difference of
+    K_ACE on 8 random probes."""
+    import synth
+    import torch
+
+    import paper_1801_09263_gb300 as lace
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    sysm = synth.config3_water_like_with_extras()
+    phi = torch.from_numpy(sysm.phi).to(dev)
+    probe = torch.from_numpy(np.random.default_rng(11).standard_normal((8,) + sysm.shape)).to(dev)
+    out = {}
+    piv = None
+    for name, prec in (("mixed", lace.LACE_MIXED), ("fp64", lace.LACE_FP64)):
+        with lace.Lace(local, prec) as c:
+            c.set_stream(torch.cuda.current_stream(dev).cuda_stream)
+            c.set_cell(sysm.cell, sysm.shape, sysm.ecut)
+            c.load_orbitals_dev(phi, 256, 128, True)
+            if piv is None:
+                piv = c.localize(STRIDE)
+            else:
+                c.set_pivots(piv)
+            npairs = c.screen(S_THR)
+            c.apply_exchange(want_W=False)
+            builds = []
+            for _ in range(reps):
+                c.build_ace(lace.LACE_SYM_AVG)
+                builds.append(c.get_timings()["ace_build"])
+            kp = torch.empty_like(probe)
+            c.apply_ace_dev(probe, kp)
+            torch.cuda.synchronize(dev)
+            t = c.get_timings()
+            out[name] = {"ace_build_ms": round(statistics.median(builds), 3), "ace_apply_ms_8": round(t["ace_apply"], 3),
+                         "pairconv_ms": round(t["pairconv_kernels"], 3), "n_pairs": npairs,
+                         "E_x_Ha": c.exchange_energy(1.0), "kprobe": kp}
+    dk = (out["mixed"]["kprobe"] - out["fp64"]["kprobe"]).abs().max() / out["fp64"]["kprobe"].abs().max()
+    for v in out.values():
+        del v["kprobe"]
+    return {"workload": "water-like L=23.5 bohr, 96^3, 256 occupied + 128 extra orbitals (N_P=384), SCDM stride 2, "
+                        "S_thr=1e-3; both forms on the same pivots",
+            "mixed": out["mixed"], "fp64_gpu": out["fp64"],
+            "ace_build_speedup_vs_fp64": round(out["fp64"]["ace_build_ms"] / out["mixed"]["ace_build_ms"], 1),
+            "dE_x_mixed_vs_fp64_Ha": out["mixed"]["E_x_Ha"] - out["fp64"]["E_x_Ha"],
+            "max_rel_dK_psi_mixed_vs_fp64": float(dk)}
+
+
 def run_batched(local, steps=5, n_instances=48):
     """Batched uneven instances: 48 cubic cells (L ~ U[10, 20] bohr, 2/3/5-smooth
     grids in [32, 64], N log-uniform in [16, 128], S_thr = 1e-3), localised
@@ -593,6 +648,11 @@ def main():
     rank, world, local = dist_env()
     if args.profile_pairconv:
         run_profile(args, local)
+    elif args.ace96:
+        from paper_1801_09263_gb300.build import build
+
+        build()
+        print(json.dumps({"ace_96": run_ace96(local)}), flush=True)
     elif args.batched:
         from paper_1801_09263_gb300.build import build
 
