@@ -35,6 +35,9 @@ extern "C" {
 
 typedef struct lace_ctx lace_ctx; /* opaque; created and freed by the library */
 
+/* Interaction kernels of lace_set_kernel. */
+typedef enum { LACE_KERNEL_COULOMB = 0, LACE_KERNEL_ERFC = 1 } lace_kernel;
+
 typedef enum {
     LACE_OK = 0,
     LACE_ERR_ARG = 1,         /* bad pointer, size or option value */
@@ -88,6 +91,18 @@ lace_status lace_set_stream(lace_ctx* ctx, void* stream);
  * the caller's records (the kernel uses every G of the grid).  Resets all
  * loaded state. */
 lace_status lace_set_cell(lace_ctx* ctx, const double cell[3], int n1, int n2, int n3, double ecut_ha);
+
+/* Interaction kernel of the exchange operator (default: LACE_KERNEL_COULOMB,
+ * alpha = 1).  K(G) = alpha 4 pi/|G|^2 with K(0) = 0 (Coulomb, Eq. 2), or, for
+ * range-separated hybrids such as HSE (Sec. 4), the erfc-screened short-range
+ * kernel K(G) = alpha 4 pi/|G|^2 (1 - exp(-|G|^2/(4 omega^2))) with
+ * K(0) = alpha pi/omega^2 (the paper cites HSE without its formula; this is
+ * the standard one).  alpha is the exact-exchange fraction (0.25 for PBE0 and
+ * HSE06): W and E_x scale with it.  omega (bohr^-1) must be > 0 for
+ * LACE_KERNEL_ERFC.  Invalidates the exchange and ACE state; may come before
+ * or after lace_set_cell.  The allocation-free call below always uses the
+ * bare Coulomb kernel. */
+lace_status lace_set_kernel(lace_ctx* ctx, int kind, double omega, double alpha);
 
 /* Load n_occ occupied orbitals followed by n_extra extra (virtual) orbitals
  * from host FP64 memory phi[(n_occ+n_extra)][n1][n2][n3] (copied).  With

@@ -15,7 +15,9 @@ Every function states the passage of the paper it follows.  Conventions
   Omega = abc, Ng = n1 n2 n3, dV = Omega / Ng.  Orbitals are normalised so
   that dV * sum_r phi(r)^2 = 1.  Inner products carry dV.
 * Coulomb kernel K(G) = 4 pi / |G|^2 on every G of the grid (no cutoff
-  sphere), with K(0) = 0 (the G = 0 term is dropped; nothing else).
+  sphere), with K(0) = 0 (the G = 0 term is dropped; nothing else).  The
+  erfc-screened kernel of range-separated hybrids (Grid.kernel = "erfc") is
+  finite at G = 0; either kernel is scaled by the exchange fraction alpha.
 * Forward FFT unscaled, inverse FFT scaled by 1/Ng (numpy convention).
 
 The FFT (scipy.fft), symmetric eigensolver, Cholesky factorisation and
@@ -37,6 +39,8 @@ import scipy.linalg
 __all__ = [
     "Grid",
     "coulomb_kernel",
+    "screened_kernel",
+    "interaction_kernel",
     "pair_potential",
     "lowdin",
     "orthonormalize_extras",
@@ -59,10 +63,18 @@ _WORKERS = max(1, len(os.sched_getaffinity(0)))
 
 @dataclass(frozen=True)
 class Grid:
-    """Orthorhombic periodic cell and its real-space grid."""
+    """Orthorhombic periodic cell and its real-space grid, and the interaction
+    kernel of the exchange operator: "coulomb" (Eq. 2) or "erfc" (the
+    short-range screened kernel of range-separated hybrids such as HSE,
+    Sec. 4, with range-separation parameter `screening` (omega of HSE, in
+    bohr^-1; not the cell volume omega below), scaled by the exact-exchange
+    fraction alpha."""
 
     cell: tuple  # (a, b, c) in bohr
     shape: tuple  # (n1, n2, n3)
+    kernel: str = "coulomb"
+    screening: float = 0.0
+    alpha: float = 1.0
 
     @property
     def omega(self) -> float:
@@ -105,6 +117,34 @@ def coulomb_kernel(grid: Grid) -> np.ndarray:
     return k
 
 
+def screened_kernel(grid: Grid, omega: float) -> np.ndarray:
+    """K(G) = 4 pi / |G|^2 (1 - exp(-|G|^2 / (4 omega^2))), K(0) = pi / omega^2.
+
+    The Fourier transform of erfc(omega r) / r, the short-range part of the
+    Coulomb interaction that range-separated hybrids such as HSE keep in the
+    exact exchange (the paper applies L-ACE to HSE in Sec. 4 without giving
+    the kernel; this is the standard one).  Finite at G = 0: the limit of
+    4 pi (1 - exp(-x)) / |G|^2 with x = |G|^2 / (4 omega^2) is pi / omega^2.
+    """
+    g2 = g_squared(grid)
+    k = np.empty_like(g2)
+    nz = g2 > 0
+    k[nz] = 4.0 * np.pi / g2[nz] * -np.expm1(-g2[nz] / (4.0 * omega * omega))
+    k[~nz] = np.pi / (omega * omega)
+    return k
+
+
+def interaction_kernel(grid: Grid) -> np.ndarray:
+    """The grid's kernel: coulomb_kernel or screened_kernel, times alpha."""
+    if grid.kernel == "coulomb":
+        k = coulomb_kernel(grid)
+    elif grid.kernel == "erfc":
+        k = screened_kernel(grid, grid.screening)
+    else:
+        raise ValueError(f"unknown kernel {grid.kernel!r}")
+    return k * grid.alpha if grid.alpha != 1.0 else k
+
+
 def pair_potential(grid: Grid, rho: np.ndarray) -> np.ndarray:
     """Potential of a (batch of) real pair densities: v = IFFT(K * FFT(rho)).
 
@@ -112,7 +152,7 @@ def pair_potential(grid: Grid, rho: np.ndarray) -> np.ndarray:
     with FFTs as the paper describes for plane waves (Sec. 2).  rho has shape
     (..., n1, n2, n3).
     """
-    k = coulomb_kernel(grid)
+    k = interaction_kernel(grid)
     n1, n2, n3 = grid.shape
     kh = k[:, :, : n3 // 2 + 1]  # real-to-complex half spectrum
     axes = (-3, -2, -1)
@@ -303,7 +343,7 @@ def exchange_energy_gspace(grid: Grid, w_occ: np.ndarray, keep_occ: np.ndarray, 
 
     Parseval form of the same energy; an independent route used by tests.
     """
-    k = coulomb_kernel(grid)
+    k = interaction_kernel(grid)
     n = w_occ.shape[0]
     tot = 0.0
     for i in range(n):

@@ -18,6 +18,7 @@ LACE_SYM_AVG, LACE_SYM_UPPER, LACE_SYM_LOWER = 0, 1, 2
 MAT_OVERLAP_MODULI, MAT_EXCHANGE, MAT_CHOLESKY, MAT_PAIR_ENERGY, MAT_SCDM_U = 0, 1, 2, 3, 4
 ORB_PSI, ORB_W, ORB_XI = 0, 1, 2
 REQ_REBUILD, REQ_APPLY = 0, 1
+KERNEL_COULOMB, KERNEL_ERFC = 0, 1
 STAGES = ("load", "localize", "screen", "exchange", "ace_build", "ace_apply", "pairconv_kernels")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -76,6 +77,7 @@ def load_library(build_if_missing: bool = False):
         "lace_get_timings": ([P, P, I], I),
         "lace_get_launch_count": ([P, P], I),
         "lace_get_device_bytes": ([P, P], I),
+        "lace_set_kernel": ([P, I, D, D], I),
         "lace_server_create": ([C.POINTER(P), I, I, I, I, C.c_ulonglong], I),
         "lace_server_destroy": ([P], I),
         "lace_server_add_system": ([P, P, I, I, I, D, I, I, D, P], I),
@@ -165,6 +167,10 @@ class Lace:
         self._check(self.lib.lace_set_cell(self.h, _ptr(c), int(shape[0]), int(shape[1]), int(shape[2]),
                                            float(ecut)), "lace_set_cell")
         self.shape = tuple(int(s) for s in shape)
+
+    def set_kernel(self, kind: int = KERNEL_COULOMB, omega: float = 0.0, alpha: float = 1.0):
+        """Coulomb (Eq. 2) or erfc-screened short-range kernel, times the exchange fraction alpha."""
+        self._check(self.lib.lace_set_kernel(self.h, int(kind), float(omega), float(alpha)), "lace_set_kernel")
 
     def load_orbitals(self, phi, n_occ: int, n_extra: int = 0, orthonormalize: bool = True):
         a = _f64(phi)

@@ -105,16 +105,31 @@ lace_status build_tables(lace_ctx* c) {
     fill(gx, n1, c->g.cell[0]);
     fill(gy, n2, c->g.cell[1]);
     fill(gz, n3, c->g.cell[2]);
+    // Kernels (scaled by the exchange fraction alpha):
+    //   Coulomb:        4 pi / |G|^2, K(0) = 0;
+    //   erfc-screened:  4 pi / |G|^2 (1 - exp(-|G|^2 / (4 omega^2))), the
+    //                   short-range part of HSE, K(0) = pi / omega^2.
     std::vector<float> kt(c->g.ng);
+    std::vector<double> ktd(c->g.ng);
     const double scale = 4.0 * M_PI / (double)c->g.ng;
+    const bool erfc_k = c->kernel_kind == LACE_KERNEL_ERFC;
+    const double w2 = c->kernel_omega * c->kernel_omega;
     for (int x = 0; x < n1; ++x)
         for (int y = 0; y < n2; ++y)
             for (int z = 0; z < n3; ++z) {
                 const double gg = gx[x] + gy[y] + gz[z];
-                kt[((size_t)x * n2 + y) * n3 + z] = gg > 0.0 ? (float)(scale / gg) : 0.0f;
+                double k;
+                if (!erfc_k) k = gg > 0.0 ? scale / gg : 0.0;
+                else k = gg > 0.0 ? scale / gg * -std::expm1(-gg / (4.0 * w2)) : M_PI / w2 / (double)c->g.ng;
+                k *= c->kernel_alpha;
+                const size_t i = ((size_t)x * n2 + y) * n3 + z;
+                ktd[i] = k;
+                kt[i] = (float)k;
             }
     CK(c->ktab_f.ensure(c->g.ng * sizeof(float)), "tables");
     CK(cudaMemcpy(c->ktab_f.p, kt.data(), c->g.ng * sizeof(float), cudaMemcpyHostToDevice), "tables");
+    CK(c->ktab_d.ensure(c->g.ng * sizeof(double)), "tables");
+    CK(cudaMemcpy(c->ktab_d.p, ktd.data(), c->g.ng * sizeof(double), cudaMemcpyHostToDevice), "tables");
     return LACE_OK;
 }
 
@@ -122,6 +137,7 @@ template <typename T> FFTTables<T> tables(lace_ctx* c);
 template <> FFTTables<double> tables<double>(lace_ctx* c) {
     FFTTables<double> t;
     for (int a = 0; a < 3; ++a) { t.tw[a] = c->tw_d[a].as<double2>(); t.g2[a] = c->g2_d[a].as<double>(); }
+    t.ktab = c->ktab_d.as<double>();
     return t;
 }
 template <> FFTTables<float> tables<float>(lace_ctx* c) {
@@ -618,7 +634,7 @@ size_t predict_ctx_bytes(int prec, const int n[3], int n_occ, int n_extra, int n
     b += mslot * kMatSlots * sizeof(double) + work + qrcp_aux_bytes(n_occ, (int)ncol);
     b += maxp * 8 + (maxp + 1) / 2 * sizeof(PairGrid);
     b += std::max(batch * ng * 2 * eb, 2 * na * ng * eb) + batch * n[0] * 2 * sizeof(double);
-    b += 2 * na * ng * sizeof(double) + ng * sizeof(float);
+    b += 2 * na * ng * sizeof(double) + ng * (sizeof(float) + sizeof(double));
     return b;
 }
 
@@ -677,6 +693,7 @@ lace_status lace_destroy(lace_ctx* c) {
     for (DevBuf* b : bufs) b->release();
     for (int a = 0; a < 3; ++a) { c->tw_d[a].release(); c->tw_f[a].release(); c->g2_d[a].release(); c->g2_f[a].release(); }
     c->ktab_f.release();
+    c->ktab_d.release();
     for (auto& e : c->ev) if (e) cudaEventDestroy(e);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
@@ -715,6 +732,20 @@ lace_status lace_set_cell(lace_ctx* c, const double cell[3], int n1, int n2, int
     c->g = g;
     c->have_cell = true;
     c->loaded = c->localized = c->screened = c->applied = c->ace = false;
+    return build_tables(c);
+}
+
+lace_status lace_set_kernel(lace_ctx* c, int kind, double omega, double alpha) {
+    if (!c) return LACE_ERR_ARG;
+    if (kind != LACE_KERNEL_COULOMB && kind != LACE_KERNEL_ERFC) return fail(c, LACE_ERR_ARG, "unknown kernel");
+    if (kind == LACE_KERNEL_ERFC && !(omega > 0.0)) return fail(c, LACE_ERR_ARG, "omega must be > 0");
+    if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(c, LACE_ERR_ARG, "alpha must be > 0");
+    c->kernel_kind = kind;
+    c->kernel_omega = omega;
+    c->kernel_alpha = alpha;
+    c->applied = c->ace = false;
+    if (!c->have_cell) return LACE_OK;
+    cudaSetDevice(c->device);
     return build_tables(c);
 }
 
@@ -966,7 +997,7 @@ lace_status lace_get_device_bytes(lace_ctx* c, unsigned long long* bytes_out) {
     if (!c || !bytes_out) return LACE_ERR_ARG;
     const DevBuf* bufs[] = {&c->psi,   &c->canon, &c->W,      &c->xi,    &c->stage64, &c->scratch, &c->work,
                             &c->aux,   &c->mat,   &c->pairs,  &c->counts, &c->grids,  &c->epart,   &c->flag,
-                            &c->piv,   &c->pivfull, &c->exd,  &c->aceio, &c->ktab_f};
+                            &c->piv,   &c->pivfull, &c->exd,  &c->aceio, &c->ktab_f, &c->ktab_d};
     unsigned long long b = 0;
     for (const DevBuf* d : bufs) b += d->bytes;
     for (int a = 0; a < 3; ++a) b += c->tw_d[a].bytes + c->tw_f[a].bytes + c->g2_d[a].bytes + c->g2_f[a].bytes;

@@ -57,6 +57,9 @@ struct lace_ctx {
     GridGeom g{};
     DevBuf tw_d[3], tw_f[3], g2_d[3], g2_f[3];
     DevBuf ktab_f;  // K(G)/Ng rounded once from FP64 (FP32 path)
+    DevBuf ktab_d;  // K(G)/Ng (FP64 path)
+    int kernel_kind = LACE_KERNEL_COULOMB;
+    double kernel_omega = 0.0, kernel_alpha = 1.0;
 
     int n_occ = 0, n_extra = 0, n_p = 0;
     bool loaded = false, localized = false, screened = false, applied = false, ace = false;

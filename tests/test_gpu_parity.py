@@ -244,6 +244,31 @@ def test_ace_on_a_grid_with_an_odd_point_count(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_screened_kernel_exchange_and_ace_match_oracle(small_loc, prec):
+    # erfc-screened short-range kernel (range-separated hybrids, Sec. 4) with the
+    # exchange fraction 0.25; L-ACE on the oracle's pivots
+    w, alpha = 0.4, 0.25
+    g0, occ, extra = oracle_orbitals(small_loc)
+    g = O.Grid(g0.cell, g0.shape, kernel="erfc", screening=w, alpha=alpha)
+    n, ne = small_loc.n_occ, small_loc.n_extra
+    piv, _, wl = O.scdm(g, occ, 2)
+    probe = np.random.default_rng(8).standard_normal((2,) + g.shape)
+    with make_ctx(small_loc, prec) as ctx:
+        ctx.set_kernel(B.KERNEL_ERFC, w, alpha)
+        ctx.set_pivots(piv)
+        ctx.screen(1e-3)
+        keep = keep_from_pairs(ctx.get_pairs(), n, ne)
+        W, ex = ctx.apply_exchange()
+        ctx.build_ace()
+        k_probe = ctx.apply_ace(probe)
+    W_ref, ex_ref, _ = O.apply_exchange(g, wl, extra, keep)
+    assert abs(ex - ex_ref) <= EX_TOL[prec]
+    assert relerr(W, W_ref) < REL_TOL[prec]
+    xi_ref, _, _ = O.ace_build(g, np.concatenate([wl, extra]), W_ref)
+    assert relerr(k_probe, O.ace_apply(g, xi_ref, probe)) < (1e-9 if prec == LACE_FP64 else 5e-5)
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
 def test_ace_exact_on_building_set_without_truncation(small_loc, prec):
     # Sec. 2: ACE equals the exchange operator on the functions used to build it
     with make_ctx(small_loc, prec) as ctx:

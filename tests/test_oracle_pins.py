@@ -29,8 +29,12 @@ def _small(seed=7, shape=(12, 12, 12), n_occ=6, n_extra=0, cell=(9.0, 9.0, 9.0),
 # ---------------------------------------------------------------- Poisson / FFT
 
 
-def _green_bruteforce(cell, shape):
-    """g(d) = (1/Ng) sum_{G != 0} 4 pi/|G|^2 cos(G.d), by explicit sums (no FFT)."""
+def _green_bruteforce(cell, shape, screening=None):
+    """g(d) = (1/Ng) sum_G K(G) cos(G.d), by explicit sums (no FFT).
+
+    Coulomb: K = 4 pi/|G|^2 without G = 0.  screening = w: the erfc kernel,
+    K = 4 pi/|G|^2 (1 - exp(-|G|^2/(4 w^2))) written out term by term, with
+    the G = 0 term pi/w^2."""
     (a, b, c), (n1, n2, n3) = cell, shape
     ng = n1 * n2 * n3
     # enumerate frequencies symmetrically; for even n take -n/2 (cos is even)
@@ -43,7 +47,12 @@ def _green_bruteforce(cell, shape):
                     continue
                 gvec.append((2 * np.pi * m1 / a, 2 * np.pi * m2 / b, 2 * np.pi * m3 / c))
     gvec = np.array(gvec)
-    kern = 4 * np.pi / np.sum(gvec ** 2, axis=1)
+    g2 = np.sum(gvec ** 2, axis=1)
+    kern = 4 * np.pi / g2
+    if screening is not None:
+        kern = kern * (1.0 - np.exp(-g2 / (4 * screening ** 2)))
+        gvec = np.vstack([gvec, np.zeros(3)])
+        kern = np.append(kern, np.pi / screening ** 2)
     d = np.array([(i * a / n1, j * b / n2, k * c / n3)
                   for i in range(n1) for j in range(n2) for k in range(n3)])
     return (np.cos(d @ gvec.T) @ kern / ng).reshape(shape)
@@ -65,6 +74,65 @@ def test_pair_potential_equals_bruteforce_real_space_sum():
                 v_bf[i, j, k] = np.sum(gi * rho)
     v = O.pair_potential(g, rho)
     assert np.max(np.abs(v - v_bf)) <= 1e-12 * np.max(np.abs(v_bf))
+
+
+def test_screened_pair_potential_equals_bruteforce_sum():
+    cell, shape, w = (5.0, 6.5, 7.3), (6, 8, 5), 0.7
+    rng = np.random.default_rng(5)
+    rho = rng.standard_normal(shape)
+    green = _green_bruteforce(cell, shape, screening=w)
+    n1, n2, n3 = shape
+    for alpha in (1.0, 0.25):
+        g = O.Grid(cell, shape, kernel="erfc", screening=w, alpha=alpha)
+        v = O.pair_potential(g, rho)
+        for (i, j, k) in ((0, 0, 0), (3, 5, 2), (5, 7, 4)):
+            gi = green[(i - np.arange(n1)) % n1][:, (j - np.arange(n2)) % n2][:, :, (k - np.arange(n3)) % n3]
+            assert abs(v[i, j, k] - alpha * np.sum(gi * rho)) <= 1e-12 * np.max(np.abs(v))
+
+
+def _erfc_self_energy(a, w):
+    """(ii|ii) for phi = (a/pi)^{3/4} exp(-a r^2/2) with erfc(w r)/r, isolated:
+    the separation of two points of rho = phi^2 is Gaussian with exponent
+    b = a/2, <1/s> = 2 sqrt(b/pi), <erf(w s)/s> = 2 sqrt(mu/pi) with
+    mu = b w^2/(b + w^2), so <erfc(w s)/s> = 2 (sqrt(b) - sqrt(mu)) / sqrt(pi)."""
+    b = a / 2.0
+    mu = b * w * w / (b + w * w)
+    return 2.0 * (np.sqrt(b) - np.sqrt(mu)) / np.sqrt(np.pi)
+
+
+@pytest.mark.parametrize("w", [0.3, 1.0])
+def test_screened_gaussian_self_energy_closed_form(w):
+    # short-range kernel: periodic images contribute erfc(w L)/L (< 1e-16 here),
+    # and the sampled Gaussian is band-limited to exp(-25) on the 64^3 grid
+    a, L, n = 1.0, 20.0, 64
+    phi = _periodic_gaussian_orbital(a, L, n, centre=(0.37 * L, 0.61 * L, 0.18 * L))[None]
+    keep = np.ones((1, 1), dtype=bool)
+    closed = _erfc_self_energy(a, w)
+    for alpha in (1.0, 0.25):
+        g = O.Grid((L, L, L), (n, n, n), kernel="erfc", screening=w, alpha=alpha)
+        _, ex, e = O.apply_exchange(g, phi, None, keep)
+        assert abs(e[0, 0] - alpha * closed) < 1e-10
+        assert abs(ex + 0.5 * alpha * closed) < 1e-10
+        assert abs(O.exchange_energy_gspace(g, phi, keep) + 0.5 * alpha * closed) < 1e-10
+    # w -> 0 approaches the bare Coulomb self-energy sqrt(2a/pi); the screened value is below it
+    assert 0 < closed < np.sqrt(2 * a / np.pi)
+
+
+def test_planted_screening_mistake_is_caught(monkeypatch):
+    """exp(-|G|^2/(2 w^2)) instead of exp(-|G|^2/(4 w^2)) must fail the closed form."""
+    def wrong(grid, omega):
+        g2 = O.lace_oracle.g_squared(grid)
+        k = np.empty_like(g2)
+        nz = g2 > 0
+        k[nz] = 4.0 * np.pi / g2[nz] * -np.expm1(-g2[nz] / (2.0 * omega * omega))
+        k[~nz] = 2.0 * np.pi / (omega * omega)
+        return k
+    monkeypatch.setattr(O.lace_oracle, "screened_kernel", wrong)
+    a, L, n, w = 1.0, 20.0, 48, 0.5
+    phi = _periodic_gaussian_orbital(a, L, n, centre=(10.0, 10.0, 10.0))[None]
+    g = O.Grid((L, L, L), (n, n, n), kernel="erfc", screening=w)
+    _, _, e = O.apply_exchange(g, phi, None, np.ones((1, 1), dtype=bool))
+    assert abs(e[0, 0] - _erfc_self_energy(a, w)) > 1e-3
 
 
 def test_pair_potential_batch_and_odd_sizes():
