@@ -132,6 +132,18 @@ lace_status lace_localize(lace_ctx* ctx, int stride, long long* pivots_out);
  * another implementation on the same point selection. */
 lace_status lace_set_pivots(lace_ctx* ctx, const long long* pivots, int n);
 
+/* Align the localised orbitals to those of the previous call (end of Sec. 2:
+ * aligning each iteration's orbitals to the previous step's lets the SCF
+ * converge to arbitrary precision).  Reading: within their span, rotate them
+ * to the orthonormal set closest to the previous one, w <- w Q with Q the
+ * polar factor of O = dV w prev^T (orthogonal Procrustes); the SCDM rotation
+ * returned by lace_get_matrix(LACE_MAT_SCDM_U) includes Q.  The first call
+ * only records the reference (*aligned_out = 0); later calls rotate
+ * (*aligned_out = 1, nullable) and record the rotated set.  Requires
+ * lace_localize (LACE_ERR_STATE); LACE_ERR_NOT_PD when O is singular (the new
+ * span is nearly orthogonal to the old one). */
+lace_status lace_align_to_previous(lace_ctx* ctx, int* aligned_out);
+
 /* Overlap-of-moduli screen (Eq. 4): an occupied pair (i, k) is dropped when
  * S_ik < s_thr (both u^(ik) and u^(ki) of Eq. 5 go); pairs with an extra
  * orbital are always kept (Sec. 4.1).  s_thr = 0 keeps everything.
@@ -224,11 +236,15 @@ lace_status lace_server_create(lace_server** out, int device, int precision, int
 /* Wait for every queued request, then free all systems.  NULL is accepted. */
 lace_status lace_server_destroy(lace_server* srv);
 
+/* Flags of lace_server_add_system. */
+#define LACE_SYSTEM_ALIGN 1 /* every REBUILD aligns its localised orbitals to the previous ones */
+
 /* Register a resident system (cell, grid and cutoff as lace_set_cell; the
- * orbital counts and screening threshold of its rebuilds).  *system_id_out
- * receives its id.  Nothing is computed until its first REBUILD. */
+ * orbital counts and screening threshold of its rebuilds; flags).
+ * *system_id_out receives its id.  Nothing is computed until its first
+ * REBUILD. */
 lace_status lace_server_add_system(lace_server* srv, const double cell[3], int n1, int n2, int n3, double ecut_ha,
-                                   int n_occ, int n_extra, double s_thr, int* system_id_out);
+                                   int n_occ, int n_extra, double s_thr, int flags, int* system_id_out);
 
 /* Queue a request (lace_request_kind) for a system.  data (host, borrowed
  * until completion) holds n_occ + n_extra orbitals for a REBUILD or n

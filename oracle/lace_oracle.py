@@ -49,6 +49,7 @@ __all__ = [
     "qrcp_pivot_ratios",
     "scdm",
     "overlap_moduli",
+    "align_orbitals",
     "kept_pairs",
     "apply_exchange",
     "apply_exchange_columns",
@@ -277,6 +278,23 @@ def scdm(grid: Grid, phi: np.ndarray, stride: int = 2, pivots=None):
     u = phic.T @ b_mhalf  # (orbitals, orbitals), orthogonal
     w = (u.T @ a).reshape(phi.shape)  # w_m = sum_k phi_k U_km
     return pivots, u, w
+
+
+def align_orbitals(grid: Grid, w: np.ndarray, w_prev: np.ndarray) -> tuple:
+    """Rotate w within its span to the orthonormal set closest to w_prev.
+
+    The paper improves tight SCF convergence by aligning the orbitals of an
+    iteration to those of the previous one (end of Sec. 2).  Reading: the
+    orthogonal Q maximising sum_j <(w Q)_j, prev_j> (orthogonal Procrustes),
+    i.e. the polar factor of O = dV w prev^T, Q = U V^T from O = U S V^T
+    (library SVD).  Returns (Q, aligned orbitals sum_i w_i Q_ij).
+    """
+    n = w.shape[0]
+    a = w.reshape(n, -1)
+    o = grid.dv * (a @ w_prev.reshape(n, -1).T)
+    u, _, vt = np.linalg.svd(o)
+    q = u @ vt
+    return q, (q.T @ a).reshape(w.shape)
 
 
 def overlap_moduli(grid: Grid, w: np.ndarray) -> np.ndarray:

@@ -19,6 +19,7 @@ MAT_OVERLAP_MODULI, MAT_EXCHANGE, MAT_CHOLESKY, MAT_PAIR_ENERGY, MAT_SCDM_U = 0,
 ORB_PSI, ORB_W, ORB_XI = 0, 1, 2
 REQ_REBUILD, REQ_APPLY = 0, 1
 KERNEL_COULOMB, KERNEL_ERFC = 0, 1
+SYSTEM_ALIGN = 1
 STAGES = ("load", "localize", "screen", "exchange", "ace_build", "ace_apply", "pairconv_kernels")
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -78,9 +79,10 @@ def load_library(build_if_missing: bool = False):
         "lace_get_launch_count": ([P, P], I),
         "lace_get_device_bytes": ([P, P], I),
         "lace_set_kernel": ([P, I, D, D], I),
+        "lace_align_to_previous": ([P, P], I),
         "lace_server_create": ([C.POINTER(P), I, I, I, I, C.c_ulonglong], I),
         "lace_server_destroy": ([P], I),
-        "lace_server_add_system": ([P, P, I, I, I, D, I, I, D, P], I),
+        "lace_server_add_system": ([P, P, I, I, I, D, I, I, D, I, P], I),
         "lace_server_submit": ([P, I, I, P, I, P, P], I),
         "lace_server_poll": ([P, LL, I, P, P, P, P, P], I),
         "lace_server_remove_system": ([P, I], I),
@@ -195,6 +197,12 @@ class Lace:
         p = np.ascontiguousarray(pivots, dtype=np.int64)
         self._check(self.lib.lace_set_pivots(self.h, _ptr(p), len(p)), "lace_set_pivots")
 
+    def align_to_previous(self) -> bool:
+        """Rotate the localised orbitals to the previous call's set (True when rotated)."""
+        a = C.c_int(0)
+        self._check(self.lib.lace_align_to_previous(self.h, C.byref(a)), "lace_align_to_previous")
+        return bool(a.value)
+
     def screen(self, s_thr: float) -> int:
         n = C.c_longlong(0)
         self._check(self.lib.lace_screen(self.h, float(s_thr), C.byref(n)), "lace_screen")
@@ -305,12 +313,14 @@ class Server:
     def __exit__(self, *exc):
         self.close()
 
-    def add_system(self, cell, shape, ecut: float, n_occ: int, n_extra: int = 0, s_thr: float = 1e-3) -> int:
+    def add_system(self, cell, shape, ecut: float, n_occ: int, n_extra: int = 0, s_thr: float = 1e-3,
+                   align: bool = False) -> int:
         c = _f64(cell)
         sid = C.c_int(-1)
         self._check(self.lib.lace_server_add_system(self.h, _ptr(c), int(shape[0]), int(shape[1]), int(shape[2]),
                                                     float(ecut), int(n_occ), int(n_extra), float(s_thr),
-                                                    C.byref(sid)), "lace_server_add_system")
+                                                    SYSTEM_ALIGN if align else 0, C.byref(sid)),
+                    "lace_server_add_system")
         self._systems[sid.value] = (tuple(int(x) for x in shape), int(n_occ) + int(n_extra))
         return sid.value
 

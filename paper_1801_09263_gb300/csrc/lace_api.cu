@@ -381,6 +381,39 @@ lace_status localize_impl(lace_ctx* c, int stride, const long long* imposed) {
     return LACE_OK;
 }
 
+// ------------------------------------------------------------------ alignment
+// w <- w Q, Q the polar factor of O = dV w ref^T (orthogonal Procrustes):
+// Q = O (O^T O)^{-1/2}, the FP64 Newton-Schulz inverse square root.
+template <typename T>
+lace_status align_impl(lace_ctx* c) {
+    Launch L{c};
+    const size_t ng = c->g.ng;
+    const int n = c->n_occ;
+    T* w = c->psi.as<T>();
+    T* ref = c->ref.as<T>();
+    double* Om = c->m(MS_A);
+    double* P = c->m(MS_B);
+    double* Pmh = c->m(MS_LINV);
+    double* Q = c->m(MS_LINVT);
+    CK(gemm_rows<T>(n, n, ng, w, ng, ref, ng, c->g.dv, false, Om, n, c->work.as<double>(),
+                    c->work.bytes / sizeof(double), c->stream, &L.n),
+       "alignment overlap");
+    CK(small_gemm_f64(n, n, n, Om, n, true, Om, n, false, 1.0, 0.0, P, n, c->stream, &L.n), "alignment");
+    int ok = 0;
+    CK(inv_sqrt_spd(n, P, Pmh, c->m(MS_NSWORK), c->flag.as<int>(), &ok, c->stream, &L.n), "alignment");
+    if (!ok) return fail(c, LACE_ERR_NOT_PD, "the orbitals are nearly orthogonal to the previous ones (no alignment)");
+    CK(small_gemm_f64(n, n, n, Om, n, false, Pmh, n, false, 1.0, 0.0, Q, n, c->stream, &L.n), "alignment");
+    // the SCDM rotation now includes Q
+    double* U = c->m(MS_U);
+    double* UQ = c->m(MS_B);
+    CK(small_gemm_f64(n, n, n, U, n, false, Q, n, false, 1.0, 0.0, UQ, n, c->stream, &L.n), "alignment");
+    CK(cudaMemcpyAsync(U, UQ, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, c->stream), "alignment");
+    T* tmp = c->W.as<T>();
+    CK(gemm_combine<T>(n, ng, n, w, ng, Q, n, 0.0, tmp, ng, c->stream, &L.n), "alignment");
+    CK(cudaMemcpyAsync(w, tmp, (size_t)n * ng * sizeof(T), cudaMemcpyDeviceToDevice, c->stream), "alignment");
+    return LACE_OK;
+}
+
 // ------------------------------------------------------------------ screening
 template <typename T>
 lace_status screen_impl(lace_ctx* c, double thr) {
@@ -689,7 +722,7 @@ lace_status lace_destroy(lace_ctx* c) {
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->psi, &c->canon, &c->W, &c->xi, &c->stage64, &c->scratch, &c->work, &c->aux, &c->mat,
                       &c->pairs, &c->counts, &c->grids, &c->epart, &c->flag, &c->piv, &c->pivfull, &c->exd,
-                      &c->aceio};
+                      &c->aceio, &c->ref};
     for (DevBuf* b : bufs) b->release();
     for (int a = 0; a < 3; ++a) { c->tw_d[a].release(); c->tw_f[a].release(); c->g2_d[a].release(); c->g2_f[a].release(); }
     c->ktab_f.release();
@@ -731,6 +764,7 @@ lace_status lace_set_cell(lace_ctx* c, const double cell[3], int n1, int n2, int
         return fail(c, LACE_ERR_UNSUPPORTED, "grid plane does not fit in shared memory at this precision");
     c->g = g;
     c->have_cell = true;
+    c->have_ref = false;
     c->loaded = c->localized = c->screened = c->applied = c->ace = false;
     return build_tables(c);
 }
@@ -788,6 +822,26 @@ lace_status lace_set_pivots(lace_ctx* c, const long long* pivots, int n) {
     std::sort(v.begin(), v.end());
     if (std::adjacent_find(v.begin(), v.end()) != v.end()) return fail(c, LACE_ERR_ARG, "pivots must be distinct");
     return localize_common(c, 0, pivots, nullptr);
+}
+
+lace_status lace_align_to_previous(lace_ctx* c, int* aligned_out) {
+    if (!c) return LACE_ERR_ARG;
+    if (!c->localized) return fail(c, LACE_ERR_STATE, "localise before aligning");
+    cudaSetDevice(c->device);
+    const size_t bytes = (size_t)c->n_occ * c->g.ng * elem_bytes(c);
+    if (aligned_out) *aligned_out = 0;
+    if (c->have_ref && c->ref_n == c->n_occ && c->ref.bytes >= bytes) {
+        c->screened = c->applied = c->ace = false;
+        lace_status st = c->prec == LACE_FP64 ? align_impl<double>(c) : align_impl<float>(c);
+        if (st) return st;
+        if (aligned_out) *aligned_out = 1;
+    }
+    CK(c->ref.ensure(bytes), "alloc alignment reference");
+    CK(cudaMemcpyAsync(c->ref.p, c->psi.p, bytes, cudaMemcpyDeviceToDevice, c->stream), "alignment");
+    CK(cudaStreamSynchronize(c->stream), "alignment");
+    c->have_ref = true;
+    c->ref_n = c->n_occ;
+    return LACE_OK;
 }
 
 lace_status lace_screen(lace_ctx* c, double s_thr, long long* n_pairs_out) {
@@ -997,7 +1051,7 @@ lace_status lace_get_device_bytes(lace_ctx* c, unsigned long long* bytes_out) {
     if (!c || !bytes_out) return LACE_ERR_ARG;
     const DevBuf* bufs[] = {&c->psi,   &c->canon, &c->W,      &c->xi,    &c->stage64, &c->scratch, &c->work,
                             &c->aux,   &c->mat,   &c->pairs,  &c->counts, &c->grids,  &c->epart,   &c->flag,
-                            &c->piv,   &c->pivfull, &c->exd,  &c->aceio, &c->ktab_f, &c->ktab_d};
+                            &c->piv,   &c->pivfull, &c->exd,  &c->aceio, &c->ktab_f, &c->ktab_d, &c->ref};
     unsigned long long b = 0;
     for (const DevBuf* d : bufs) b += d->bytes;
     for (int a = 0; a < 3; ++a) b += c->tw_d[a].bytes + c->tw_f[a].bytes + c->g2_d[a].bytes + c->g2_f[a].bytes;

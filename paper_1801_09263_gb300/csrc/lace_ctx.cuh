@@ -78,6 +78,9 @@ struct lace_ctx {
     DevBuf mat;     // small FP64 matrices (see offsets below)
     DevBuf pairs, counts, grids, epart, flag, piv, pivfull, exd;
     DevBuf aceio;   // FP64 device copies of a host ACE apply's input and output
+    DevBuf ref;     // [n_occ][ng] localised orbitals of the previous alignment
+    bool have_ref = false;
+    int ref_n = 0;
     long long n_pairs = 0;
     std::vector<long long> pivots_host;
 

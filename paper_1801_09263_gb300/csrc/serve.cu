@@ -73,6 +73,7 @@ struct GpuExec {
         lace_ctx* c = h->ctx;
         if ((st = lace_load_orbitals(c, r.data, d.n_occ, d.n_extra, 1))) return st;
         if ((st = lace_localize(c, 2, nullptr))) return st;
+        if ((d.flags & LACE_SYSTEM_ALIGN) && (st = lace_align_to_previous(c, nullptr))) return st;
         if ((st = lace_screen(c, d.s_thr, &r.n_pairs))) return st;
         if ((st = lace_apply_exchange(c, nullptr, &r.ex))) return st;
         return lace_build_ace(c, LACE_SYM_AVG);
@@ -134,13 +135,14 @@ lace_status lace_server_destroy(lace_server* s) {
 }
 
 lace_status lace_server_add_system(lace_server* s, const double cell[3], int n1, int n2, int n3, double ecut_ha,
-                                   int n_occ, int n_extra, double s_thr, int* id_out) {
+                                   int n_occ, int n_extra, double s_thr, int flags, int* id_out) {
     if (!s || !cell || !id_out) return LACE_ERR_ARG;
     if (!(cell[0] > 0) || !(cell[1] > 0) || !(cell[2] > 0) || !(ecut_ha > 0) || !(s_thr >= 0)) return LACE_ERR_ARG;
     if (n1 < 4 || n2 < 4 || n3 < 4 || n1 > lace::kMaxN || n2 > lace::kMaxN || n3 > lace::kMaxN)
         return LACE_ERR_UNSUPPORTED;
     if (n_occ < 1 || n_extra < 0 || n_occ > 1024 || n_occ + n_extra > 2048) return LACE_ERR_ARG;
-    lace_serve::SystemDesc d{{cell[0], cell[1], cell[2]}, {n1, n2, n3}, ecut_ha, n_occ, n_extra, s_thr};
+    if (flags & ~LACE_SYSTEM_ALIGN) return LACE_ERR_ARG;
+    lace_serve::SystemDesc d{{cell[0], cell[1], cell[2]}, {n1, n2, n3}, ecut_ha, n_occ, n_extra, s_thr, flags};
     *id_out = s->sched->add_system(d);
     return LACE_OK;
 }

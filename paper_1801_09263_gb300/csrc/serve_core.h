@@ -43,6 +43,7 @@ struct SystemDesc {
     double ecut;
     int n_occ, n_extra;
     double s_thr;
+    int flags;
 };
 
 struct Request {

@@ -71,7 +71,7 @@ struct FakeExec {
 };
 
 static SystemDesc sys_desc(int base, int transient, double seconds) {
-    return SystemDesc{{10, 10, 10}, {16, 16, 16}, 10.0, base, transient, seconds};
+    return SystemDesc{{10, 10, 10}, {16, 16, 16}, 10.0, base, transient, seconds, 0};
 }
 
 struct Sub {

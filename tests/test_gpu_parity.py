@@ -148,6 +148,32 @@ def test_scdm_pivots_are_deterministic(prec):
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_alignment_to_previous_orbitals_matches_oracle(small_loc, prec):
+    g, occ1, _ = oracle_orbitals(small_loc)
+    n = small_loc.n_occ
+    drift = synth.small_localized_system(78, small_loc.cell, small_loc.shape, small_loc.ecut, 14, n).phi
+    phi2 = small_loc.phi.copy()
+    phi2[:n] += 0.05 * drift
+    with make_ctx(small_loc, prec) as ctx:
+        piv1 = ctx.localize(2)
+        assert ctx.align_to_previous() is False  # first call: reference only
+        ctx.load_orbitals(phi2, n, small_loc.n_extra, True)
+        piv2 = ctx.localize(2)
+        assert ctx.align_to_previous() is True
+        psi2 = ctx.get_orbitals(B.ORB_PSI)[:n]
+        u = ctx.get_matrix(B.MAT_SCDM_U)
+    _, _, w1 = O.scdm(g, occ1, 2, pivots=piv1)
+    occ2 = O.lowdin(g, phi2[:n])
+    _, u2, w2 = O.scdm(g, occ2, 2, pivots=piv2)
+    q, aligned = O.align_orbitals(g, w2, w1)
+    tol = 1e-10 if prec == LACE_FP64 else 2e-5
+    assert relerr(psi2, aligned) < tol
+    assert relerr(u, u2 @ q) < (1e-10 if prec == LACE_FP64 else 1e-5)
+    # closer to the previous set than the unaligned localised orbitals
+    assert np.sum((psi2 - w1) ** 2) <= np.sum((w2 - w1) ** 2) + 1e-12
+
+
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
 def test_scdm_rotation_with_imposed_pivots(small_loc, prec):
     g, occ, _ = oracle_orbitals(small_loc)
     piv, u_ref, w_ref = O.scdm(g, occ, 2)

@@ -59,7 +59,8 @@ def _sequence(srv, sid, inp):
 
 def _add(srv, inp):
     s = inp["sys"]
-    return srv.add_system(s.cell, s.shape, s.ecut, s.n_occ, s.n_extra, inp["thr"])
+    # the 32^3 system aligns each rebuild's orbitals to the previous ones
+    return srv.add_system(s.cell, s.shape, s.ecut, s.n_occ, s.n_extra, inp["thr"], align=s.shape == (32, 32, 32))
 
 
 def _collect(srv, ids):

@@ -312,6 +312,31 @@ def test_subsample_indices_odd_grid():
 # ---------------------------------------------------------------- screening
 
 
+def test_alignment_recovers_a_rotated_set_and_is_optimal():
+    g, occ, _ = _small(seed=21, n_occ=6)
+    _, _, w = O.scdm(g, occ, 2)
+    rng = np.random.default_rng(4)
+    r = synth.random_orthogonal(6, rng)
+    rotated = np.tensordot(r.T, w, axes=(1, 0))  # rotated_j = sum_i w_i r_ij
+    q, aligned = O.align_orbitals(g, rotated, w)
+    assert np.max(np.abs(aligned - w)) < 1e-12
+    assert np.max(np.abs(q - r.T)) < 1e-12
+    # a drifted set: the aligned one is orthonormal, spans the same space and is
+    # closer to the reference than any other rotation tried
+    drift = synth.small_localized_system(22, g.cell, g.shape, 6.0, 4, 6).phi
+    new = O.lowdin(g, occ + 0.05 * drift)
+    _, aligned = O.align_orbitals(g, new, w)
+    a2 = aligned.reshape(6, -1)
+    assert np.max(np.abs(g.dv * a2 @ a2.T - np.eye(6))) < 1e-12
+    proj = g.dv * new.reshape(6, -1) @ a2.T
+    assert np.max(np.abs(proj.T @ proj - np.eye(6))) < 1e-10  # same span
+    dist = np.sum((aligned - w) ** 2)
+    for _ in range(20):
+        rr = synth.random_orthogonal(6, rng)
+        other = np.tensordot(rr.T, aligned, axes=(1, 0))
+        assert np.sum((other - w) ** 2) >= dist - 1e-12
+
+
 def test_overlap_moduli_diagonal_is_one_and_threshold_rule():
     g, occ, _ = _small(seed=41, n_occ=6)
     s = O.overlap_moduli(g, occ)
