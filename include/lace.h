@@ -202,6 +202,41 @@ lace_status lace_get_launch_count(lace_ctx* ctx, long long* count_out);
  * request seen and are freed by lace_destroy). */
 lace_status lace_get_device_bytes(lace_ctx* ctx, unsigned long long* bytes_out);
 
+/* ------------------------------------------------------------------ plane waves
+ * Front end for orbitals given as plane-wave coefficients, the basis of the
+ * paper's V_X matrix (Sec. 2), with grids derived from cutoffs (Sec. 3).
+ * Basis of real (Gamma-point) orbitals: the half sphere of
+ * G = 2 pi (m1/a, m2/b, m3/c) with |G|^2/2 < ecut, half-space m3 > 0, or
+ * m3 = 0 and m2 > 0, or m3 = m2 = 0 and m1 >= 0, ordered by |G|^2 and then
+ * (m1, m2, m3); phi(r) = c(0) + 2 Re sum_{G != 0} c(G) exp(i G.r), so
+ * c(G) = (1/Ng) sum_r phi(r) exp(-i G.r).  Coefficients are interleaved FP64
+ * (re, im) [orbital][n_pw]; the imaginary part of c(0) is ignored.  The
+ * transforms run on the device in FP64 (two orbitals per complex FFT). */
+
+/* The basis of a cell and cutoff: *n_pw_out = its size; m_out (nullable)
+ * receives up to cap triples (m1, m2, m3).  Host only. */
+lace_status lace_pw_basis(const double cell[3], double ecut_ha, int* m_out, long long cap, long long* n_pw_out);
+
+/* Smallest 2^a 3^b 5^c grid holding the sphere |G|^2/2 < ecut_ha without
+ * folding (n >= 2 m_max + 1 on each axis).  For an exchange grid free of
+ * aliasing pass the cutoff of the pair densities (4x the orbital cutoff).
+ * LACE_ERR_UNSUPPORTED beyond 128 points.  Host only. */
+lace_status lace_grid_for_cutoff(const double cell[3], double ecut_ha, int dims_out[3]);
+
+/* lace_load_orbitals from coefficients in the basis of the context's cell and
+ * cutoff (lace_set_cell).  coef: host, n_occ + n_extra rows of n_pw complex
+ * values, copied.  LACE_ERR_ARG when n_pw is not the basis size or the sphere
+ * does not fit the grid (|m| < n/2 on every axis); LACE_ERR_UNSUPPORTED when an
+ * FP64 grid plane does not fit in shared memory. */
+lace_status lace_load_orbitals_pw(lace_ctx* ctx, const double* coef, long long n_pw, int n_occ, int n_extra,
+                                  int orthonormalize);
+
+/* Orbitals (LACE_ORB_PSI / W / XI, as lace_get_orbitals) as coefficients of
+ * the context's basis: coef_out host, n_p rows of n_pw complex values.  W in
+ * this form is the V_X matrix applied to the orbitals, as plane-wave codes
+ * use it (with the sign convention of lace_apply_exchange). */
+lace_status lace_get_orbitals_pw(lace_ctx* ctx, int which, double* coef_out, long long n_pw);
+
 /* ------------------------------------------------------------------ serving
  * A request server over resident systems (the paper's double SCF loop, Sec. 2,
  * rebuilds ACE once per outer iteration and applies it many times; a server

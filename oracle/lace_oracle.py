@@ -50,6 +50,9 @@ __all__ = [
     "scdm",
     "overlap_moduli",
     "align_orbitals",
+    "pw_basis",
+    "pw_to_grid",
+    "grid_to_pw",
     "kept_pairs",
     "apply_exchange",
     "apply_exchange_columns",
@@ -295,6 +298,53 @@ def align_orbitals(grid: Grid, w: np.ndarray, w_prev: np.ndarray) -> tuple:
     u, _, vt = np.linalg.svd(o)
     q = u @ vt
     return q, (q.T @ a).reshape(w.shape)
+
+
+def pw_basis(cell, ecut: float) -> np.ndarray:
+    """Plane-wave basis of real (Gamma-point) orbitals: the half sphere of
+    G = 2 pi (m1/a, m2/b, m3/c) with |G|^2/2 < ecut (the orbital cutoff of
+    Sec. 3), half-space m3 > 0, or m3 = 0 and m2 > 0, or m3 = m2 = 0 and
+    m1 >= 0; ordered by |G|^2, ties by (m1, m2, m3).  Returns int (n_pw, 3).
+
+    An orbital is phi(r) = c(0) + 2 Re sum_{G != 0} c(G) exp(i G.r), the
+    real-orbital form of the plane-wave expansion the paper's V_X matrix is
+    written in (Sec. 2)."""
+    a, b, c = cell
+    mm = [int(np.floor(np.sqrt(2.0 * ecut) * L / (2.0 * np.pi))) for L in (a, b, c)]
+    out = []
+    for m1 in range(-mm[0], mm[0] + 1):
+        for m2 in range(-mm[1], mm[1] + 1):
+            for m3 in range(-mm[2], mm[2] + 1):
+                if not (m3 > 0 or (m3 == 0 and m2 > 0) or (m3 == 0 and m2 == 0 and m1 >= 0)):
+                    continue
+                g2 = (2 * np.pi * m1 / a) ** 2 + (2 * np.pi * m2 / b) ** 2 + (2 * np.pi * m3 / c) ** 2
+                if g2 / 2.0 < ecut:
+                    out.append((g2, m1, m2, m3))
+    out.sort()
+    return np.array([o[1:] for o in out], dtype=np.int64).reshape(-1, 3)
+
+
+def pw_to_grid(grid: Grid, mvec: np.ndarray, coef: np.ndarray) -> np.ndarray:
+    """phi(r_j) = c(0) + 2 Re sum_{G != 0} c(G) exp(i G.r_j) on the grid:
+    the full spectrum (c at G, conj(c) at -G) through the library inverse FFT.
+    coef: complex (n_orb, n_pw) in pw_basis order."""
+    n1, n2, n3 = grid.shape
+    spec = np.zeros((coef.shape[0], n1, n2, n3), dtype=np.complex128)
+    i1, i2, i3 = mvec[:, 0] % n1, mvec[:, 1] % n2, mvec[:, 2] % n3
+    j1, j2, j3 = -mvec[:, 0] % n1, -mvec[:, 1] % n2, -mvec[:, 2] % n3
+    zero = np.all(mvec == 0, axis=1)
+    c = coef.copy()
+    c[:, zero] = c[:, zero].real
+    spec[:, j1, j2, j3] = np.conj(c)
+    spec[:, i1, i2, i3] = c
+    return np.real(np.fft.ifftn(spec, axes=(1, 2, 3))) * grid.ng
+
+
+def grid_to_pw(grid: Grid, mvec: np.ndarray, phi: np.ndarray) -> np.ndarray:
+    """c(G) = (1/Ng) sum_j phi(r_j) exp(-i G.r_j) at the basis vectors."""
+    n1, n2, n3 = grid.shape
+    spec = np.fft.fftn(phi, axes=(1, 2, 3)) / grid.ng
+    return spec[:, mvec[:, 0] % n1, mvec[:, 1] % n2, mvec[:, 2] % n3]
 
 
 def overlap_moduli(grid: Grid, w: np.ndarray) -> np.ndarray:

@@ -80,6 +80,10 @@ def load_library(build_if_missing: bool = False):
         "lace_get_device_bytes": ([P, P], I),
         "lace_set_kernel": ([P, I, D, D], I),
         "lace_align_to_previous": ([P, P], I),
+        "lace_pw_basis": ([P, D, P, LL, P], I),
+        "lace_grid_for_cutoff": ([P, D, P], I),
+        "lace_load_orbitals_pw": ([P, P, LL, I, I, I], I),
+        "lace_get_orbitals_pw": ([P, I, P, LL], I),
         "lace_server_create": ([C.POINTER(P), I, I, I, I, C.c_ulonglong], I),
         "lace_server_destroy": ([P], I),
         "lace_server_add_system": ([P, P, I, I, I, D, I, I, D, I, P], I),
@@ -180,6 +184,19 @@ class Lace:
         self._check(self.lib.lace_load_orbitals(self.h, _ptr(a), n_occ, n_extra, int(orthonormalize)),
                     "lace_load_orbitals")
         self.n_occ, self.n_extra = n_occ, n_extra
+
+    def load_orbitals_pw(self, coef, n_occ: int, n_extra: int = 0, orthonormalize: bool = True):
+        """coef: complex array [n_occ + n_extra, n_pw] in the basis of pw_basis(cell, ecut)."""
+        c = np.ascontiguousarray(coef, dtype=np.complex128)
+        self._check(self.lib.lace_load_orbitals_pw(self.h, c.ctypes.data_as(C.c_void_p), c.shape[1], n_occ, n_extra,
+                                                   int(orthonormalize)), "lace_load_orbitals_pw")
+        self.n_occ, self.n_extra = n_occ, n_extra
+
+    def get_orbitals_pw(self, which: int, n_pw: int) -> np.ndarray:
+        out = np.empty((self.n_p, n_pw), dtype=np.complex128)
+        self._check(self.lib.lace_get_orbitals_pw(self.h, int(which), out.ctypes.data_as(C.c_void_p), int(n_pw)),
+                    "lace_get_orbitals_pw")
+        return out
 
     def load_orbitals_dev(self, phi_dev, n_occ: int, n_extra: int = 0, orthonormalize: bool = True):
         """phi_dev: a contiguous float64 CUDA torch tensor [(n_occ+n_extra), n1, n2, n3]."""
@@ -458,3 +475,27 @@ class Batch:
         return dict(threads=th.value, ctas_per_sm=ct.value, chunks=ch.value, graph_replays=rp.value,
                     launches=ln.value, setup_ms=ms[0], pairconv_ms=ms[1], hot_ms=ms[2], call_ms=ms[3],
                     tune_ms={f"{a}x{b}": round(float(t), 3) for (a, b), t in zip(TUNE_SHAPES, tune)})
+
+
+def pw_basis(cell, ecut: float) -> np.ndarray:
+    """lace_pw_basis: the (m1, m2, m3) of the half-sphere basis, int [n_pw, 3]."""
+    lib = load_library()
+    c = _f64(cell)
+    n = C.c_longlong(0)
+    st = lib.lace_pw_basis(_ptr(c), float(ecut), None, 0, C.byref(n))
+    if st != LACE_OK:
+        raise LaceError(st, "lace_pw_basis", lib.lace_status_string(st).decode())
+    m = np.zeros((max(n.value, 1), 3), dtype=np.int32)
+    lib.lace_pw_basis(_ptr(c), float(ecut), _ptr(m), n.value, C.byref(n))
+    return m[: n.value]
+
+
+def grid_for_cutoff(cell, ecut: float) -> tuple:
+    """lace_grid_for_cutoff: the smallest 2/3/5-smooth grid holding the sphere."""
+    lib = load_library()
+    c = _f64(cell)
+    d = np.zeros(3, dtype=np.int32)
+    st = lib.lace_grid_for_cutoff(_ptr(c), float(ecut), _ptr(d))
+    if st != LACE_OK:
+        raise LaceError(st, "lace_grid_for_cutoff", lib.lace_status_string(st).decode())
+    return tuple(int(x) for x in d)

@@ -637,6 +637,33 @@ lace_status copy_orbitals_out(lace_ctx* c, const T* src, size_t count, double* h
 
 namespace lace {
 
+lace_status ctx_fail(lace_ctx* c, lace_status st, const std::string& msg) { return fail(c, st, msg); }
+
+lace_status ctx_load_dev64(lace_ctx* c, const double* d_phi, int n_occ, int n_extra, int ortho) {
+    return load_common(c, d_phi, true, n_occ, n_extra, ortho);
+}
+
+lace_status ctx_orbitals(lace_ctx* c, int which, const void** src) {
+    if (!c->loaded) return fail(c, LACE_ERR_STATE, "load orbitals first");
+    switch (which) {
+        case LACE_ORB_PSI: {
+            lace_status st = materialize_psi(c);
+            if (st) return st;
+            *src = c->psi.p;
+            return LACE_OK;
+        }
+        case LACE_ORB_W:
+            if (!c->applied) return fail(c, LACE_ERR_STATE, "apply the exchange first");
+            *src = c->W.p;
+            return LACE_OK;
+        case LACE_ORB_XI:
+            if (!c->ace) return fail(c, LACE_ERR_STATE, "build ACE first");
+            *src = c->xi.p;
+            return LACE_OK;
+        default: return fail(c, LACE_ERR_ARG, "unknown orbital set");
+    }
+}
+
 // Device bytes a context holds after loading n_occ + n_extra orbitals on an
 // n[0] x n[1] x n[2] grid, localising them (stride 2), screening, applying the
 // exchange, building ACE and applying it to n_apply host functions: the
@@ -722,7 +749,7 @@ lace_status lace_destroy(lace_ctx* c) {
     cudaStreamSynchronize(c->stream);
     DevBuf* bufs[] = {&c->psi, &c->canon, &c->W, &c->xi, &c->stage64, &c->scratch, &c->work, &c->aux, &c->mat,
                       &c->pairs, &c->counts, &c->grids, &c->epart, &c->flag, &c->piv, &c->pivfull, &c->exd,
-                      &c->aceio, &c->ref};
+                      &c->aceio, &c->ref, &c->pw_idx, &c->pw_io, &c->pw_real};
     for (DevBuf* b : bufs) b->release();
     for (int a = 0; a < 3; ++a) { c->tw_d[a].release(); c->tw_f[a].release(); c->g2_d[a].release(); c->g2_f[a].release(); }
     c->ktab_f.release();
@@ -763,6 +790,7 @@ lace_status lace_set_cell(lace_ctx* c, const double cell[3], int n1, int n2, int
     if (need > prop.sharedMemPerBlockOptin)
         return fail(c, LACE_ERR_UNSUPPORTED, "grid plane does not fit in shared memory at this precision");
     c->g = g;
+    c->ecut = ecut_ha;
     c->have_cell = true;
     c->have_ref = false;
     c->loaded = c->localized = c->screened = c->applied = c->ace = false;
@@ -1051,7 +1079,8 @@ lace_status lace_get_device_bytes(lace_ctx* c, unsigned long long* bytes_out) {
     if (!c || !bytes_out) return LACE_ERR_ARG;
     const DevBuf* bufs[] = {&c->psi,   &c->canon, &c->W,      &c->xi,    &c->stage64, &c->scratch, &c->work,
                             &c->aux,   &c->mat,   &c->pairs,  &c->counts, &c->grids,  &c->epart,   &c->flag,
-                            &c->piv,   &c->pivfull, &c->exd,  &c->aceio, &c->ktab_f, &c->ktab_d, &c->ref};
+                            &c->piv,   &c->pivfull, &c->exd,  &c->aceio, &c->ktab_f, &c->ktab_d, &c->ref,
+                            &c->pw_idx, &c->pw_io,  &c->pw_real};
     unsigned long long b = 0;
     for (const DevBuf* d : bufs) b += d->bytes;
     for (int a = 0; a < 3; ++a) b += c->tw_d[a].bytes + c->tw_f[a].bytes + c->g2_d[a].bytes + c->g2_f[a].bytes;

@@ -79,6 +79,8 @@ struct lace_ctx {
     DevBuf pairs, counts, grids, epart, flag, piv, pivfull, exd;
     DevBuf aceio;   // FP64 device copies of a host ACE apply's input and output
     DevBuf ref;     // [n_occ][ng] localised orbitals of the previous alignment
+    DevBuf pw_idx, pw_io, pw_real;  // plane-wave front end: G offsets, coefficients, FP64 orbitals
+    double ecut = 0.0;              // orbital cutoff of lace_set_cell (Ha)
     bool have_ref = false;
     int ref_n = 0;
     long long n_pairs = 0;
@@ -91,3 +93,12 @@ struct lace_ctx {
     size_t mslot = 0;
     double* m(int k) { return mat.as<double>() + (size_t)k * mslot; }
 };
+
+namespace lace {
+// Shared with the other translation units (defined in lace_api.cu).
+lace_status ctx_fail(lace_ctx* c, lace_status st, const std::string& msg);
+// lace_load_orbitals from FP64 device memory (borrowed for the call)
+lace_status ctx_load_dev64(lace_ctx* c, const double* d_phi, int n_occ, int n_extra, int ortho);
+// device pointer of PSI / W / XI (working precision, [n_p][ng]) after the state checks
+lace_status ctx_orbitals(lace_ctx* c, int which, const void** src);
+}  // namespace lace

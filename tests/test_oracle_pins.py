@@ -337,6 +337,45 @@ def test_alignment_recovers_a_rotated_set_and_is_optimal():
         assert np.sum((other - w) ** 2) >= dist - 1e-12
 
 
+def test_pw_basis_half_sphere_and_order():
+    cell, ecut = (7.0, 8.0, 9.5), 6.0
+    m = O.pw_basis(cell, ecut)
+    g2 = np.sum((2 * np.pi * m / np.array(cell)) ** 2, axis=1)
+    assert np.all(g2 / 2 < ecut) and np.all(np.diff(g2) >= 0) and tuple(m[0]) == (0, 0, 0)
+    # every G of the full sphere is in the half sphere exactly once, as G or -G
+    full = set()
+    mm = [int(np.floor(np.sqrt(2 * ecut) * L / (2 * np.pi))) for L in cell]
+    for m1 in range(-mm[0], mm[0] + 1):
+        for m2 in range(-mm[1], mm[1] + 1):
+            for m3 in range(-mm[2], mm[2] + 1):
+                if (2 * np.pi * m1 / cell[0]) ** 2 + (2 * np.pi * m2 / cell[1]) ** 2 + (2 * np.pi * m3 / cell[2]) ** 2 < 2 * ecut:
+                    full.add((m1, m2, m3))
+    half = {tuple(x) for x in m}
+    assert len(half) == len(m) and len(full) == 2 * len(m) - 1
+    assert all((x in half) != ((-x[0], -x[1], -x[2]) in half) or x == (0, 0, 0) for x in full)
+
+
+def test_pw_transforms_against_direct_sums():
+    cell, shape, ecut = (7.0, 8.0, 9.5), (16, 18, 20), 6.0
+    g = O.Grid(cell, shape)
+    m = O.pw_basis(cell, ecut)
+    rng = np.random.default_rng(9)
+    coef = rng.standard_normal((2, len(m))) + 1j * rng.standard_normal((2, len(m)))
+    phi = O.pw_to_grid(g, m, coef)
+    gv = 2 * np.pi * m / np.array(cell)
+    for (i, j, k) in ((0, 0, 0), (3, 11, 7), (15, 17, 19)):
+        r = np.array([i * cell[0] / shape[0], j * cell[1] / shape[1], k * cell[2] / shape[2]])
+        ph = np.exp(1j * gv @ r)
+        direct = coef[:, 0].real + 2 * np.real(coef[:, 1:] @ ph[1:])
+        assert np.max(np.abs(phi[:, i, j, k] - direct)) < 1e-11
+    back = O.grid_to_pw(g, m, phi)
+    assert np.max(np.abs(back[:, 1:] - coef[:, 1:])) < 1e-12
+    assert np.max(np.abs(back[:, 0] - coef[:, 0].real)) < 1e-12
+    # Parseval: dV sum phi^2 = Omega (c0^2 + 2 sum |c|^2)
+    nrm = g.dv * np.sum(phi ** 2, axis=(1, 2, 3))
+    assert np.allclose(nrm, g.omega * (coef[:, 0].real ** 2 + 2 * np.sum(np.abs(coef[:, 1:]) ** 2, axis=1)))
+
+
 def test_overlap_moduli_diagonal_is_one_and_threshold_rule():
     g, occ, _ = _small(seed=41, n_occ=6)
     s = O.overlap_moduli(g, occ)
