@@ -66,6 +66,31 @@ def parse():
     return p.parse_args()
 
 
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time: every rank runs its own replica (weak scaling),
+    so the job is done when the last one is."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(units: float, world: int, device=None) -> float:
+    """Units processed by all ranks together."""
+    if world <= 1:
+        return units
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -213,13 +238,8 @@ def run_lace(args, rank, world, local):
     launches = ctx.launch_count() - launches0
     stages = ctx.get_timings()
     ex_mixed = ctx.exchange_energy(1.0)
-    if world > 1:
-        import torch.distributed as dist
-
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = npairs * args.steps * world / (total_ms / 1e3)
+    total_ms = max_over_ranks(total_ms, world, dev)
+    value = sum_over_ranks(npairs * args.steps, world, dev) / (total_ms / 1e3)
 
     # ---------------- plain FP64 GPU form (same step)
     fp64 = None
@@ -268,8 +288,8 @@ def run_lace(args, rank, world, local):
         for _ in range(ksteps):
             e2e_step()
         barrier()
-        dt = time.perf_counter() - t0
-        e2e = {"value": npairs * ksteps * world / dt, "unit": UNIT,
+        dt = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": sum_over_ranks(npairs * ksteps, world, dev) / dt, "unit": UNIT,
                "h2d_bytes_per_step": 2 * phi_np.nbytes, "d2h_bytes_per_step": w_np.nbytes + k_np.nbytes + 8,
                "steps": ksteps}
     ctx.close()
