@@ -30,8 +30,9 @@ __global__ void __launch_bounds__(GR_THREADS) gemm_rows_kernel(int M, int N, siz
                                                                 size_t lda, const T* __restrict__ B, size_t ldb,
                                                                 bool absval, bool sym, size_t kchunk,
                                                                 double* __restrict__ work) {
-    __shared__ T As[GR_BK][GR_BM + 1];
-    __shared__ T Bs[GR_BK][GR_BN + 1];
+    // row pitch GR_BM + 4 keeps the 4-wide reads of a row 16-byte aligned
+    __shared__ __align__(16) T As[GR_BK][GR_BM + 4];
+    __shared__ __align__(16) T Bs[GR_BK][GR_BN + 4];
     if (sym && blockIdx.y < blockIdx.x) return;  // symmetric: upper tiles only
     const int m0 = blockIdx.x * GR_BM, n0 = blockIdx.y * GR_BN;
     const size_t k_begin = (size_t)blockIdx.z * kchunk;
@@ -69,10 +70,17 @@ __global__ void __launch_bounds__(GR_THREADS) gemm_rows_kernel(int M, int N, siz
 #pragma unroll
         for (int kk = 0; kk < GR_BK; ++kk) {
             T a[4], b[4];
+            if constexpr (sizeof(T) == 4) {
+                const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
+                const float4 b4 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
+                a[0] = a4.x; a[1] = a4.y; a[2] = a4.z; a[3] = a4.w;
+                b[0] = b4.x; b[1] = b4.y; b[2] = b4.z; b[3] = b4.w;
+            } else {
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+                for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+                for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+            }
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
