@@ -323,7 +323,11 @@ lace_status lace_server_stats(lace_server* srv, unsigned long long* bytes_reside
  * first lace_batch_run and is captured into a CUDA graph on the second;
  * later runs replay it.  The launch shape of the persistent kernel (threads
  * per CTA, CTAs per SM) is chosen by timing every candidate on the first
- * run. */
+ * run, against a per-instance mode that runs each instance's pair
+ * convolutions through the single-system (size-specialised) passes; the
+ * faster is kept.  A graph of the per-instance mode is re-captured (and
+ * updated in place) every run, since its launch sizes follow the pair
+ * counts. */
 typedef struct lace_batch lace_batch;
 
 typedef struct {
@@ -362,8 +366,11 @@ lace_ctx* lace_batch_context(lace_batch* batch, int inst);
  * kernel), graph replays so far, kernel launches so far (all instances),
  * milliseconds of the last run ([0] setup, host; [1] pair convolutions,
  * device, of the last eager run or of the autotuned shape; [2] pair
- * convolutions + energies + ACE builds, device; [3] the whole call, host) and the timed candidates (-1: did not fit).  Any output
- * may be NULL. */
+ * convolutions + energies + ACE builds, device; [3] the whole call, host) and the timed candidates
+ * (-1: did not fit; seven persistent launch shapes 128x1, 128x2, 128x3,
+ * 128x4, 256x1, 256x2, 512x1, then the per-instance mode).  The shape
+ * outputs name the best persistent shape even when the per-instance mode
+ * was kept (it was when its time is the smallest).  Any output may be NULL. */
 lace_status lace_batch_info(lace_batch* batch, int* threads, int* ctas_per_sm, int* chunks, long long* graph_replays,
                             long long* launches, double* ms_out, double* tune_ms_out, int tune_count);
 

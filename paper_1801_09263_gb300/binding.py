@@ -469,12 +469,16 @@ class Batch:
         th, ct, ch = C.c_int(0), C.c_int(0), C.c_int(0)
         rp, ln = C.c_longlong(0), C.c_longlong(0)
         ms = np.zeros(4, dtype=np.float64)
-        tune = np.zeros(len(TUNE_SHAPES), dtype=np.float64)
+        tune = np.zeros(len(TUNE_SHAPES) + 1, dtype=np.float64)
         self._check(self.lib.lace_batch_info(self.h, C.byref(th), C.byref(ct), C.byref(ch), C.byref(rp), C.byref(ln),
-                                             _ptr(ms), _ptr(tune), len(TUNE_SHAPES)), "lace_batch_info")
+                                             _ptr(ms), _ptr(tune), len(tune)), "lace_batch_info")
+        shapes = [t for t in tune[:-1] if t >= 0]
+        per_instance = tune[-1] > 0 and (not shapes or tune[-1] < min(shapes))
+        tune_ms = {f"{a}x{b}": round(float(t), 3) for (a, b), t in zip(TUNE_SHAPES, tune)}
+        tune_ms["per_instance"] = round(float(tune[-1]), 3)
         return dict(threads=th.value, ctas_per_sm=ct.value, chunks=ch.value, graph_replays=rp.value,
                     launches=ln.value, setup_ms=ms[0], pairconv_ms=ms[1], hot_ms=ms[2], call_ms=ms[3],
-                    tune_ms={f"{a}x{b}": round(float(t), 3) for (a, b), t in zip(TUNE_SHAPES, tune)})
+                    mode="per_instance" if per_instance else "persistent", tune_ms=tune_ms)
 
 
 def pw_basis(cell, ecut: float) -> np.ndarray:

@@ -101,13 +101,14 @@ struct lace_batch {
     int* h_ngrids = nullptr;  // pinned
     size_t pool_elems = 0, epart_elems = 0, smem = 0;
     int threads = 0, ctas = 0, chunks = 0;
+    int mode = 0;  // 0: one persistent multi-instance launch per chunk; 1: per-instance specialised passes
     bool prepared = false;
     cudaGraphExec_t exec = nullptr;
     long long runs = 0, replays = 0, launches = 0, hot_launches = 0;
     bool graph_ok = true;  // false once a capture has failed: the hot part then runs eagerly
     double ms[4] = {};  // setup (host), pair convolutions (device), hot part (device), whole call (host)
     double pc_eager_ms = 0.0;  // pair convolutions of the last eager run (events are not recorded in the graph)
-    std::vector<double> tune;  // ms per candidate launch shape
+    std::vector<double> tune;  // ms per candidate launch shape; the last entry: the per-instance mode
     std::string err;
 };
 
@@ -214,8 +215,34 @@ lace_status prepare(lace_batch* b) {
     return LACE_OK;
 }
 
-// Time every launch shape once on the real batch (W and E are zeroed by
-// the hot part afterwards).
+// Per-instance mode: each instance's pair convolutions through the
+// single-system passes (size-specialised where they exist), one instance
+// after another on the shared scratch pool.  The launch sizes follow the
+// current pair counts, so a graph of this mode is re-captured every run.
+lace_status pairconv_per_instance(lace_batch* b, cudaStream_t s, int* launches) {
+    for (int q = 0; q < b->n; ++q) {
+        if (!b->in_graph[q] || b->h_ngrids[q] == 0) continue;
+        lace_ctx* c = b->ctx[q];
+        FFTTables<float> tb;
+        for (int a = 0; a < 3; ++a) {
+            tb.tw[a] = c->tw_f[a].as<cplx<float>>();
+            tb.g2[a] = c->g2_f[a].as<float>();
+        }
+        tb.ktab = c->ktab_f.as<float>();
+        const size_t ng = c->g.ng;
+        const int batch = (int)std::max<size_t>(
+            1, std::min<size_t>({(size_t)b->h_ngrids[q], b->pool_elems / ng, b->epart_elems / (2 * (size_t)c->g.n[0]),
+                                 (size_t)1024}));
+        BCK(pairconv_run<float>(c->g, tb, c->psi.as<float>(), c->n_occ, c->W.as<float>(), c->grids.as<PairGrid>(),
+                                b->h_ngrids[q], b->pool.as<cplx<float>>(), batch, b->epart.as<double>(), c->m(MS_E), s,
+                                launches, nullptr, nullptr),
+            "per-instance pair convolutions");
+    }
+    return LACE_OK;
+}
+
+// Time every launch shape once on the real batch, and the per-instance mode
+// (W and E are zeroed by the hot part afterwards).
 lace_status autotune(lace_batch* b) {
     const int cand[][2] = {{128, 1}, {128, 2}, {128, 3}, {128, 4}, {256, 1}, {256, 2}, {512, 1}};
     const MultiArgs A = multi_args(b);
@@ -245,6 +272,25 @@ lace_status autotune(lace_batch* b) {
         }
     }
     if (!b->threads) return bfail(b, LACE_ERR_UNSUPPORTED, "no launch shape of the batched pair convolutions fits");
+    {
+        int l = 0;
+        lace_status st = pairconv_per_instance(b, b->main, &l);  // warm-up
+        if (st) return st;
+        BCK(cudaEventRecord(b->ev_pc0, b->main), "autotune");
+        if ((st = pairconv_per_instance(b, b->main, &l))) return st;
+        BCK(cudaEventRecord(b->ev_pc1, b->main), "autotune");
+        BCK(cudaEventSynchronize(b->ev_pc1), "autotune");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, b->ev_pc0, b->ev_pc1);
+        b->tune.push_back(ms);
+        b->launches += l;
+        b->mode = ms < best ? 1 : 0;
+        // LACE_BATCH_MODE=persistent | per_instance overrides the timing
+        const char* fm = getenv("LACE_BATCH_MODE");
+        if (fm && !strcmp(fm, "persistent")) b->mode = 0;
+        if (fm && !strcmp(fm, "per_instance")) b->mode = 1;
+        if (b->mode == 1) best = ms;
+    }
     b->pc_eager_ms = best;
     return LACE_OK;
 }
@@ -260,8 +306,13 @@ lace_status enqueue_hot(lace_batch* b, bool capturing) {
         BCK(fill_zero_f64(c->m(MS_E), (size_t)c->n_occ * c->n_occ, b->main, &l), "zero E");
     }
     if (!capturing) BCK(cudaEventRecord(b->ev_pc0, b->main), "batch");
-    BCK(pairconv_multi_run(multi_args(b), b->chunks, b->smem, b->threads, b->ctas, b->main, &l),
-        "batched pair convolutions");
+    if (b->mode == 1) {
+        lace_status st = pairconv_per_instance(b, b->main, &l);
+        if (st) return st;
+    } else {
+        BCK(pairconv_multi_run(multi_args(b), b->chunks, b->smem, b->threads, b->ctas, b->main, &l),
+            "batched pair convolutions");
+    }
     if (!capturing) BCK(cudaEventRecord(b->ev_pc1, b->main), "batch");
     for (int q = 0; q < b->n; ++q) {
         if (!b->in_graph[q]) continue;
@@ -284,11 +335,10 @@ lace_status enqueue_hot(lace_batch* b, bool capturing) {
     return LACE_OK;
 }
 
+// Capture the hot part; an existing executable graph is updated in place
+// when the new capture has its topology (the per-instance mode re-captures
+// every run with new launch sizes), else rebuilt.
 lace_status capture(lace_batch* b) {
-    if (b->exec) {
-        cudaGraphExecDestroy(b->exec);
-        b->exec = nullptr;
-    }
     BCK(cudaStreamBeginCapture(b->main, cudaStreamCaptureModeThreadLocal), "graph capture");
     lace_status st = enqueue_hot(b, true);
     cudaGraph_t g = nullptr;
@@ -298,6 +348,16 @@ lace_status capture(lace_batch* b) {
         return st;
     }
     BCK(e, "graph capture");
+    if (b->exec) {
+        cudaGraphExecUpdateResultInfo info{};
+        if (cudaGraphExecUpdate(b->exec, g, &info) == cudaSuccess) {
+            cudaGraphDestroy(g);
+            return LACE_OK;
+        }
+        cudaGetLastError();
+        cudaGraphExecDestroy(b->exec);
+        b->exec = nullptr;
+    }
     const cudaError_t ei = cudaGraphInstantiate(&b->exec, g, 0);
     cudaGraphDestroy(g);
     BCK(ei, "graph instantiate");
@@ -436,7 +496,7 @@ lace_status lace_batch_run(lace_batch* b, double* ex_out, int* status_out) {
         if ((st = autotune(b))) return st;
     }
     bool eager = b->runs == 0 || !b->graph_ok;  // first call: eager (sets kernel attributes, checks the path)
-    if (!eager && (!b->exec || need > b->chunks)) {
+    if (!eager && (!b->exec || need > b->chunks || b->mode == 1)) {
         b->chunks = std::max(need, b->chunks);
         if (capture(b) != LACE_OK) {
             // capture unsupported here: run eagerly from now on

@@ -137,3 +137,29 @@ def test_small_scratch_pool_gives_the_same_results(batch_runs, monkeypatch):
             assert (st == 0).all()
             assert np.max(np.abs(ex - out["runs"][0][0])) <= 1e-6
         assert b.info()["chunks"] > 1
+
+
+def test_per_instance_mode_matches_the_persistent_kernel(batch_runs, monkeypatch):
+    """The per-instance mode (single-system passes, re-captured every run)
+    against the persistent multi-instance kernel and single contexts."""
+    sy, out = batch_runs
+    monkeypatch.setenv("LACE_BATCH_MODE", "per_instance")
+    phis = [p.copy() for _, _, p in sy]
+    with Batch([(s.cell, s.shape, s.ecut, s.n_occ, thr) for s, thr, _ in sy]) as b:
+        for q, p in enumerate(phis):
+            b.set_orbitals(q, p)
+        for _ in range(3):  # eager, capture, re-capture
+            ex, st = b.run()
+            assert (st == 0).all()
+            assert np.max(np.abs(ex - out["runs"][0][0])) <= 1e-5
+        info = b.info()
+        assert info["mode"] == "per_instance" and info["graph_replays"] >= 2
+        assert info["tune_ms"]["per_instance"] > 0
+        for p in phis:
+            synth.perturb_in_place(p, 3e-2)
+        ex2, st2 = b.run()
+        assert (st2 == 0).all()
+        for q in (0, 2, 5):
+            s, thr, _ = sy[q]
+            assert len(b.context(q).get_pairs()) == len(single(s, thr, phis[q])["pairs"])
+            assert abs(ex2[q] - single(s, thr, phis[q])["ex"]) <= 1e-5
