@@ -216,27 +216,67 @@ lace_status prepare(lace_batch* b) {
 }
 
 // Per-instance mode: each instance's pair convolutions through the
-// single-system passes (size-specialised where they exist), one instance
-// after another on the shared scratch pool.  The launch sizes follow the
-// current pair counts, so a graph of this mode is re-captured every run.
+// single-system passes (size-specialised where they exist).  The instances
+// are spread over the branch streams (largest first, each to the least
+// loaded stream), each stream with its own slice of the scratch pool, so
+// small instances overlap.  The launch sizes follow the current pair counts,
+// so a graph of this mode is re-captured every run.
 lace_status pairconv_per_instance(lace_batch* b, cudaStream_t s, int* launches) {
+    std::vector<int> act;
+    size_t max_ng = 1;
+    int max_n1 = 1;
     for (int q = 0; q < b->n; ++q) {
         if (!b->in_graph[q] || b->h_ngrids[q] == 0) continue;
-        lace_ctx* c = b->ctx[q];
-        FFTTables<float> tb;
-        for (int a = 0; a < 3; ++a) {
-            tb.tw[a] = c->tw_f[a].as<cplx<float>>();
-            tb.g2[a] = c->g2_f[a].as<float>();
+        act.push_back(q);
+        max_ng = std::max(max_ng, b->ctx[q]->g.ng);
+        max_n1 = std::max(max_n1, b->ctx[q]->g.n[0]);
+    }
+    if (act.empty()) return LACE_OK;
+    const auto work = [&](int q) { return (double)b->h_ngrids[q] * (double)b->ctx[q]->g.ng; };
+    std::sort(act.begin(), act.end(), [&](int x, int y) { return work(x) > work(y); });
+    int P = std::min<int>(kBranches, (int)act.size());
+    P = (int)std::max<size_t>(1, std::min<size_t>({(size_t)P, b->pool_elems / (max_ng + 256),
+                                                   b->epart_elems / (2 * (size_t)max_n1 + 256)}));
+    // slices start on 2 KB boundaries (the FFT passes use vector accesses);
+    // P was bounded so that a rounded slice still holds the largest grid
+    const size_t part = P > 1 ? b->pool_elems / P / 256 * 256 : b->pool_elems;
+    const size_t epart = P > 1 ? b->epart_elems / P / 256 * 256 : b->epart_elems;
+    std::vector<double> load(P, 0.0);
+    std::vector<std::vector<int>> lanes(P);
+    for (int q : act) {
+        const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+        lanes[k].push_back(q);
+        load[k] += work(q);
+    }
+    if (P > 1) {
+        BCK(cudaEventRecord(b->ev_fork, s), "batch");
+        for (int k = 0; k < P; ++k) BCK(cudaStreamWaitEvent(b->branch[k], b->ev_fork, 0), "batch");
+    }
+    for (int k = 0; k < P; ++k) {
+        cudaStream_t sk = P > 1 ? b->branch[k] : s;
+        cplx<float>* pool = b->pool.as<cplx<float>>() + k * part;
+        double* ep = b->epart.as<double>() + k * epart;
+        for (int q : lanes[k]) {
+            lace_ctx* c = b->ctx[q];
+            FFTTables<float> tb;
+            for (int a = 0; a < 3; ++a) {
+                tb.tw[a] = c->tw_f[a].as<cplx<float>>();
+                tb.g2[a] = c->g2_f[a].as<float>();
+            }
+            tb.ktab = c->ktab_f.as<float>();
+            const size_t ng = c->g.ng;
+            const int batch = (int)std::max<size_t>(
+                1, std::min<size_t>({(size_t)b->h_ngrids[q], part / ng, epart / (2 * (size_t)c->g.n[0]), (size_t)1024}));
+            BCK(pairconv_run<float>(c->g, tb, c->psi.as<float>(), c->n_occ, c->W.as<float>(), c->grids.as<PairGrid>(),
+                                    b->h_ngrids[q], pool, batch, ep, c->m(MS_E), sk, launches, nullptr, nullptr),
+                "per-instance pair convolutions");
         }
-        tb.ktab = c->ktab_f.as<float>();
-        const size_t ng = c->g.ng;
-        const int batch = (int)std::max<size_t>(
-            1, std::min<size_t>({(size_t)b->h_ngrids[q], b->pool_elems / ng, b->epart_elems / (2 * (size_t)c->g.n[0]),
-                                 (size_t)1024}));
-        BCK(pairconv_run<float>(c->g, tb, c->psi.as<float>(), c->n_occ, c->W.as<float>(), c->grids.as<PairGrid>(),
-                                b->h_ngrids[q], b->pool.as<cplx<float>>(), batch, b->epart.as<double>(), c->m(MS_E), s,
-                                launches, nullptr, nullptr),
-            "per-instance pair convolutions");
+    }
+    if (P > 1) {
+        for (int k = 0; k < P; ++k) {
+            BCK(cudaEventRecord(b->ev_join[k], b->branch[k]), "batch");
+            BCK(cudaStreamWaitEvent(s, b->ev_join[k], 0), "batch");
+        }
     }
     return LACE_OK;
 }

@@ -533,7 +533,11 @@ static cudaError_t qr_persistent_launch(int nrow, int ncol, T* R, int npiv, Best
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes)))
         return e;
     const int ngroups = QC_WARPS / wpt;
-    const int ntiles = (ncol + 31) / 32, total_groups = sms * ngroups;
+    const int ntiles = (ncol + 31) / 32;
+    // no more CTAs than it takes to hold every tile in registers: a small
+    // matrix then syncs fewer CTAs per step and leaves SMs to other work
+    const int ctas = std::min(sms, std::max(1, (ntiles + ngroups * std::max(NREG, 1) - 1) / (ngroups * std::max(NREG, 1))));
+    const int total_groups = ctas * ngroups;
     const int max_k = (ntiles + total_groups - 1) / total_groups;
     const size_t tile_bytes = (size_t)wpt * RPW * 32 * sizeof(T);  // one tile slot of one group
     const size_t red_bytes = (size_t)2 * QC_WARPS * 32 * sizeof(T);  // dot and norm partials of one tile slot
@@ -549,7 +553,7 @@ static cudaError_t qr_persistent_launch(int nrow, int ncol, T* R, int npiv, Best
     if ((e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s))) return e;
     void* args[] = {(void*)&nrow, (void*)&ncol, (void*)&R,   (void*)&npiv,   (void*)&wpt,  (void*)&nsm,
                     (void*)&best, (void*)&pub,  (void*)&chosen, (void*)&d_piv, (void*)&bar};
-    if ((e = cudaLaunchCooperativeKernel(fn, dim3(sms), dim3(QC_THREADS), args, dyn, s))) return e;
+    if ((e = cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(QC_THREADS), args, dyn, s))) return e;
     *launches += 1;
     *ran = true;
     return cudaSuccess;
