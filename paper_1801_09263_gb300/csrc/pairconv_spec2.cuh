@@ -1,0 +1,377 @@
+// Size-specialised FP32 FFT passes of the pair convolutions, out-of-place
+// form.  Same three passes and the same arithmetic as pairconv_spec.cuh
+// (Eq. 2 evaluated with FFTs, Sec. 2; truncated by Eq. 5), laid out for
+// fewer barriers and more memory-level parallelism:
+//   * every radix stage reads one shared-memory plane and writes the other
+//     (ping-pong), so a thread keeps one butterfly live and a stage ends in
+//     one barrier instead of two;
+//   * the first stage of a pass loads its butterfly straight from global
+//     memory (pass A forms rho = w_i psi_j there) and the last stage of
+//     passes A and B stores straight to global memory;
+//   * pass B runs the forward x-FFT as decimation in time and the inverse as
+//     decimation in frequency, so the second forward stage, the product
+//     with K(G)/Ng and the first inverse stage act on the same registers:
+//     for n = A*B (A = r2, B = r1), x index n1 + A n2 and k index k2 + B k1,
+//       X[k2 + B k1] = sum_n1 w_A^{n1 k1} w_N^{n1 k2} sum_n2 w_B^{n2 k2} x[n1 + A n2]
+//       x[n1 + A n2] = sum_k2 w_B^{-n2 k2} w_N^{-n1 k2} sum_k1 w_A^{-n1 k1} Y[k2 + B k1]
+//     and a group of fixed k2 is one forward and one inverse butterfly.
+//     Pass B needs two barriers.
+#pragma once
+
+#include <atomic>
+#include <cstdlib>
+
+#include "pairconv_spec.cuh"
+
+namespace lace {
+namespace spec2 {
+
+using C = float2;
+using spec::plan2;
+using spec::Plan2;
+
+// Dynamic shared memory: two complex planes, the twiddle table and (pass B)
+// the |G|^2 tables of x and z.
+__host__ __device__ constexpr size_t smem_bytes(int n, int pass) {
+    return sizeof(C) * (2 * (size_t)n * n + n) + (pass == 1 ? 2 * sizeof(float) * n : 0);
+}
+
+// Registers a thread may use when m CTAs of nt threads share an SM: the
+// register file is split over the SM's four sub-partitions (16K registers
+// each), every warp takes its registers from one of them, and a thread's
+// count is a multiple of 8.
+__host__ __device__ constexpr int regs_at(int nt, int m) {
+    const int warps = (nt + 31) / 32;
+    const int per_part = (m * warps + 3) / 4;
+    const int r = 16384 / (per_part * 32) / 8 * 8;
+    return r > 255 ? 255 : r;
+}
+
+// CTAs of nt threads per SM with at least 48 registers a thread, within the
+// shared memory (227 KB, 1 KB reserved per CTA) and 2048 threads of an SM.
+__host__ __device__ constexpr int blocks_at(int n, int nt) {
+    int m = (int)((227u * 1024u) / (smem_bytes(n, 1) + 1024));
+    const int by_thr = 2048 / ((nt + 31) / 32 * 32);
+    if (m > by_thr) m = by_thr;
+    while (m > 1 && regs_at(nt, m) < 48) --m;
+    return m < 1 ? 1 : m;
+}
+
+// Threads per CTA: one butterfly per thread in the stage with the most
+// butterflies, or in the one with the fewest when that is what lets two
+// CTAs share an SM (the larger stage then takes a second round); at most
+// 1024.
+__host__ __device__ constexpr int threads_for(int n) {
+    const Plan2 p = plan2(n);
+    const int a = n * (n / p.r1), b = n * (n / p.r2);
+    int hi = a > b ? a : b, lo = a > b ? b : a;
+    hi = (hi + 31) / 32 * 32;
+    lo = (lo + 31) / 32 * 32;
+    if (hi > 1024) hi = 1024;
+    if (lo > 1024) lo = 1024;
+    return (blocks_at(n, hi) >= 2 || blocks_at(n, lo) < 2) ? hi : lo;
+}
+
+// Register cap of the passes.
+__host__ __device__ constexpr int max_regs(int n) { return regs_at(threads_for(n), blocks_at(n, threads_for(n))); }
+
+// One radix-R Stockham stage over LINES lines of length N, out of place:
+// butterfly i of a line reads elements i + t N/R through ld(line, e),
+// multiplies by w_{P R}^{t k} (k = i mod P), runs DFT_R and writes element
+// (i - k) R + k + s P through st(line, e, v).  LF: consecutive threads take
+// consecutive lines (else consecutive butterflies of one line).
+template <int N, int R, int P, int DIR, int LINES, bool LF, int NT, class Ld, class St>
+__device__ __forceinline__ void stage(const C* __restrict__ tw, Ld ld, St st) {
+    constexpr int TN = N / R;
+    constexpr int ITEMS = LINES * TN;
+    constexpr int TWSTEP = N / (P * R);
+#pragma unroll
+    for (int item0 = 0; item0 < ITEMS; item0 += NT) {
+        const int item = item0 + (int)threadIdx.x;
+        if (item0 + NT <= ITEMS || item < ITEMS) {
+            const int line = LF ? item % LINES : item / TN;
+            const int i = LF ? item / LINES : item % TN;
+            C v[R];
+#pragma unroll
+            for (int t = 0; t < R; ++t) v[t] = ld(line, i + t * TN);
+            const int k = P > 1 ? i % P : 0;
+            if (P > 1) {
+#pragma unroll
+                for (int t = 1; t < R; ++t) {
+                    C w = tw[t * k * TWSTEP];
+                    if (DIR > 0) w.y = -w.y;
+                    v[t] = cmul(v[t], w);
+                }
+            }
+            DFT<R, DIR>::run(v);
+            const int base = (i - k) * R + k;
+#pragma unroll
+            for (int s = 0; s < R; ++s) st(line, base + s * P, v[s]);
+        }
+    }
+}
+
+// Pass A: rho of plane x, forward FFT along z then y.
+template <int N>
+__global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_a(ConvArgs<float> P, int g0) {
+    constexpr int NT = threads_for(N);
+    constexpr int NP = N * N;
+    constexpr Plan2 pl = plan2(N);
+    extern __shared__ float4 smem_v4[];
+    C* b0 = reinterpret_cast<C*>(smem_v4);
+    C* b1 = b0 + NP;
+    C* tw = b1 + NP;
+    const int g = blockIdx.y, x = blockIdx.x;
+    const PairGrid d = P.grids[g0 + g];
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = P.tw[2][i];
+    const size_t off = (size_t)x * NP;
+    const bool two = d.j2 >= 0;
+    const float* a1 = P.psi + (size_t)d.i1 * P.ng + off;
+    const float* c1 = P.psi + (size_t)d.j1 * P.ng + off;
+    const float* a2 = P.psi + (size_t)(two ? d.i2 : d.i1) * P.ng + off;
+    const float* c2 = P.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off;
+    // z lines (line = y): rho straight from the orbitals
+    stage<N, pl.r1, 1, -1, N, false, NT>(
+        tw,
+        [&](int y, int z) {
+            const int q = y * N + z;
+            const float u = __ldg(a1 + q) * __ldg(c1 + q);
+            const float v = two ? __ldg(a2 + q) * __ldg(c2 + q) : 0.f;
+            return C{u, v};
+        },
+        [&](int y, int z, C v) { b0[y * N + z] = v; });
+    __syncthreads();
+    stage<N, pl.r2, pl.r1, -1, N, false, NT>(
+        tw, [&](int y, int z) { return b0[y * N + z]; }, [&](int y, int z, C v) { b1[y * N + z] = v; });
+    __syncthreads();
+    // y lines (line = z)
+    stage<N, pl.r1, 1, -1, N, true, NT>(
+        tw, [&](int z, int y) { return b1[y * N + z]; }, [&](int z, int y, C v) { b0[y * N + z] = v; });
+    __syncthreads();
+    C* out = P.scratch + (size_t)g * P.ng + off;
+    stage<N, pl.r2, pl.r1, -1, N, true, NT>(
+        tw, [&](int z, int y) { return b0[y * N + z]; }, [&](int z, int y, C v) { out[y * N + z] = v; });
+}
+
+// Pass B: slab ky: forward x-FFT (decimation in time), * K(G)/Ng, inverse
+// x-FFT (decimation in frequency); the middle three steps share registers.
+template <int N>
+__global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_b(ConvArgs<float> P, int g0) {
+    constexpr int NT = threads_for(N);
+    constexpr int NP = N * N;
+    constexpr Plan2 pl = plan2(N);
+    constexpr int RB = pl.r1, RA = pl.r2;  // N = RA * RB
+    extern __shared__ float4 smem_v4[];
+    C* b0 = reinterpret_cast<C*>(smem_v4);
+    C* b1 = b0 + NP;
+    C* tw = b1 + NP;
+    float* gx2 = reinterpret_cast<float*>(tw + N);
+    float* gz2 = gx2 + N;
+    const int g = blockIdx.y, ky = blockIdx.x;
+    for (int i = threadIdx.x; i < N; i += NT) {
+        tw[i] = P.tw[0][i];
+        gx2[i] = P.g2[0][i];
+        gz2[i] = P.g2[2][i];
+    }
+    C* base = P.scratch + (size_t)g * P.ng + (size_t)ky * N;
+    // forward stage 1 (line = z): DFT_RB over n2 of x[n1 + RA n2], to y[n1 RB + k2]
+    stage<N, RB, 1, -1, N, true, NT>(
+        tw, [&](int z, int xx) { return base[(size_t)xx * NP + z]; },
+        [&](int z, int xx, C v) { b0[xx * N + z] = v; });
+    __syncthreads();
+    const float gy2 = P.g2[1][ky];
+    // middle: for each (z, k2): twiddle, DFT_RA -> X[k2 + RB k1], * K, inverse
+    // DFT_RA -> z[k2][n1], twiddle w_N^{-n1 k2}, stored at n1 RB + k2
+    constexpr int MID = N * RB;
+#pragma unroll
+    for (int item0 = 0; item0 < MID; item0 += NT) {
+        const int item = item0 + (int)threadIdx.x;
+        if (item0 + NT <= MID || item < MID) {
+            const int z = item % N, k2 = item / N;
+            C v[RA];
+#pragma unroll
+            for (int t = 0; t < RA; ++t) {
+                v[t] = b0[(k2 + t * RB) * N + z];
+                if (t > 0) v[t] = cmul(v[t], tw[t * k2]);
+            }
+            DFT<RA, -1>::run(v);
+#pragma unroll
+            for (int s = 0; s < RA; ++s) {
+                const int xx = k2 + s * RB;
+                float k;
+                if (P.ktab) {
+                    k = __ldg(P.ktab + ((size_t)xx * N + ky) * N + z);
+                } else {
+                    const float gg = gx2[xx] + gy2 + gz2[z];
+                    k = gg > 0.f ? P.kscale / gg : 0.f;
+                }
+                v[s] = C{v[s].x * k, v[s].y * k};
+            }
+            DFT<RA, +1>::run(v);
+#pragma unroll
+            for (int n1 = 0; n1 < RA; ++n1) {
+                C w = tw[n1 * k2];
+                w.y = -w.y;
+                b1[(n1 * RB + k2) * N + z] = n1 > 0 ? cmul(v[n1], w) : v[n1];
+            }
+        }
+    }
+    __syncthreads();
+    // inverse stage 2 (line = z): for each n1, DFT_RB over k2 -> x[n1 + RA n2]
+    constexpr int LAST = N * RA;
+#pragma unroll
+    for (int item0 = 0; item0 < LAST; item0 += NT) {
+        const int item = item0 + (int)threadIdx.x;
+        if (item0 + NT <= LAST || item < LAST) {
+            const int z = item % N, n1 = item / N;
+            C v[RB];
+#pragma unroll
+            for (int t = 0; t < RB; ++t) v[t] = b1[(n1 * RB + t) * N + z];
+            DFT<RB, +1>::run(v);
+#pragma unroll
+            for (int s = 0; s < RB; ++s) base[(size_t)(n1 + RA * s) * NP + z] = v[s];
+        }
+    }
+    (void)g0;
+}
+
+// Pass C: inverse FFT along y then z of plane x, then the W updates
+// (16-byte vector reductions) and the real-space pair energies.
+template <int N>
+__global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_c(ConvArgs<float> P, int g0) {
+    constexpr int NT = threads_for(N);
+    constexpr int NP = N * N;
+    constexpr Plan2 pl = plan2(N);
+    extern __shared__ float4 smem_v4[];
+    C* b0 = reinterpret_cast<C*>(smem_v4);
+    C* b1 = b0 + NP;
+    C* tw = b1 + NP;
+    __shared__ double red[2][(NT + 31) / 32];
+    const int g = blockIdx.y, x = blockIdx.x;
+    const PairGrid d = P.grids[g0 + g];
+    for (int i = threadIdx.x; i < N; i += NT) tw[i] = P.tw[2][i];
+    const size_t off = (size_t)x * NP;
+    const C* in = P.scratch + (size_t)g * P.ng + off;
+    stage<N, pl.r1, 1, +1, N, true, NT>(
+        tw, [&](int z, int y) { return in[y * N + z]; }, [&](int z, int y, C v) { b0[y * N + z] = v; });
+    __syncthreads();
+    stage<N, pl.r2, pl.r1, +1, N, true, NT>(
+        tw, [&](int z, int y) { return b0[y * N + z]; }, [&](int z, int y, C v) { b1[y * N + z] = v; });
+    __syncthreads();
+    stage<N, pl.r1, 1, +1, N, false, NT>(
+        tw, [&](int y, int z) { return b1[y * N + z]; }, [&](int y, int z, C v) { b0[y * N + z] = v; });
+    __syncthreads();
+    stage<N, pl.r2, pl.r1, +1, N, false, NT>(
+        tw, [&](int y, int z) { return b0[y * N + z]; }, [&](int y, int z, C v) { b1[y * N + z] = v; });
+    __syncthreads();
+    const bool two = d.j2 >= 0;
+    const bool a_occ = d.j1 < P.n_occ, a_sym = a_occ && d.j1 != d.i1;
+    const bool b_occ = two && d.j2 < P.n_occ, b_sym = b_occ && d.j2 != d.i2;
+    const float4* wi1 = reinterpret_cast<const float4*>(P.psi + (size_t)d.i1 * P.ng + off);
+    const float4* pj1 = reinterpret_cast<const float4*>(P.psi + (size_t)d.j1 * P.ng + off);
+    float4* Wj1 = reinterpret_cast<float4*>(P.W + (size_t)d.j1 * P.ng + off);
+    float4* Wi1 = reinterpret_cast<float4*>(P.W + (size_t)d.i1 * P.ng + off);
+    const float4* wi2 = reinterpret_cast<const float4*>(P.psi + (size_t)(two ? d.i2 : d.i1) * P.ng + off);
+    const float4* pj2 = reinterpret_cast<const float4*>(P.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off);
+    float4* Wj2 = reinterpret_cast<float4*>(P.W + (size_t)(two ? d.j2 : d.j1) * P.ng + off);
+    float4* Wi2 = reinterpret_cast<float4*>(P.W + (size_t)(two ? d.i2 : d.i1) * P.ng + off);
+    const bool merge_i = two && a_sym && b_sym && d.i1 == d.i2;
+    const float4* pl4 = reinterpret_cast<const float4*>(b1);
+    float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
+#pragma unroll
+    for (int e0 = 0; e0 < NP / 4; e0 += NT) {
+        const int e = e0 + (int)threadIdx.x;
+        if (e0 + NT <= NP / 4 || e < NP / 4) {
+            const float4 v01 = pl4[2 * e], v23 = pl4[2 * e + 1];
+            const float4 x1 = __ldg(wi1 + e), y1 = __ldg(pj1 + e);
+            atomicAdd(Wj1 + e, make_float4(-x1.x * v01.x, -x1.y * v01.z, -x1.z * v23.x, -x1.w * v23.z));
+            const float4 wi_acc = make_float4(-y1.x * v01.x, -y1.y * v01.z, -y1.z * v23.x, -y1.w * v23.z);
+            if (a_sym && !merge_i) atomicAdd(Wi1 + e, wi_acc);
+            if (a_occ)
+                spec::kahan(sa, ca,
+                            x1.x * y1.x * v01.x + x1.y * y1.y * v01.z + x1.z * y1.z * v23.x + x1.w * y1.w * v23.z);
+            if (two) {
+                const float4 x2 = merge_i ? x1 : __ldg(wi2 + e);
+                const float4 y2 = __ldg(pj2 + e);
+                atomicAdd(Wj2 + e, make_float4(-x2.x * v01.y, -x2.y * v01.w, -x2.z * v23.y, -x2.w * v23.w));
+                const float4 w2 = make_float4(-y2.x * v01.y, -y2.y * v01.w, -y2.z * v23.y, -y2.w * v23.w);
+                if (merge_i) {
+                    atomicAdd(Wi1 + e,
+                              make_float4(wi_acc.x + w2.x, wi_acc.y + w2.y, wi_acc.z + w2.z, wi_acc.w + w2.w));
+                } else if (b_sym) {
+                    atomicAdd(Wi2 + e, w2);
+                }
+                if (b_occ)
+                    spec::kahan(sb, cb,
+                                x2.x * y2.x * v01.y + x2.y * y2.y * v01.w + x2.z * y2.z * v23.y + x2.w * y2.w * v23.w);
+            }
+        }
+    }
+    sa -= ca;
+    sb -= cb;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        sa += __shfl_xor_sync(0xffffffffu, sa, o);
+        sb += __shfl_xor_sync(0xffffffffu, sb, o);
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[0][warp] = (double)sa; red[1][warp] = (double)sb; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double ta = 0.0, tbb = 0.0;
+        for (int w = 0; w < (NT + 31) / 32; ++w) { ta += red[0][w]; tbb += red[1][w]; }
+        double* ep = P.epart + ((size_t)g * gridDim.x + x) * 2;
+        ep[0] = ta * P.dv;
+        ep[1] = tbb * P.dv;
+    }
+}
+
+// Launch pass 0/1/2 of a batch of nb complex grids.
+template <int N>
+bool launch_one(int pass, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s) {
+    static std::atomic<unsigned long long> attr_done{0};  // one bit per device
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && !(attr_done.load() & (1ull << dev))) {
+        cudaFuncSetAttribute(pass_a<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(N, 0));
+        cudaFuncSetAttribute(pass_b<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(N, 1));
+        cudaFuncSetAttribute(pass_c<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(N, 2));
+        cudaFuncSetAttribute(pass_a<N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(pass_b<N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaFuncSetAttribute(pass_c<N>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        attr_done.fetch_or(1ull << dev);
+    }
+    const size_t sm = smem_bytes(N, pass);
+    const dim3 grid(N, nb);
+    constexpr int NT = threads_for(N);
+    if (pass == 0) pass_a<N><<<grid, NT, sm, s>>>(P, g0);
+    else if (pass == 1) pass_b<N><<<grid, NT, sm, s>>>(P, g0);
+    else pass_c<N><<<grid, NT, sm, s>>>(P, g0);
+    return true;
+}
+
+// LACE_FFT_INPLACE=1 selects the in-place passes of pairconv_spec.cuh (kept
+// for comparison and for grids whose two planes do not fit on chip).
+inline bool enabled() {
+    static const int on = [] {
+        const char* e = getenv("LACE_FFT_INPLACE");
+        return (e && e[0] == '1') ? 0 : 1;
+    }();
+    return on != 0;
+}
+
+}  // namespace spec2
+
+namespace spec {
+
+// Out-of-place passes where two planes fit in shared memory, else in place.
+template <int N>
+bool launch_any(int pass, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s) {
+    if constexpr (spec2::smem_bytes(N, 1) <= 200 * 1024) {
+        if (spec2::enabled()) return spec2::launch_one<N>(pass, nb, P, g0, s);
+    }
+    return spec_launch_one<N>(pass, nb, P, g0, s);
+}
+
+}  // namespace spec
+}  // namespace lace
