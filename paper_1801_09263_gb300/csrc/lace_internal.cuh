@@ -50,6 +50,7 @@ template <typename T> struct ConvArgs {
     double* epart;  // [batch][n1][2]
     size_t ng;
     double dv;
+    int pf_ahead = 0;  // L2 prefetch distance in CTAs of the out-of-place passes (0: none)
 };
 
 // Size-specialised FP32 passes for cubic grids (pairconv_spec_*.cu): launch

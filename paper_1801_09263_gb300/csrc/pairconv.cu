@@ -162,6 +162,17 @@ cudaError_t pairconv_run(const GridGeom& g, const FFTTables<T>& tb, const T* psi
         }
         if (dev < 64) attr_done.fetch_or(1ull << dev);
     }
+    {
+        // the out-of-place passes prefetch into L2 what the CTA two waves
+        // later (at two CTAs per SM) will read
+        int nsm = 0;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
+        static const int per_sm = [] {
+            const char* v = getenv("LACE_L2_PREFETCH_PER_SM");  // tuning: CTAs ahead per SM (0: off)
+            return v ? atoi(v) : 2;
+        }();
+        P.pf_ahead = per_sm * nsm;
+    }
     if (sm_plane > (size_t)INT32_MAX || sm_slab > (size_t)INT32_MAX) return cudaErrorInvalidValue;
     // size-specialised FP32 kernels for cubic grids with n % 4 == 0 (or LACE_GENERIC_FFT=1 to disable)
     const char* gen = getenv("LACE_GENERIC_FFT");

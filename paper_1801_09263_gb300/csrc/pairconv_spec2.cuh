@@ -75,6 +75,22 @@ __host__ __device__ constexpr int threads_for(int n) {
 // Register cap of the passes.
 __host__ __device__ constexpr int max_regs(int n) { return regs_at(threads_for(n), blocks_at(n, threads_for(n))); }
 
+// Hint: fetch bytes (a multiple of 16, 16-byte aligned) at p into L2.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// The CTA pf_ahead launch positions after this one (x fastest), if any:
+// its plane or slab index and its grid within the batch.
+__device__ __forceinline__ bool ahead_cta(int pf_ahead, int& xa, int& ga) {
+    if (pf_ahead <= 0) return false;
+    const long lin = (long)blockIdx.y * gridDim.x + blockIdx.x + pf_ahead;
+    if (lin >= (long)gridDim.x * gridDim.y) return false;
+    xa = (int)(lin % gridDim.x);
+    ga = (int)(lin / gridDim.x);
+    return true;
+}
+
 // One radix-R Stockham stage over LINES lines of length N, out of place:
 // butterfly i of a line reads elements i + t N/R through ld(line, e),
 // multiplies by w_{P R}^{t k} (k = i mod P), runs DFT_R and writes element
@@ -130,6 +146,13 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     const float* c1 = P.psi + (size_t)d.j1 * P.ng + off;
     const float* a2 = P.psi + (size_t)(two ? d.i2 : d.i1) * P.ng + off;
     const float* c2 = P.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off;
+    int xa = 0, ga = 0;
+    const bool pf = threadIdx.x < 4 && ahead_cta(P.pf_ahead, xa, ga);
+    int pf_orb = -1;  // orbital plane of the CTA ahead that this thread prefetches
+    if (pf) {
+        const int* dd = reinterpret_cast<const int*>(P.grids + g0 + ga);
+        pf_orb = __ldg(dd + threadIdx.x);  // i1, j1, i2, j2 (j2 < 0: one pair)
+    }
     // z lines (line = y): rho straight from the orbitals
     stage<N, pl.r1, 1, -1, N, false, NT>(
         tw,
@@ -151,6 +174,7 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     C* out = P.scratch + (size_t)g * P.ng + off;
     stage<N, pl.r2, pl.r1, -1, N, true, NT>(
         tw, [&](int z, int y) { return b0[y * N + z]; }, [&](int z, int y, C v) { out[y * N + z] = v; });
+    if (pf && pf_orb >= 0) prefetch_l2(P.psi + (size_t)pf_orb * P.ng + (size_t)xa * NP, NP * sizeof(float));
 }
 
 // Pass B: slab ky: forward x-FFT (decimation in time), * K(G)/Ng, inverse
@@ -174,6 +198,11 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
         gz2[i] = P.g2[2][i];
     }
     C* base = P.scratch + (size_t)g * P.ng + (size_t)ky * N;
+    {
+        int ka = 0, ga = 0;
+        if (threadIdx.x < N && ahead_cta(P.pf_ahead, ka, ga))
+            prefetch_l2(P.scratch + (size_t)ga * P.ng + (size_t)threadIdx.x * NP + (size_t)ka * N, N * sizeof(C));
+    }
     // forward stage 1 (line = z): DFT_RB over n2 of x[n1 + RA n2], to y[n1 RB + k2]
     stage<N, RB, 1, -1, N, true, NT>(
         tw, [&](int z, int xx) { return base[(size_t)xx * NP + z]; },
@@ -252,8 +281,23 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = P.tw[2][i];
     const size_t off = (size_t)x * NP;
     const C* in = P.scratch + (size_t)g * P.ng + off;
+    {
+        int xa = 0, ga = 0;
+        if (threadIdx.x == 32 && ahead_cta(P.pf_ahead, xa, ga))
+            prefetch_l2(P.scratch + (size_t)ga * P.ng + (size_t)xa * NP, NP * sizeof(C));
+    }
     stage<N, pl.r1, 1, +1, N, true, NT>(
         tw, [&](int z, int y) { return in[y * N + z]; }, [&](int z, int y, C v) { b0[y * N + z] = v; });
+    if (P.pf_ahead > 0 && threadIdx.x < 8) {
+        // the epilogue's orbital planes and W planes, fetched into L2 while
+        // the FFT stages run
+        const int q = threadIdx.x & 3;
+        const int o = q == 0 ? d.i1 : q == 1 ? d.j1 : q == 2 ? d.i2 : d.j2;
+        if (o >= 0) {
+            const float* src = (threadIdx.x < 4 ? P.psi : P.W) + (size_t)o * P.ng + off;
+            prefetch_l2(src, NP * sizeof(float));
+        }
+    }
     __syncthreads();
     stage<N, pl.r2, pl.r1, +1, N, true, NT>(
         tw, [&](int z, int y) { return b0[y * N + z]; }, [&](int z, int y, C v) { b1[y * N + z] = v; });
