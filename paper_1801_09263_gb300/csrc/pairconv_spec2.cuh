@@ -80,14 +80,14 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// The CTA pf_ahead launch positions after this one (x fastest), if any:
-// its plane or slab index and its grid within the batch.
-__device__ __forceinline__ bool ahead_cta(int pf_ahead, int& xa, int& ga) {
+// The CTA pf_ahead launch positions after this one, if any: its
+// blockIdx.x (fast) and blockIdx.y (slow).
+__device__ __forceinline__ bool ahead_cta(int pf_ahead, int& fast, int& slow) {
     if (pf_ahead <= 0) return false;
     const long lin = (long)blockIdx.y * gridDim.x + blockIdx.x + pf_ahead;
     if (lin >= (long)gridDim.x * gridDim.y) return false;
-    xa = (int)(lin % gridDim.x);
-    ga = (int)(lin / gridDim.x);
+    fast = (int)(lin % gridDim.x);
+    slow = (int)(lin / gridDim.x);
     return true;
 }
 
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     C* b0 = reinterpret_cast<C*>(smem_v4);
     C* b1 = b0 + NP;
     C* tw = b1 + NP;
-    const int g = blockIdx.y, x = blockIdx.x;
+    const int g = blockIdx.x, x = blockIdx.y;  // plane-major: the CTAs in flight share plane x
     const PairGrid d = P.grids[g0 + g];
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = P.tw[2][i];
     const size_t off = (size_t)x * NP;
@@ -147,7 +147,7 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     const float* a2 = P.psi + (size_t)(two ? d.i2 : d.i1) * P.ng + off;
     const float* c2 = P.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off;
     int xa = 0, ga = 0;
-    const bool pf = threadIdx.x < 4 && ahead_cta(P.pf_ahead, xa, ga);
+    const bool pf = threadIdx.x < 4 && ahead_cta(P.pf_ahead, ga, xa);
     int pf_orb = -1;  // orbital plane of the CTA ahead that this thread prefetches
     if (pf) {
         const int* dd = reinterpret_cast<const int*>(P.grids + g0 + ga);
@@ -276,14 +276,14 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     C* b1 = b0 + NP;
     C* tw = b1 + NP;
     __shared__ double red[2][(NT + 31) / 32];
-    const int g = blockIdx.y, x = blockIdx.x;
+    const int g = blockIdx.x, x = blockIdx.y;  // plane-major: the CTAs in flight share plane x
     const PairGrid d = P.grids[g0 + g];
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = P.tw[2][i];
     const size_t off = (size_t)x * NP;
     const C* in = P.scratch + (size_t)g * P.ng + off;
     {
         int xa = 0, ga = 0;
-        if (threadIdx.x == 32 && ahead_cta(P.pf_ahead, xa, ga))
+        if (threadIdx.x == 32 && ahead_cta(P.pf_ahead, ga, xa))
             prefetch_l2(P.scratch + (size_t)ga * P.ng + (size_t)xa * NP, NP * sizeof(C));
     }
     stage<N, pl.r1, 1, +1, N, true, NT>(
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     if (threadIdx.x == 0) {
         double ta = 0.0, tbb = 0.0;
         for (int w = 0; w < (NT + 31) / 32; ++w) { ta += red[0][w]; tbb += red[1][w]; }
-        double* ep = P.epart + ((size_t)g * gridDim.x + x) * 2;
+        double* ep = P.epart + ((size_t)g * N + x) * 2;
         ep[0] = ta * P.dv;
         ep[1] = tbb * P.dv;
     }
@@ -386,11 +386,10 @@ bool launch_one(int pass, int nb, const ConvArgs<float>& P, int g0, cudaStream_t
         attr_done.fetch_or(1ull << dev);
     }
     const size_t sm = smem_bytes(N, pass);
-    const dim3 grid(N, nb);
     constexpr int NT = threads_for(N);
-    if (pass == 0) pass_a<N><<<grid, NT, sm, s>>>(P, g0);
-    else if (pass == 1) pass_b<N><<<grid, NT, sm, s>>>(P, g0);
-    else pass_c<N><<<grid, NT, sm, s>>>(P, g0);
+    if (pass == 0) pass_a<N><<<dim3(nb, N), NT, sm, s>>>(P, g0);
+    else if (pass == 1) pass_b<N><<<dim3(N, nb), NT, sm, s>>>(P, g0);
+    else pass_c<N><<<dim3(nb, N), NT, sm, s>>>(P, g0);
     return true;
 }
 
