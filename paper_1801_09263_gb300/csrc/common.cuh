@@ -97,6 +97,16 @@ __device__ __forceinline__ C twiddle_ct(C a) {
         return cmul_i<DIR>(a);
     } else if constexpr (4 * m == 3 * N) {
         return cmul_i<-DIR>(a);
+    } else if constexpr ((8 * m) % N == 0) {
+        // odd multiple of pi/4: cos and sin are +-sqrt(1/2); add first,
+        // then one constant product per component
+        constexpr int e8 = 8 * m / N;
+        constexpr int cx = (e8 == 1 || e8 == 7) ? 1 : -1;
+        constexpr int ss = DIR * ((e8 == 1 || e8 == 3) ? 1 : -1);
+        constexpr double h = 0.707106781186547524400844362104849039;
+        const T u = cx > 0 ? (ss > 0 ? a.x - a.y : a.x + a.y) : (ss > 0 ? -a.x - a.y : a.y - a.x);
+        const T w = cx > 0 ? (ss > 0 ? a.x + a.y : a.y - a.x) : (ss > 0 ? a.x - a.y : -a.x - a.y);
+        return C{mulk(u, h), mulk(w, h)};
     } else {
         constexpr double c = ct_cos2pi(m, N);
         constexpr double s = DIR * ct_sin2pi(m, N);

@@ -30,10 +30,14 @@ using C = float2;
 using spec::plan2;
 using spec::Plan2;
 
-// Dynamic shared memory: two complex planes, the twiddle table and (pass B)
-// the |G|^2 tables of x and z.
+// Dynamic shared memory: two complex planes (rows padded to n + 1 in passes
+// A and C), the twiddle table and (pass B) the |G|^2 tables of x and z.
 __host__ __device__ constexpr size_t smem_bytes(int n, int pass) {
-    return sizeof(C) * (2 * (size_t)n * n + n) + (pass == 1 ? 2 * sizeof(float) * n : 0);
+    return pass == 1 ? sizeof(C) * (2 * (size_t)n * n + n) + 2 * sizeof(float) * n
+                     : sizeof(C) * (2 * (size_t)n * (n + 1) + n);
+}
+__host__ __device__ constexpr size_t smem_max(int n) {
+    return smem_bytes(n, 0) > smem_bytes(n, 1) ? smem_bytes(n, 0) : smem_bytes(n, 1);
 }
 
 // Registers a thread may use when m CTAs of nt threads share an SM: the
@@ -50,7 +54,7 @@ __host__ __device__ constexpr int regs_at(int nt, int m) {
 // CTAs of nt threads per SM with at least 48 registers a thread, within the
 // shared memory (227 KB, 1 KB reserved per CTA) and 2048 threads of an SM.
 __host__ __device__ constexpr int blocks_at(int n, int nt) {
-    int m = (int)((227u * 1024u) / (smem_bytes(n, 1) + 1024));
+    int m = (int)((227u * 1024u) / (smem_max(n) + 1024));
     const int by_thr = 2048 / ((nt + 31) / 32 * 32);
     if (m > by_thr) m = by_thr;
     while (m > 1 && regs_at(nt, m) < 48) --m;
@@ -134,9 +138,10 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     constexpr int NP = N * N;
     constexpr Plan2 pl = plan2(N);
     extern __shared__ float4 smem_v4[];
+    constexpr int LP = N + 1;  // odd row pitch: line-fast z stages are free of bank conflicts
     C* b0 = reinterpret_cast<C*>(smem_v4);
-    C* b1 = b0 + NP;
-    C* tw = b1 + NP;
+    C* b1 = b0 + N * LP;
+    C* tw = b1 + N * LP;
     const int g = blockIdx.x, x = blockIdx.y;  // plane-major: the CTAs in flight share plane x
     const PairGrid d = P.grids[g0 + g];
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = P.tw[2][i];
@@ -162,18 +167,18 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
             const float v = two ? __ldg(a2 + q) * __ldg(c2 + q) : 0.f;
             return C{u, v};
         },
-        [&](int y, int z, C v) { b0[y * N + z] = v; });
+        [&](int y, int z, C v) { b0[y * N + z] = v; });  // pitch N here: conflict-free stores
     __syncthreads();
     stage<N, pl.r2, pl.r1, -1, N, false, NT>(
-        tw, [&](int y, int z) { return b0[y * N + z]; }, [&](int y, int z, C v) { b1[y * N + z] = v; });
+        tw, [&](int y, int z) { return b0[y * N + z]; }, [&](int y, int z, C v) { b1[y * LP + z] = v; });
     __syncthreads();
     // y lines (line = z)
     stage<N, pl.r1, 1, -1, N, true, NT>(
-        tw, [&](int z, int y) { return b1[y * N + z]; }, [&](int z, int y, C v) { b0[y * N + z] = v; });
+        tw, [&](int z, int y) { return b1[y * LP + z]; }, [&](int z, int y, C v) { b0[y * LP + z] = v; });
     __syncthreads();
     C* out = P.scratch + (size_t)g * P.ng + off;
     stage<N, pl.r2, pl.r1, -1, N, true, NT>(
-        tw, [&](int z, int y) { return b0[y * N + z]; }, [&](int z, int y, C v) { out[y * N + z] = v; });
+        tw, [&](int z, int y) { return b0[y * LP + z]; }, [&](int z, int y, C v) { out[y * N + z] = v; });
     if (pf && pf_orb >= 0) prefetch_l2(P.psi + (size_t)pf_orb * P.ng + (size_t)xa * NP, NP * sizeof(float));
 }
 
@@ -272,9 +277,10 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     constexpr int NP = N * N;
     constexpr Plan2 pl = plan2(N);
     extern __shared__ float4 smem_v4[];
+    constexpr int LP = N + 1;  // odd row pitch (the last stage writes pitch N for the epilogue)
     C* b0 = reinterpret_cast<C*>(smem_v4);
-    C* b1 = b0 + NP;
-    C* tw = b1 + NP;
+    C* b1 = b0 + N * LP;
+    C* tw = b1 + N * LP;
     __shared__ double red[2][(NT + 31) / 32];
     const int g = blockIdx.x, x = blockIdx.y;  // plane-major: the CTAs in flight share plane x
     const PairGrid d = P.grids[g0 + g];
@@ -287,7 +293,7 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
             prefetch_l2(P.scratch + (size_t)ga * P.ng + (size_t)xa * NP, NP * sizeof(C));
     }
     stage<N, pl.r1, 1, +1, N, true, NT>(
-        tw, [&](int z, int y) { return in[y * N + z]; }, [&](int z, int y, C v) { b0[y * N + z] = v; });
+        tw, [&](int z, int y) { return in[y * N + z]; }, [&](int z, int y, C v) { b0[y * LP + z] = v; });
     if (P.pf_ahead > 0 && threadIdx.x < 8) {
         // the epilogue's orbital planes and W planes, fetched into L2 while
         // the FFT stages run
@@ -300,13 +306,13 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     }
     __syncthreads();
     stage<N, pl.r2, pl.r1, +1, N, true, NT>(
-        tw, [&](int z, int y) { return b0[y * N + z]; }, [&](int z, int y, C v) { b1[y * N + z] = v; });
+        tw, [&](int z, int y) { return b0[y * LP + z]; }, [&](int z, int y, C v) { b1[y * LP + z] = v; });
     __syncthreads();
-    stage<N, pl.r1, 1, +1, N, false, NT>(
-        tw, [&](int y, int z) { return b1[y * N + z]; }, [&](int y, int z, C v) { b0[y * N + z] = v; });
+    stage<N, pl.r1, 1, +1, N, true, NT>(
+        tw, [&](int y, int z) { return b1[y * LP + z]; }, [&](int y, int z, C v) { b0[y * LP + z] = v; });
     __syncthreads();
     stage<N, pl.r2, pl.r1, +1, N, false, NT>(
-        tw, [&](int y, int z) { return b0[y * N + z]; }, [&](int y, int z, C v) { b1[y * N + z] = v; });
+        tw, [&](int y, int z) { return b0[y * LP + z]; }, [&](int y, int z, C v) { b1[y * N + z] = v; });
     __syncthreads();
     const bool two = d.j2 >= 0;
     const bool a_occ = d.j1 < P.n_occ, a_sym = a_occ && d.j1 != d.i1;
@@ -410,7 +416,7 @@ namespace spec {
 // Out-of-place passes where two planes fit in shared memory, else in place.
 template <int N>
 bool launch_any(int pass, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s) {
-    if constexpr (spec2::smem_bytes(N, 1) <= 200 * 1024) {
+    if constexpr (spec2::smem_max(N) <= 200 * 1024) {
         if (spec2::enabled()) return spec2::launch_one<N>(pass, nb, P, g0, s);
     }
     return spec_launch_one<N>(pass, nb, P, g0, s);
