@@ -34,7 +34,7 @@ UNIT = "pair-convolutions/s"
 S_THR = 1e-3
 STRIDE = 2
 B_ALG_PER_PAIR_FP32 = 16  # bytes per grid point per real pair (3-pass FFT model)
-TRAFFIC_TAG = "pairconv-spec-v2"  # kernels the committed DRAM-traffic measurement belongs to
+TRAFFIC_TAG = "pairconv-oop-v1"  # kernels the committed DRAM-traffic measurement belongs to
 
 
 def parse():

@@ -32,9 +32,14 @@ using spec::Plan2;
 
 // Dynamic shared memory: two complex planes (rows padded to n + 1 in passes
 // A and C), the twiddle table and (pass B) the |G|^2 tables of x and z.
+__host__ __device__ constexpr size_t smem_bytes_b(int n, bool kslab) {
+    return sizeof(C) * (2 * (size_t)n * n + n) + 2 * sizeof(float) * n + (kslab ? sizeof(float) * n * n : 0);
+}
+// Pass B stages its slab of the K(G)/Ng table in shared memory when two
+// CTAs an SM still fit.
+__host__ __device__ constexpr bool kslab_fits(int n) { return 2 * (smem_bytes_b(n, true) + 1024) <= 227 * 1024; }
 __host__ __device__ constexpr size_t smem_bytes(int n, int pass) {
-    return pass == 1 ? sizeof(C) * (2 * (size_t)n * n + n) + 2 * sizeof(float) * n
-                     : sizeof(C) * (2 * (size_t)n * (n + 1) + n);
+    return pass == 1 ? smem_bytes_b(n, kslab_fits(n)) : sizeof(C) * (2 * (size_t)n * (n + 1) + n);
 }
 __host__ __device__ constexpr size_t smem_max(int n) {
     return smem_bytes(n, 0) > smem_bytes(n, 1) ? smem_bytes(n, 0) : smem_bytes(n, 1);
@@ -189,14 +194,27 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     constexpr int NT = threads_for(N);
     constexpr int NP = N * N;
     constexpr Plan2 pl = plan2(N);
-    constexpr int RB = pl.r1, RA = pl.r2;  // N = RA * RB
+    constexpr int RB = pl.r2, RA = pl.r1;  // N = RA * RB; the middle (the heaviest step) takes the stage with fewer butterflies
+    constexpr bool KS = kslab_fits(N);
     extern __shared__ float4 smem_v4[];
     C* b0 = reinterpret_cast<C*>(smem_v4);
     C* b1 = b0 + NP;
-    C* tw = b1 + NP;
+    float* ks = reinterpret_cast<float*>(b1 + NP);  // K(G)/Ng of this slab, [x][z] (KS)
+    C* tw = reinterpret_cast<C*>(ks + (KS ? NP : 0));
     float* gx2 = reinterpret_cast<float*>(tw + N);
     float* gz2 = gx2 + N;
     const int g = blockIdx.y, ky = blockIdx.x;
+    const bool kstage = KS && P.ktab != nullptr;
+    if (kstage) {
+        // asynchronous 16-byte copies, waited for before the middle
+        const unsigned ks_s = (unsigned)__cvta_generic_to_shared(ks);
+        for (int q = threadIdx.x; q < NP / 4; q += NT) {
+            const int xx = q / (N / 4), z4 = q % (N / 4);
+            const float* src = P.ktab + ((size_t)xx * N + ky) * N + 4 * z4;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(ks_s + 16u * q), "l"(src) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    }
     for (int i = threadIdx.x; i < N; i += NT) {
         tw[i] = P.tw[0][i];
         gx2[i] = P.g2[0][i];
@@ -212,6 +230,7 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     stage<N, RB, 1, -1, N, true, NT>(
         tw, [&](int z, int xx) { return base[(size_t)xx * NP + z]; },
         [&](int z, int xx, C v) { b0[xx * N + z] = v; });
+    if (kstage) asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
     const float gy2 = P.g2[1][ky];
     // middle: for each (z, k2): twiddle, DFT_RA -> X[k2 + RB k1], * K, inverse
@@ -233,7 +252,9 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
             for (int s = 0; s < RA; ++s) {
                 const int xx = k2 + s * RB;
                 float k;
-                if (P.ktab) {
+                if (kstage) {
+                    k = ks[xx * N + z];
+                } else if (P.ktab) {
                     k = __ldg(P.ktab + ((size_t)xx * N + ky) * N + z);
                 } else {
                     const float gg = gx2[xx] + gy2 + gz2[z];
