@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <vector>
+#include <cstdint>
 
 #include "lace_internal.cuh"
 
@@ -25,7 +26,28 @@ constexpr int GR_INNER = 1;
 template <typename T> __device__ __forceinline__ T opv(T x, bool a) { return a ? (x < T(0) ? -x : x) : x; }
 
 // Partial C over one K-chunk: work[chunk][m][n] = sum_{r in chunk} op(A[m][r]) op(B[n][r]).
-template <typename T>
+// Four consecutive k of row r of X (zero outside the rows or the chunk).
+// VEC: one 16-byte load (the caller guarantees ldx, the base and the chunk
+// starts are multiples of 4 elements).
+template <typename T, bool VEC>
+__device__ __forceinline__ void load4_row(const T* __restrict__ X, size_t ldx, int r, int rows, size_t k, size_t k_end,
+                                          bool absval, T* v) {
+    v[0] = v[1] = v[2] = v[3] = T(0);
+    if (r >= rows) return;
+    const T* p = X + (size_t)r * ldx + k;
+    if constexpr (VEC && sizeof(T) == 4) {
+        if (k + 4 <= k_end) {
+            const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+            v[0] = opv(q.x, absval); v[1] = opv(q.y, absval); v[2] = opv(q.z, absval); v[3] = opv(q.w, absval);
+            return;
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+        if (k + c < k_end) v[c] = opv(__ldg(p + c), absval);
+}
+
+template <typename T, bool VEC>
 __global__ void __launch_bounds__(GR_THREADS) gemm_rows_kernel(int M, int N, size_t K, const T* __restrict__ A,
                                                                 size_t lda, const T* __restrict__ B, size_t ldb,
                                                                 bool absval, bool sym, size_t kchunk,
@@ -44,29 +66,26 @@ __global__ void __launch_bounds__(GR_THREADS) gemm_rows_kernel(int M, int N, siz
 #pragma unroll
         for (int j = 0; j < 4; ++j) { acc[i][j] = T(0); fold[i][j] = T(0); comp[i][j] = T(0); }
     int inner = 0;
-    // each thread loads 4 elements of A tile and 4 of B tile per step
+    // each thread loads 4 consecutive k of one row of the A tile and of the B
+    // tile per step; the next step's values are loaded while this one is used
     const int lrow = tid / 4;       // 0..63
     const int lcol = (tid % 4) * 4;  // 0,4,8,12
+    T pa[4], pb[4];
+    if (k_begin < k_end) {
+        load4_row<T, VEC>(A + (size_t)m0 * lda, lda, lrow, M - m0, k_begin + lcol, k_end, absval, pa);
+        load4_row<T, VEC>(B + (size_t)n0 * ldb, ldb, lrow, N - n0, k_begin + lcol, k_end, absval, pb);
+    }
     for (size_t k0 = k_begin; k0 < k_end; k0 += GR_BK) {
-        {
-            const int m = m0 + lrow;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const size_t k = k0 + lcol + c;
-                T v = T(0);
-                if (m < M && k < k_end) v = opv(A[(size_t)m * lda + k], absval);
-                As[lcol + c][lrow] = v;
-            }
-            const int n = n0 + lrow;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const size_t k = k0 + lcol + c;
-                T v = T(0);
-                if (n < N && k < k_end) v = opv(B[(size_t)n * ldb + k], absval);
-                Bs[lcol + c][lrow] = v;
-            }
+        for (int c = 0; c < 4; ++c) {
+            As[lcol + c][lrow] = pa[c];
+            Bs[lcol + c][lrow] = pb[c];
         }
         __syncthreads();
+        if (k0 + GR_BK < k_end) {
+            load4_row<T, VEC>(A + (size_t)m0 * lda, lda, lrow, M - m0, k0 + GR_BK + lcol, k_end, absval, pa);
+            load4_row<T, VEC>(B + (size_t)n0 * ldb, ldb, lrow, N - n0, k0 + GR_BK + lcol, k_end, absval, pb);
+        }
 #pragma unroll
         for (int kk = 0; kk < GR_BK; ++kk) {
             T a[4], b[4];
@@ -129,10 +148,27 @@ __global__ void reduce_chunks_kernel(int M, int N, int nchunk, const double* __r
     C[(size_t)m * ldc + n] = alpha * s;
 }
 
-size_t n_chunks_for(int M, int N, size_t K) {
-    const size_t tiles = (size_t)((M + GR_BM - 1) / GR_BM) * ((N + GR_BN - 1) / GR_BN);
-    size_t want = (4 * 152 + tiles - 1) / tiles;
-    size_t maxc = (K + 1023) / 1024;
+// CTAs of gemm_rows_kernel resident on the device at once (SMs x occupancy).
+int gr_resident() {
+    static const int r = [] {
+        int dev = 0, nsm = 0, occ = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 456;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 456;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, gemm_rows_kernel<float, true>, GR_THREADS, 0) !=
+            cudaSuccess)
+            return 456;
+        return std::max(1, nsm * std::max(1, occ));
+    }();
+    return r;
+}
+
+// K chunks: as many as fill the resident CTA slots once over the computed
+// tiles (upper triangle only for a symmetric product), at least 1024 of K each.
+size_t n_chunks_for(int M, int N, size_t K, bool sym) {
+    const size_t tm = (size_t)(M + GR_BM - 1) / GR_BM, tn = (size_t)(N + GR_BN - 1) / GR_BN;
+    const size_t tiles = sym ? tm * (tm + 1) / 2 : tm * tn;
+    const size_t want = std::max<size_t>(1, (size_t)gr_resident() / tiles);
+    const size_t maxc = (K + 1023) / 1024;
     return std::max<size_t>(1, std::min(want, maxc));
 }
 
@@ -471,21 +507,28 @@ __global__ void fill_zero_kernel(double* p, size_t n) {
 
 // ============================================================================
 
-size_t gemm_rows_work_elems(int M, int N, size_t K) { return n_chunks_for(M, N, K) * (size_t)M * N; }
+size_t gemm_rows_work_elems(int M, int N, size_t K) {
+    // a symmetric product takes the most chunks
+    return n_chunks_for(M, N, K, M == N) * (size_t)M * N;
+}
 
 template <typename T>
 cudaError_t gemm_rows(int M, int N, size_t K, const T* A, size_t lda, const T* B, size_t ldb, double alpha,
                       bool absval, double* C, int ldc, double* work, size_t work_elems, cudaStream_t s,
                       int* launches) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    const size_t nch = n_chunks_for(M, N, K);
-    if (nch * (size_t)M * N > work_elems) return cudaErrorInvalidValue;
+    const bool sym = (A == B) && (lda == ldb) && (M == N);
+    // as many chunks as the workspace holds, up to the balanced count
+    const size_t nch = std::min(n_chunks_for(M, N, K, sym), work_elems / ((size_t)M * N));
+    if (nch == 0) return cudaErrorInvalidValue;
     size_t kchunk = (K + nch - 1) / nch;
     kchunk = (kchunk + GR_BK - 1) / GR_BK * GR_BK;
     const size_t nch_eff = (K + kchunk - 1) / kchunk;
     dim3 grid((M + GR_BM - 1) / GR_BM, (N + GR_BN - 1) / GR_BN, (unsigned)nch_eff);
-    const bool sym = (A == B) && (lda == ldb) && (M == N);
-    gemm_rows_kernel<T><<<grid, GR_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, absval, sym, kchunk, work);
+    const bool vec = sizeof(T) == 4 && lda % 4 == 0 && ldb % 4 == 0 && ((uintptr_t)A & 15) == 0 &&
+                     ((uintptr_t)B & 15) == 0;
+    if (vec) gemm_rows_kernel<T, true><<<grid, GR_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, absval, sym, kchunk, work);
+    else gemm_rows_kernel<T, false><<<grid, GR_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, absval, sym, kchunk, work);
     const size_t tot = (size_t)M * N;
     reduce_chunks_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, N, (int)nch_eff, work, alpha, sym, C,
                                                                        ldc);
