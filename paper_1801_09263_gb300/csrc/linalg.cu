@@ -7,6 +7,7 @@
 #include <cmath>
 #include <vector>
 #include <cstdint>
+#include <type_traits>
 
 #include "lace_internal.cuh"
 
@@ -293,6 +294,42 @@ __global__ void small_gemm_f32_kernel(int N, const float* __restrict__ A, const 
     if (m < N && n < N) C[(size_t)m * N + n] = acc;
 }
 
+// C = A B for N x N row-major, N <= 376: the block's 16 rows of A and 16
+// columns of B are staged in shared memory with all loads in flight at once
+// (the products are latency-bound at N ~ 256), then one output per thread
+// over the full K = N, in the same order as small_gemm_f32_kernel.
+__global__ void small_gemm_f32_staged_kernel(int N, const float* __restrict__ A, const float* __restrict__ B,
+                                             float* __restrict__ C) {
+    extern __shared__ float sg_smem[];
+    const int lp = N + 1;               // row pitch of As: the two rows a warp reads sit in different banks
+    float* As = sg_smem;                // [SG][N + 1]
+    float* Bs = sg_smem + SG * lp;      // [N][SG]
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * SG + tx;
+    const int m0 = blockIdx.y * SG, n0 = blockIdx.x * SG;
+    for (int q = t; q < SG * N; q += SG * SG) {
+        const int r = q / N, k = q % N;
+        As[r * lp + k] = m0 + r < N ? __ldg(A + (size_t)(m0 + r) * N + k) : 0.f;
+    }
+    for (int q = t; q < SG * N; q += SG * SG) {
+        const int k = q / SG, c = q % SG;
+        Bs[q] = n0 + c < N ? __ldg(B + (size_t)k * N + n0 + c) : 0.f;
+    }
+    __syncthreads();
+    const int m = m0 + ty, n = n0 + tx;
+    float acc = 0.f;
+    const float* ar = As + ty * lp;
+#pragma unroll 8
+    for (int k = 0; k < N; ++k) acc = fmaf(ar[k], Bs[k * SG + tx], acc);
+    if (m < N && n < N) C[(size_t)m * N + n] = acc;
+}
+
+void sgemm_f32_square(int N, const float* A, const float* B, float* C, cudaStream_t s) {
+    const dim3 gg((N + SG - 1) / SG, (N + SG - 1) / SG), bb(SG, SG);
+    const size_t smem = (size_t)SG * (2 * N + 1) * sizeof(float);  // <= 48 KB
+    if (N <= 376) small_gemm_f32_staged_kernel<<<gg, bb, smem, s>>>(N, A, B, C);
+    else small_gemm_f32_kernel<<<gg, bb, 0, s>>>(N, A, B, C);
+}
+
 // T = (3 I - P) / 2 in place (FP32)
 __global__ void ns_t_f32_kernel(int N, float* P) {
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -498,6 +535,47 @@ __global__ void convert_kernel(const Tin* __restrict__ in, Tout* __restrict__ ou
         out[i] = (Tout)in[i];
 }
 
+// Vector form for 16-byte aligned arrays: 4 elements per thread and
+// iteration, two iterations' loads issued together; n4 = n / 4 groups (the
+// tail, n % 4 elements, is converted by thread 0 of block 0).
+template <typename Tin, typename Tout>
+__global__ void convert4_kernel(const Tin* __restrict__ in, Tout* __restrict__ out, size_t n) {
+    const size_t n4 = n / 4, stride = (size_t)gridDim.x * blockDim.x;
+    auto ld4 = [&](size_t q, Tin* v) {
+        if constexpr (sizeof(Tin) == 8) {
+            const double2 a = __ldg(reinterpret_cast<const double2*>(in) + 2 * q);
+            const double2 b = __ldg(reinterpret_cast<const double2*>(in) + 2 * q + 1);
+            v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+        } else {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(in) + q);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        }
+    };
+    auto st4 = [&](size_t q, const Tin* v) {
+        if constexpr (sizeof(Tout) == 4) {
+            reinterpret_cast<float4*>(out)[q] = make_float4((float)v[0], (float)v[1], (float)v[2], (float)v[3]);
+        } else {
+            reinterpret_cast<double2*>(out)[2 * q] = make_double2((double)v[0], (double)v[1]);
+            reinterpret_cast<double2*>(out)[2 * q + 1] = make_double2((double)v[2], (double)v[3]);
+        }
+    };
+    size_t q = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    for (; q + stride < n4; q += 2 * stride) {
+        Tin a[4], b[4];
+        ld4(q, a);
+        ld4(q + stride, b);
+        st4(q, a);
+        st4(q + stride, b);
+    }
+    if (q < n4) {
+        Tin a[4];
+        ld4(q, a);
+        st4(q, a);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (size_t i = 4 * n4; i < n; ++i) out[i] = (Tout)in[i];
+}
+
 __global__ void fill_zero_kernel(double* p, size_t n) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         p[i] = 0.0;
@@ -630,7 +708,6 @@ cudaError_t inv_sqrt_spd_mixed(int N, const double* A, double* X, double* work, 
     float* Z2 = Y2 + nn;
     double* scal = work + 3 * nn;  // past the five FP32 matrices (2.5 nn doubles)
     const int nb = (int)((nn + 255) / 256);
-    const dim3 gg((N + SG - 1) / SG, (N + SG - 1) / SG), bb(SG, SG);
     double h = 0.0;
     frob<double>(N, A, 0, scal, s, launches);
     cudaMemcpyAsync(&h, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -644,15 +721,15 @@ cudaError_t inv_sqrt_spd_mixed(int N, const double* A, double* X, double* work, 
     *launches += 2;
     double prev = INFINITY;
     for (int it = 0; it < 160; ++it) {
-        small_gemm_f32_kernel<<<gg, bb, 0, s>>>(N, Z, Y, T);
+        sgemm_f32_square(N, Z, Y, T, s);
         ns_t_f32_kernel<<<nb, 256, 0, s>>>(N, T);
-        small_gemm_f32_kernel<<<gg, bb, 0, s>>>(N, Y, T, Y2);
-        small_gemm_f32_kernel<<<gg, bb, 0, s>>>(N, T, Z, Z2);
+        sgemm_f32_square(N, Y, T, Y2, s);
+        sgemm_f32_square(N, T, Z, Z2, s);
         std::swap(Y, Y2);
         std::swap(Z, Z2);
         *launches += 4;
         if (it >= 5 && (it % 3 == 2)) {
-            small_gemm_f32_kernel<<<gg, bb, 0, s>>>(N, Z, Y, T);
+            sgemm_f32_square(N, Z, Y, T, s);
             frob<float>(N, T, 1, scal, s, launches);
             cudaMemcpyAsync(&h, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
             *launches += 1;
@@ -766,8 +843,13 @@ cudaError_t transpose_f64(int N, const double* A, double* B, cudaStream_t s, int
 template <typename Tin, typename Tout>
 cudaError_t convert(const Tin* in, Tout* out, size_t n, cudaStream_t s, int* launches) {
     if (n == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
-    convert_kernel<Tin, Tout><<<blocks, 256, 0, s>>>(in, out, n);
+    if ((((uintptr_t)in | (uintptr_t)out) & 15) == 0 && (std::is_same<Tin, double>::value || std::is_same<Tin, float>::value)) {
+        const unsigned blocks = (unsigned)std::max<size_t>(1, std::min<size_t>((n / 4 + 255) / 256, 152 * 8));
+        convert4_kernel<Tin, Tout><<<blocks, 256, 0, s>>>(in, out, n);
+    } else {
+        const unsigned blocks = (unsigned)std::min<size_t>((n + 255) / 256, 152 * 16);
+        convert_kernel<Tin, Tout><<<blocks, 256, 0, s>>>(in, out, n);
+    }
     *launches += 1;
     return cudaGetLastError();
 }
