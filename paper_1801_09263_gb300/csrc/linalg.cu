@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <vector>
+#include <cstdlib>
 #include <cstdint>
 #include <type_traits>
 
@@ -576,6 +577,107 @@ __global__ void convert4_kernel(const Tin* __restrict__ in, Tout* __restrict__ o
         for (size_t i = 4 * n4; i < n; ++i) out[i] = (Tout)in[i];
 }
 
+// FP32 combination with the A tiles double-buffered by cp.async (16-byte
+// chunks, zero-filled past the ends) and the coefficient tile one step ahead
+// in registers; same tile shape, thread map and summation order as
+// gemm_combine_kernel.  Needs lda % 4 == 0 and a 16-byte aligned A.
+__global__ void __launch_bounds__(GC_THREADS) gemm_combine_f32_kernel(int N, size_t K, int Kc,
+                                                                       const float* __restrict__ A, size_t lda,
+                                                                       const double* __restrict__ Coef, int ldcoef,
+                                                                       double beta, float* __restrict__ Out,
+                                                                       size_t ldo) {
+    __shared__ __align__(16) float As[2][GC_BK][GC_BR];
+    __shared__ __align__(16) float Cs[2][GC_BK][GC_BN];
+    const size_t r0 = (size_t)blockIdx.x * GC_BR;
+    const int n0 = blockIdx.y * GC_BN;
+    const int tid = threadIdx.x;
+    const int tr = tid % 32;  // 4 r each: r = r0 + tr + 32*i
+    const int tn = tid / 32;  // 8 n each: n = n0 + tn*8 + j
+    float acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    const unsigned as_s = (unsigned)__cvta_generic_to_shared(&As[0][0][0]);
+    // A tile: 16 rows x 32 chunks of 4 floats, 2 chunks per thread
+    auto issue_a = [&](int k0, int buf) {
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const int q = tid + c * GC_THREADS;
+            const int kk = q / (GC_BR / 4), r4 = 4 * (q % (GC_BR / 4));
+            const int k = k0 + kk;
+            const size_t r = r0 + r4;
+            int bytes = 0;
+            const float* src = A;
+            if (k < Kc && r < K) {
+                bytes = (int)(min((size_t)4, K - r) * 4);
+                src = A + (size_t)k * lda + r;
+            }
+            const unsigned dst = as_s + (unsigned)(((buf * GC_BK + kk) * GC_BR + r4) * 4);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(bytes) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    float cr[4];
+    auto load_c = [&](int k0) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int e = tid + c * GC_THREADS;
+            const int kk = e / GC_BN, nn = e % GC_BN;
+            const int k = k0 + kk, n = n0 + nn;
+            cr[c] = (k < Kc && n < N) ? (float)__ldg(Coef + (size_t)k * ldcoef + n) : 0.f;
+        }
+    };
+    auto store_c = [&](int buf) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int e = tid + c * GC_THREADS;
+            Cs[buf][e / GC_BN][e % GC_BN] = cr[c];
+        }
+    };
+    issue_a(0, 0);
+    load_c(0);
+    store_c(0);
+    int buf = 0;
+    for (int k0 = 0; k0 < Kc; k0 += GC_BK, buf ^= 1) {
+        const bool more = k0 + GC_BK < Kc;
+        if (more) {
+            issue_a(k0 + GC_BK, buf ^ 1);
+            load_c(k0 + GC_BK);
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GC_BK; ++kk) {
+            float a[4], c[8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][tr + 32 * i];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) c[j] = Cs[buf][kk][tn * 8 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * c[j];
+        }
+        if (more) store_c(buf ^ 1);
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int n = n0 + tn * 8 + j;
+        if (n >= N) continue;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const size_t r = r0 + tr + 32 * i;
+            if (r >= K) continue;
+            float* o = Out + (size_t)n * ldo + r;
+            *o = beta == 0.0 ? acc[i][j] : (float)beta * *o + acc[i][j];
+        }
+    }
+}
+
 __global__ void fill_zero_kernel(double* p, size_t n) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
         p[i] = 0.0;
@@ -619,7 +721,18 @@ cudaError_t gemm_combine(int N, size_t K, int Kc, const T* A, size_t lda, const 
                          T* Out, size_t ldo, cudaStream_t s, int* launches) {
     if (N <= 0 || K == 0) return cudaSuccess;
     dim3 grid((unsigned)((K + GC_BR - 1) / GC_BR), (N + GC_BN - 1) / GC_BN);
-    gemm_combine_kernel<T><<<grid, GC_THREADS, 0, s>>>(N, K, Kc, A, lda, Coef, ldcoef, beta, Out, ldo);
+    bool done = false;
+    if constexpr (std::is_same<T, float>::value) {
+        static const bool off = [] {
+            const char* e = getenv("LACE_COMBINE_SYNC");  // tuning: 1 = the synchronous kernel
+            return e && e[0] == '1';
+        }();
+        if (!off && Kc > 0 && lda % 4 == 0 && ((uintptr_t)A & 15) == 0) {
+            gemm_combine_f32_kernel<<<grid, GC_THREADS, 0, s>>>(N, K, Kc, A, lda, Coef, ldcoef, beta, Out, ldo);
+            done = true;
+        }
+    }
+    if (!done) gemm_combine_kernel<T><<<grid, GC_THREADS, 0, s>>>(N, K, Kc, A, lda, Coef, ldcoef, beta, Out, ldo);
     *launches += 1;
     return cudaGetLastError();
 }

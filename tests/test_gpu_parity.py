@@ -113,6 +113,26 @@ def test_single_orbital_and_odd_pair_count(prec):
     assert relerr(W, W_ref) < REL_TOL[prec]
 
 
+# Every cubic size with compile-time specialised FP32 passes: the
+# out-of-place passes (24 ... 100) and the in-place ones (128, whose two planes
+# do not fit on chip).  3 occupied + 1 extra orbital: 6 occupied pairs and 3
+# occupied-extra pairs, 5 complex grids of which the last holds one pair.
+SPEC_SIZES = [24, 32, 36, 40, 48, 60, 64, 72, 80, 96, 100, 128]
+
+
+@pytest.mark.parametrize("n", SPEC_SIZES)
+def test_size_specialised_fft_passes_match_oracle(n):
+    side = 10.0 * n / 48
+    sysm = synth.small_localized_system(400 + n, (side, side, side), (n, n, n), 10.0, 3, 3, 1)
+    g, occ, extra = oracle_orbitals(sysm)
+    W_ref, ex_ref, _ = O.apply_exchange(g, occ, extra, np.ones((3, 4), dtype=bool))
+    with make_ctx(sysm, LACE_MIXED) as ctx:
+        W, ex = ctx.apply_exchange()
+        assert len(ctx.get_pairs()) == 9
+    assert abs(ex - ex_ref) <= EX_TOL[LACE_MIXED], (ex, ex_ref)
+    assert relerr(W, W_ref) < REL_TOL[LACE_MIXED]
+
+
 # ------------------------------------------------------------------ SCDM, screening, L-ACE
 
 
