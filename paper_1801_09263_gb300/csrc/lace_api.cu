@@ -474,15 +474,17 @@ lace_status make_pairs(lace_ctx* c, bool use_S, double thr, Launch& L) {
     return LACE_OK;
 }
 
-int batch_for_sizes(size_t ng, size_t eb) {
+// Complex grids per batch of the FFT passes within a scratch budget (2 GiB by
+// default: fewer, fuller launches; at 72^3 the pair convolutions ran 2.86,
+// 2.75, 2.71 and 2.69 us per pair with 128, 256, 512 and 1024 grids a batch).
+int batch_for_sizes(size_t ng, size_t eb, size_t budget) {
     const size_t per = ng * 2 * eb;
     const char* envb = getenv("LACE_BATCH");
-    long long b = envb ? atoll(envb) : (long long)((768ull << 20) / per);
+    long long b = envb ? atoll(envb) : (long long)(budget / per);
     b = std::max<long long>(4, std::min<long long>(b, 1024));
     return (int)b;
 }
-
-int batch_for(lace_ctx* c) { return batch_for_sizes(c->g.ng, elem_bytes(c)); }
+int batch_for(lace_ctx* c) { return batch_for_sizes(c->g.ng, elem_bytes(c), c->fft_scratch_budget); }
 
 // ------------------------------------------------------------------ exchange
 template <typename T>
@@ -669,12 +671,12 @@ lace_status ctx_orbitals(lace_ctx* c, int which, const void** src) {
 // exchange, building ACE and applying it to n_apply host functions: the
 // buffers of the calls above at their largest (the tables excepted, which
 // are far smaller than one orbital).
-size_t predict_ctx_bytes(int prec, const int n[3], int n_occ, int n_extra, int n_apply) {
+size_t predict_ctx_bytes(int prec, const int n[3], int n_occ, int n_extra, int n_apply, size_t fft_budget) {
     const size_t ng = (size_t)n[0] * n[1] * n[2], eb = prec == LACE_FP64 ? 8 : 4;
     const size_t n_p = (size_t)n_occ + n_extra, na = (size_t)std::max(n_apply, 0);
     const size_t ncol = (size_t)((n[0] + 1) / 2) * ((n[1] + 1) / 2) * ((n[2] + 1) / 2);
     const size_t maxp = (size_t)n_occ * (n_occ + 1) / 2 + (size_t)n_occ * n_extra;
-    const size_t batch = (size_t)std::min<long long>(batch_for_sizes(ng, eb), std::max<long long>((maxp + 1) / 2, 1));
+    const size_t batch = (size_t)std::min<long long>(batch_for_sizes(ng, eb, fft_budget), std::max<long long>((maxp + 1) / 2, 1));
     size_t work = gemm_rows_work_elems((int)n_p, (int)n_p, ng) * sizeof(double);
     work = std::max(work, (size_t)n_occ * ncol * eb);
     if (prec != LACE_FP64) {

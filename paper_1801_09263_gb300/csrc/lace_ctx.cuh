@@ -52,6 +52,7 @@ struct lace_ctx {
     cudaStream_t own_stream = nullptr;
     std::string err;
     long long launches = 0;
+    size_t fft_scratch_budget = lace::kFftScratchBudget;  // bytes of complex grids per batch of the FFT passes
 
     bool have_cell = false;
     GridGeom g{};

@@ -10,6 +10,7 @@
 #include <string>
 
 #include "../../include/lace.h"
+#include "lace_ctx.cuh"
 #include "lace_internal.cuh"
 #include "serve_core.h"
 
@@ -31,7 +32,8 @@ struct GpuExec {
         const size_t now = held(h);
         if (kind == lace_serve::REQ_APPLY && !(h && h->ctx)) return now;  // fails with LACE_ERR_STATE
         const size_t full = lace::predict_ctx_bytes(prec, d.n, d.n_occ, d.n_extra,
-                                                    kind == lace_serve::REQ_APPLY ? n : 0);
+                                                    kind == lace_serve::REQ_APPLY ? n : 0,
+                                                    lace::kServeFftScratchBudget);
         return std::max(now, full);
     }
 
@@ -62,6 +64,7 @@ struct GpuExec {
         if (!h) h = new SysState();
         if (!h->ctx) {
             if ((st = lace_create(&h->ctx, device, prec))) return st;
+            h->ctx->fft_scratch_budget = lace::kServeFftScratchBudget;
             if ((st = lace_set_cell(h->ctx, d.cell, d.n[0], d.n[1], d.n[2], d.ecut))) return st;
             int least = 0, greatest = 0;
             cudaDeviceGetStreamPriorityRange(&least, &greatest);
