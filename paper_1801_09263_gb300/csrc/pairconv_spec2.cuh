@@ -36,8 +36,14 @@ __host__ __device__ constexpr size_t smem_bytes_b(int n, bool kslab) {
     return sizeof(C) * (2 * (size_t)n * n + n) + 2 * sizeof(float) * n + (kslab ? sizeof(float) * n * n : 0);
 }
 // Pass B stages its slab of the K(G)/Ng table in shared memory when two
-// CTAs an SM still fit.
-__host__ __device__ constexpr bool kslab_fits(int n) { return 2 * (smem_bytes_b(n, true) + 1024) <= 227 * 1024; }
+// CTAs an SM still fit, or when the planes leave room for one CTA only and
+// the slab fits beside them.
+__host__ __device__ constexpr bool kslab_fits(int n) {
+    const size_t plane_ac = sizeof(C) * (2 * (size_t)n * (n + 1) + n);
+    const size_t without = plane_ac > smem_bytes_b(n, false) ? plane_ac : smem_bytes_b(n, false);
+    const bool one_cta = 2 * (without + 1024) > 227 * 1024;
+    return 2 * (smem_bytes_b(n, true) + 1024) <= 227 * 1024 || (one_cta && smem_bytes_b(n, true) + 1024 <= 227 * 1024);
+}
 __host__ __device__ constexpr size_t smem_bytes(int n, int pass) {
     return pass == 1 ? smem_bytes_b(n, kslab_fits(n)) : sizeof(C) * (2 * (size_t)n * (n + 1) + n);
 }
