@@ -15,7 +15,16 @@
 //       X[k2 + B k1] = sum_n1 w_A^{n1 k1} w_N^{n1 k2} sum_n2 w_B^{n2 k2} x[n1 + A n2]
 //       x[n1 + A n2] = sum_k2 w_B^{-n2 k2} w_N^{-n1 k2} sum_k1 w_A^{-n1 k1} Y[k2 + B k1]
 //     and a group of fixed k2 is one forward and one inverse butterfly.
-//     Pass B needs two barriers.
+//     Pass B needs two barriers; its slab of the K(G)/Ng table is staged in
+//     shared memory by cp.async while the first stage runs;
+//   * passes A and C launch plane-major (the CTAs in flight share one plane
+//     of the orbitals and of W, which then stay in L2), and every CTA
+//     prefetches into L2 what the CTA one wave ahead will read;
+//   * rows of the planes that z lines cross line-fast are padded to n + 1
+//     complex values, which keeps those stages free of bank conflicts;
+//   * threads and the register cap are sized so that two CTAs share an SM
+//     where shared memory allows (the register file is split over the SM's
+//     four sub-partitions).
 #pragma once
 
 #include <atomic>
