@@ -299,8 +299,13 @@ __global__ void small_gemm_f32_kernel(int N, const float* __restrict__ A, const 
 // columns of B are staged in shared memory with all loads in flight at once
 // (the products are latency-bound at N ~ 256), then one output per thread
 // over the full K = N, in the same order as small_gemm_f32_kernel.
-__global__ void small_gemm_f32_staged_kernel(int N, const float* __restrict__ A, const float* __restrict__ B,
-                                             float* __restrict__ C) {
+__global__ void small_gemm_f32_staged_kernel(int N, const float* __restrict__ A0, const float* __restrict__ B0,
+                                             float* __restrict__ C0, const float* __restrict__ A1,
+                                             const float* __restrict__ B1, float* __restrict__ C1) {
+    // blockIdx.z selects one of two independent products (C0 = A0 B0, C1 = A1 B1)
+    const float* __restrict__ A = blockIdx.z ? A1 : A0;
+    const float* __restrict__ B = blockIdx.z ? B1 : B0;
+    float* __restrict__ C = blockIdx.z ? C1 : C0;
     extern __shared__ float sg_smem[];
     const int lp = N + 1;               // row pitch of As: the two rows a warp reads sit in different banks
     float* As = sg_smem;                // [SG][N + 1]
@@ -327,8 +332,21 @@ __global__ void small_gemm_f32_staged_kernel(int N, const float* __restrict__ A,
 void sgemm_f32_square(int N, const float* A, const float* B, float* C, cudaStream_t s) {
     const dim3 gg((N + SG - 1) / SG, (N + SG - 1) / SG), bb(SG, SG);
     const size_t smem = (size_t)SG * (2 * N + 1) * sizeof(float);  // <= 48 KB
-    if (N <= 376) small_gemm_f32_staged_kernel<<<gg, bb, smem, s>>>(N, A, B, C);
+    if (N <= 376) small_gemm_f32_staged_kernel<<<gg, bb, smem, s>>>(N, A, B, C, A, B, C);
     else small_gemm_f32_kernel<<<gg, bb, 0, s>>>(N, A, B, C);
+}
+
+// C0 = A0 B0 and C1 = A1 B1 (independent N x N products) in one launch.
+void sgemm_f32_square_pair(int N, const float* A0, const float* B0, float* C0, const float* A1, const float* B1,
+                           float* C1, cudaStream_t s) {
+    if (N <= 376) {
+        const dim3 gg((N + SG - 1) / SG, (N + SG - 1) / SG, 2), bb(SG, SG);
+        const size_t smem = (size_t)SG * (2 * N + 1) * sizeof(float);
+        small_gemm_f32_staged_kernel<<<gg, bb, smem, s>>>(N, A0, B0, C0, A1, B1, C1);
+    } else {
+        sgemm_f32_square(N, A0, B0, C0, s);
+        sgemm_f32_square(N, A1, B1, C1, s);
+    }
 }
 
 // T = (3 I - P) / 2 in place (FP32)
@@ -836,11 +854,10 @@ cudaError_t inv_sqrt_spd_mixed(int N, const double* A, double* X, double* work, 
     for (int it = 0; it < 160; ++it) {
         sgemm_f32_square(N, Z, Y, T, s);
         ns_t_f32_kernel<<<nb, 256, 0, s>>>(N, T);
-        sgemm_f32_square(N, Y, T, Y2, s);
-        sgemm_f32_square(N, T, Z, Z2, s);
+        sgemm_f32_square_pair(N, Y, T, Y2, T, Z, Z2, s);
         std::swap(Y, Y2);
         std::swap(Z, Z2);
-        *launches += 4;
+        *launches += 3;
         if (it >= 5 && (it % 3 == 2)) {
             sgemm_f32_square(N, Z, Y, T, s);
             frob<float>(N, T, 1, scal, s, launches);
