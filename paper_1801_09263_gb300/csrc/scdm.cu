@@ -542,7 +542,9 @@ static cudaError_t qr_persistent_launch(int nrow, int ncol, T* R, int npiv, Best
     const size_t tile_bytes = (size_t)wpt * RPW * 32 * sizeof(T);  // one tile slot of one group
     const size_t red_bytes = (size_t)2 * QC_WARPS * 32 * sizeof(T);  // dot and norm partials of one tile slot
     const size_t budget = (size_t)std::max(0, optin - (int)fa.sharedSizeBytes - 1024);
-    if (budget < NREG * red_bytes) return cudaSuccess;
+    if constexpr (NREG > 0) {
+        if (budget < NREG * red_bytes) return cudaSuccess;
+    }
     int nsm = std::max(0, max_k - NREG);
     nsm = (int)std::min<size_t>((size_t)nsm, (budget - NREG * red_bytes) / (ngroups * tile_bytes + red_bytes));
     nsm = std::min(nsm, 30 - NREG);  // the per-lane chosen mask has 32 bits
