@@ -41,9 +41,13 @@ def test_noalloc_exchange_matches_context_call_twice():
     cell = np.ascontiguousarray(sysm.cell, dtype=np.float64)
     lib = B.load_library()
     stream = torch.cuda.current_stream(dev)
-    for call in range(2):
-        d_W = torch.full_like(d_psi, float("nan"))  # outputs start dirty: the call must clear them
-        d_e = torch.full((n_occ, n_occ), float("nan"), dtype=torch.float64, device=dev)
+    # outputs start dirty (the call must clear them), allocated before the
+    # calls so that nothing else allocates device memory between them
+    outs = [(torch.full_like(d_psi, float("nan")),
+             torch.full((n_occ, n_occ), float("nan"), dtype=torch.float64, device=dev)) for _ in range(2)]
+    torch.cuda.synchronize(dev)
+    for call, (d_W, d_e) in enumerate(outs):
+        free_before = torch.cuda.mem_get_info(dev)[0]
         st = lib.lace_exchange_pairs_noalloc(cell.ctypes.data_as(C.c_void_p), *sysm.shape,
                                              C.c_void_p(d_psi.data_ptr()), n_occ, n_p,
                                              C.c_void_p(d_pairs.data_ptr()), len(pairs),
@@ -51,6 +55,10 @@ def test_noalloc_exchange_matches_context_call_twice():
                                              C.c_void_p(stream.cuda_stream))
         assert st == 0, (call, lib.lace_status_string(st))
         torch.cuda.synchronize(dev)
+        if call == 1:
+            # after the first call (which may load the library's device code
+            # and look up the array), a call takes no device memory at all
+            assert torch.cuda.mem_get_info(dev)[0] == free_before
         W = d_W.cpu().numpy()
         e = d_e.cpu().numpy()
         assert np.abs(W - W_ref).max() <= 1e-10 * np.abs(W_ref).max(), call
@@ -74,3 +82,34 @@ def test_noalloc_rejects_bad_pairs_and_sizes():
     assert lib.lace_exchange_pairs_noalloc(*args(bad, 1, (16, 16, 7))) == 7  # 7 is not 2^a 3^b 5^c
     assert lib.lace_exchange_pairs_noalloc(*args(bad, 1, (128, 128, 128))) == 7  # FP64 planes exceed shared memory
     assert lib.lace_exchange_pairs_noalloc(*args(bad, 1, (16, 16, 16))) == 0
+    dup = torch.tensor([[0, 1], [0, 1]], dtype=torch.int32, device=dev)  # the same pair twice
+    assert lib.lace_exchange_pairs_noalloc(*args(dup, 2, (16, 16, 16))) == 1
+
+
+def test_noalloc_rejects_a_pair_list_one_grid_short_of_fitting():
+    """The 32 MiB array holds the flag, the FFT tables, the pair bitmap, the
+    pair descriptors and at least one complex grid with its energy partials;
+    a pair list 256 bytes of descriptors past that is refused (status 7)
+    before anything is read or queued."""
+    torch = pytest.importorskip("torch")
+    dev = torch.device("cuda", 0)
+    lib = B.load_library()
+    n, n_occ, n_p = 4, 1024, 8192
+    r256 = lambda b: (b + 255) // 256 * 256
+    seen = r256((n_occ * n_p + 31) // 32 * 4)
+    fits = (32 << 20) - (256 + 16384 + seen + r256(n * 2 * 8) + n ** 3 * 16)  # descriptor bytes that still fit
+    n_grids = (fits + 256) // 16
+    n_pairs = 2 * n_grids
+    # a real, in-range, duplicate-free list of that length (occupied x extra pairs)
+    i = torch.arange(n_pairs, device=dev) % n_occ
+    j = n_occ + torch.arange(n_pairs, device=dev) // n_occ
+    assert int(j.max()) < n_p
+    pairs = torch.stack([i, j], 1).to(torch.int32).contiguous()
+    d_psi = torch.zeros((n_p, n, n, n), dtype=torch.float64, device=dev)
+    d_W = torch.zeros_like(d_psi)
+    d_e = torch.zeros((n_occ, n_occ), dtype=torch.float64, device=dev)
+    cell = np.array([5.0, 5.0, 5.0])
+    st = lib.lace_exchange_pairs_noalloc(cell.ctypes.data_as(C.c_void_p), n, n, n, C.c_void_p(d_psi.data_ptr()),
+                                         n_occ, n_p, C.c_void_p(pairs.data_ptr()), n_pairs,
+                                         C.c_void_p(d_W.data_ptr()), C.c_void_p(d_e.data_ptr()), None)
+    assert st == 7, lib.lace_status_string(st)
