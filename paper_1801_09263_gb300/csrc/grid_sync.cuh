@@ -24,8 +24,9 @@ constexpr unsigned long long kBarrierLimitNs = 2000000000ull;  // 2 s
 // (all zero at launch).  A CTA whose wait runs out sets the flag and returns
 // false (the same for every thread of the CTA); it then leaves the kernel,
 // so the other CTAs run out of time at their next barrier and leave too.
-// gen is the caller's per-CTA generation count.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* abort_sh) {
+// gen is the caller's per-CTA generation count; limit_ns bounds one wait.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* abort_sh,
+                                             unsigned long long limit_ns = kBarrierLimitNs) {
     __syncthreads();
     if (threadIdx.x == 0) {
         const unsigned target = gen + 1;
@@ -39,7 +40,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned& gen, int* 
             const unsigned long long t0 = global_ns();
             while (ld_acquire_u32(&bar[1]) != target) {
                 __nanosleep(32);
-                if (global_ns() - t0 > kBarrierLimitNs) {
+                if (global_ns() - t0 > limit_ns) {
                     atomicExch(&bar[2], 1u);
                     timed_out = 1;
                     break;

@@ -53,6 +53,7 @@ struct lace_ctx {
     std::string err;
     long long launches = 0;
     size_t fft_scratch_budget = lace::kFftScratchBudget;  // bytes of complex grids per batch of the FFT passes
+    unsigned long long wait_limit_ns = 2000000000ull;     // bound of one grid-barrier wait (lace_set_wait_limit)
 
     bool have_cell = false;
     GridGeom g{};

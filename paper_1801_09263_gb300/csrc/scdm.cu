@@ -216,7 +216,7 @@ template <typename T, int RPW, int NREG>
 __global__ void __launch_bounds__(QC_THREADS, 1)
     qr_persistent_kernel(int nrow, int ncol, T* __restrict__ R, int npiv, int wpt, int nsm,
                          Best* __restrict__ block_best, T* __restrict__ pub, unsigned char* __restrict__ chosen,
-                         int* __restrict__ piv, unsigned* bar) {
+                         int* __restrict__ piv, unsigned* bar, unsigned long long limit_ns) {
     extern __shared__ __align__(16) unsigned char qr_smem_raw[];
     const int ngroups = QC_WARPS / wpt;
     const int kres_max = NREG + nsm;                 // resident tiles per group at most
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(QC_THREADS, 1)
                 }
             }
         }
-        if (!grid_barrier(bar, gen, &abort_sh)) return;
+        if (!grid_barrier(bar, gen, &abort_sh, limit_ns)) return;
         // every CTA: global argmax (one block winner per thread: a single round
         // of loads), then q = (winner's column) x (its inverse norm)
         {
@@ -512,8 +512,8 @@ size_t qrcp_aux_bytes(int nrow, int ncol) {
 // do not fit its warp layout or the device cannot co-schedule it.
 template <typename T, int RPW, int NREG>
 static cudaError_t qr_persistent_launch(int nrow, int ncol, T* R, int npiv, Best* best, T* pub,
-                                        unsigned char* chosen, int* d_piv, unsigned* bar, cudaStream_t s,
-                                        int* launches, bool* ran) {
+                                        unsigned char* chosen, int* d_piv, unsigned* bar,
+                                        unsigned long long limit_ns, cudaStream_t s, int* launches, bool* ran) {
     *ran = false;
     int dev = 0, sms = 0, coop = 0, optin = 0;
     cudaGetDevice(&dev);
@@ -554,7 +554,7 @@ static cudaError_t qr_persistent_launch(int nrow, int ncol, T* R, int npiv, Best
     if (per_sm < 1) return cudaSuccess;
     if ((e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s))) return e;
     void* args[] = {(void*)&nrow, (void*)&ncol, (void*)&R,   (void*)&npiv,   (void*)&wpt,  (void*)&nsm,
-                    (void*)&best, (void*)&pub,  (void*)&chosen, (void*)&d_piv, (void*)&bar};
+                    (void*)&best, (void*)&pub,  (void*)&chosen, (void*)&d_piv, (void*)&bar, (void*)&limit_ns};
     if ((e = cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(QC_THREADS), args, dyn, s))) return e;
     *launches += 1;
     *ran = true;
@@ -564,8 +564,8 @@ static cudaError_t qr_persistent_launch(int nrow, int ncol, T* R, int npiv, Best
 // R (nrow x ncol, row-major, leading dimension ncol) is overwritten.  aux is
 // caller-provided scratch of qrcp_aux_bytes(nrow, ncol) bytes.
 template <typename T>
-cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* aux, int* h_timeout, cudaStream_t s,
-                        int* launches) {
+cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* aux, int* h_timeout,
+                        unsigned long long wait_limit_ns, cudaStream_t s, int* launches) {
     *h_timeout = 0;
     if (nrow > QR_MAXROWS || npiv > ncol) return cudaErrorInvalidValue;
     const int nblocks = (ncol + QR_THREADS - 1) / QR_THREADS;
@@ -582,11 +582,14 @@ cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* au
     cudaError_t e;
     if constexpr (sizeof(T) == 4) {
         if (nrow <= 512)
-            e = qr_persistent_launch<T, 32, 2>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, s, launches, &ran);
+            e = qr_persistent_launch<T, 32, 2>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, wait_limit_ns, s,
+                                              launches, &ran);
         else
-            e = qr_persistent_launch<T, 64, 0>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, s, launches, &ran);
+            e = qr_persistent_launch<T, 64, 0>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, wait_limit_ns, s,
+                                              launches, &ran);
     } else {
-        e = qr_persistent_launch<T, 32, 0>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, s, launches, &ran);
+        e = qr_persistent_launch<T, 32, 0>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, wait_limit_ns, s,
+                                              launches, &ran);
     }
     if (e) return e;
     if (ran) {
@@ -626,8 +629,10 @@ cudaError_t gather_columns(const T* psi, size_t ldpsi, int norb, const long long
     return cudaGetLastError();
 }
 
-template cudaError_t qrcp_pivots<float>(int, int, float*, int, int*, void*, int*, cudaStream_t, int*);
-template cudaError_t qrcp_pivots<double>(int, int, double*, int, int*, void*, int*, cudaStream_t, int*);
+template cudaError_t qrcp_pivots<float>(int, int, float*, int, int*, void*, int*, unsigned long long, cudaStream_t,
+                                         int*);
+template cudaError_t qrcp_pivots<double>(int, int, double*, int, int*, void*, int*, unsigned long long, cudaStream_t,
+                                          int*);
 template cudaError_t gather_subsample<float>(const GridGeom&, int, const float*, int, float*, int*, cudaStream_t, int*);
 template cudaError_t gather_subsample<double>(const GridGeom&, int, const double*, int, double*, int*, cudaStream_t,
                                               int*);
