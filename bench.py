@@ -34,7 +34,34 @@ UNIT = "pair-convolutions/s"
 S_THR = 1e-3
 STRIDE = 2
 B_ALG_PER_PAIR_FP32 = 16  # bytes per grid point per real pair (3-pass FFT model)
-TRAFFIC_TAG = "pairconv-oop-v1"  # kernels the committed DRAM-traffic measurement belongs to
+# sources of the pair-convolution kernels: the committed DRAM-traffic capture
+# (profiles/pairconv_traffic.json) holds their hash and counts only while they match
+PAIRCONV_SOURCES = ("common.cuh", "lace_internal.cuh", "pairconv.cu", "pairconv_spec.cuh", "pairconv_spec2.cuh",
+                    "pairconv_spec_s.cu", "pairconv_spec_m.cu", "pairconv_spec_l.cu")
+
+
+def pairconv_sources_sha256() -> str:
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in PAIRCONV_SOURCES:
+        with open(os.path.join(ROOT, "paper_1801_09263_gb300", "csrc", f), "rb") as fh:
+            h.update(f.encode() + b"\0" + fh.read())
+    return h.hexdigest()
+
+
+def committed_traffic():
+    """(bytes per step, note) of the committed DRAM-traffic capture; bytes is
+    None when the kernels changed since the capture."""
+    tr = os.path.join(ROOT, "profiles", "pairconv_traffic.json")
+    try:
+        d = json.load(open(tr))
+    except Exception:
+        return None, "no committed capture"
+    when = d.get("captured", "?")
+    if d.get("kernel_sources_sha256") != pairconv_sources_sha256():
+        return None, f"stale: the pair-convolution sources changed since the capture of {when}"
+    return d["traffic_bytes_per_step"], f"ncu capture of {when} ({d.get('workload', '')})"
 
 
 def parse():
@@ -304,14 +331,7 @@ def run_lace(args, rank, world, local):
     roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
             "frac": round(achieved / peak, 4), "traffic": None, "peak_kind": peak_kind,
             "kernel": "pairconv passes A+B+C (per step)", "alg_bytes_per_step": alg_bytes}
-    tr = os.path.join(ROOT, "profiles", "pairconv_traffic.json")
-    if os.path.exists(tr):
-        try:
-            d = json.load(open(tr))
-            if d.get("valid_for") == TRAFFIC_TAG:
-                roof["traffic"] = d["traffic_bytes_per_step"]
-        except Exception:
-            pass
+    roof["traffic"], roof["traffic_source"] = committed_traffic()
     result = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 3), "higher_is_better": True,
@@ -328,6 +348,10 @@ def run_lace(args, rank, world, local):
         "roofline": roof, "clocks": clocks, "gpu_launches": launches, "e2e": e2e,
         "fp64_gpu": fp64, "E_x_Ha": ex_mixed,
     }
+    try:
+        result["alu_peaks_measured"] = {k: round(v, 2) for k, v in lace.probe_peak_rates(local).items()}
+    except Exception as exc:  # reported, not fatal
+        result["alu_peaks_measured"] = {"error": str(exc)}
     if not args.no_serving:
         # the serving stream (each rank serves its own replica of it)
         del phi_dev, out_dev
@@ -537,12 +561,18 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
     }
 
 
+ACE96_ORACLE = os.path.join(ROOT, "tests", "golden", "ace96_oracle_sample.json")
+
+
 def run_ace96(local, reps=3):
     """ACE build and apply on the 96^3 workload: 256 water-like occupied + 128
     extra orbitals (N_P = 384), S_thr = 1e-3.  Mixed precision (tcgen05 3xBF16
-    M' and xi, FP64 Cholesky) against the plain FP64 GPU form on the same
-    pivots: ACE build ms (CUDA events), E_x, and the relative difference of
-    K_ACE on 8 random probes."""
+    M' and xi, FP64 Cholesky) and the plain FP64 GPU form, both on the FP64
+    oracle's SCDM points: ACE build ms (CUDA events), E_x, and K_ACE on 8
+    random probes, each against the oracle's values stored in
+    tests/golden/ace96_oracle_sample.json (written by the committed script
+    beside it from oracle/ alone: E_x and K_ACE psi on 512 seeded points per
+    probe, scaled by the probe's largest |K_ACE psi|) and against each other."""
     import synth
     import torch
 
@@ -550,20 +580,22 @@ def run_ace96(local, reps=3):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    with open(ACE96_ORACLE) as f:
+        gold = json.load(f)
     sysm = synth.config3_water_like_with_extras()
     phi = torch.from_numpy(sysm.phi).to(dev)
-    probe = torch.from_numpy(np.random.default_rng(11).standard_normal((8,) + sysm.shape)).to(dev)
+    probe = torch.from_numpy(np.random.default_rng(gold["probe"]["seed"]).standard_normal(
+        (gold["probe"]["count"],) + sysm.shape)).to(dev)
+    pts = torch.tensor(gold["sample_points"], dtype=torch.long, device=dev)
+    k_ref = np.array(gold["k_ace_sample"])
+    k_scale = np.array(gold["k_ace_max_abs"])
     out = {}
-    piv = None
     for name, prec in (("mixed", lace.LACE_MIXED), ("fp64", lace.LACE_FP64)):
         with lace.Lace(local, prec) as c:
             c.set_stream(torch.cuda.current_stream(dev).cuda_stream)
             c.set_cell(sysm.cell, sysm.shape, sysm.ecut)
             c.load_orbitals_dev(phi, 256, 128, True)
-            if piv is None:
-                piv = c.localize(STRIDE)
-            else:
-                c.set_pivots(piv)
+            c.set_pivots(np.array(gold["pivots"], dtype=np.int64))
             npairs = c.screen(S_THR)
             c.apply_exchange(want_W=False)
             builds = []
@@ -574,14 +606,21 @@ def run_ace96(local, reps=3):
             c.apply_ace_dev(probe, kp)
             torch.cuda.synchronize(dev)
             t = c.get_timings()
+            ex = c.exchange_energy(1.0)
+            ks = kp.reshape(kp.shape[0], -1)[:, pts].cpu().numpy()
             out[name] = {"ace_build_ms": round(statistics.median(builds), 3), "ace_apply_ms_8": round(t["ace_apply"], 3),
-                         "pairconv_ms": round(t["pairconv_kernels"], 3), "n_pairs": npairs,
-                         "E_x_Ha": c.exchange_energy(1.0), "kprobe": kp}
+                         "pairconv_ms": round(t["pairconv_kernels"], 3), "n_pairs": npairs, "E_x_Ha": ex,
+                         "dE_x_vs_oracle_Ha": ex - gold["E_x_Ha"],
+                         "max_rel_dK_psi_vs_oracle": float(np.max(np.abs(ks - k_ref) / k_scale[:, None])),
+                         "kprobe": kp}
     dk = (out["mixed"]["kprobe"] - out["fp64"]["kprobe"]).abs().max() / out["fp64"]["kprobe"].abs().max()
     for v in out.values():
         del v["kprobe"]
     return {"workload": "water-like L=23.5 bohr, 96^3, 256 occupied + 128 extra orbitals (N_P=384), SCDM stride 2, "
-                        "S_thr=1e-3; both forms on the same pivots",
+                        "S_thr=1e-3; both forms on the FP64 oracle's SCDM points",
+            "oracle": {"E_x_Ha": gold["E_x_Ha"], "n_pairs": gold["n_pairs"],
+                       "sample": f"K_ACE psi of {gold['probe']['count']} probes on {len(gold['sample_points'])} "
+                                 "seeded grid points each (tests/golden/ace96_oracle_sample.json)"},
             "mixed": out["mixed"], "fp64_gpu": out["fp64"],
             "ace_build_speedup_vs_fp64": round(out["fp64"]["ace_build_ms"] / out["mixed"]["ace_build_ms"], 1),
             "dE_x_mixed_vs_fp64_Ha": out["mixed"]["E_x_Ha"] - out["fp64"]["E_x_Ha"],

@@ -84,6 +84,18 @@ lace_status lace_destroy(lace_ctx* ctx);
  * context's own stream). */
 lace_status lace_set_stream(lace_ctx* ctx, void* stream);
 
+/* Time limit, in seconds (0 to 3600; default 2), of each bounded device
+ * wait of this context's persistent pivoted-QR kernel (lace_localize): a
+ * grid-barrier wait for the other CTAs of the launch.  A wait that runs out
+ * sets an error flag and its CTA leaves the kernel (the others then run out
+ * at their next barrier and leave too); lace_localize returns
+ * LACE_ERR_TIMEOUT and the context stays usable, with its orbitals loaded
+ * but not localised (localise again).  A short limit turns a stalled
+ * launch into an error quickly; 0 makes every wait that has to wait at all
+ * give up.
+ * Returns LACE_ERR_ARG for a limit outside [0, 3600]. */
+lace_status lace_set_wait_limit(lace_ctx* ctx, double seconds);
+
 /* Cell, grid and orbital cutoff (Sec. 3: the exchange grid follows from the
  * cell and the cutoff; here the caller gives the grid).  cell = (a, b, c) in
  * bohr.  Every grid size must factor into 2, 3 and 5; this build handles
@@ -111,7 +123,10 @@ lace_status lace_set_kernel(lace_ctx* ctx, int kind, double omega, double alpha)
  * of the occupied span and Loewdin-orthonormalised; otherwise the caller
  * guarantees orthonormality.  Until lace_localize, the occupied orbitals
  * used by the exchange are these (canonical) ones.  Resets localisation,
- * screening and ACE state.  LACE_ERR_NOT_PD if an overlap matrix is
+ * screening and exchange state; the ACE projector of the last successful
+ * lace_build_ace stays usable by lace_apply_ace while n_occ + n_extra is
+ * unchanged (the paper's inner loop applies the previous outer iteration's
+ * ACE until the next build).  LACE_ERR_NOT_PD if an overlap matrix is
  * singular. */
 lace_status lace_load_orbitals(lace_ctx* ctx, const double* phi, int n_occ, int n_extra, int orthonormalize);
 
@@ -124,7 +139,7 @@ lace_status lace_load_orbitals_dev(lace_ctx* ctx, const double* d_phi, int n_occ
  * w = phi U with U = phi_C^T (phi_C phi_C^T)^{-1/2}.  pivots_out (nullable,
  * n_occ entries) receives the selected points as full-grid linear indices
  * in selection order.  Ties in the pivot choice go to the lowest index.
- * Resets screening and ACE state. */
+ * Resets screening and exchange state (not the ACE projector). */
 lace_status lace_localize(lace_ctx* ctx, int stride, long long* pivots_out);
 
 /* SCDM with imposed pivots (full-grid linear indices, n == n_occ, all
@@ -165,8 +180,12 @@ lace_status lace_exchange_energy(lace_ctx* ctx, double f_spin, double* ex_out);
 
 /* Build the ACE projector from the last W (Eq. 3 and its Cholesky form):
  * M' = dV Psi^T W, symmetrised by `sym` (lace_sym), -M'_sym = L L^T in
- * FP64, xi = W L^{-T}.  LACE_ERR_NOT_PD leaves any previous ACE state
- * intact. */
+ * FP64, xi = W L^{-T}.  LACE_ERR_NOT_PD (the Cholesky factorisation met a
+ * pivot <= 0, e.g. M' = 0 when every pair was screened out) stops before L
+ * and xi are written: the previous ACE projector, its L and lace_apply_ace
+ * stay as they were (LACE_MAT_EXCHANGE then holds the failing M').  After
+ * any other failure lace_apply_ace returns LACE_ERR_STATE until a build
+ * succeeds. */
 lace_status lace_build_ace(lace_ctx* ctx, int sym);
 
 /* K_ACE psi = -xi (dV xi^T psi) for n functions psi (host FP64,
@@ -187,6 +206,11 @@ lace_status lace_get_orbitals(lace_ctx* ctx, int which, double* out, long long c
 /* Copy the kept pair list: pairs_out[2*p], pairs_out[2*p+1] = (i, j) with i
  * occupied and i <= j for occupied j; up to `cap` pairs; *n_out = count. */
 lace_status lace_get_pairs(lace_ctx* ctx, int* pairs_out, long long cap, long long* n_out);
+
+/* The SCDM points of the last lace_localize or lace_set_pivots (Sec. 2):
+ * n_occ full-grid linear indices in selection order, into pivots_out (n
+ * entries, n >= n_occ).  LACE_ERR_STATE before localisation. */
+lace_status lace_get_pivots(lace_ctx* ctx, long long* pivots_out, int n);
 
 /* Device milliseconds of the stages of the last calls (CUDA events on the
  * context's stream): [0] load+orthonormalise, [1] localise, [2] screen,
@@ -391,7 +415,8 @@ const char* lace_batch_last_error(lace_batch* batch);
  *             passes' shared memory (n <= 108 on GB300)
  *   d_psi     device FP64 [n_p][n1][n2][n3]; rows < n_occ are the occupied w_i
  *   d_pairs   device int32 [n_pairs][2] of (i, j): i < n_occ, j < n_p, i <= j
- *             when j < n_occ (the layout lace_get_pairs returns)
+ *             when j < n_occ, each pair at most once (the layout
+ *             lace_get_pairs returns)
  *   d_W       device FP64 [n_p][n1][n2][n3], overwritten (cleared first)
  *   d_pair_e  device FP64 [n_occ][n_occ], overwritten: (ij|ji) of each pair,
  *             both (i, j) and (j, i), zero elsewhere; E_x = -1/2 sum
@@ -402,17 +427,32 @@ const char* lace_batch_last_error(lace_batch* batch);
  * everything a call reads from it is rewritten by that call first.  Calls
  * that overlap on the GPU (different streams, or different host threads on
  * one device) share the array and race: serialise them.
- * Set-up: the first call on a device looks up the array's device address
- * (with that device current); make that first call before any stream
- * capture.  Each call synchronises `stream` once, after checking the pair
- * list on the device and before queueing the FFT passes.
- * Returns LACE_ERR_ARG for null pointers, bad counts or a pair outside the
- * ranges above; LACE_ERR_UNSUPPORTED for a grid size outside the list above
- * or when one complex FFT grid plus the pair descriptors ((n_pairs+1)/2 x 16
- * bytes) do not fit in the 32 MiB array; LACE_ERR_CUDA on a CUDA error. */
+ * Set-up: the first call on a device, and the first call after a
+ * cudaDeviceReset of it, looks up the array's device address with that
+ * device current (the reset gives the device code a new context, where the
+ * array can sit at another address); make that first call before any
+ * stream capture.  Each call synchronises `stream` once, after checking the
+ * pair list on the device and before queueing the FFT passes.
+ * Returns LACE_ERR_ARG for null pointers, bad counts, a pair outside the
+ * ranges above or a pair listed twice; LACE_ERR_UNSUPPORTED for a grid size
+ * outside the list above or when one complex FFT grid (16 n1 n2 n3 bytes)
+ * with its energy partials, the pair descriptors ((n_pairs+1)/2 x 16 bytes)
+ * and a bitmap of n_occ x n_p bits do not fit in the 32 MiB array together;
+ * LACE_ERR_CUDA on a CUDA error. */
 lace_status lace_exchange_pairs_noalloc(const double cell[3], int n1, int n2, int n3, const double* d_psi,
                                         int n_occ, int n_p, const int* d_pairs, long long n_pairs, double* d_W,
                                         double* d_pair_e, void* stream);
+
+/* Arithmetic peaks of device `device`, measured: rates_out[0] FP32 FLOP/s
+ * of scalar fused multiply-adds, [1] FP32 FLOP/s of packed pair FMAs
+ * (fma.rn.f32x2, two per instruction), [2] FP64 FLOP/s of fused
+ * multiply-adds (2 FLOP per FMA; entries past [2] are set to 0).  Each is the
+ * best of five CUDA-event-timed launches of independent dependent-FMA chains
+ * filling every SM.  These are the ceilings the ALU-bound steps of the path
+ * (FFT butterflies, FP32 Gram matrices, FP64 factorisations) are reported
+ * against; the paper gives none (its timings are whole CPU runs, Sec. 4).
+ * Takes about 0.3 s; allocates and frees a small device buffer. */
+lace_status lace_probe_peak_rates(int device, double* rates_out, int count);
 
 /* Static description of a status code. */
 const char* lace_status_string(lace_status status);

@@ -19,4 +19,5 @@ from .binding import (  # noqa: F401
     exported_symbols,
     library_path,
     load_library,
+    probe_peak_rates,
 )

@@ -61,6 +61,7 @@ def load_library(build_if_missing: bool = False):
         "lace_create": ([C.POINTER(P), I, I], I),
         "lace_destroy": ([P], I),
         "lace_set_stream": ([P, P], I),
+        "lace_set_wait_limit": ([P, D], I),
         "lace_set_cell": ([P, P, I, I, I, D], I),
         "lace_load_orbitals": ([P, P, I, I, I], I),
         "lace_load_orbitals_dev": ([P, P, I, I, I], I),
@@ -75,6 +76,7 @@ def load_library(build_if_missing: bool = False):
         "lace_get_matrix": ([P, I, P, LL], I),
         "lace_get_orbitals": ([P, I, P, LL], I),
         "lace_get_pairs": ([P, P, LL, P], I),
+        "lace_get_pivots": ([P, P, I], I),
         "lace_get_timings": ([P, P, I], I),
         "lace_get_launch_count": ([P, P], I),
         "lace_get_device_bytes": ([P, P], I),
@@ -100,6 +102,7 @@ def load_library(build_if_missing: bool = False):
         "lace_batch_last_error": ([P], C.c_char_p),
         "lace_server_stats": ([P, P, P, P], I),
         "lace_exchange_pairs_noalloc": ([P, I, I, I, P, I, I, P, LL, P, P, P], I),
+        "lace_probe_peak_rates": ([I, P, I], I),
         "lace_status_string": ([I], C.c_char_p),
         "lace_last_error": ([P], C.c_char_p),
     }
@@ -167,6 +170,9 @@ class Lace:
     # -- the C calls
     def set_stream(self, stream_ptr: int | None):
         self._check(self.lib.lace_set_stream(self.h, C.c_void_p(stream_ptr or 0)), "lace_set_stream")
+
+    def set_wait_limit(self, seconds: float):
+        self._check(self.lib.lace_set_wait_limit(self.h, float(seconds)), "lace_set_wait_limit")
 
     def set_cell(self, cell, shape, ecut: float):
         c = _f64(cell)
@@ -270,6 +276,11 @@ class Lace:
         out = np.empty((max(n.value, 1), 2), dtype=np.int32)
         self._check(self.lib.lace_get_pairs(self.h, _ptr(out), n.value, C.byref(n)), "lace_get_pairs")
         return out[: n.value]
+
+    def get_pivots(self) -> np.ndarray:
+        out = np.empty(self.n_occ, dtype=np.int64)
+        self._check(self.lib.lace_get_pivots(self.h, _ptr(out), int(self.n_occ)), "lace_get_pivots")
+        return out
 
     def get_timings(self) -> dict:
         ms = np.zeros(len(STAGES), dtype=np.float64)
@@ -479,6 +490,16 @@ class Batch:
         return dict(threads=th.value, ctas_per_sm=ct.value, chunks=ch.value, graph_replays=rp.value,
                     launches=ln.value, setup_ms=ms[0], pairconv_ms=ms[1], hot_ms=ms[2], call_ms=ms[3],
                     mode="per_instance" if per_instance else "persistent", tune_ms=tune_ms)
+
+
+def probe_peak_rates(device: int = 0) -> dict:
+    """Measured FP32 (scalar and packed-pair FMA) and FP64 FMA rates of a device, in TFLOP/s."""
+    lib = load_library()
+    r = np.zeros(3, dtype=np.float64)
+    st = lib.lace_probe_peak_rates(int(device), _ptr(r), 3)
+    if st != LACE_OK:
+        raise LaceError(st, "lace_probe_peak_rates", lib.lace_status_string(st).decode())
+    return {"fp32_tflops": r[0] / 1e12, "fp32x2_tflops": r[1] / 1e12, "fp64_tflops": r[2] / 1e12}
 
 
 def pw_basis(cell, ecut: float) -> np.ndarray:

@@ -274,7 +274,11 @@ lace_status load_common(lace_ctx* c, const double* phi, bool dev, int n_occ, int
     if (!phi || n_occ < 1 || n_extra < 0 || n_occ > 1024 || n_occ + n_extra > 2048)
         return fail(c, LACE_ERR_ARG, "bad orbital pointer or counts (1 <= n_occ <= 1024, n_occ + n_extra <= 2048)");
     cudaSetDevice(c->device);
-    c->loaded = c->localized = c->screened = c->applied = c->ace = false;
+    // The ACE projector of the last successful build stays usable across new
+    // orbitals of the same count (the inner loop of the paper's double loop
+    // applies the previous outer iteration's ACE), until the next build.
+    c->loaded = c->localized = c->screened = c->applied = false;
+    if (n_occ + n_extra != c->n_p) c->ace = false;
     lace_status st = ensure_orbital_buffers(c, n_occ, n_extra);
     if (st) return st;
     c->n_occ = n_occ;
@@ -327,7 +331,8 @@ lace_status localize_impl(lace_ctx* c, int stride, const long long* imposed) {
                "subsample");
         }
         int timeout = 0;
-        CK(qrcp_pivots<T>(n, ncol, R, n, c->piv.as<int>(), c->aux.p, &timeout, c->stream, &L.n), "qrcp");
+        CK(qrcp_pivots<T>(n, ncol, R, n, c->piv.as<int>(), c->aux.p, &timeout, c->wait_limit_ns, c->stream, &L.n),
+           "qrcp");
         if (timeout) return fail(c, LACE_ERR_TIMEOUT, "pivoted QR: a grid barrier wait timed out");
         std::vector<int> hp(n);
         CK(cudaMemcpyAsync(hp.data(), c->piv.p, sizeof(int) * n, cudaMemcpyDeviceToHost, c->stream), "pivots");
@@ -498,7 +503,10 @@ lace_status apply_impl(lace_ctx* c) {
         c->s_thr = 0.0;
     }
     const long long n_grids = (c->n_pairs + 1) / 2;
-    const int batch = (int)std::min<long long>(batch_for(c), std::max<long long>(n_grids, 1));
+    // complex grids the scratch holds: the chunk size, even (the paired FFT
+    // passes take two grids per CTA)
+    int batch = (int)std::min<long long>(batch_for(c), std::max<long long>(n_grids, 1));
+    batch += batch & 1;
     CK(c->scratch.ensure((size_t)batch * ng * 2 * sizeof(T)), "alloc FFT scratch");
     CK(c->epart.ensure((size_t)batch * c->g.n[0] * 2 * sizeof(double)), "alloc energies");
     CK(cudaMemsetAsync(c->W.p, 0, (size_t)c->n_p * ng * sizeof(T), c->stream), "zero W");
@@ -768,6 +776,13 @@ lace_status lace_set_stream(lace_ctx* c, void* stream) {
     return LACE_OK;
 }
 
+lace_status lace_set_wait_limit(lace_ctx* c, double seconds) {
+    if (!c) return LACE_ERR_ARG;
+    if (!(seconds >= 0.0 && seconds <= 3600.0)) return fail(c, LACE_ERR_ARG, "wait limit must be in [0, 3600] s");
+    c->wait_limit_ns = (unsigned long long)(seconds * 1e9);
+    return LACE_OK;
+}
+
 lace_status lace_set_cell(lace_ctx* c, const double cell[3], int n1, int n2, int n3, double ecut_ha) {
     if (!c) return LACE_ERR_ARG;
     if (!cell || !(cell[0] > 0) || !(cell[1] > 0) || !(cell[2] > 0) || !(ecut_ha > 0))
@@ -826,7 +841,7 @@ static lace_status localize_common(lace_ctx* c, int stride, const long long* imp
     if (!c->loaded) return fail(c, LACE_ERR_STATE, "load orbitals before localising");
     if (!imposed && (stride < 1 || stride > 8)) return fail(c, LACE_ERR_ARG, "stride must be in [1, 8]");
     cudaSetDevice(c->device);
-    c->localized = c->screened = c->applied = c->ace = false;
+    c->localized = c->screened = c->applied = false;
     ev_begin(c, ST_LOCALIZE);
     lace_status st = c->prec == LACE_FP64 ? localize_impl<double>(c, stride, imposed)
                                           : localize_impl<float>(c, stride, imposed);
@@ -861,7 +876,7 @@ lace_status lace_align_to_previous(lace_ctx* c, int* aligned_out) {
     const size_t bytes = (size_t)c->n_occ * c->g.ng * elem_bytes(c);
     if (aligned_out) *aligned_out = 0;
     if (c->have_ref && c->ref_n == c->n_occ && c->ref.bytes >= bytes) {
-        c->screened = c->applied = c->ace = false;
+        c->screened = c->applied = false;
         lace_status st = c->prec == LACE_FP64 ? align_impl<double>(c) : align_impl<float>(c);
         if (st) return st;
         if (aligned_out) *aligned_out = 1;
@@ -879,7 +894,7 @@ lace_status lace_screen(lace_ctx* c, double s_thr, long long* n_pairs_out) {
     if (!c->loaded) return fail(c, LACE_ERR_STATE, "load orbitals before screening");
     if (!(s_thr >= 0.0)) return fail(c, LACE_ERR_ARG, "threshold must be >= 0");
     cudaSetDevice(c->device);
-    c->screened = c->applied = c->ace = false;
+    c->screened = c->applied = false;
     {
         lace_status st = materialize_psi(c);
         if (st) return st;
@@ -941,7 +956,12 @@ lace_status lace_build_ace(lace_ctx* c, int sym) {
     ev_begin(c, ST_ACE_BUILD);
     lace_status st = c->prec == LACE_FP64 ? build_ace_impl<double>(c, sym) : build_ace_impl<float>(c, sym);
     ev_end(c, ST_ACE_BUILD);
-    if (st) return st;
+    if (st) {
+        // a failed Cholesky stops the build before xi and L are written: the
+        // previous projector stays; any other failure may have left xi half written
+        if (st != LACE_ERR_NOT_PD) c->ace = false;
+        return st;
+    }
     CK(cudaStreamSynchronize(c->stream), "build ace");
     c->ace = true;
     return LACE_OK;
@@ -1059,6 +1079,14 @@ lace_status lace_get_pairs(lace_ctx* c, int* pairs_out, long long cap, long long
         CK(cudaMemcpyAsync(pairs_out, c->pairs.p, sizeof(int2) * k, cudaMemcpyDeviceToHost, c->stream), "get pairs");
         CK(cudaStreamSynchronize(c->stream), "get pairs");
     }
+    return LACE_OK;
+}
+
+lace_status lace_get_pivots(lace_ctx* c, long long* pivots_out, int n) {
+    if (!c || !pivots_out) return LACE_ERR_ARG;
+    if (!c->localized) return fail(c, LACE_ERR_STATE, "localise first");
+    if (n < c->n_occ) return fail(c, LACE_ERR_ARG, "output buffer too small");
+    std::copy(c->pivots_host.begin(), c->pivots_host.end(), pivots_out);
     return LACE_OK;
 }
 

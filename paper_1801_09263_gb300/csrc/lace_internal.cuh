@@ -55,9 +55,11 @@ template <typename T> struct ConvArgs {
 
 // Size-specialised FP32 passes for cubic grids (pairconv_spec_*.cu): launch
 // pass 0/1/2 (A/B/C) for grid size n if a specialisation exists.
-bool spec_launch_s(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
-bool spec_launch_m(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
-bool spec_launch_l(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
+// allow_pair: the scratch holds nb rounded up to even grids, so the passes
+// that take two complex grids per CTA may run.
+bool spec_launch_s(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s, bool allow_pair);
+bool spec_launch_m(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s, bool allow_pair);
+bool spec_launch_l(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s, bool allow_pair);
 
 // Persistent multi-instance pair convolutions (pairconv_multi.cu): the kept
 // pairs of many independent systems in one cooperative launch.
@@ -89,6 +91,8 @@ int pairconv_multi_chunks(const std::vector<int>& n_grids, const std::vector<siz
 bool plan_axis(int n, AxisPlan* out);
 size_t pairconv_smem_bytes(const GridGeom& g, int elem_bytes, int pass);
 
+// batch: complex grids the scratch (and epart) hold; the grids are processed
+// in chunks of at most that many.
 template <typename T>
 cudaError_t pairconv_run(const GridGeom& g, const FFTTables<T>& tb, const T* psi, int n_occ, T* W,
                          const PairGrid* d_grids, int n_grids, cplx<T>* scratch, int batch, double* epart,
@@ -153,10 +157,11 @@ cudaError_t symmetrize(int N, const double* A, double* B, int mode, bool neg, cu
 // row-major, overwritten).  Pivots are column indices, ties to the lowest
 // index.  aux: caller scratch of qrcp_aux_bytes(nrow, ncol) bytes.
 // *h_timeout = 1 when a grid-barrier wait of the persistent kernel ran out of
-// time (the pivots are then invalid); the persistent path waits for s.
+// time (the pivots are then invalid); wait_limit_ns bounds each such wait.
+// The persistent path waits for s.
 template <typename T>
-cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* aux, int* h_timeout, cudaStream_t s,
-                        int* launches);
+cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* aux, int* h_timeout,
+                        unsigned long long wait_limit_ns, cudaStream_t s, int* launches);
 size_t qrcp_aux_bytes(int nrow, int ncol);
 
 // Subsample gather: out[o][c] = psi[o][full index of subsample point c]

@@ -451,16 +451,4 @@ inline bool enabled() {
 
 }  // namespace spec2
 
-namespace spec {
-
-// Out-of-place passes where two planes fit in shared memory, else in place.
-template <int N>
-bool launch_any(int pass, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s) {
-    if constexpr (spec2::smem_max(N) <= 200 * 1024) {
-        if (spec2::enabled()) return spec2::launch_one<N>(pass, nb, P, g0, s);
-    }
-    return spec_launch_one<N>(pass, nb, P, g0, s);
-}
-
-}  // namespace spec
 }  // namespace lace

@@ -72,6 +72,7 @@ def batch_runs():
         out["W"] = [v.get_orbitals(B.ORB_W) for v in views]
         out["xi"] = [v.get_orbitals(B.ORB_XI) for v in views]
         out["pairs"] = [v.get_pairs() for v in views]
+        out["piv"] = [v.get_pivots() for v in views]
         # drift the orbitals (out of their span) and replay the graph
         for p in phis:
             synth.perturb_in_place(p, 3e-2)
@@ -124,6 +125,41 @@ def test_unscreened_instance_matches_the_fp64_oracle(batch_runs):
     occ = O.lowdin(g, phi)
     _, ex_ref, _ = O.apply_exchange(g, occ, None, np.ones((s.n_occ, s.n_occ), dtype=bool))
     assert abs(out["runs"][0][0][0] - ex_ref) <= 1e-5
+
+
+@pytest.mark.parametrize("q", [3, 4])
+def test_screened_instance_matches_the_fp64_oracle(batch_runs, q):
+    """A localised, screened instance (S_thr = 1e-3) against the oracle on the
+    instance's own SCDM points: the points must be a valid pivoted-QR order
+    of the oracle's canonical orbitals (every choice within 1e-4 of the
+    largest residual norm, the FP32 QR's rounding), the kept pair set must
+    equal the oracle's outside a 1e-5 band around the threshold, and E_x, W
+    and xi must match the oracle's localised exchange and ACE build
+    (Sec. 2, Eqs. 2-5 and the Cholesky form of ACE)."""
+    sy, out = batch_runs
+    s, thr, phi = sy[q]
+    assert thr > 0
+    n = s.n_occ
+    g = O.Grid(s.cell, s.shape)
+    occ = O.lowdin(g, phi)
+    piv = out["piv"][q]
+    sub = O.subsample_indices(s.shape, 2)
+    col = {int(p): k for k, p in enumerate(sub)}
+    ratios = O.qrcp_pivot_ratios(occ.reshape(n, -1)[:, sub], [col[int(p)] for p in piv])
+    assert ratios.min() >= 1.0 - 1e-4, ratios.min()
+    _, _, w = O.scdm(g, occ, 2, pivots=piv)
+    S = O.overlap_moduli(g, w)
+    keep = np.zeros((n, n), dtype=bool)
+    for i, j in out["pairs"][q]:
+        keep[i, j] = keep[j, i] = True
+    outside = np.abs(S - thr) > 1e-5 * thr
+    assert np.array_equal(keep[outside], (S >= thr)[outside])
+    assert keep.sum() < n * n  # the screen dropped pairs
+    W_ref, ex_ref, _ = O.apply_exchange(g, w, None, keep)
+    xi_ref, _, _ = O.ace_build(g, w, W_ref)
+    assert abs(out["runs"][0][0][q] - ex_ref) <= 1e-5
+    assert relerr(out["W"][q], W_ref) <= 2e-5
+    assert relerr(out["xi"][q], xi_ref) <= 5e-5
 
 
 def test_small_scratch_pool_gives_the_same_results(batch_runs, monkeypatch):

@@ -1,0 +1,96 @@
+"""The ACE workload end to end against the FP64 oracle, at full size.
+
+96^3 grid, 256 water-like occupied + 128 extra orbitals (N_P = 384), SCDM on
+the stride-2 subsample, S_thr = 1e-3, mixed precision (FP32 pair
+convolutions, 3xBF16 tensor-core ACE contractions, FP64 Cholesky).  Both
+sides run on the oracle's own SCDM points (imposed with lace_set_pivots):
+the oracle localises, screens, applies the exchange to all 384 targets
+(about 35,000 FP64 pair potentials on the host), builds ACE (Eq. 3 / Eq. 7
+and the Cholesky form, Sec. 2) and applies it to four probes.  Compared:
+the kept pair set (outside a 1e-5 band around the threshold), E_x
+(|dE_x| <= 1e-5 Ha, the mixed-precision target), W element by element,
+M'_sym and L, and K_ACE psi on the probes (max relative difference, the
+error measure the mixed path reports).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from paper_1801_09263_gb300 import LACE_MIXED, Lace
+from paper_1801_09263_gb300 import binding as B
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+S_THR = 1e-3
+
+
+def relerr(a, b):
+    return float(np.max(np.abs(a - b)) / np.max(np.abs(b)))
+
+
+@pytest.fixture(scope="module")
+def both():
+    sysm = synth.config3_water_like_with_extras()
+    n_occ, n_extra = sysm.n_occ, sysm.n_extra
+    g = O.Grid(sysm.cell, sysm.shape)
+    occ = O.lowdin(g, sysm.phi[:n_occ])
+    extra = O.orthonormalize_extras(g, occ, sysm.phi[n_occ:])
+    piv, _, w = O.scdm(g, occ, 2)
+    S = O.overlap_moduli(g, w)
+    probe = np.random.default_rng(11).standard_normal((4,) + sysm.shape)
+    with Lace(0, LACE_MIXED) as ctx:
+        ctx.set_cell(sysm.cell, sysm.shape, sysm.ecut)
+        ctx.load_orbitals(sysm.phi, n_occ, n_extra, True)
+        ctx.set_pivots(piv)
+        ctx.screen(S_THR)
+        W, ex = ctx.apply_exchange()
+        ctx.build_ace()
+        gpu = dict(W=W, ex=ex, pairs=ctx.get_pairs(), M=ctx.get_matrix(B.MAT_EXCHANGE),
+                   L=ctx.get_matrix(B.MAT_CHOLESKY), k=ctx.apply_ace(probe))
+    keep = np.zeros((n_occ, n_occ + n_extra), dtype=bool)
+    for i, j in gpu["pairs"]:
+        keep[i, j] = True
+        if j < n_occ:
+            keep[j, i] = True
+    psi = np.concatenate([w, extra])
+    W_ref, ex_ref, _ = O.apply_exchange(g, w, extra, keep)
+    xi_ref, L_ref, M_ref = O.ace_build(g, psi, W_ref)
+    ref = dict(S=S, W=W_ref, ex=ex_ref, L=L_ref, M=M_ref, k=O.ace_apply(g, xi_ref, probe))
+    return sysm, gpu, ref
+
+
+def test_kept_pairs_match_the_oracle_screen(both):
+    sysm, gpu, ref = both
+    n_occ = sysm.n_occ
+    keep = np.zeros((n_occ, n_occ), dtype=bool)
+    extras = 0
+    for i, j in gpu["pairs"]:
+        if j < n_occ:
+            keep[i, j] = keep[j, i] = True
+        else:
+            extras += 1
+    assert extras == n_occ * sysm.n_extra  # every pair with an extra orbital (Sec. 4.1)
+    S = ref["S"]
+    outside = np.abs(S - S_THR) > 1e-5 * S_THR
+    assert np.array_equal(keep[outside], (S >= S_THR)[outside])
+
+
+def test_exchange_energy_and_w_match_the_oracle(both):
+    _, gpu, ref = both
+    assert abs(gpu["ex"] - ref["ex"]) <= 1e-5, (gpu["ex"], ref["ex"])
+    for j in range(gpu["W"].shape[0]):
+        assert relerr(gpu["W"][j], ref["W"][j]) <= 2e-5, j
+
+
+def test_ace_matrix_and_cholesky_factor_match_the_oracle(both):
+    _, gpu, ref = both
+    m_sym = 0.5 * (gpu["M"] + gpu["M"].T)
+    assert relerr(m_sym, ref["M"]) <= 5e-5
+    assert relerr(gpu["L"], ref["L"]) <= 1e-4
+
+
+def test_ace_application_matches_the_oracle(both):
+    _, gpu, ref = both
+    for q in range(ref["k"].shape[0]):
+        assert relerr(gpu["k"][q], ref["k"][q]) <= 1e-4, q
