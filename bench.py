@@ -36,8 +36,9 @@ STRIDE = 2
 B_ALG_PER_PAIR_FP32 = 16  # bytes per grid point per real pair (3-pass FFT model)
 # sources of the pair-convolution kernels: the committed DRAM-traffic capture
 # (profiles/pairconv_traffic.json) holds their hash and counts only while they match
-PAIRCONV_SOURCES = ("common.cuh", "lace_internal.cuh", "pairconv.cu", "pairconv_spec.cuh", "pairconv_spec2.cuh",
-                    "pairconv_spec_s.cu", "pairconv_spec_m.cu", "pairconv_spec_l.cu")
+PAIRCONV_SOURCES = ("common.cuh", "dft_packed.cuh", "f32x2.cuh", "lace_internal.cuh", "pairconv.cu", "pairconv_spec.cuh",
+                    "pairconv_spec2.cuh", "pairconv_pair.cuh", "pairconv_spec_s.cu", "pairconv_spec_m.cu",
+                    "pairconv_spec_l.cu")
 
 
 def pairconv_sources_sha256() -> str:
@@ -76,6 +77,7 @@ def parse():
     p.add_argument("--profile-pairconv", action="store_true",
                    help="only the pair convolutions of a 64-orbital 72^3 set (for ncu captures)")
     p.add_argument("--fp64", action="store_true", help="with --profile-pairconv: FP64 path")
+    p.add_argument("--profile-n", type=int, default=72, help="with --profile-pairconv: cubic grid size")
     p.add_argument("--serving", action="store_true",
                    help="only the serving stream (32 resident systems, Poisson arrivals, p50/p99 latency)")
     p.add_argument("--serve-iters", type=int, default=10, help="SCF-like iterations per system (--serving)")
@@ -580,6 +582,8 @@ def run_ace96(local, reps=3):
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if not os.path.exists(ACE96_ORACLE):
+        return {"error": "tests/golden/ace96_oracle_sample.json missing (run tests/golden/make_ace96_oracle.py)"}
     with open(ACE96_ORACLE) as f:
         gold = json.load(f)
     sysm = synth.config3_water_like_with_extras()
@@ -680,7 +684,7 @@ def run_batched(local, steps=5, n_instances=48):
 
 
 def run_profile(args, local):
-    """Pair convolutions only: 64 orbitals on the 72^3 grid, every pair (2080)."""
+    """Pair convolutions only: 64 orbitals on the 72^3 grid (--profile-n), every pair (2080)."""
     import synth
     import torch
 
@@ -689,16 +693,18 @@ def run_profile(args, local):
 
     build()
     torch.cuda.set_device(local)
-    sysm = synth.small_localized_system(7, (23.5, 23.5, 23.5), (72, 72, 72), 40.0, 48, 64)
+    n = args.profile_n
+    L = 23.5 * n / 72.0
+    sysm = synth.small_localized_system(7, (L, L, L), (n, n, n), 40.0 * min(1.0, (n / 72.0) ** 2), 48, 64)
     ctx = lace.Lace(local, lace.LACE_FP64 if args.fp64 else lace.LACE_MIXED)
     ctx.set_cell(sysm.cell, sysm.shape, sysm.ecut)
     ctx.load_orbitals(sysm.phi, sysm.n_occ, 0, False)
     for _ in range(max(1, args.steps)):
         ctx.apply_exchange(want_W=False)
     t = ctx.get_timings()
-    n = sysm.n_occ * (sysm.n_occ + 1) // 2
-    print(json.dumps({"profile": "pairconv", "n_pairs": n, "pairconv_ms": t["pairconv_kernels"],
-                      "us_per_pair": 1e3 * t["pairconv_kernels"] / n}), flush=True)
+    npairs = sysm.n_occ * (sysm.n_occ + 1) // 2
+    print(json.dumps({"profile": "pairconv", "grid": n, "n_pairs": npairs, "pairconv_ms": t["pairconv_kernels"],
+                      "us_per_pair": 1e3 * t["pairconv_kernels"] / npairs}), flush=True)
     ctx.close()
 
 

@@ -25,12 +25,14 @@
 // and last stages, pass B's forward stage / K(G) product / inverse stage in
 // registers with its K slab staged by cp.async, plane-major launch order of
 // passes A and C, L2 prefetch one wave ahead, odd row pitch for line-fast z
-// stages.  Used where two paired planes fit in shared memory (n <= 80).
+// stages.  Built where two paired planes fit in shared memory (n <= 80), run
+// by default where two paired CTAs share an SM (n <= 48; see enabled()).
 #pragma once
 
 #include <atomic>
 #include <cstdlib>
 
+#include "f32x2.cuh"
 #include "pairconv_spec2.cuh"
 
 namespace lace {
@@ -38,42 +40,6 @@ namespace pair2 {
 
 using spec::Plan2;
 using spec::plan2;
-
-// ---------------------------------------------------------------------------
-// Packed FP32 pairs.
-struct f2 {
-    unsigned long long v;
-};
-__device__ __forceinline__ f2 mk2(float lo, float hi) {
-    f2 r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
-    return r;
-}
-__device__ __forceinline__ f2 bc2(float a) { return mk2(a, a); }
-__device__ __forceinline__ void unpk2(f2 a, float& lo, float& hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
-}
-__device__ __forceinline__ f2 operator+(f2 a, f2 b) {
-    f2 r;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ f2 operator-(f2 a, f2 b) {
-    f2 r;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ f2 operator*(f2 a, f2 b) {
-    f2 r;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
-    return r;
-}
-__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
-    f2 r;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
-    return r;
-}
-__device__ __forceinline__ f2 neg2(f2 a) { return bc2(0.f) - a; }
 
 // Two complex values: x = (re of grid a, re of grid b), y = (im a, im b).
 struct P2 {
@@ -92,20 +58,6 @@ template <int S> __device__ __forceinline__ P2 padd_i(P2 a, P2 b) {
     else return P2{a.x + b.y, a.y - b.x};
 }
 template <int S> __device__ __forceinline__ P2 psub_i(P2 a, P2 b) { return padd_i<-S>(a, b); }
-
-// x * c for a compile-time constant c carried as hi + lo floats (the product
-// rounded once, as mulk in common.cuh: an unbiased transform).
-__device__ __forceinline__ f2 mulk2(f2 x, double c) {
-    const float hi = (float)c;
-    const float lo = (float)(c - (double)hi);
-    return fma2(x, bc2(hi), x * bc2(lo));
-}
-// acc + x * c with c as hi + lo
-__device__ __forceinline__ f2 fmak2(f2 x, double c, f2 acc) {
-    const float hi = (float)c;
-    const float lo = (float)(c - (double)hi);
-    return fma2(x, bc2(hi), fma2(x, bc2(lo), acc));
-}
 
 // Multiply by exp(DIR 2 pi i M / N), compile-time constant; the trivial
 // cases need no multiplication and the odd multiples of pi/4 one constant
@@ -655,13 +607,19 @@ bool launch_one(int pass, int nb, const ConvArgs<float>& P, int g0, cudaStream_t
     return true;
 }
 
-// LACE_FFT_UNPAIRED=1 selects the one-grid-per-CTA passes (for comparison).
+// Pairing halves the instructions a point but doubles the shared memory of a
+// CTA; where that leaves one CTA per SM, its barriers are no longer hidden
+// behind a second CTA and the passes are slower (72^3: 3.31 us per pair
+// paired at one CTA per SM, 2.70 unpaired at two).  So the paired passes run
+// by default only where two or more paired CTAs share an SM.
+// LACE_FFT_PAIRED=1 forces them wherever they fit, =0 turns them off.
+template <int N>
 inline bool enabled() {
-    static const int on = [] {
-        const char* e = getenv("LACE_FFT_UNPAIRED");
-        return (e && e[0] == '1') ? 0 : 1;
+    static const int mode = [] {
+        const char* e = getenv("LACE_FFT_PAIRED");
+        return e ? (e[0] == '1' ? 1 : 0) : 2;
     }();
-    return on != 0;
+    return mode == 1 || (mode == 2 && blocks_at(N, threads_for(N)) >= 2);
 }
 
 }  // namespace pair2
@@ -674,7 +632,7 @@ namespace spec {
 template <int N>
 bool launch_any(int pass, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s, bool allow_pair) {
     if constexpr (pair2::fits(N)) {
-        if (allow_pair && pair2::enabled()) return pair2::launch_one<N>(pass, nb, P, g0, s);
+        if (allow_pair && pair2::enabled<N>()) return pair2::launch_one<N>(pass, nb, P, g0, s);
     }
     if constexpr (spec2::smem_max(N) <= 200 * 1024) {
         if (spec2::enabled()) return spec2::launch_one<N>(pass, nb, P, g0, s);

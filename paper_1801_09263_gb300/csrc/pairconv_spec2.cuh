@@ -20,16 +20,22 @@
 //   * passes A and C launch plane-major (the CTAs in flight share one plane
 //     of the orbitals and of W, which then stay in L2), and every CTA
 //     prefetches into L2 what the CTA one wave ahead will read;
-//   * rows of the planes that z lines cross line-fast are padded to n + 1
-//     complex values, which keeps those stages free of bank conflicts;
+//   * each hand-off between two stages picks the row pitch (n or n + 1
+//     complex values) that keeps the 8-byte accesses of a half-warp on
+//     distinct banks for both stages, found with a bank model of every
+//     stage's addresses;
 //   * threads and the register cap are sized so that two CTAs share an SM
 //     where shared memory allows (the register file is split over the SM's
-//     four sub-partitions).
+//     four sub-partitions);
+//   * the butterflies keep each complex value's real and imaginary parts in
+//     one register pair, so complex additions and products with real
+//     constants are single packed FP32 instructions (dft_packed.cuh).
 #pragma once
 
 #include <atomic>
 #include <cstdlib>
 
+#include "dft_packed.cuh"
 #include "pairconv_spec.cuh"
 
 namespace lace {
@@ -103,6 +109,22 @@ __host__ __device__ constexpr int threads_for(int n) {
 // Register cap of the passes.
 __host__ __device__ constexpr int max_regs(int n) { return regs_at(threads_for(n), blocks_at(n, threads_for(n))); }
 
+// Row pitch (n or n + 1 complex values) of the shared-memory plane handed
+// from one stage to the next: hand-offs 0-2 are pass A's stages 1->2, 2->3,
+// 3->4, hand-offs 3-5 pass C's.  Chosen per size with a model of the 8-byte
+// accesses of every stage (a half-warp's 16 addresses on 16 8-byte bank
+// slots; a pitch that sends two of them to one slot costs a second wavefront):
+// bit h set = pitch n + 1 for hand-off h.
+__host__ __device__ constexpr int pad_mask(int n) {
+    switch (n) {
+        case 32: case 40: case 48: case 64: case 80: case 96: return (1 << 0) | (1 << 5);
+        case 72: return 1 << 1;
+        case 100: return (1 << 0) | (1 << 1) | (1 << 4) | (1 << 5);
+        default: return 0;  // 24, 36, 60: pitch n throughout
+    }
+}
+__host__ __device__ constexpr int pitch(int n, int h) { return (pad_mask(n) >> h) & 1 ? n + 1 : n; }
+
 // Hint: fetch bytes (a multiple of 16, 16-byte aligned) at p into L2.
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
@@ -147,7 +169,7 @@ __device__ __forceinline__ void stage(const C* __restrict__ tw, Ld ld, St st) {
                     v[t] = cmul(v[t], w);
                 }
             }
-            DFT<R, DIR>::run(v);
+            fx::FDFT<R, DIR>::run(v);
             const int base = (i - k) * R + k;
 #pragma unroll
             for (int s = 0; s < R; ++s) st(line, base + s * P, v[s]);
@@ -162,7 +184,8 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     constexpr int NP = N * N;
     constexpr Plan2 pl = plan2(N);
     extern __shared__ float4 smem_v4[];
-    constexpr int LP = N + 1;  // odd row pitch: line-fast z stages are free of bank conflicts
+    constexpr int LP = N + 1;  // buffer rows hold up to n + 1 complex values
+    constexpr int P01 = pitch(N, 0), P12 = pitch(N, 1), P23 = pitch(N, 2);
     C* b0 = reinterpret_cast<C*>(smem_v4);
     C* b1 = b0 + N * LP;
     C* tw = b1 + N * LP;
@@ -191,18 +214,18 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
             const float v = two ? __ldg(a2 + q) * __ldg(c2 + q) : 0.f;
             return C{u, v};
         },
-        [&](int y, int z, C v) { b0[y * N + z] = v; });  // pitch N here: conflict-free stores
+        [&](int y, int z, C v) { b0[y * P01 + z] = v; });
     __syncthreads();
     stage<N, pl.r2, pl.r1, -1, N, false, NT>(
-        tw, [&](int y, int z) { return b0[y * N + z]; }, [&](int y, int z, C v) { b1[y * LP + z] = v; });
+        tw, [&](int y, int z) { return b0[y * P01 + z]; }, [&](int y, int z, C v) { b1[y * P12 + z] = v; });
     __syncthreads();
     // y lines (line = z)
     stage<N, pl.r1, 1, -1, N, true, NT>(
-        tw, [&](int z, int y) { return b1[y * LP + z]; }, [&](int z, int y, C v) { b0[y * LP + z] = v; });
+        tw, [&](int z, int y) { return b1[y * P12 + z]; }, [&](int z, int y, C v) { b0[y * P23 + z] = v; });
     __syncthreads();
     C* out = P.scratch + (size_t)g * P.ng + off;
     stage<N, pl.r2, pl.r1, -1, N, true, NT>(
-        tw, [&](int z, int y) { return b0[y * LP + z]; }, [&](int z, int y, C v) { out[y * N + z] = v; });
+        tw, [&](int z, int y) { return b0[y * P23 + z]; }, [&](int z, int y, C v) { out[y * N + z] = v; });
     if (pf && pf_orb >= 0) prefetch_l2(P.psi + (size_t)pf_orb * P.ng + (size_t)xa * NP, NP * sizeof(float));
 }
 
@@ -266,7 +289,7 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
                 v[t] = b0[(k2 + t * RB) * N + z];
                 if (t > 0) v[t] = cmul(v[t], tw[t * k2]);
             }
-            DFT<RA, -1>::run(v);
+            fx::FDFT<RA, -1>::run(v);
 #pragma unroll
             for (int s = 0; s < RA; ++s) {
                 const int xx = k2 + s * RB;
@@ -281,7 +304,7 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
                 }
                 v[s] = C{v[s].x * k, v[s].y * k};
             }
-            DFT<RA, +1>::run(v);
+            fx::FDFT<RA, +1>::run(v);
 #pragma unroll
             for (int n1 = 0; n1 < RA; ++n1) {
                 C w = tw[n1 * k2];
@@ -301,7 +324,7 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
             C v[RB];
 #pragma unroll
             for (int t = 0; t < RB; ++t) v[t] = b1[(n1 * RB + t) * N + z];
-            DFT<RB, +1>::run(v);
+            fx::FDFT<RB, +1>::run(v);
 #pragma unroll
             for (int s = 0; s < RB; ++s) base[(size_t)(n1 + RA * s) * NP + z] = v[s];
         }
@@ -317,7 +340,8 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     constexpr int NP = N * N;
     constexpr Plan2 pl = plan2(N);
     extern __shared__ float4 smem_v4[];
-    constexpr int LP = N + 1;  // odd row pitch (the last stage writes pitch N for the epilogue)
+    constexpr int LP = N + 1;  // buffer rows hold up to n + 1 complex values (the last stage writes pitch n)
+    constexpr int P01 = pitch(N, 3), P12 = pitch(N, 4), P23 = pitch(N, 5);
     C* b0 = reinterpret_cast<C*>(smem_v4);
     C* b1 = b0 + N * LP;
     C* tw = b1 + N * LP;
@@ -333,7 +357,7 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
             prefetch_l2(P.scratch + (size_t)ga * P.ng + (size_t)xa * NP, NP * sizeof(C));
     }
     stage<N, pl.r1, 1, +1, N, true, NT>(
-        tw, [&](int z, int y) { return in[y * N + z]; }, [&](int z, int y, C v) { b0[y * LP + z] = v; });
+        tw, [&](int z, int y) { return in[y * N + z]; }, [&](int z, int y, C v) { b0[y * P01 + z] = v; });
     if (P.pf_ahead > 0 && threadIdx.x < 8) {
         // the epilogue's orbital planes and W planes, fetched into L2 while
         // the FFT stages run
@@ -346,13 +370,14 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     }
     __syncthreads();
     stage<N, pl.r2, pl.r1, +1, N, true, NT>(
-        tw, [&](int z, int y) { return b0[y * LP + z]; }, [&](int z, int y, C v) { b1[y * LP + z] = v; });
+        tw, [&](int z, int y) { return b0[y * P01 + z]; }, [&](int z, int y, C v) { b1[y * P12 + z] = v; });
     __syncthreads();
+    // z lines (line = y)
     stage<N, pl.r1, 1, +1, N, true, NT>(
-        tw, [&](int y, int z) { return b1[y * LP + z]; }, [&](int y, int z, C v) { b0[y * LP + z] = v; });
+        tw, [&](int y, int z) { return b1[y * P12 + z]; }, [&](int y, int z, C v) { b0[y * P23 + z] = v; });
     __syncthreads();
     stage<N, pl.r2, pl.r1, +1, N, false, NT>(
-        tw, [&](int y, int z) { return b0[y * LP + z]; }, [&](int y, int z, C v) { b1[y * N + z] = v; });
+        tw, [&](int y, int z) { return b0[y * P23 + z]; }, [&](int y, int z, C v) { b1[y * N + z] = v; });
     __syncthreads();
     const bool two = d.j2 >= 0;
     const bool a_occ = d.j1 < P.n_occ, a_sym = a_occ && d.j1 != d.i1;

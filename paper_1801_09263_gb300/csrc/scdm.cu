@@ -4,6 +4,7 @@
 // rotation computed by the caller.
 #include <algorithm>
 
+#include "f32x2.cuh"
 #include "grid_sync.cuh"
 #include "lace_internal.cuh"
 
@@ -491,6 +492,304 @@ __global__ void gather_columns_kernel(const T* __restrict__ psi, size_t ldpsi, i
     out[e] = (double)psi[(size_t)o * ldpsi + (size_t)idx[p]];
 }
 
+
+// ---------------------------------------------------------------------------
+// Register-resident pivoted QR (FP32): the same Businger-Golub steps as the
+// kernels above (take the live column with the largest residual norm, ties
+// to the lowest index; remove its direction from every column; recompute
+// every norm exactly from the updated values), laid out so that one step is
+// a short dependent chain.  LPC lanes hold one column (RPL rows each), so
+// the q.r dot products and the norms reduce with lane shuffles alone; the
+// columns of a CTA that do not fit in registers live in shared memory with a
+// padded row pitch (16-byte accesses free of bank conflicts).  The row work
+// runs on packed FP32 pairs.  Per step each warp publishes its best column
+// (values and FP64 partial sums of squares) to global memory; the CTAs
+// then agree on the global winner through one 64-bit atomicMax per CTA
+// (key = norm bits above the complemented column index: the largest norm,
+// then the lowest index) and a grid barrier on a monotone arrival counter;
+// every CTA reads the winner's published column and forms q in FP64 scale.
+constexpr int QR2_THREADS = 256, QR2_WARPS = QR2_THREADS / 32;
+
+__device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <int RPL>
+__device__ __forceinline__ float qdot(const float* __restrict__ qs, const float* v) {
+    f2 a0 = bc2(0.f), a1 = bc2(0.f);
+#pragma unroll
+    for (int j = 0; j < RPL; j += 4) {
+        const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
+        a0 = fma2(mk2(q4.x, q4.y), mk2(v[j], v[j + 1]), a0);
+        a1 = fma2(mk2(q4.z, q4.w), mk2(v[j + 2], v[j + 3]), a1);
+    }
+    float x0, x1;
+    unpk2(a0 + a1, x0, x1);
+    return x0 + x1;
+}
+
+// v -= q d, and the squared norm of the result
+template <int RPL>
+__device__ __forceinline__ float qupdate(const float* __restrict__ qs, float* v, float d) {
+    const f2 nd = bc2(-d);
+    f2 n0 = bc2(0.f), n1 = bc2(0.f);
+#pragma unroll
+    for (int j = 0; j < RPL; j += 4) {
+        const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
+        const f2 u0 = fma2(mk2(q4.x, q4.y), nd, mk2(v[j], v[j + 1]));
+        const f2 u1 = fma2(mk2(q4.z, q4.w), nd, mk2(v[j + 2], v[j + 3]));
+        n0 = fma2(u0, u0, n0);
+        n1 = fma2(u1, u1, n1);
+        unpk2(u0, v[j], v[j + 1]);
+        unpk2(u1, v[j + 2], v[j + 3]);
+    }
+    float x0, x1;
+    unpk2(n0 + n1, x0, x1);
+    return x0 + x1;
+}
+
+template <int RPL>
+__device__ __forceinline__ float qnorm(const float* v) {
+    f2 n0 = bc2(0.f), n1 = bc2(0.f);
+#pragma unroll
+    for (int j = 0; j < RPL; j += 4) {
+        const f2 u0 = mk2(v[j], v[j + 1]), u1 = mk2(v[j + 2], v[j + 3]);
+        n0 = fma2(u0, u0, n0);
+        n1 = fma2(u1, u1, n1);
+    }
+    float x0, x1;
+    unpk2(n0 + n1, x0, x1);
+    return x0 + x1;
+}
+
+// The same three for a column chunk in shared memory (16-byte accesses,
+// nothing held in registers across the chunk).
+template <int RPL>
+__device__ __forceinline__ float sdot(const float* __restrict__ qs, const float* w) {
+    f2 a0 = bc2(0.f), a1 = bc2(0.f);
+#pragma unroll 8
+    for (int j = 0; j < RPL; j += 4) {
+        const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
+        const float4 x = *reinterpret_cast<const float4*>(w + j);
+        a0 = fma2(mk2(q4.x, q4.y), mk2(x.x, x.y), a0);
+        a1 = fma2(mk2(q4.z, q4.w), mk2(x.z, x.w), a1);
+    }
+    float x0, x1;
+    unpk2(a0 + a1, x0, x1);
+    return x0 + x1;
+}
+template <int RPL>
+__device__ __forceinline__ float supdate(const float* __restrict__ qs, float* w, float d, bool store) {
+    const f2 nd = bc2(-d);
+    f2 n0 = bc2(0.f), n1 = bc2(0.f);
+#pragma unroll 8
+    for (int j = 0; j < RPL; j += 4) {
+        const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
+        const float4 x = *reinterpret_cast<const float4*>(w + j);
+        const f2 u0 = fma2(mk2(q4.x, q4.y), nd, mk2(x.x, x.y));
+        const f2 u1 = fma2(mk2(q4.z, q4.w), nd, mk2(x.z, x.w));
+        n0 = fma2(u0, u0, n0);
+        n1 = fma2(u1, u1, n1);
+        if (store) {
+            float4 o;
+            unpk2(u0, o.x, o.y);
+            unpk2(u1, o.z, o.w);
+            *reinterpret_cast<float4*>(w + j) = o;
+        }
+    }
+    float x0, x1;
+    unpk2(n0 + n1, x0, x1);
+    return x0 + x1;
+}
+template <int RPL>
+__device__ __forceinline__ float snorm(const float* w) {
+    f2 n0 = bc2(0.f), n1 = bc2(0.f);
+#pragma unroll 8
+    for (int j = 0; j < RPL; j += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(w + j);
+        const f2 u0 = mk2(x.x, x.y), u1 = mk2(x.z, x.w);
+        n0 = fma2(u0, u0, n0);
+        n1 = fma2(u1, u1, n1);
+    }
+    float x0, x1;
+    unpk2(n0 + n1, x0, x1);
+    return x0 + x1;
+}
+
+// sum over the LPC lanes of one column (consecutive lanes)
+template <int LPC>
+__device__ __forceinline__ float lane_sum(float x) {
+#pragma unroll
+    for (int o = 1; o < LPC; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+}
+
+__device__ __forceinline__ unsigned long long col_key(float nrm, int col) {
+    return ((unsigned long long)__float_as_uint(nrm) << 32) | (unsigned long long)(0xffffffffu - (unsigned)col);
+}
+
+// The columns of CTA b are [b cpb, (b + 1) cpb): the first G = 256 / LPC in
+// registers (group g = thread / LPC), the rest (s = 0, 1, ...) in shared
+// memory, handled by group s % G.  Rows: lane l of a group holds rows
+// [l RPL, (l + 1) RPL).  keys[npiv] and bar[0] are zero at launch.
+template <int RPL, int LPC>
+__global__ void __launch_bounds__(QR2_THREADS, 1)
+    qr_resident_kernel(int nrow, int ncol, const float* __restrict__ R, int npiv, int cpb, float* __restrict__ pub,
+                       double* __restrict__ pubn, unsigned long long* __restrict__ keys, int* __restrict__ piv,
+                       unsigned* bar, unsigned long long limit_ns) {
+    constexpr int G = QR2_THREADS / LPC;
+    constexpr int NPAD = RPL * LPC;     // padded rows
+    constexpr int PITCH = RPL + 4;      // shared-memory row-chunk pitch (floats)
+    extern __shared__ __align__(16) float qr2_smem[];
+    float* qs = qr2_smem;                // [NPAD] q of the current step
+    float* sc = qr2_smem + NPAD;         // [SC][LPC][PITCH] shared-memory columns
+    __shared__ unsigned long long wkey[QR2_WARPS];
+    __shared__ int abort_sh;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int g = tid / LPC, l = tid % LPC;
+    const int c0 = blockIdx.x * cpb;
+    const int ncta = min(cpb, ncol - c0);  // columns of this CTA
+    const int SC = max(0, ncta - G);       // of them in shared memory
+    const int rounds = (SC + G - 1) / G;
+    const int myreg = g < ncta ? c0 + g : -1;
+    float v[RPL];
+    unsigned chosen = 0u;  // bit 0: the register column; bit 1 + r: shared column of round r
+#pragma unroll
+    for (int j = 0; j < RPL; ++j) {
+        const int row = l * RPL + j;
+        v[j] = (myreg >= 0 && row < nrow) ? R[(size_t)row * ncol + myreg] : 0.f;
+    }
+    for (int r = 0; r < rounds; ++r) {
+        const int s = r * G + g;
+        if (s < SC) {
+            float* dst = sc + ((size_t)s * LPC + l) * PITCH;
+            const int col = c0 + G + s;
+            for (int j = 0; j < RPL; ++j) {
+                const int row = l * RPL + j;
+                dst[j] = row < nrow ? R[(size_t)row * ncol + col] : 0.f;
+            }
+        }
+    }
+    for (int j = tid; j < NPAD; j += QR2_THREADS) qs[j] = 0.f;
+    __syncthreads();
+    for (int step = 0; step < npiv; ++step) {
+        const float* qrow = qs + l * RPL;
+        unsigned long long best = 0ull;
+        // register column
+        {
+            float nrm;
+            if (step > 0) {
+                const float d = lane_sum<LPC>(qdot<RPL>(qrow, v));
+                nrm = lane_sum<LPC>(qupdate<RPL>(qrow, v, d));
+            } else {
+                nrm = lane_sum<LPC>(qnorm<RPL>(v));
+            }
+            if (myreg >= 0 && !(chosen & 1u)) best = col_key(nrm, myreg);
+        }
+        // shared-memory columns
+        for (int r = 0; r < rounds; ++r) {
+            const int s = r * G + g;
+            const bool has = s < SC;  // uniform over the LPC lanes of the group
+            float* w = sc + ((size_t)(has ? s : 0) * LPC + l) * PITCH;
+            float nrm;
+            if (step > 0) {
+                const float d = lane_sum<LPC>(sdot<RPL>(qrow, w));
+                nrm = lane_sum<LPC>(supdate<RPL>(qrow, w, d, has));
+            } else {
+                nrm = lane_sum<LPC>(snorm<RPL>(w));
+            }
+            if (has && !((chosen >> (1 + r)) & 1u)) {
+                const unsigned long long k = col_key(nrm, c0 + G + s);
+                best = k > best ? k : best;
+            }
+        }
+        // warp argmax of the keys
+        unsigned long long wb = best;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long x = __shfl_xor_sync(0xffffffffu, wb, o);
+            wb = x > wb ? x : wb;
+        }
+        // the lanes holding the warp's best column publish it
+        if (wb != 0ull) {
+            const int wcol = (int)(0xffffffffu - (unsigned)(wb & 0xffffffffu));
+            const size_t slot = ((size_t)(step & 1) * gridDim.x + blockIdx.x) * QR2_WARPS + warp;
+            float* out = pub + slot * NPAD + l * RPL;
+            if (wcol == myreg) {
+                double sq = 0.0;
+#pragma unroll
+                for (int j = 0; j < RPL; j += 4) {
+                    *reinterpret_cast<float4*>(out + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    sq += (double)v[j] * v[j] + (double)v[j + 1] * v[j + 1] + (double)v[j + 2] * v[j + 2] +
+                          (double)v[j + 3] * v[j + 3];
+                }
+                pubn[slot * LPC + l] = sq;
+            } else {
+                const int s = wcol - c0 - G;
+                if (s >= 0 && s < SC && s % G == g) {
+                    const float* w = sc + ((size_t)s * LPC + l) * PITCH;
+                    double sq = 0.0;
+                    for (int j = 0; j < RPL; j += 4) {
+                        const float4 x = *reinterpret_cast<const float4*>(w + j);
+                        *reinterpret_cast<float4*>(out + j) = x;
+                        sq += (double)x.x * x.x + (double)x.y * x.y + (double)x.z * x.z + (double)x.w * x.w;
+                    }
+                    pubn[slot * LPC + l] = sq;
+                }
+            }
+        }
+        if (lane == 0) wkey[warp] = wb;
+        // grid barrier: arrive with this CTA's best key, wait for every CTA
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long kb = 0ull;
+#pragma unroll
+            for (int w = 0; w < QR2_WARPS; ++w) kb = wkey[w] > kb ? wkey[w] : kb;
+            __threadfence();
+            if (kb) atomicMax(keys + step, kb);
+            const unsigned target = (unsigned)(step + 1) * gridDim.x;
+            unsigned cnt;
+            asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(cnt) : "l"(bar) : "memory");
+            int timed_out = 0;
+            if (cnt + 1 < target) {
+                const unsigned long long t0 = global_ns();
+                while (ld_acquire_u32(bar) < target) {
+                    if (global_ns() - t0 > limit_ns) {
+                        atomicExch(bar + 2, 1u);
+                        timed_out = 1;
+                        break;
+                    }
+                }
+            }
+            abort_sh = timed_out;
+        }
+        __syncthreads();
+        if (abort_sh) return;
+        const unsigned long long key = ld_cg_u64(keys + step);
+        if (key == 0ull) {  // no live column left: cannot happen for npiv <= ncol
+            if (tid == 0) atomicExch(bar + 2, 2u);
+            return;
+        }
+        const int p = (int)(0xffffffffu - (unsigned)(key & 0xffffffffu));
+        const int wcta = p / cpb, li = p - wcta * cpb;
+        const int wg = li < G ? li : (li - G) % G;
+        const size_t slot = ((size_t)(step & 1) * gridDim.x + wcta) * QR2_WARPS + (wg * LPC) / 32;
+        double nn = 0.0;
+#pragma unroll
+        for (int k = 0; k < LPC; ++k) nn += __ldcg(pubn + slot * LPC + k);
+        const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+        for (int j = tid; j < NPAD; j += QR2_THREADS) qs[j] = (float)((double)__ldcg(pub + slot * NPAD + j) * inv);
+        if (wcta == (int)blockIdx.x && wg == g) {
+            if (li < G) chosen |= 1u;
+            else chosen |= 1u << (1 + (li - G) / G);
+        }
+        if (tid == 0 && blockIdx.x == 0) piv[step] = p;
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
@@ -498,9 +797,23 @@ static size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 // Capacity (in Best entries) of the block-winner buffer of qrcp_aux_bytes.
 static int nblocks_cap(int ncol) { return std::max((ncol + QR_THREADS - 1) / QR_THREADS, 2 * 152 * 8); }
 
-// Published candidate columns of the persistent kernel: 2 (step parity) x
-// CTAs (up to 304) x padded rows (< 2 nrow + 64), FP64 at most.
-static size_t pub_bytes(int nrow) { return align256((size_t)2 * 304 * (2 * (size_t)nrow + 64) * sizeof(double)); }
+// Row layout of the register-resident QR: RPL rows per lane, LPC lanes per column.
+static void qr2_layout(int nrow, int* rpl, int* lpc) {
+    *rpl = nrow <= 32 ? 32 : nrow <= 64 ? 64 : 128;
+    *lpc = nrow <= 128 ? 1 : nrow <= 256 ? 2 : nrow <= 512 ? 4 : 8;
+}
+
+// Published candidate columns: of the persistent kernel, 2 (step parity) x
+// CTAs (up to 304) x padded rows (< 2 nrow + 64), FP64 at most; of the
+// register-resident kernel, 2 x CTAs x 8 warps x padded rows (FP32) plus
+// their FP64 partial norms.
+static size_t pub_bytes(int nrow) {
+    int rpl = 0, lpc = 0;
+    qr2_layout(nrow, &rpl, &lpc);
+    const size_t old = (size_t)2 * 304 * (2 * (size_t)nrow + 64) * sizeof(double);
+    const size_t res = align256((size_t)2 * 304 * 8 * rpl * lpc * sizeof(float)) + (size_t)2 * 304 * 8 * lpc * sizeof(double);
+    return align256(std::max(old, res));
+}
 
 size_t qrcp_aux_bytes(int nrow, int ncol) {
     const int nblocks = nblocks_cap(ncol);
@@ -561,6 +874,59 @@ static cudaError_t qr_persistent_launch(int nrow, int ncol, T* R, int npiv, Best
     return cudaSuccess;
 }
 
+// The register-resident kernel for one (RPL, LPC); *ran = false when the
+// matrix does not fit on chip (registers of 256 threads an SM plus shared
+// memory) or the device cannot co-schedule the CTAs.
+template <int RPL, int LPC>
+static cudaError_t qr_resident_launch(int nrow, int ncol, const float* R, int npiv, unsigned long long* keys,
+                                      float* pub, int* d_piv, unsigned* bar, unsigned long long limit_ns,
+                                      cudaStream_t s, int* launches, bool* ran) {
+    *ran = false;
+    int dev = 0, sms = 0, coop = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    constexpr int G = QR2_THREADS / LPC, NPAD = RPL * LPC, PITCH = RPL + 4;
+    if (!coop || nrow > NPAD || sms > 304 || npiv > 4864) return cudaSuccess;
+    int ctas = std::min(sms, (ncol + G - 1) / G);
+    const int cpb = (ncol + ctas - 1) / ctas;
+    ctas = (ncol + cpb - 1) / cpb;
+    const int sc = std::max(0, cpb - G);
+    if ((sc + G - 1) / G > 31) return cudaSuccess;  // the per-thread chosen mask has 32 bits
+    const void* fn = (const void*)qr_resident_kernel<RPL, LPC>;
+    cudaFuncAttributes fa{};
+    cudaError_t e;
+    if ((e = cudaFuncGetAttributes(&fa, fn))) return e;
+    const size_t dyn = ((size_t)NPAD + (size_t)sc * LPC * PITCH) * sizeof(float);
+    if (dyn + fa.sharedSizeBytes + 1024 > (size_t)optin) return cudaSuccess;
+    // one limit for every caller of this kernel: the opt-in maximum
+    if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes)))
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, QR2_THREADS, dyn))) return e;
+    if (per_sm < 1 || ctas > per_sm * sms) return cudaSuccess;
+    double* pubn = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(pub) +
+                                             align256((size_t)2 * ctas * QR2_WARPS * NPAD * sizeof(float)));
+    if ((e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s))) return e;
+    if ((e = cudaMemsetAsync(keys, 0, (size_t)npiv * sizeof(unsigned long long), s))) return e;
+    int cpb_arg = cpb;
+    void* args[] = {(void*)&nrow, (void*)&ncol, (void*)&R,     (void*)&npiv, (void*)&cpb_arg, (void*)&pub,
+                    (void*)&pubn, (void*)&keys, (void*)&d_piv, (void*)&bar, (void*)&limit_ns};
+    if ((e = cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(QR2_THREADS), args, dyn, s))) return e;
+    *launches += 1;
+    *ran = true;
+    return cudaSuccess;
+}
+
+static bool qr_resident_enabled() {
+    static const int on = [] {
+        const char* e = getenv("LACE_QR_RESIDENT");  // tuning: 0 selects the tile-group persistent kernel
+        return (e && e[0] == '0') ? 0 : 1;
+    }();
+    return on != 0;
+}
+
 // R (nrow x ncol, row-major, leading dimension ncol) is overwritten.  aux is
 // caller-provided scratch of qrcp_aux_bytes(nrow, ncol) bytes.
 template <typename T>
@@ -581,15 +947,34 @@ cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* au
     bool ran = false;
     cudaError_t e;
     if constexpr (sizeof(T) == 4) {
-        if (nrow <= 512)
-            e = qr_persistent_launch<T, 32, 2>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, wait_limit_ns, s,
-                                              launches, &ran);
-        else
-            e = qr_persistent_launch<T, 64, 0>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, wait_limit_ns, s,
-                                              launches, &ran);
+        // register-resident kernel where the matrix fits on chip, else the
+        // tile-group persistent kernel
+        e = cudaSuccess;
+        if (qr_resident_enabled()) {
+            int rpl = 0, lpc = 0;
+            qr2_layout(nrow, &rpl, &lpc);
+            unsigned long long* keys = reinterpret_cast<unsigned long long*>(best);
+            auto go = [&](auto launch) {
+                return launch(nrow, ncol, R, npiv, keys, pub, d_piv, bar, wait_limit_ns, s, launches, &ran);
+            };
+            if (rpl == 32) e = go(qr_resident_launch<32, 1>);
+            else if (rpl == 64) e = go(qr_resident_launch<64, 1>);
+            else if (lpc == 1) e = go(qr_resident_launch<128, 1>);
+            else if (lpc == 2) e = go(qr_resident_launch<128, 2>);
+            else if (lpc == 4) e = go(qr_resident_launch<128, 4>);
+            else e = go(qr_resident_launch<128, 8>);
+        }
+        if (!e && !ran) {
+            if (nrow <= 512)
+                e = qr_persistent_launch<T, 32, 2>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, wait_limit_ns,
+                                                  s, launches, &ran);
+            else
+                e = qr_persistent_launch<T, 64, 0>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, wait_limit_ns,
+                                                  s, launches, &ran);
+        }
     } else {
         e = qr_persistent_launch<T, 32, 0>(nrow, ncol, R, npiv, best, pub, chosen, d_piv, bar, wait_limit_ns, s,
-                                              launches, &ran);
+                                          launches, &ran);
     }
     if (e) return e;
     if (ran) {
