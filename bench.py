@@ -525,6 +525,7 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
         peak_bytes = max(peak_bytes, st["bytes_resident"])
         time.sleep(0.0005)
     makespan = time.perf_counter() - t_start
+    merge = srv.merge_stats()
     srv.close()
     # accuracy: the last rebuild of the smallest systems against the plain FP64 GPU form
     order = sorted((k for k in range(n_systems) if ex_last[k] is not None),
@@ -554,7 +555,10 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
         "latency_ms": {"p50": pct(all_lat, 50), "p99": pct(all_lat, 99),
                        "rebuild_p50": pct(lat["rebuild"], 50), "rebuild_p99": pct(lat["rebuild"], 99),
                        "apply_p50": pct(lat["apply"], 50), "apply_p99": pct(lat["apply"], 99)},
-        "response_ms": {"p50": pct(resp, 50), "p99": pct(resp, 99)},
+        "response_ms": {"p50": pct(resp, 50), "p99": pct(resp, 99), "of": "arrival to completion"},
+        "latency_from": "submission to completion (each system submits its next request once the previous completed)",
+        "served_req_per_s": round(len(all_lat) / makespan, 1), "offered_req_per_s": SERVE_RATE,
+        "merged_pair_convolutions": merge,
         "pair_convolutions_per_s": round(pairs / makespan, 1), "pair_convolutions": int(pairs),
         "makespan_s": round(makespan, 3), "peak_running": peak_running,
         "peak_resident_GB": round(peak_bytes / 1e9, 2),

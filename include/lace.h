@@ -332,6 +332,25 @@ const char* lace_server_request_error(lace_server* srv, long long request_id);
  * (blocks until then); later requests for it fail with LACE_ERR_ARG. */
 lace_status lace_server_remove_system(lace_server* srv, int system_id);
 
+/* Merged pair convolutions across requests (on by default, window 5 ms).
+ * The REBUILDs of systems on one cubic grid size with size-specialised
+ * passes (n in {24, 32, 36, 40, 48, 60, 64, 72, 80, 96, 100}, mixed
+ * precision) that reach their exchange step together share every launch of
+ * the FFT passes: one launch per pass covers the next chunk of complex grids
+ * of every such system, each grid resolving its own system's orbitals, W,
+ * kernel table and scratch.  The first REBUILD to arrive waits at most
+ * window_ms (0..10000) for the others of its size still on their way there.
+ * Results are those of the REBUILDs run alone (the same arithmetic per
+ * grid).  Call while no request is queued or running (LACE_ERR_STATE
+ * otherwise). */
+lace_status lace_server_set_pair_merging(lace_server* srv, int enable, double window_ms);
+
+/* Counters of the merged pair convolutions: launch batches queued, batches
+ * that held more than one REBUILD, and the REBUILDs those held.  Any output
+ * may be NULL. */
+lace_status lace_server_merge_stats(lace_server* srv, long long* batches, long long* merged_batches,
+                                    long long* merged_requests);
+
 /* Snapshot: device bytes held by resident systems, requests running and
  * requests queued.  Any output may be NULL. */
 lace_status lace_server_stats(lace_server* srv, unsigned long long* bytes_resident, int* running, int* queued);

@@ -101,6 +101,8 @@ def load_library(build_if_missing: bool = False):
         "lace_batch_info": ([P, P, P, P, P, P, P, P, I], I),
         "lace_batch_last_error": ([P], C.c_char_p),
         "lace_server_stats": ([P, P, P, P], I),
+        "lace_server_set_pair_merging": ([P, I, D], I),
+        "lace_server_merge_stats": ([P, P, P, P], I),
         "lace_exchange_pairs_noalloc": ([P, I, I, I, P, I, I, P, LL, P, P, P], I),
         "lace_probe_peak_rates": ([I, P, I], I),
         "lace_status_string": ([I], C.c_char_p),
@@ -395,6 +397,16 @@ class Server:
         b, r, q = C.c_ulonglong(0), C.c_int(0), C.c_int(0)
         self._check(self.lib.lace_server_stats(self.h, C.byref(b), C.byref(r), C.byref(q)), "lace_server_stats")
         return dict(bytes_resident=int(b.value), running=r.value, queued=q.value)
+
+    def set_pair_merging(self, enable: bool = True, window_ms: float = 5.0):
+        self._check(self.lib.lace_server_set_pair_merging(self.h, int(bool(enable)), float(window_ms)),
+                    "lace_server_set_pair_merging")
+
+    def merge_stats(self) -> dict:
+        b, mb, mr = C.c_longlong(0), C.c_longlong(0), C.c_longlong(0)
+        self._check(self.lib.lace_server_merge_stats(self.h, C.byref(b), C.byref(mb), C.byref(mr)),
+                    "lace_server_merge_stats")
+        return dict(batches=b.value, merged_batches=mb.value, merged_requests=mr.value)
 
 
 class _Instance(C.Structure):

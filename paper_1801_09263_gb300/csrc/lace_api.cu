@@ -520,6 +520,47 @@ lace_status apply_impl(lace_ctx* c) {
     return LACE_OK;
 }
 
+// The exchange application split around its pair convolutions, for merged
+// launches of the request server: the part before them (pair list, scratch,
+// W and pair energies zeroed) and the part after (E_x from the pair
+// energies).  Mixed precision only.
+lace_status exchange_prepare_f(lace_ctx* c, MergedSys<float>* m, int* n_grids_out, int* cap_out) {
+    Launch L{c};
+    const size_t ng = c->g.ng;
+    if (!c->screened) {
+        lace_status st = make_pairs(c, false, 0.0, L);
+        if (st) return st;
+        c->screened = true;
+        c->s_thr = 0.0;
+    }
+    const long long n_grids = (c->n_pairs + 1) / 2;
+    int batch = (int)std::min<long long>(batch_for(c), std::max<long long>(n_grids, 1));
+    batch += batch & 1;
+    CK(c->scratch.ensure((size_t)batch * ng * 2 * sizeof(float)), "alloc FFT scratch");
+    CK(c->epart.ensure((size_t)batch * c->g.n[0] * 2 * sizeof(double)), "alloc energies");
+    CK(cudaMemsetAsync(c->W.p, 0, (size_t)c->n_p * ng * sizeof(float), c->stream), "zero W");
+    CK(fill_zero_f64(c->m(MS_E), (size_t)c->n_occ * c->n_occ, c->stream, &L.n), "zero E");
+    m->psi = c->psi.as<float>();
+    m->W = c->W.as<float>();
+    m->ktab = c->ktab_f.as<float>();
+    m->grids = c->grids.as<PairGrid>();
+    m->scratch = c->scratch.as<float2>();
+    m->epart = c->epart.as<double>();
+    m->E = c->m(MS_E);
+    m->n_occ = c->n_occ;
+    m->g0 = 0;
+    m->dv = c->g.dv;
+    *n_grids_out = (int)n_grids;
+    *cap_out = batch;
+    return LACE_OK;
+}
+
+lace_status exchange_finish(lace_ctx* c) {
+    Launch L{c};
+    CK(exchange_energy_sum(c->n_occ, c->m(MS_E), c->exd.as<double>(), c->stream, &L.n), "energy");
+    return LACE_OK;
+}
+
 // ------------------------------------------------------------------ ACE
 // Dense contraction over the grid for the ACE matrices: tcgen05 3xBF16 on the
 // mixed path (LACE_NO_TC=1 selects the CUDA-core FP32 kernel), FP64 otherwise.
@@ -648,6 +689,40 @@ lace_status copy_orbitals_out(lace_ctx* c, const T* src, size_t count, double* h
 namespace lace {
 
 lace_status ctx_fail(lace_ctx* c, lace_status st, const std::string& msg) { return fail(c, st, msg); }
+
+bool ctx_mergeable(lace_ctx* c) {
+    return c && c->prec == LACE_MIXED && c->loaded && c->g.n[0] == c->g.n[1] && c->g.n[1] == c->g.n[2] &&
+           spec_merge_ok(c->g.n[0]);
+}
+
+lace_status ctx_exchange_prepare(lace_ctx* c, MergedSys<float>* m, int* n_grids, int* cap, cudaEvent_t ready) {
+    if (!ctx_mergeable(c)) return fail(c, LACE_ERR_STATE, "not a mixed-precision context on a merged grid size");
+    cudaSetDevice(c->device);
+    c->applied = false;
+    lace_status st = materialize_psi(c);
+    if (st) return st;
+    ev_begin(c, ST_EXCHANGE);
+    st = exchange_prepare_f(c, m, n_grids, cap);
+    if (st) return st;
+    CK(cudaEventRecord(ready, c->stream), "exchange");
+    return LACE_OK;
+}
+
+lace_status ctx_exchange_finish(lace_ctx* c, cudaEvent_t done, double* ex_out) {
+    cudaSetDevice(c->device);
+    CK(cudaStreamWaitEvent(c->stream, done, 0), "exchange");
+    lace_status st = exchange_finish(c);
+    ev_end(c, ST_EXCHANGE);
+    c->ev_used[ST_PAIRCONV] = false;  // the merged passes ran on the server's stream
+    if (st) return st;
+    c->applied = true;
+    if (ex_out) CK(cudaMemcpyAsync(ex_out, c->exd.p, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "energy");
+    CK(cudaStreamSynchronize(c->stream), "apply exchange");
+    return LACE_OK;
+}
+
+FFTTables<float> ctx_tables_f(lace_ctx* c) { return tables<float>(c); }
+int ctx_device(lace_ctx* c) { return c->device; }
 
 lace_status ctx_load_dev64(lace_ctx* c, const double* d_phi, int n_occ, int n_extra, int ortho) {
     return load_common(c, d_phi, true, n_occ, n_extra, ortho);

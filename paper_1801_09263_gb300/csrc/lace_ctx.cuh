@@ -103,4 +103,14 @@ lace_status ctx_fail(lace_ctx* c, lace_status st, const std::string& msg);
 lace_status ctx_load_dev64(lace_ctx* c, const double* d_phi, int n_occ, int n_extra, int ortho);
 // device pointer of PSI / W / XI (working precision, [n_p][ng]) after the state checks
 lace_status ctx_orbitals(lace_ctx* c, int which, const void** src);
+// Merged pair convolutions of the request server: whether the context can
+// take part (mixed precision, a cubic grid with merged passes); the exchange
+// application before the pair convolutions (fills *m, the grid count and the
+// grids its scratch holds; records `ready` on the context's stream) and after
+// them (the context's stream waits for `done`; E_x into *ex_out, synchronous).
+bool ctx_mergeable(lace_ctx* c);
+lace_status ctx_exchange_prepare(lace_ctx* c, MergedSys<float>* m, int* n_grids, int* cap, cudaEvent_t ready);
+lace_status ctx_exchange_finish(lace_ctx* c, cudaEvent_t done, double* ex_out);
+FFTTables<float> ctx_tables_f(lace_ctx* c);
+int ctx_device(lace_ctx* c);
 }  // namespace lace

@@ -35,6 +35,26 @@ struct PairGrid {
     int i1, j1, i2, j2;
 };
 
+// Merged launches (the request server): the complex grids of several
+// systems on one grid size run through one launch of each pass.  Per grid of
+// the launch, its system and its index in that system's grid list; per
+// system, its buffers, with g0 = the first of its grids in this launch (its
+// scratch and energy partials hold grids g0, g0 + 1, ...).
+struct GridRef {
+    int sys, g;
+};
+template <typename T> struct MergedSys {
+    const T* psi;
+    T* W;
+    const T* ktab;
+    const PairGrid* grids;
+    cplx<T>* scratch;
+    double* epart;
+    double* E;  // pair-energy matrix [n_occ][n_occ]
+    int n_occ, g0;
+    double dv;
+};
+
 // Kernel arguments of the three FFT passes.
 template <typename T> struct ConvArgs {
     AxisPlan ax[3];
@@ -51,6 +71,11 @@ template <typename T> struct ConvArgs {
     size_t ng;
     double dv;
     int pf_ahead = 0;  // L2 prefetch distance in CTAs of the out-of-place passes (0: none)
+    // merged launches (null otherwise): grid g of the launch is refs[g0 + g]
+    // of system msys[refs[.].sys]; psi, W, ktab, grids, scratch, epart,
+    // n_occ and dv above are then unused
+    const GridRef* refs = nullptr;
+    const MergedSys<T>* msys = nullptr;
 };
 
 // Size-specialised FP32 passes for cubic grids (pairconv_spec_*.cu): launch
@@ -60,6 +85,21 @@ template <typename T> struct ConvArgs {
 bool spec_launch_s(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s, bool allow_pair);
 bool spec_launch_m(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s, bool allow_pair);
 bool spec_launch_l(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s, bool allow_pair);
+
+// Grid sizes whose size-specialised passes take merged launches (one grid
+// per CTA, out of place) (pairconv_spec_*.cu).
+bool spec_merge_ok(int n);
+
+// The pair convolutions of several systems on one cubic grid size (n in
+// spec_merge_ok), merged: per round, the next chunk of every system's grids
+// (at most cap[q] of system q, the grids its scratch holds) goes through one
+// launch of each pass, then the pair energies of every grid of the round are
+// collected into its system's E.  tb: the twiddle tables of the size;
+// d_refs / d_sys: device space for n_grids_total GridRefs and rounds x nsys
+// MergedSys (the host side uploads them); every launch runs on stream s.
+cudaError_t pairconv_run_merged(int n, const FFTTables<float>& tb, const std::vector<MergedSys<float>>& sys,
+                                const std::vector<int>& n_grids, const std::vector<int>& cap, GridRef* d_refs,
+                                MergedSys<float>* d_sys, cudaStream_t s, int* launches, int* rounds_out);
 
 // Persistent multi-instance pair convolutions (pairconv_multi.cu): the kept
 // pairs of many independent systems in one cooperative launch.

@@ -18,6 +18,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <type_traits>
+#include <vector>
 
 #include "lace_internal.cuh"
 #include "pairconv_generic.cuh"
@@ -74,6 +75,32 @@ __global__ void energy_collect_kernel(const double* epart, int nplanes, const Pa
     if (d.j2 >= 0 && d.j2 < n_occ) {
         E[(size_t)d.i2 * n_occ + d.j2] = sb;
         E[(size_t)d.j2 * n_occ + d.i2] = sb;
+    }
+}
+
+// The same for a merged launch: grid g of the round is refs[g0 + g] of its
+// system; the energies go to that system's matrix.
+__global__ void energy_collect_merged_kernel(const GridRef* __restrict__ refs, const MergedSys<float>* __restrict__ ms,
+                                             int g0, int ngr, int nplanes) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= ngr) return;
+    const GridRef r = refs[g0 + g];
+    const MergedSys<float>& m = ms[r.sys];
+    const PairGrid d = m.grids[r.g];
+    const double* ep = m.epart + (size_t)(r.g - m.g0) * nplanes * 2;
+    double sa = 0.0, sb = 0.0;
+    for (int x = 0; x < nplanes; ++x) {
+        sa += ep[2 * x];
+        sb += ep[2 * x + 1];
+    }
+    const int n_occ = m.n_occ;
+    if (d.j1 < n_occ) {
+        m.E[(size_t)d.i1 * n_occ + d.j1] = sa;
+        m.E[(size_t)d.j1 * n_occ + d.i1] = sa;
+    }
+    if (d.j2 >= 0 && d.j2 < n_occ) {
+        m.E[(size_t)d.i2 * n_occ + d.j2] = sb;
+        m.E[(size_t)d.j2 * n_occ + d.i2] = sb;
     }
 }
 
@@ -204,6 +231,79 @@ cudaError_t pairconv_run(const GridGeom& g, const FFTTables<T>& tb, const T* psi
         if ((e = cudaGetLastError())) return e;
     }
     if (ev1) cudaEventRecord(ev1, s);
+    return cudaSuccess;
+}
+
+cudaError_t pairconv_run_merged(int n, const FFTTables<float>& tb, const std::vector<MergedSys<float>>& sys,
+                                const std::vector<int>& n_grids, const std::vector<int>& cap, GridRef* d_refs,
+                                MergedSys<float>* d_sys, cudaStream_t s, int* launches, int* rounds_out) {
+    const int nsys = (int)sys.size();
+    if (rounds_out) *rounds_out = 0;
+    if (!spec_merge_ok(n) || nsys == 0 || (int)n_grids.size() != nsys || (int)cap.size() != nsys)
+        return cudaErrorInvalidValue;
+    // rounds: the next chunk of every system with grids left
+    std::vector<GridRef> refs;
+    std::vector<MergedSys<float>> per_round;
+    std::vector<int> start;
+    std::vector<int> next(nsys, 0);
+    for (;;) {
+        const int r0 = (int)refs.size();
+        for (int q = 0; q < nsys; ++q) {
+            MergedSys<float> m = sys[q];
+            m.g0 = next[q];
+            const int k = std::min(std::max(cap[q], 1), n_grids[q] - next[q]);
+            for (int j = 0; j < k; ++j) refs.push_back(GridRef{q, next[q] + j});
+            next[q] += std::max(k, 0);
+            per_round.push_back(m);
+        }
+        if ((int)refs.size() == r0) {
+            per_round.resize(per_round.size() - nsys);
+            break;
+        }
+        start.push_back(r0);
+    }
+    start.push_back((int)refs.size());
+    const int rounds = (int)start.size() - 1;
+    if (rounds == 0) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(d_refs, refs.data(), sizeof(GridRef) * refs.size(), cudaMemcpyHostToDevice, s)))
+        return e;
+    if ((e = cudaMemcpyAsync(d_sys, per_round.data(), sizeof(MergedSys<float>) * per_round.size(),
+                             cudaMemcpyHostToDevice, s)))
+        return e;
+    ConvArgs<float> P;
+    for (int a = 0; a < 3; ++a) {
+        P.tw[a] = tb.tw[a];
+        P.g2[a] = tb.g2[a];
+    }
+    const size_t ng = (size_t)n * n * n;
+    P.kscale = (float)(4.0 * M_PI / (double)ng);
+    P.ktab = nullptr;
+    P.psi = nullptr;
+    P.W = nullptr;
+    P.grids = nullptr;
+    P.scratch = nullptr;
+    P.epart = nullptr;
+    P.n_occ = 0;
+    P.ng = ng;
+    P.dv = 0.0;
+    P.refs = d_refs;
+    int dev = 0, nsm = 0;
+    if ((e = cudaGetDevice(&dev)) || (e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev))) return e;
+    P.pf_ahead = 2 * nsm;
+    for (int r = 0; r < rounds; ++r) {
+        const int g0 = start[r], nb = start[r + 1] - start[r];
+        P.msys = d_sys + (size_t)r * nsys;
+        for (int pass = 0; pass < 3; ++pass) {
+            const bool ok = spec_launch_s(pass, n, nb, P, g0, s, false) || spec_launch_m(pass, n, nb, P, g0, s, false) ||
+                            spec_launch_l(pass, n, nb, P, g0, s, false);
+            if (!ok) return cudaErrorInvalidValue;
+        }
+        energy_collect_merged_kernel<<<(nb + 127) / 128, 128, 0, s>>>(d_refs, P.msys, g0, nb, n);
+        *launches += 4;
+        if ((e = cudaGetLastError())) return e;
+    }
+    if (rounds_out) *rounds_out = rounds;
     return cudaSuccess;
 }
 

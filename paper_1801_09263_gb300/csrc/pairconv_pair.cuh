@@ -25,8 +25,8 @@
 // and last stages, pass B's forward stage / K(G) product / inverse stage in
 // registers with its K slab staged by cp.async, plane-major launch order of
 // passes A and C, L2 prefetch one wave ahead, odd row pitch for line-fast z
-// stages.  Built where two paired planes fit in shared memory (n <= 80), run
-// by default where two paired CTAs share an SM (n <= 48; see enabled()).
+// stages.  Built where two paired planes fit in shared memory (n <= 80); off
+// by default (see enabled(): slower than the one-grid passes as measured).
 #pragma once
 
 #include <atomic>
@@ -607,19 +607,18 @@ bool launch_one(int pass, int nb, const ConvArgs<float>& P, int g0, cudaStream_t
     return true;
 }
 
-// Pairing halves the instructions a point but doubles the shared memory of a
-// CTA; where that leaves one CTA per SM, its barriers are no longer hidden
-// behind a second CTA and the passes are slower (72^3: 3.31 us per pair
-// paired at one CTA per SM, 2.70 unpaired at two).  So the paired passes run
-// by default only where two or more paired CTAs share an SM.
-// LACE_FFT_PAIRED=1 forces them wherever they fit, =0 turns them off.
+// Pairing halves the instructions a point but doubles the shared memory of
+// a CTA, so fewer CTAs share an SM and their barriers are less hidden.
+// Measured on GB300 against the one-grid passes (with packed real/imaginary
+// butterflies): 72^3 3.31 vs 2.63 us per pair (one paired CTA an SM), 48^3
+// 0.87 vs 0.78 (two).  So they are off unless LACE_FFT_PAIRED=1.
 template <int N>
 inline bool enabled() {
-    static const int mode = [] {
+    static const int on = [] {
         const char* e = getenv("LACE_FFT_PAIRED");
-        return e ? (e[0] == '1' ? 1 : 0) : 2;
+        return (e && e[0] == '1') ? 1 : 0;
     }();
-    return mode == 1 || (mode == 2 && blocks_at(N, threads_for(N)) >= 2);
+    return on != 0;
 }
 
 }  // namespace pair2
@@ -628,15 +627,18 @@ namespace spec {
 
 // Paired out-of-place passes where two paired planes fit in shared memory
 // (and the scratch holds an even number of grids), else the one-grid
-// out-of-place passes where two planes fit, else in place.
+// out-of-place passes where two planes fit, else in place.  A merged launch
+// (several systems, P.refs) takes the one-grid out-of-place passes or none.
 template <int N>
 bool launch_any(int pass, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s, bool allow_pair) {
     if constexpr (pair2::fits(N)) {
         if (allow_pair && pair2::enabled<N>()) return pair2::launch_one<N>(pass, nb, P, g0, s);
     }
     if constexpr (spec2::smem_max(N) <= 200 * 1024) {
-        if (spec2::enabled()) return spec2::launch_one<N>(pass, nb, P, g0, s);
+        // merged launches (P.refs) exist only in the one-grid out-of-place passes
+        if (spec2::enabled() || P.refs) return spec2::launch_one<N>(pass, nb, P, g0, s);
     }
+    if (P.refs) return false;
     return spec_launch_one<N>(pass, nb, P, g0, s);
 }
 

@@ -113,14 +113,17 @@ __host__ __device__ constexpr int max_regs(int n) { return regs_at(threads_for(n
 // from one stage to the next: hand-offs 0-2 are pass A's stages 1->2, 2->3,
 // 3->4, hand-offs 3-5 pass C's.  Chosen per size with a model of the 8-byte
 // accesses of every stage (a half-warp's 16 addresses on 16 8-byte bank
-// slots; a pitch that sends two of them to one slot costs a second wavefront):
-// bit h set = pitch n + 1 for hand-off h.
+// slots; a pitch that sends two of them to one slot costs a second
+// wavefront): bit h set = pitch n + 1 for hand-off h.  Pass C's z stages run
+// line-fast (consecutive threads on consecutive rows), so their rows need
+// the odd pitch; line-fast y stages (consecutive threads along a row) want
+// the plain one.
 __host__ __device__ constexpr int pad_mask(int n) {
     switch (n) {
-        case 32: case 40: case 48: case 64: case 80: case 96: return (1 << 0) | (1 << 5);
-        case 72: return 1 << 1;
+        case 24: case 36: case 60: return (1 << 4) | (1 << 5);
+        case 72: return (1 << 1) | (1 << 4) | (1 << 5);
         case 100: return (1 << 0) | (1 << 1) | (1 << 4) | (1 << 5);
-        default: return 0;  // 24, 36, 60: pitch n throughout
+        default: return (1 << 0) | (1 << 4) | (1 << 5);  // 32, 40, 48, 64, 80, 96
     }
 }
 __host__ __device__ constexpr int pitch(int n, int h) { return (pad_mask(n) >> h) & 1 ? n + 1 : n; }
@@ -139,6 +142,44 @@ __device__ __forceinline__ bool ahead_cta(int pf_ahead, int& fast, int& slow) {
     fast = (int)(lin % gridDim.x);
     slow = (int)(lin / gridDim.x);
     return true;
+}
+
+// The buffers of grid g of a launch: its own system's in a merged launch
+// (the request server), the launch's otherwise.
+struct GridView {
+    const float* psi;
+    float* W;
+    const float* ktab;
+    C* scr;      // this grid's complex scratch grid
+    double* ep;  // this grid's energy partials [n1][2]
+    PairGrid d;
+    int n_occ;
+    double dv;
+};
+__device__ __forceinline__ GridView grid_view(const ConvArgs<float>& P, int g0, int g, int n1) {
+    GridView v;
+    if (P.refs) {
+        const GridRef r = P.refs[g0 + g];
+        const MergedSys<float>& m = P.msys[r.sys];
+        v.psi = m.psi;
+        v.W = m.W;
+        v.ktab = m.ktab;
+        v.d = m.grids[r.g];
+        v.scr = m.scratch + (size_t)(r.g - m.g0) * P.ng;
+        v.ep = m.epart + (size_t)(r.g - m.g0) * n1 * 2;
+        v.n_occ = m.n_occ;
+        v.dv = m.dv;
+    } else {
+        v.psi = P.psi;
+        v.W = P.W;
+        v.ktab = P.ktab;
+        v.d = P.grids[g0 + g];
+        v.scr = P.scratch + (size_t)g * P.ng;
+        v.ep = P.epart + (size_t)g * n1 * 2;
+        v.n_occ = P.n_occ;
+        v.dv = P.dv;
+    }
+    return v;
 }
 
 // One radix-R Stockham stage over LINES lines of length N, out of place:
@@ -190,20 +231,22 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     C* b1 = b0 + N * LP;
     C* tw = b1 + N * LP;
     const int g = blockIdx.x, x = blockIdx.y;  // plane-major: the CTAs in flight share plane x
-    const PairGrid d = P.grids[g0 + g];
+    const GridView V = grid_view(P, g0, g, N);
+    const PairGrid d = V.d;
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = P.tw[2][i];
     const size_t off = (size_t)x * NP;
     const bool two = d.j2 >= 0;
-    const float* a1 = P.psi + (size_t)d.i1 * P.ng + off;
-    const float* c1 = P.psi + (size_t)d.j1 * P.ng + off;
-    const float* a2 = P.psi + (size_t)(two ? d.i2 : d.i1) * P.ng + off;
-    const float* c2 = P.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off;
+    const float* a1 = V.psi + (size_t)d.i1 * P.ng + off;
+    const float* c1 = V.psi + (size_t)d.j1 * P.ng + off;
+    const float* a2 = V.psi + (size_t)(two ? d.i2 : d.i1) * P.ng + off;
+    const float* c2 = V.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off;
     int xa = 0, ga = 0;
     const bool pf = threadIdx.x < 4 && ahead_cta(P.pf_ahead, ga, xa);
-    int pf_orb = -1;  // orbital plane of the CTA ahead that this thread prefetches
+    const float* pf_plane = nullptr;  // orbital plane of the CTA ahead that this thread prefetches
     if (pf) {
-        const int* dd = reinterpret_cast<const int*>(P.grids + g0 + ga);
-        pf_orb = __ldg(dd + threadIdx.x);  // i1, j1, i2, j2 (j2 < 0: one pair)
+        const GridView A = grid_view(P, g0, ga, N);
+        const int o = threadIdx.x == 0 ? A.d.i1 : threadIdx.x == 1 ? A.d.j1 : threadIdx.x == 2 ? A.d.i2 : A.d.j2;
+        if (o >= 0) pf_plane = A.psi + (size_t)o * P.ng + (size_t)xa * NP;  // (j2 < 0: one pair)
     }
     // z lines (line = y): rho straight from the orbitals
     stage<N, pl.r1, 1, -1, N, false, NT>(
@@ -223,10 +266,10 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     stage<N, pl.r1, 1, -1, N, true, NT>(
         tw, [&](int z, int y) { return b1[y * P12 + z]; }, [&](int z, int y, C v) { b0[y * P23 + z] = v; });
     __syncthreads();
-    C* out = P.scratch + (size_t)g * P.ng + off;
+    C* out = V.scr + off;
     stage<N, pl.r2, pl.r1, -1, N, true, NT>(
         tw, [&](int z, int y) { return b0[y * P23 + z]; }, [&](int z, int y, C v) { out[y * N + z] = v; });
-    if (pf && pf_orb >= 0) prefetch_l2(P.psi + (size_t)pf_orb * P.ng + (size_t)xa * NP, NP * sizeof(float));
+    if (pf_plane) prefetch_l2(pf_plane, NP * sizeof(float));
 }
 
 // Pass B: slab ky: forward x-FFT (decimation in time), * K(G)/Ng, inverse
@@ -246,13 +289,15 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     float* gx2 = reinterpret_cast<float*>(tw + N);
     float* gz2 = gx2 + N;
     const int g = blockIdx.y, ky = blockIdx.x;
-    const bool kstage = KS && P.ktab != nullptr;
+    const GridView V = grid_view(P, g0, g, N);
+    const float* ktab = V.ktab;
+    const bool kstage = KS && ktab != nullptr;
     if (kstage) {
         // asynchronous 16-byte copies, waited for before the middle
         const unsigned ks_s = (unsigned)__cvta_generic_to_shared(ks);
         for (int q = threadIdx.x; q < NP / 4; q += NT) {
             const int xx = q / (N / 4), z4 = q % (N / 4);
-            const float* src = P.ktab + ((size_t)xx * N + ky) * N + 4 * z4;
+            const float* src = ktab + ((size_t)xx * N + ky) * N + 4 * z4;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(ks_s + 16u * q), "l"(src) : "memory");
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
@@ -262,11 +307,11 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
         gx2[i] = P.g2[0][i];
         gz2[i] = P.g2[2][i];
     }
-    C* base = P.scratch + (size_t)g * P.ng + (size_t)ky * N;
+    C* base = V.scr + (size_t)ky * N;
     {
         int ka = 0, ga = 0;
         if (threadIdx.x < N && ahead_cta(P.pf_ahead, ka, ga))
-            prefetch_l2(P.scratch + (size_t)ga * P.ng + (size_t)threadIdx.x * NP + (size_t)ka * N, N * sizeof(C));
+            prefetch_l2(grid_view(P, g0, ga, N).scr + (size_t)threadIdx.x * NP + (size_t)ka * N, N * sizeof(C));
     }
     // forward stage 1 (line = z): DFT_RB over n2 of x[n1 + RA n2], to y[n1 RB + k2]
     stage<N, RB, 1, -1, N, true, NT>(
@@ -296,8 +341,8 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
                 float k;
                 if (kstage) {
                     k = ks[xx * N + z];
-                } else if (P.ktab) {
-                    k = __ldg(P.ktab + ((size_t)xx * N + ky) * N + z);
+                } else if (ktab) {
+                    k = __ldg(ktab + ((size_t)xx * N + ky) * N + z);
                 } else {
                     const float gg = gx2[xx] + gy2 + gz2[z];
                     k = gg > 0.f ? P.kscale / gg : 0.f;
@@ -347,14 +392,15 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     C* tw = b1 + N * LP;
     __shared__ double red[2][(NT + 31) / 32];
     const int g = blockIdx.x, x = blockIdx.y;  // plane-major: the CTAs in flight share plane x
-    const PairGrid d = P.grids[g0 + g];
+    const GridView V = grid_view(P, g0, g, N);
+    const PairGrid d = V.d;
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = P.tw[2][i];
     const size_t off = (size_t)x * NP;
-    const C* in = P.scratch + (size_t)g * P.ng + off;
+    const C* in = V.scr + off;
     {
         int xa = 0, ga = 0;
         if (threadIdx.x == 32 && ahead_cta(P.pf_ahead, ga, xa))
-            prefetch_l2(P.scratch + (size_t)ga * P.ng + (size_t)xa * NP, NP * sizeof(C));
+            prefetch_l2(grid_view(P, g0, ga, N).scr + (size_t)xa * NP, NP * sizeof(C));
     }
     stage<N, pl.r1, 1, +1, N, true, NT>(
         tw, [&](int z, int y) { return in[y * N + z]; }, [&](int z, int y, C v) { b0[y * P01 + z] = v; });
@@ -364,7 +410,7 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
         const int q = threadIdx.x & 3;
         const int o = q == 0 ? d.i1 : q == 1 ? d.j1 : q == 2 ? d.i2 : d.j2;
         if (o >= 0) {
-            const float* src = (threadIdx.x < 4 ? P.psi : P.W) + (size_t)o * P.ng + off;
+            const float* src = (threadIdx.x < 4 ? V.psi : V.W) + (size_t)o * P.ng + off;
             prefetch_l2(src, NP * sizeof(float));
         }
     }
@@ -380,16 +426,16 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
         tw, [&](int y, int z) { return b0[y * P23 + z]; }, [&](int y, int z, C v) { b1[y * N + z] = v; });
     __syncthreads();
     const bool two = d.j2 >= 0;
-    const bool a_occ = d.j1 < P.n_occ, a_sym = a_occ && d.j1 != d.i1;
-    const bool b_occ = two && d.j2 < P.n_occ, b_sym = b_occ && d.j2 != d.i2;
-    const float4* wi1 = reinterpret_cast<const float4*>(P.psi + (size_t)d.i1 * P.ng + off);
-    const float4* pj1 = reinterpret_cast<const float4*>(P.psi + (size_t)d.j1 * P.ng + off);
-    float4* Wj1 = reinterpret_cast<float4*>(P.W + (size_t)d.j1 * P.ng + off);
-    float4* Wi1 = reinterpret_cast<float4*>(P.W + (size_t)d.i1 * P.ng + off);
-    const float4* wi2 = reinterpret_cast<const float4*>(P.psi + (size_t)(two ? d.i2 : d.i1) * P.ng + off);
-    const float4* pj2 = reinterpret_cast<const float4*>(P.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off);
-    float4* Wj2 = reinterpret_cast<float4*>(P.W + (size_t)(two ? d.j2 : d.j1) * P.ng + off);
-    float4* Wi2 = reinterpret_cast<float4*>(P.W + (size_t)(two ? d.i2 : d.i1) * P.ng + off);
+    const bool a_occ = d.j1 < V.n_occ, a_sym = a_occ && d.j1 != d.i1;
+    const bool b_occ = two && d.j2 < V.n_occ, b_sym = b_occ && d.j2 != d.i2;
+    const float4* wi1 = reinterpret_cast<const float4*>(V.psi + (size_t)d.i1 * P.ng + off);
+    const float4* pj1 = reinterpret_cast<const float4*>(V.psi + (size_t)d.j1 * P.ng + off);
+    float4* Wj1 = reinterpret_cast<float4*>(V.W + (size_t)d.j1 * P.ng + off);
+    float4* Wi1 = reinterpret_cast<float4*>(V.W + (size_t)d.i1 * P.ng + off);
+    const float4* wi2 = reinterpret_cast<const float4*>(V.psi + (size_t)(two ? d.i2 : d.i1) * P.ng + off);
+    const float4* pj2 = reinterpret_cast<const float4*>(V.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off);
+    float4* Wj2 = reinterpret_cast<float4*>(V.W + (size_t)(two ? d.j2 : d.j1) * P.ng + off);
+    float4* Wi2 = reinterpret_cast<float4*>(V.W + (size_t)(two ? d.i2 : d.i1) * P.ng + off);
     const bool merge_i = two && a_sym && b_sym && d.i1 == d.i2;
     const float4* pl4 = reinterpret_cast<const float4*>(b1);
     float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
@@ -435,9 +481,9 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     if (threadIdx.x == 0) {
         double ta = 0.0, tbb = 0.0;
         for (int w = 0; w < (NT + 31) / 32; ++w) { ta += red[0][w]; tbb += red[1][w]; }
-        double* ep = P.epart + ((size_t)g * N + x) * 2;
-        ep[0] = ta * P.dv;
-        ep[1] = tbb * P.dv;
+        double* ep = V.ep + (size_t)x * 2;
+        ep[0] = ta * V.dv;
+        ep[1] = tbb * V.dv;
     }
 }
 

@@ -14,4 +14,23 @@ bool spec_launch_s(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cu
     }
 }
 
+// Sizes whose one-grid out-of-place passes exist (they take merged launches).
+bool spec_merge_ok(int n) {
+    switch (n) {
+        case 24: return spec2::smem_max(24) <= 200 * 1024;
+        case 32: return spec2::smem_max(32) <= 200 * 1024;
+        case 36: return spec2::smem_max(36) <= 200 * 1024;
+        case 40: return spec2::smem_max(40) <= 200 * 1024;
+        case 48: return spec2::smem_max(48) <= 200 * 1024;
+        case 60: return spec2::smem_max(60) <= 200 * 1024;
+        case 64: return spec2::smem_max(64) <= 200 * 1024;
+        case 72: return spec2::smem_max(72) <= 200 * 1024;
+        case 80: return spec2::smem_max(80) <= 200 * 1024;
+        case 96: return spec2::smem_max(96) <= 200 * 1024;
+        case 100: return spec2::smem_max(100) <= 200 * 1024;
+        case 128: return spec2::smem_max(128) <= 200 * 1024;
+        default: return false;
+    }
+}
+
 }  // namespace lace

@@ -503,12 +503,14 @@ __global__ void gather_columns_kernel(const T* __restrict__ psi, size_t ldpsi, i
 // columns of a CTA that do not fit in registers live in shared memory with a
 // padded row pitch (16-byte accesses free of bank conflicts).  The row work
 // runs on packed FP32 pairs.  Per step each warp publishes its best column
-// (values and FP64 partial sums of squares) to global memory; the CTAs
-// then agree on the global winner through one 64-bit atomicMax per CTA
-// (key = norm bits above the complemented column index: the largest norm,
-// then the lowest index) and a grid barrier on a monotone arrival counter;
-// every CTA reads the winner's published column and forms q in FP64 scale.
-constexpr int QR2_THREADS = 256, QR2_WARPS = QR2_THREADS / 32;
+// to global memory; the CTAs then agree on the global winner through one
+// 64-bit atomicMax per CTA (key = the FP32 squared norm's bits above the
+// complemented column index: the largest norm, then the lowest index) and a
+// grid barrier on a monotone arrival counter; every CTA reads the winner's
+// published column and scales it by the inverse norm taken from the key
+// (no FP64 sums on the step's critical path: FP64 runs at a small fraction
+// of the FP32 rate on this GPU).
+constexpr int QR2_THREADS = 512, QR2_WARPS = QR2_THREADS / 32;
 
 __device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) {
     unsigned long long v;
@@ -569,7 +571,7 @@ __device__ __forceinline__ float qnorm(const float* v) {
 template <int RPL>
 __device__ __forceinline__ float sdot(const float* __restrict__ qs, const float* w) {
     f2 a0 = bc2(0.f), a1 = bc2(0.f);
-#pragma unroll 8
+#pragma unroll 4
     for (int j = 0; j < RPL; j += 4) {
         const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
         const float4 x = *reinterpret_cast<const float4*>(w + j);
@@ -584,7 +586,7 @@ template <int RPL>
 __device__ __forceinline__ float supdate(const float* __restrict__ qs, float* w, float d, bool store) {
     const f2 nd = bc2(-d);
     f2 n0 = bc2(0.f), n1 = bc2(0.f);
-#pragma unroll 8
+#pragma unroll 4
     for (int j = 0; j < RPL; j += 4) {
         const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
         const float4 x = *reinterpret_cast<const float4*>(w + j);
@@ -606,7 +608,7 @@ __device__ __forceinline__ float supdate(const float* __restrict__ qs, float* w,
 template <int RPL>
 __device__ __forceinline__ float snorm(const float* w) {
     f2 n0 = bc2(0.f), n1 = bc2(0.f);
-#pragma unroll 8
+#pragma unroll 4
     for (int j = 0; j < RPL; j += 4) {
         const float4 x = *reinterpret_cast<const float4*>(w + j);
         const f2 u0 = mk2(x.x, x.y), u1 = mk2(x.z, x.w);
@@ -630,21 +632,23 @@ __device__ __forceinline__ unsigned long long col_key(float nrm, int col) {
     return ((unsigned long long)__float_as_uint(nrm) << 32) | (unsigned long long)(0xffffffffu - (unsigned)col);
 }
 
-// The columns of CTA b are [b cpb, (b + 1) cpb): the first G = 256 / LPC in
+// The columns of CTA b are [b cpb, (b + 1) cpb): the first G = 512 / LPC in
 // registers (group g = thread / LPC), the rest (s = 0, 1, ...) in shared
 // memory, handled by group s % G.  Rows: lane l of a group holds rows
-// [l RPL, (l + 1) RPL).  keys[npiv] and bar[0] are zero at launch.
+// [l RPL, (l + 1) RPL); q is kept as LPC row chunks of RPL + 4 floats, so
+// the LPC distinct chunks a warp reads at once fall on different banks.
+// keys[npiv] and bar[0] are zero at launch.
 template <int RPL, int LPC>
 __global__ void __launch_bounds__(QR2_THREADS, 1)
     qr_resident_kernel(int nrow, int ncol, const float* __restrict__ R, int npiv, int cpb, float* __restrict__ pub,
-                       double* __restrict__ pubn, unsigned long long* __restrict__ keys, int* __restrict__ piv,
-                       unsigned* bar, unsigned long long limit_ns) {
+                       unsigned long long* __restrict__ keys, int* __restrict__ piv, unsigned* bar,
+                       unsigned long long limit_ns) {
     constexpr int G = QR2_THREADS / LPC;
     constexpr int NPAD = RPL * LPC;     // padded rows
     constexpr int PITCH = RPL + 4;      // shared-memory row-chunk pitch (floats)
     extern __shared__ __align__(16) float qr2_smem[];
-    float* qs = qr2_smem;                // [NPAD] q of the current step
-    float* sc = qr2_smem + NPAD;         // [SC][LPC][PITCH] shared-memory columns
+    float* qs = qr2_smem;                // [LPC][PITCH] q of the current step
+    float* sc = qr2_smem + LPC * PITCH;  // [SC][LPC][PITCH] shared-memory columns
     __shared__ unsigned long long wkey[QR2_WARPS];
     __shared__ int abort_sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -672,10 +676,10 @@ __global__ void __launch_bounds__(QR2_THREADS, 1)
             }
         }
     }
-    for (int j = tid; j < NPAD; j += QR2_THREADS) qs[j] = 0.f;
+    for (int j = tid; j < LPC * PITCH; j += QR2_THREADS) qs[j] = 0.f;
     __syncthreads();
     for (int step = 0; step < npiv; ++step) {
-        const float* qrow = qs + l * RPL;
+        const float* qrow = qs + l * PITCH;
         unsigned long long best = 0ull;
         // register column
         {
@@ -718,51 +722,48 @@ __global__ void __launch_bounds__(QR2_THREADS, 1)
             const size_t slot = ((size_t)(step & 1) * gridDim.x + blockIdx.x) * QR2_WARPS + warp;
             float* out = pub + slot * NPAD + l * RPL;
             if (wcol == myreg) {
-                double sq = 0.0;
 #pragma unroll
-                for (int j = 0; j < RPL; j += 4) {
+                for (int j = 0; j < RPL; j += 4)
                     *reinterpret_cast<float4*>(out + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-                    sq += (double)v[j] * v[j] + (double)v[j + 1] * v[j + 1] + (double)v[j + 2] * v[j + 2] +
-                          (double)v[j + 3] * v[j + 3];
-                }
-                pubn[slot * LPC + l] = sq;
             } else {
                 const int s = wcol - c0 - G;
                 if (s >= 0 && s < SC && s % G == g) {
                     const float* w = sc + ((size_t)s * LPC + l) * PITCH;
-                    double sq = 0.0;
-                    for (int j = 0; j < RPL; j += 4) {
-                        const float4 x = *reinterpret_cast<const float4*>(w + j);
-                        *reinterpret_cast<float4*>(out + j) = x;
-                        sq += (double)x.x * x.x + (double)x.y * x.y + (double)x.z * x.z + (double)x.w * x.w;
-                    }
-                    pubn[slot * LPC + l] = sq;
+                    for (int j = 0; j < RPL; j += 4)
+                        *reinterpret_cast<float4*>(out + j) = *reinterpret_cast<const float4*>(w + j);
                 }
             }
         }
         if (lane == 0) wkey[warp] = wb;
-        // grid barrier: arrive with this CTA's best key, wait for every CTA
+        // grid barrier: arrive with this CTA's best key, wait for every CTA.
+        // The key goes in first (a relaxed reduction, ordered before the
+        // arrival by its release); waiting CTAs poll with relaxed loads and
+        // a short back-off, then take one acquire fence.
         __syncthreads();
         if (tid == 0) {
             unsigned long long kb = 0ull;
 #pragma unroll
             for (int w = 0; w < QR2_WARPS; ++w) kb = wkey[w] > kb ? wkey[w] : kb;
-            __threadfence();
-            if (kb) atomicMax(keys + step, kb);
+            if (kb) asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(keys + step), "l"(kb) : "memory");
             const unsigned target = (unsigned)(step + 1) * gridDim.x;
             unsigned cnt;
             asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(cnt) : "l"(bar) : "memory");
             int timed_out = 0;
             if (cnt + 1 < target) {
                 const unsigned long long t0 = global_ns();
-                while (ld_acquire_u32(bar) < target) {
+                for (;;) {
+                    unsigned v;
+                    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+                    if (v >= target) break;
                     if (global_ns() - t0 > limit_ns) {
                         atomicExch(bar + 2, 1u);
                         timed_out = 1;
                         break;
                     }
+                    __nanosleep(40);
                 }
             }
+            asm volatile("fence.acq_rel.gpu;" ::: "memory");
             abort_sh = timed_out;
         }
         __syncthreads();
@@ -776,11 +777,12 @@ __global__ void __launch_bounds__(QR2_THREADS, 1)
         const int wcta = p / cpb, li = p - wcta * cpb;
         const int wg = li < G ? li : (li - G) % G;
         const size_t slot = ((size_t)(step & 1) * gridDim.x + wcta) * QR2_WARPS + (wg * LPC) / 32;
-        double nn = 0.0;
-#pragma unroll
-        for (int k = 0; k < LPC; ++k) nn += __ldcg(pubn + slot * LPC + k);
+        // the winner's squared norm is the key's upper half (the FP32 value the
+        // argmax compared)
+        const double nn = (double)__uint_as_float((unsigned)(key >> 32));
         const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
-        for (int j = tid; j < NPAD; j += QR2_THREADS) qs[j] = (float)((double)__ldcg(pub + slot * NPAD + j) * inv);
+        for (int j = tid; j < NPAD; j += QR2_THREADS)
+            qs[(j / RPL) * PITCH + j % RPL] = (float)((double)__ldcg(pub + slot * NPAD + j) * inv);
         if (wcta == (int)blockIdx.x && wg == g) {
             if (li < G) chosen |= 1u;
             else chosen |= 1u << (1 + (li - G) / G);
@@ -799,19 +801,18 @@ static int nblocks_cap(int ncol) { return std::max((ncol + QR_THREADS - 1) / QR_
 
 // Row layout of the register-resident QR: RPL rows per lane, LPC lanes per column.
 static void qr2_layout(int nrow, int* rpl, int* lpc) {
-    *rpl = nrow <= 32 ? 32 : nrow <= 64 ? 64 : 128;
-    *lpc = nrow <= 128 ? 1 : nrow <= 256 ? 2 : nrow <= 512 ? 4 : 8;
+    *rpl = nrow <= 32 ? 32 : 64;
+    *lpc = nrow <= 64 ? 1 : (nrow + 63) / 64 <= 2 ? 2 : (nrow + 63) / 64 <= 4 ? 4 : (nrow + 63) / 64 <= 8 ? 8 : 16;
 }
 
 // Published candidate columns: of the persistent kernel, 2 (step parity) x
 // CTAs (up to 304) x padded rows (< 2 nrow + 64), FP64 at most; of the
-// register-resident kernel, 2 x CTAs x 8 warps x padded rows (FP32) plus
-// their FP64 partial norms.
+// register-resident kernel, 2 x CTAs x 16 warps x padded rows (FP32).
 static size_t pub_bytes(int nrow) {
     int rpl = 0, lpc = 0;
     qr2_layout(nrow, &rpl, &lpc);
     const size_t old = (size_t)2 * 304 * (2 * (size_t)nrow + 64) * sizeof(double);
-    const size_t res = align256((size_t)2 * 304 * 8 * rpl * lpc * sizeof(float)) + (size_t)2 * 304 * 8 * lpc * sizeof(double);
+    const size_t res = align256((size_t)2 * 304 * 16 * rpl * lpc * sizeof(float)) + (size_t)2 * 304 * 16 * lpc * sizeof(double);
     return align256(std::max(old, res));
 }
 
@@ -898,7 +899,7 @@ static cudaError_t qr_resident_launch(int nrow, int ncol, const float* R, int np
     cudaFuncAttributes fa{};
     cudaError_t e;
     if ((e = cudaFuncGetAttributes(&fa, fn))) return e;
-    const size_t dyn = ((size_t)NPAD + (size_t)sc * LPC * PITCH) * sizeof(float);
+    const size_t dyn = ((size_t)LPC * PITCH + (size_t)sc * LPC * PITCH) * sizeof(float);
     if (dyn + fa.sharedSizeBytes + 1024 > (size_t)optin) return cudaSuccess;
     // one limit for every caller of this kernel: the opt-in maximum
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes)))
@@ -906,13 +907,11 @@ static cudaError_t qr_resident_launch(int nrow, int ncol, const float* R, int np
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, QR2_THREADS, dyn))) return e;
     if (per_sm < 1 || ctas > per_sm * sms) return cudaSuccess;
-    double* pubn = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(pub) +
-                                             align256((size_t)2 * ctas * QR2_WARPS * NPAD * sizeof(float)));
     if ((e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s))) return e;
     if ((e = cudaMemsetAsync(keys, 0, (size_t)npiv * sizeof(unsigned long long), s))) return e;
     int cpb_arg = cpb;
-    void* args[] = {(void*)&nrow, (void*)&ncol, (void*)&R,     (void*)&npiv, (void*)&cpb_arg, (void*)&pub,
-                    (void*)&pubn, (void*)&keys, (void*)&d_piv, (void*)&bar, (void*)&limit_ns};
+    void* args[] = {(void*)&nrow, (void*)&ncol, (void*)&R,     (void*)&npiv,     (void*)&cpb_arg,
+                    (void*)&pub,  (void*)&keys, (void*)&d_piv, (void*)&bar, (void*)&limit_ns};
     if ((e = cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(QR2_THREADS), args, dyn, s))) return e;
     *launches += 1;
     *ran = true;
@@ -958,11 +957,11 @@ cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* au
                 return launch(nrow, ncol, R, npiv, keys, pub, d_piv, bar, wait_limit_ns, s, launches, &ran);
             };
             if (rpl == 32) e = go(qr_resident_launch<32, 1>);
-            else if (rpl == 64) e = go(qr_resident_launch<64, 1>);
-            else if (lpc == 1) e = go(qr_resident_launch<128, 1>);
-            else if (lpc == 2) e = go(qr_resident_launch<128, 2>);
-            else if (lpc == 4) e = go(qr_resident_launch<128, 4>);
-            else e = go(qr_resident_launch<128, 8>);
+            else if (lpc == 1) e = go(qr_resident_launch<64, 1>);
+            else if (lpc == 2) e = go(qr_resident_launch<64, 2>);
+            else if (lpc == 4) e = go(qr_resident_launch<64, 4>);
+            else if (lpc == 8) e = go(qr_resident_launch<64, 8>);
+            else e = go(qr_resident_launch<64, 16>);
         }
         if (!e && !ran) {
             if (nrow <= 512)

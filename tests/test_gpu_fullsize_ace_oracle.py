@@ -104,8 +104,19 @@ def test_exchange_energy_and_w_match_the_oracle(both):
     assert abs(gpu["ex"] - ref["ex"]) <= 1e-5, (gpu["ex"], ref["ex"])
     if len(gpu["pairs"]) == ref["gold"]["n_pairs"]:  # same kept set as the stored oracle run
         assert abs(ref["ex"] - ref["gold"]["E_x_Ha"]) <= 1e-9
+    # W_j sums the potentials of the k_j pairs kept with target j in FP32 (every
+    # one of the 256 occupied orbitals for an extra target, Sec. 4.1; about 7
+    # for an occupied one); rounding errors of independent terms grow like
+    # sqrt(k_j): 2e-5 of max|W_j| (the mixed-precision bound of the parity
+    # tests, up to 8 terms) times sqrt(k_j / 8)
+    keep = np.zeros((256, gpu["W"].shape[0]), dtype=bool)
+    for i, j in gpu["pairs"]:
+        keep[i, j] = True
+        if j < 256:
+            keep[j, i] = True
     for j in range(gpu["W"].shape[0]):
-        assert relerr(gpu["W"][j], ref["W"][j]) <= 2e-5, j
+        tol = 2e-5 * max(1.0, np.sqrt(keep[:, j].sum() / 8.0))
+        assert relerr(gpu["W"][j], ref["W"][j]) <= tol, (j, tol)
 
 
 def test_ace_matrix_and_cholesky_factor_match_the_oracle(both):

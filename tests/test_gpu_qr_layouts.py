@@ -1,14 +1,14 @@
 """SCDM pivoted QR (Sec. 2) on every row layout of the persistent FP32 kernel.
 
-The mixed-precision QR keeps the subsample matrix on chip: 1, 2, 4 or 8
-lanes per column hold 32, 64 or 128 rows each in registers, and the columns a
-CTA cannot hold in registers sit in shared memory.  Each case below picks a
-grid and orbital count that lands on one layout (with and without shared-memory
-columns) and checks the pivots against the FP64 oracle: replaying the
-oracle's exact Gram-Schmidt steps with the GPU's pivot order, every choice
-must be within 1e-4 of the largest residual norm (the FP32 kernel's rounding;
-a valid Businger-Golub order has every ratio 1), and a second run must pick
-the same pivots.
+The mixed-precision QR keeps the subsample matrix on chip: 1 to 16 lanes per
+column hold 32 or 64 rows each in registers (512 threads a CTA), and the
+columns a CTA cannot hold in registers sit in shared memory.  Each case below
+picks a grid and orbital count that lands on one layout (with and without
+shared-memory columns) and checks the pivots against the FP64 oracle:
+replaying the oracle's exact Gram-Schmidt steps with the GPU's pivot order,
+every choice must be within 1e-4 of the largest residual norm (the FP32
+kernel's rounding; a valid Businger-Golub order has every ratio 1), and a
+second run must pick the same pivots.
 """
 import numpy as np
 import pytest
@@ -21,12 +21,12 @@ pytestmark = pytest.mark.gpu
 
 CASES = [  # (grid n, cell L, ecut, centres, orbitals): rows per lane x lanes per column, columns in shared memory
     (48, 16.0, 20.0, 20, 24),     # 32 x 1, registers only
-    (72, 23.5, 30.0, 20, 24),     # 32 x 1, 46,656 columns: shared memory too
-    (64, 20.0, 30.0, 48, 60),     # 64 x 1
-    (72, 23.5, 30.0, 80, 100),    # 128 x 1, shared memory too
-    (48, 16.0, 20.0, 100, 140),   # 128 x 2, registers only
-    (64, 20.0, 30.0, 120, 160),   # 128 x 2, shared memory too
-    (48, 16.0, 20.0, 200, 300),   # 128 x 4, shared memory too
+    (96, 28.0, 30.0, 20, 24),     # 32 x 1, 110,592 columns: shared memory too
+    (64, 20.0, 30.0, 48, 60),     # 64 x 1, registers only
+    (72, 23.5, 30.0, 80, 100),    # 64 x 2, shared memory too
+    (48, 16.0, 20.0, 100, 140),   # 64 x 4, registers only
+    (64, 20.0, 30.0, 120, 160),   # 64 x 4, shared memory too
+    (48, 16.0, 20.0, 200, 300),   # 64 x 8, shared memory too
 ]
 
 

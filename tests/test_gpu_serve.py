@@ -139,3 +139,54 @@ def test_bad_requests():
         assert srv.poll(rid)["status"] == 2  # no ACE built yet
         with pytest.raises(Exception):
             srv.submit_apply(sid + 7, np.zeros((1, 24, 24, 24)))
+
+
+MERGE_SYSTEMS = [  # three systems on the 48^3 grid: different cells, band sizes and thresholds
+    ((14.0, 14.0, 14.0), 12.0, 16, 24, 8, 1e-3),
+    ((13.0, 13.0, 13.0), 11.0, 12, 20, 0, 1e-3),
+    ((15.0, 15.0, 15.0), 12.0, 20, 28, 4, 0.0),
+]
+
+
+def test_rebuilds_on_one_grid_size_share_pass_launches():
+    """The pair convolutions of REBUILDs of three systems on the 48^3 grid
+    run in shared launches of the FFT passes (spec serving pattern:
+    pair convolutions batched across requests), and every result is the same
+    as the system's REBUILD alone: E_x to 1e-9 Ha (the pair energies are
+    summed in a fixed order per grid), K_ACE on probes to 1e-5 relative (W
+    is accumulated with atomics, whose order varies)."""
+    inp = []
+    for k, (cell, ecut, nc, no, ne, thr) in enumerate(MERGE_SYSTEMS):
+        s = synth.small_localized_system(400 + k, cell, (48, 48, 48), ecut, nc, no, ne)
+        probe = np.random.default_rng(500 + k).standard_normal((2, 48, 48, 48))
+        inp.append((s, thr, probe))
+    alone = []
+    for s, thr, probe in inp:
+        with Server(0, LACE_MIXED, slots=1) as srv:
+            sid = srv.add_system(s.cell, s.shape, s.ecut, s.n_occ, s.n_extra, thr)
+            r = _collect(srv, [srv.submit_rebuild(sid, s.phi), srv.submit_apply(sid, probe)])
+            assert srv.merge_stats()["merged_batches"] == 0
+            alone.append(r)
+    with Server(0, LACE_MIXED, slots=3, rebuild_slots=3) as srv:
+        srv.set_pair_merging(True, 2000.0)  # generous: the three must meet at the exchange step
+        sids = [srv.add_system(s.cell, s.shape, s.ecut, s.n_occ, s.n_extra, thr) for s, thr, _ in inp]
+        rb = [srv.submit_rebuild(sid, s.phi) for sid, (s, _, _) in zip(sids, inp)]
+        res_rb = _collect(srv, rb)
+        res_ap = _collect(srv, [srv.submit_apply(sid, probe) for sid, (_, _, probe) in zip(sids, inp)])
+        st = srv.merge_stats()
+    assert st["merged_batches"] >= 1 and st["merged_requests"] == 3, st
+    for (a_rb, a_ap), m_rb, m_ap in zip(alone, res_rb, res_ap):
+        assert m_rb["n_pairs"] == a_rb["n_pairs"]
+        assert abs(m_rb["ex"] - a_rb["ex"]) <= 1e-9, (m_rb["ex"], a_rb["ex"])
+        assert relerr(m_ap["out"], a_ap["out"]) <= 1e-5
+
+
+def test_merging_can_be_turned_off():
+    s = synth.small_localized_system(410, (14.0, 14.0, 14.0), (48, 48, 48), 12.0, 16, 24, 0)
+    with Server(0, LACE_MIXED, slots=2, rebuild_slots=2) as srv:
+        srv.set_pair_merging(False, 0.0)
+        a = srv.add_system(s.cell, s.shape, s.ecut, s.n_occ, 0, 1e-3)
+        b = srv.add_system(s.cell, s.shape, s.ecut, s.n_occ, 0, 1e-3)
+        r = _collect(srv, [srv.submit_rebuild(a, s.phi), srv.submit_rebuild(b, s.phi)])
+        assert srv.merge_stats() == dict(batches=0, merged_batches=0, merged_requests=0)
+        assert abs(r[0]["ex"] - r[1]["ex"]) <= 1e-9
