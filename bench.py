@@ -438,24 +438,31 @@ def run_reference(args, rank, world):
 
 
 SERVE_RATE = 200.0        # offered requests per second over all systems
-SERVE_APPLIES = 4         # inner-loop K_ACE applications per ACE rebuild
+SERVE_MAX_INNER = 8       # inner-loop K_ACE applications per ACE rebuild at most
 SERVE_BLOCK = 32          # functions per application (a block of trial vectors)
 SERVE_EPS = 1e-3          # SCF-like drift of the orbitals between rebuilds
+SERVE_INNER_DECAY = 0.3   # the inner loop's block moves by SERVE_EPS x decay^k at its k-th step
+SERVE_CADENCE_TOL = 1e-5  # rebuild once the block's ACE energy moves by less than this (relative)
 
 
 def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp64=False):
     """The serving stream: resident systems (N log-uniform in [32, 512],
-    2/3/5-smooth cubic grids in [48, 128]), each an SCF-like client whose
-    requests are REBUILD (orthonormalise, SCDM, screen, pair convolutions,
-    ACE build) then SERVE_APPLIES x APPLY (K_ACE on a block of SERVE_BLOCK
-    orbitals), for `iters` outer iterations with the orbitals drifting by
-    SERVE_EPS between rebuilds.  Request k of a system arrives at its Poisson
-    time (rate SERVE_RATE / n_systems per system, seeded) and is submitted at
-    max(arrival, completion of request k-1): a client sends its next request
-    only after the previous result.  Latency = submission to completion (the
-    server's), response = arrival to completion.  Mixed precision (or plain
-    FP64 with fp64=True); memory admission with the default budget (90% of
-    free device memory)."""
+    2/3/5-smooth cubic grids in [48, 128]), each an SCF-like client running
+    the double loop of the paper (Sec. 2): an outer iteration is a REBUILD
+    (orthonormalise, SCDM, screen, pair convolutions, ACE build); its inner
+    loop applies that ACE projector (APPLY: K_ACE on a block of SERVE_BLOCK
+    functions) to a block that moves by SERVE_EPS x SERVE_INNER_DECAY^k at
+    step k, until the server reports the block's ACE energy converged
+    (relative change below SERVE_CADENCE_TOL; at most SERVE_MAX_INNER
+    applies); then the orbitals drift by SERVE_EPS and the next REBUILD
+    follows, for `iters` outer iterations.  Request k of a system arrives at
+    its Poisson time (rate SERVE_RATE / n_systems per system, seeded) and is
+    submitted at max(arrival, completion of request k-1): a client sends its
+    next request only after the previous result.  Latency = submission to
+    completion (the server's), response = arrival to completion.  Mixed
+    precision (or plain FP64 with fp64=True); memory admission with the
+    default budget (90% of free device memory); REBUILDs on one grid size
+    share pass launches (merged pair convolutions)."""
     import synth
     import torch
 
@@ -464,43 +471,50 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
     torch.cuda.set_device(local)
     systems = synth.serving_systems(n_systems=n_systems)
     t0 = time.perf_counter()
-    # the client's orbitals and results live in pinned host memory
-    phis, outs = [], []
+    # the client's orbitals, inner-loop blocks and results live in pinned host memory
+    phis, blocks, outs = [], [], []
     for s in systems:
         nb = min(SERVE_BLOCK, s.n_occ)
         phis.append(synth.serving_orbitals(
             s, torch.empty((s.n_occ,) + s.shape, dtype=torch.float64, pin_memory=True).numpy()))
+        blocks.append(torch.empty((nb,) + s.shape, dtype=torch.float64, pin_memory=True).numpy())
         outs.append(torch.empty((nb,) + s.shape, dtype=torch.float64, pin_memory=True).numpy())
     gen_s = time.perf_counter() - t0
     rng = np.random.default_rng(1801 + 4 + 1000)
-    per = SERVE_APPLIES + 1
-    nreq = iters * per
-    gaps = rng.exponential(n_systems / SERVE_RATE, size=(n_systems, nreq))
+    nreq_max = iters * (SERVE_MAX_INNER + 1)
+    gaps = rng.exponential(n_systems / SERVE_RATE, size=(n_systems, nreq_max))
     arrivals = np.cumsum(gaps, axis=1)
     srv = lace.Server(local, lace.LACE_FP64 if fp64 else lace.LACE_MIXED, slots=slots, rebuild_slots=rebuild_slots)
     sids = [srv.add_system(s.cell, s.shape, s.ecut, s.n_occ, 0, S_THR) for s in systems]
-    step = [0] * n_systems
+    for sid in sids:
+        srv.set_rebuild_tolerance(sid, SERVE_CADENCE_TOL)
+    step = [0] * n_systems        # requests sent
+    outer = [0] * n_systems       # REBUILDs sent
+    inner = [0] * n_systems       # APPLYs sent since the last REBUILD
+    next_kind = ["rebuild"] * n_systems
     outstanding = [None] * n_systems
-    submitted = [0.0] * n_systems
     lat = {"rebuild": [], "apply": []}
     resp = []
     pairs = 0
     ex_last = [None] * n_systems
+    inner_counts, due_count = [], 0
     peak_running, peak_bytes = 0, 0
     fails = []
-    launches = 0
     t_start = time.perf_counter()
     done_all = 0
+    finished = [False] * n_systems
     while done_all < n_systems:
         now = time.perf_counter() - t_start
         for k in range(n_systems):
-            rid = outstanding[k]
-            if rid is not None:
+            if finished[k]:
+                continue
+            cur = outstanding[k]
+            if cur is not None:
+                rid, kind = cur
                 r = srv.poll(rid, wait=False)
                 if r is None:
                     continue
                 outstanding[k] = None
-                kind = "rebuild" if (step[k] - 1) % per == 0 else "apply"
                 if r["status"] != 0:
                     fails.append({"system": k, "kind": kind, "status": r["status"], "error": r["error"]})
                 lat[kind].append(r["latency_ms"])
@@ -508,17 +522,32 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
                 if kind == "rebuild":
                     pairs += r["n_pairs"]
                     ex_last[k] = r["ex"] if r["status"] == 0 else None
-                if step[k] == nreq:
-                    done_all += 1
-            if outstanding[k] is None and step[k] < nreq and now >= arrivals[k][step[k]]:
-                j = step[k]
-                if j % per == 0:
-                    if j > 0:
-                        synth.perturb_in_place(phis[k], SERVE_EPS)
-                    outstanding[k] = srv.submit_rebuild(sids[k], phis[k])
+                    next_kind[k] = "apply"
                 else:
-                    outstanding[k] = srv.submit_apply(sids[k], phis[k][: len(outs[k])], outs[k])
-                submitted[k] = now
+                    due = r["rebuild_due"]
+                    due_count += int(due)
+                    if due or inner[k] >= SERVE_MAX_INNER:
+                        inner_counts.append(inner[k])
+                        next_kind[k] = "rebuild" if outer[k] < iters else "done"
+                    else:
+                        next_kind[k] = "apply"
+                if next_kind[k] == "done":
+                    finished[k] = True
+                    done_all += 1
+                    continue
+            if outstanding[k] is None and now >= arrivals[k][step[k]]:
+                if next_kind[k] == "rebuild":
+                    if outer[k] > 0:
+                        synth.perturb_in_place(phis[k], SERVE_EPS)
+                    outstanding[k] = (srv.submit_rebuild(sids[k], phis[k]), "rebuild")
+                    outer[k] += 1
+                    inner[k] = 0
+                    blocks[k][...] = phis[k][: len(blocks[k])]
+                else:
+                    if inner[k] > 0:  # the inner loop's block moves less at every step
+                        synth.perturb_in_place(blocks[k], SERVE_EPS * SERVE_INNER_DECAY ** inner[k])
+                    outstanding[k] = (srv.submit_apply(sids[k], blocks[k], outs[k]), "apply")
+                    inner[k] += 1
                 step[k] += 1
         st = srv.stats()
         peak_running = max(peak_running, st["running"])
@@ -547,7 +576,8 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
 
     return {
         "workload": f"{n_systems} resident systems, N log-uniform [32,512], cubic 2/3/5-smooth grids [48,128], "
-                    f"{iters} SCF-like iterations x (1 rebuild + {SERVE_APPLIES} applies of {SERVE_BLOCK} orbitals), "
+                    f"{iters} SCF-like outer iterations x (1 rebuild + applies of {SERVE_BLOCK} orbitals until the "
+                    f"block's ACE energy moves by < {SERVE_CADENCE_TOL:g} relative, at most {SERVE_MAX_INNER}), "
                     f"Poisson arrivals {SERVE_RATE:g} req/s offered, closed loop per system, {slots} slots "
                     f"({rebuild_slots} for rebuilds), "
                     f"S_thr={S_THR:g}, {'plain FP64' if fp64 else 'mixed precision'}",
@@ -559,6 +589,9 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
         "latency_from": "submission to completion (each system submits its next request once the previous completed)",
         "served_req_per_s": round(len(all_lat) / makespan, 1), "offered_req_per_s": SERVE_RATE,
         "merged_pair_convolutions": merge,
+        "inner_applies_per_rebuild": {"mean": round(float(np.mean(inner_counts)), 2) if inner_counts else None,
+                                      "max": int(max(inner_counts)) if inner_counts else None,
+                                      "ended_by_convergence": due_count, "outer_iterations": len(inner_counts)},
         "pair_convolutions_per_s": round(pairs / makespan, 1), "pair_convolutions": int(pairs),
         "makespan_s": round(makespan, 3), "peak_running": peak_running,
         "peak_resident_GB": round(peak_bytes / 1e9, 2),

@@ -192,6 +192,15 @@ lace_status lace_build_ace(lace_ctx* ctx, int sym);
  * [n][n1][n2][n3]); kpsi_out (host FP64, same shape) receives the result. */
 lace_status lace_apply_ace(lace_ctx* ctx, const double* psi, int n, double* kpsi_out);
 
+/* The ACE energy of the block of the last lace_apply_ace(_dev):
+ * sum_j <psi_j| K_ACE |psi_j> = dV sum_j psi_j . (K_ACE psi)_j = -|X|^2 with
+ * X = dV xi^T psi (in Ha for dV-normalised psi_j), formed on the device from
+ * the application's own N_P x n coefficients.  Its change between
+ * consecutive applications of one projector measures how far the inner loop
+ * of the paper's double loop (Sec. 2) still moves.  LACE_ERR_STATE before
+ * the first application. */
+lace_status lace_get_ace_energy(lace_ctx* ctx, double* e_out);
+
 /* As lace_apply_ace with device FP64 buffers (borrowed). */
 lace_status lace_apply_ace_dev(lace_ctx* ctx, const double* d_psi, int n, double* d_kpsi_out);
 
@@ -327,6 +336,23 @@ lace_status lace_server_poll(lace_server* srv, long long request_id, int wait, i
 /* What made a completed request fail ("" when it succeeded); NULL for an
  * unknown or unfinished request.  The string lives as long as the server. */
 const char* lace_server_request_error(lace_server* srv, long long request_id);
+
+/* Rebuild cadence of a system (the double loop of Sec. 2: the projector of
+ * an outer iteration serves the inner iterations until they converge, then
+ * the outer loop rebuilds it).  With tol > 0, every completed APPLY of the
+ * system reports rebuild_due = 1 (lace_server_apply_info) once its block's
+ * ACE energy sum_j <data_j|K_ACE|data_j> differs by at most tol (relative)
+ * from that of the system's previous APPLY of as many functions on the same
+ * projector; the first APPLY after a REBUILD reports 0.  tol = 0 (default)
+ * never reports a rebuild as due.  LACE_ERR_ARG for an unknown system or
+ * tol < 0. */
+lace_status lace_server_set_rebuild_tolerance(lace_server* srv, int system_id, double tol);
+
+/* APPLY results of a completed request: *e_block_out its block's ACE energy
+ * (lace_get_ace_energy) and *rebuild_due_out the cadence's verdict.  Any
+ * output may be NULL; LACE_ERR_ARG for an unknown or unfinished request. */
+lace_status lace_server_apply_info(lace_server* srv, long long request_id, double* e_block_out,
+                                   int* rebuild_due_out);
 
 /* Free a system's device memory once its queued requests have completed
  * (blocks until then); later requests for it fail with LACE_ERR_ARG. */

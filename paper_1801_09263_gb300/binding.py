@@ -103,6 +103,9 @@ def load_library(build_if_missing: bool = False):
         "lace_server_stats": ([P, P, P, P], I),
         "lace_server_set_pair_merging": ([P, I, D], I),
         "lace_server_merge_stats": ([P, P, P, P], I),
+        "lace_server_set_rebuild_tolerance": ([P, I, D], I),
+        "lace_server_apply_info": ([P, LL, P, P], I),
+        "lace_get_ace_energy": ([P, P], I),
         "lace_exchange_pairs_noalloc": ([P, I, I, I, P, I, I, P, LL, P, P, P], I),
         "lace_probe_peak_rates": ([I, P, I], I),
         "lace_status_string": ([I], C.c_char_p),
@@ -279,6 +282,12 @@ class Lace:
         self._check(self.lib.lace_get_pairs(self.h, _ptr(out), n.value, C.byref(n)), "lace_get_pairs")
         return out[: n.value]
 
+    def ace_energy(self) -> float:
+        """sum_j <psi_j|K_ACE|psi_j> of the last ACE application's block."""
+        e = C.c_double(0)
+        self._check(self.lib.lace_get_ace_energy(self.h, C.byref(e)), "lace_get_ace_energy")
+        return e.value
+
     def get_pivots(self) -> np.ndarray:
         out = np.empty(self.n_occ, dtype=np.int64)
         self._check(self.lib.lace_get_pivots(self.h, _ptr(out), int(self.n_occ)), "lace_get_pivots")
@@ -387,8 +396,11 @@ class Server:
             return None
         _, out = self._live.pop(request, (None, None))
         err = self.lib.lace_server_request_error(self.h, int(request)) if res.value else b""
+        eb, due = C.c_double(0), C.c_int(0)
+        self._check(self.lib.lace_server_apply_info(self.h, int(request), C.byref(eb), C.byref(due)),
+                    "lace_server_apply_info")
         return dict(status=res.value, latency_ms=lat.value, ex=ex.value, n_pairs=npairs.value, out=out,
-                    error=(err or b"").decode())
+                    error=(err or b"").decode(), e_block=eb.value, rebuild_due=bool(due.value))
 
     def remove_system(self, system: int):
         self._check(self.lib.lace_server_remove_system(self.h, int(system)), "lace_server_remove_system")
@@ -397,6 +409,10 @@ class Server:
         b, r, q = C.c_ulonglong(0), C.c_int(0), C.c_int(0)
         self._check(self.lib.lace_server_stats(self.h, C.byref(b), C.byref(r), C.byref(q)), "lace_server_stats")
         return dict(bytes_resident=int(b.value), running=r.value, queued=q.value)
+
+    def set_rebuild_tolerance(self, system: int, tol: float):
+        self._check(self.lib.lace_server_set_rebuild_tolerance(self.h, int(system), float(tol)),
+                    "lace_server_set_rebuild_tolerance")
 
     def set_pair_merging(self, enable: bool = True, window_ms: float = 5.0):
         self._check(self.lib.lace_server_set_pair_merging(self.h, int(bool(enable)), float(window_ms)),

@@ -661,6 +661,8 @@ lace_status apply_ace_impl(lace_ctx* c, const double* d_psi64, int nf, double* d
         lace_status st = ace_contract<T>(c, n, nf, c->xi.as<T>(), in, -c->g.dv, X, L);
         if (st) return st;
     }
+    // the block's ACE energy sum_j <psi_j|K_ACE|psi_j> = dV psi^T xi X = -|X|^2
+    CK(neg_sum_squares((size_t)n * nf, X, c->exd.as<double>() + 1, c->stream, &L.n), "ace energy");
     T* dst = sizeof(T) == 8 ? reinterpret_cast<T*>(d_out64) : out;
     {
         lace_status st = ace_combine<T>(c, nf, n, c->xi.as<T>(), X, dst, L);
@@ -1067,6 +1069,7 @@ static lace_status apply_ace_common(lace_ctx* c, const double* psi, int n, doubl
     cudaError_t e = cudaStreamSynchronize(c->stream);
     if (st) return st;
     if (e) return cuda_fail(c, e, "apply ace");
+    c->ace_applied = true;
     return LACE_OK;
 }
 
@@ -1154,6 +1157,14 @@ lace_status lace_get_pairs(lace_ctx* c, int* pairs_out, long long cap, long long
         CK(cudaMemcpyAsync(pairs_out, c->pairs.p, sizeof(int2) * k, cudaMemcpyDeviceToHost, c->stream), "get pairs");
         CK(cudaStreamSynchronize(c->stream), "get pairs");
     }
+    return LACE_OK;
+}
+
+lace_status lace_get_ace_energy(lace_ctx* c, double* e_out) {
+    if (!c || !e_out) return LACE_ERR_ARG;
+    if (!c->ace_applied) return fail(c, LACE_ERR_STATE, "apply ACE first");
+    CK(cudaMemcpyAsync(e_out, c->exd.as<double>() + 1, sizeof(double), cudaMemcpyDeviceToHost, c->stream), "energy");
+    CK(cudaStreamSynchronize(c->stream), "energy");
     return LACE_OK;
 }
 

@@ -65,6 +65,7 @@ struct lace_ctx {
 
     int n_occ = 0, n_extra = 0, n_p = 0;
     bool loaded = false, localized = false, screened = false, applied = false, ace = false;
+    bool ace_applied = false;    // exd[1] holds the block ACE energy of the last ACE application
     bool x_identity = false;     // X = I (loaded without orthonormalisation)
     bool psi_occ_ready = false;  // psi[0 .. n_occ) holds canon X (or its SCDM rotation)
     double s_thr = 0.0;

@@ -104,7 +104,27 @@ __global__ void energy_sum_kernel(int n, const double* __restrict__ E, double* _
     if (threadIdx.x == 0) ex[0] = -0.5 * sh[0];
 }
 
+// out[0] = -sum of squares of X (m entries), one block, fixed order.
+__global__ void neg_sum_sq_kernel(size_t m, const double* __restrict__ X, double* __restrict__ out) {
+    __shared__ double sh[SC_THREADS];
+    double s = 0.0;
+    for (size_t idx = threadIdx.x; idx < m; idx += blockDim.x) s += X[idx] * X[idx];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = -sh[0];
+}
+
 }  // namespace
+
+cudaError_t neg_sum_squares(size_t m, const double* d_X, double* d_out, cudaStream_t s, int* launches) {
+    neg_sum_sq_kernel<<<1, SC_THREADS, 0, s>>>(m, d_X, d_out);
+    *launches += 1;
+    return cudaGetLastError();
+}
 
 cudaError_t build_pair_list(int n_occ, int n_extra, const double* d_S, double thr, bool use_S, int2* d_pairs,
                             int* d_counts, long long* n_pairs, cudaStream_t s, int* launches) {

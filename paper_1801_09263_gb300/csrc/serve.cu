@@ -224,7 +224,8 @@ struct GpuExec {
         if (r.kind == lace_serve::REQ_APPLY) {
             if (!h || !h->ctx) return LACE_ERR_STATE;
             lace_set_stream(h->ctx, h->hi);
-            const lace_status st = lace_apply_ace(h->ctx, r.data, r.n, r.out);
+            lace_status st = lace_apply_ace(h->ctx, r.data, r.n, r.out);
+            if (st == LACE_OK) st = lace_get_ace_energy(h->ctx, &r.e_block);
             lace_set_stream(h->ctx, nullptr);
             return st;
         }
@@ -387,6 +388,16 @@ lace_status lace_server_set_pair_merging(lace_server* s, int enable, double wind
     s->merger.enabled = enable != 0;
     s->merger.window_ms = window_ms;
     return LACE_OK;
+}
+
+lace_status lace_server_set_rebuild_tolerance(lace_server* s, int sys, double tol) {
+    if (!s || !(tol >= 0.0)) return LACE_ERR_ARG;
+    return (lace_status)s->sched->set_rebuild_tolerance(sys, tol);
+}
+
+lace_status lace_server_apply_info(lace_server* s, long long id, double* e_block, int* rebuild_due) {
+    if (!s) return LACE_ERR_ARG;
+    return (lace_status)s->sched->apply_info(id, e_block, rebuild_due);
 }
 
 lace_status lace_server_merge_stats(lace_server* s, long long* batches, long long* merged_batches,

@@ -13,12 +13,14 @@
 //   using Handle = ...;                                   // per-system state, default-constructible
 //   size_t predict(const SystemDesc&, const Handle&, int kind, int n);  // bytes the system holds after the request
 //   size_t held(const Handle&);                           // bytes the system holds now
-//   int run(const SystemDesc&, Handle&, Request&);        // status code (0 = ok); fills ex / n_pairs / err
+//   int run(const SystemDesc&, Handle&, Request&);        // status code (0 = ok); fills ex / n_pairs /
+//                                                         // e_block (APPLY) / err
 //   void release(Handle&);                                // free the system's memory
 #pragma once
 
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstddef>
 #include <deque>
@@ -56,7 +58,38 @@ struct Request {
     int result = 0;
     double ex = 0.0;
     long long n_pairs = 0;
-    std::string err;  // what failed (empty when result == 0)
+    double e_block = 0.0;  // APPLY: sum_j <data_j| K_ACE |data_j> (set by the executor)
+    int rebuild_due = 0;   // APPLY: the inner loop has converged on this projector (see Scheduler)
+    std::string err;       // what failed (empty when result == 0)
+};
+
+// The rebuild cadence of the paper's double loop (Sec. 2): the ACE projector
+// built in an outer iteration serves the inner iterations until they have
+// converged, then the outer loop rebuilds it.  The inner loop is seen through
+// the APPLY requests of a system: consecutive applications of one projector
+// to the evolving block of functions; once the block's ACE energy changes by
+// at most tol (relative) from one application to the next, the inner loop has
+// converged and a rebuild is due.  The first application after a rebuild
+// has nothing to compare with.
+struct RebuildCadence {
+    double tol = 0.0;  // 0: never report a rebuild as due
+    bool have_prev = false;
+    int prev_n = 0;
+    double prev_e = 0.0;
+
+    void rebuilt() { have_prev = false; }
+    // after a successful APPLY of n functions with block energy e
+    int applied(int n, double e) {
+        int due = 0;
+        if (tol > 0.0 && have_prev && prev_n == n) {
+            const double scale = std::max(std::abs(e), 1e-300);
+            due = std::abs(e - prev_e) <= tol * scale ? 1 : 0;
+        }
+        have_prev = true;
+        prev_n = n;
+        prev_e = e;
+        return due;
+    }
 };
 
 template <class Exec>
@@ -129,6 +162,25 @@ class Scheduler {
         return S_OK;
     }
 
+    // APPLY results of a completed request: block energy and whether a
+    // rebuild is due.
+    int apply_info(long long id, double* e_block, int* rebuild_due) {
+        std::lock_guard<std::mutex> lk(mu_);
+        auto it = reqs_.find(id);
+        if (it == reqs_.end() || !it->second->done) return S_ERR_ARG;
+        if (e_block) *e_block = it->second->e_block;
+        if (rebuild_due) *rebuild_due = it->second->rebuild_due;
+        return S_OK;
+    }
+
+    // Relative tolerance of a system's rebuild cadence (0: off).
+    int set_rebuild_tolerance(int sys, double tol) {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (!valid(sys) || !(tol >= 0.0)) return S_ERR_ARG;
+        systems_[sys]->cadence.tol = tol;
+        return S_OK;
+    }
+
     // The failure message of a completed request ("" if none); the storage
     // lives as long as the scheduler.
     const char* error(long long id) {
@@ -168,6 +220,7 @@ class Scheduler {
         size_t growth = 0;   // predicted growth of the running request
         int queued = 0;      // requests submitted and not yet completed
         bool busy = false, removing = false, alive = true;
+        RebuildCadence cadence;
     };
 
     bool valid(int sys) const { return sys >= 0 && sys < (int)systems_.size() && systems_[sys]->alive; }
@@ -236,6 +289,10 @@ class Scheduler {
             s.growth = 0;
             running_--;
             rebuilds_running_ -= rebuild;
+            if (st == S_OK) {
+                if (rebuild) s.cadence.rebuilt();
+                else r->rebuild_due = s.cadence.applied(r->n, r->e_block);
+            }
             finish(s, *r, st);
             work_cv_.notify_all();  // memory and the system are free again
         }

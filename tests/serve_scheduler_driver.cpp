@@ -4,6 +4,7 @@
 // and the largest number of requests seen running at once.
 #include <atomic>
 #include <chrono>
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 #include <string>
@@ -57,7 +58,12 @@ struct FakeExec {
                 r.ex = -1.0 * (r.sys + 1);
                 r.n_pairs = 10 * (r.sys + 1);
             } else {
-                for (int k = 0; k < r.n; ++k) r.out[k] = 2.0 * r.data[k];
+                double e = 0.0;
+                for (int k = 0; k < r.n; ++k) {
+                    r.out[k] = 2.0 * r.data[k];
+                    e -= r.data[k] * r.data[k];
+                }
+                r.e_block = e;
             }
         }
         if (r.kind == REQ_REBUILD) --rebuilding;
@@ -78,34 +84,46 @@ struct Sub {
     int sys, kind;
 };
 
+// scales: per submission, the factor of its 8 input values (1.5 each by
+// default); cadence_tol: the rebuild-cadence tolerance of every system.
 static void scenario(const char* name, int slots, size_t budget, const std::vector<SystemDesc>& systems,
                      const std::vector<Sub>& subs, int remove_after = -1, int remove_sys = -1,
-                     int rebuild_slots = 0) {
+                     int rebuild_slots = 0, const std::vector<double>& scales = {}, double cadence_tol = 0.0) {
     FakeExec ex;
-    std::vector<double> in(8, 1.5), out(8 * subs.size(), 0.0);
+    std::vector<double> in(8 * subs.size(), 1.5), out(8 * subs.size(), 0.0);
+    for (size_t k = 0; k < scales.size() && k < subs.size(); ++k)
+        for (int j = 0; j < 8; ++j) in[8 * k + j] = 1.5 * scales[k];
     std::vector<long long> ids;
-    std::vector<int> res, done_flags;
-    std::vector<double> exs, lat;
+    std::vector<int> res, done_flags, dues;
+    std::vector<double> exs, lat, eblocks;
     std::vector<long long> npairs;
     {
         Scheduler<FakeExec> s(ex, slots, rebuild_slots > 0 ? rebuild_slots : slots, budget);
-        for (auto& d : systems) s.add_system(d);
+        for (auto& d : systems) {
+            const int id = s.add_system(d);
+            if (cadence_tol > 0.0) s.set_rebuild_tolerance(id, cadence_tol);
+        }
         for (size_t k = 0; k < subs.size(); ++k) {
             long long id = -1;
-            const int st = s.submit(subs[k].sys, subs[k].kind, in.data(), 8, out.data() + 8 * k, &id);
+            const int st = s.submit(subs[k].sys, subs[k].kind, in.data() + 8 * k, 8, out.data() + 8 * k, &id);
             ids.push_back(st == S_OK ? id : -st);
             if ((int)k == remove_after) s.remove_system(remove_sys);
         }
         for (long long id : ids) {
-            int d = 0, r = -1;
-            double l = 0, e = 0;
+            int d = 0, r = -1, due = 0;
+            double l = 0, e = 0, eb = 0;
             long long np = 0;
-            if (id > 0) s.poll(id, true, &d, &r, &l, &e, &np);
+            if (id > 0) {
+                s.poll(id, true, &d, &r, &l, &e, &np);
+                s.apply_info(id, &eb, &due);
+            }
             done_flags.push_back(d);
             res.push_back(id > 0 ? r : (int)id);
             exs.push_back(e);
             lat.push_back(l);
             npairs.push_back(np);
+            eblocks.push_back(eb);
+            dues.push_back(due);
         }
     }
     std::string o = std::string("{\"name\": \"") + name + "\", \"max_running\": " + std::to_string(ex.max_running.load()) +
@@ -115,12 +133,13 @@ static void scenario(const char* name, int slots, size_t budget, const std::vect
         double st = -1, en = -1;
         for (auto& r : ex.log)
             if (r.id == ids[k]) { st = r.start; en = r.end; }
-        char buf[512];
+        char buf[640];
         snprintf(buf, sizeof buf,
                  "%s{\"id\": %lld, \"sys\": %d, \"kind\": %d, \"status\": %d, \"done\": %d, \"start\": %.3f, "
-                 "\"end\": %.3f, \"latency\": %.3f, \"ex\": %.1f, \"n_pairs\": %lld, \"out0\": %.2f}",
+                 "\"end\": %.3f, \"latency\": %.3f, \"ex\": %.1f, \"n_pairs\": %lld, \"out0\": %.2f, "
+                 "\"e_block\": %.17g, \"rebuild_due\": %d}",
                  k ? ", " : "", ids[k], subs[k].sys, subs[k].kind, res[k], done_flags[k], st, en, lat[k], exs[k],
-                 npairs[k], subs[k].kind == REQ_APPLY ? out[8 * k] : 0.0);
+                 npairs[k], subs[k].kind == REQ_APPLY ? out[8 * k] : 0.0, eblocks[k], dues[k]);
         o += buf;
     }
     o += "]}";
@@ -171,6 +190,24 @@ int main() {
         std::vector<SystemDesc> sys{sys_desc(10, 10, 0.03), sys_desc(10, 10, 0.1), sys_desc(10, 10, 0.1)};
         std::vector<Sub> subs{{0, REQ_REBUILD}, {1, REQ_REBUILD}, {2, REQ_REBUILD}, {0, REQ_APPLY}, {0, REQ_APPLY}};
         scenario("rebuild_slots", 4, 1000, sys, subs, -1, -1, /*rebuild_slots=*/1);
+    }
+    // rebuild cadence: the inputs of an inner loop converge geometrically
+    // (factor 1 + 0.5^k); a REBUILD resets the comparison
+    {
+        std::vector<SystemDesc> sys{sys_desc(10, 10, 0.001)};
+        std::vector<Sub> subs{{0, REQ_REBUILD}};
+        std::vector<double> scales{1.0};
+        for (int k = 0; k < 14; ++k) {
+            subs.push_back({0, REQ_APPLY});
+            scales.push_back(1.0 + std::pow(0.5, k));
+        }
+        subs.push_back({0, REQ_REBUILD});
+        scales.push_back(1.0);
+        for (int k = 0; k < 2; ++k) {
+            subs.push_back({0, REQ_APPLY});
+            scales.push_back(1.25);
+        }
+        scenario("cadence", 1, 1000, sys, subs, -1, -1, 0, scales, 1e-3);
     }
     return 0;
 }

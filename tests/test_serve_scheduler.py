@@ -8,7 +8,8 @@ count; one system's requests run in submission order; an apply before the
 first rebuild fails with the state error; memory admission makes a request
 wait while its growth does not fit and fails it with the out-of-memory status
 when it can never fit; removing a system frees its memory; a rebuild-slot
-limit keeps slots free for applies.
+limit keeps slots free for applies; the rebuild cadence reports a rebuild as
+due once the block energy of consecutive applies has converged.
 """
 import json
 import os
@@ -93,3 +94,21 @@ def test_rebuild_slots_leave_room_for_applies(runs):
     # system 0's applies ran while the later rebuilds were still running
     last_rebuild_end = max(x["end"] for x in q if x["kind"] == REBUILD)
     assert all(x["end"] < last_rebuild_end for x in q if x["kind"] == APPLY)
+
+
+def test_rebuild_is_due_once_the_inner_loop_has_converged(runs):
+    """The double loop of the paper (Sec. 2): the inputs of the inner loop
+    converge (factor 1 + 0.5^k); an APPLY reports a rebuild as due when its
+    block energy differs from the previous APPLY's by at most the tolerance
+    (1e-3 relative), and never right after a REBUILD."""
+    q = runs["cadence"]["requests"]
+    assert all(x["status"] == OK for x in q)
+    applies = [x for x in q[1:15]]
+    e = [x["e_block"] for x in applies]
+    assert e == sorted(e)  # |e| shrinks toward its limit
+    expect = [False] + [abs(b - a) <= 1e-3 * abs(b) for a, b in zip(e, e[1:])]
+    assert [bool(x["rebuild_due"]) for x in applies] == expect
+    first_due = expect.index(True)
+    assert 9 <= first_due <= 12 and all(expect[first_due:])
+    assert q[15]["kind"] == REBUILD
+    assert [bool(x["rebuild_due"]) for x in q[16:]] == [False, True]  # the same block twice after the rebuild
