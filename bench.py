@@ -37,7 +37,7 @@ B_ALG_PER_PAIR_FP32 = 16  # bytes per grid point per real pair (3-pass FFT model
 # sources of the pair-convolution kernels: the committed DRAM-traffic capture
 # (profiles/pairconv_traffic.json) holds their hash and counts only while they match
 PAIRCONV_SOURCES = ("common.cuh", "dft_packed.cuh", "f32x2.cuh", "lace_internal.cuh", "pairconv.cu", "pairconv_spec.cuh",
-                    "pairconv_spec2.cuh", "pairconv_pair.cuh", "pairconv_spec_s.cu", "pairconv_spec_m.cu",
+                    "pairconv_spec2.cuh", "pairconv_spec_s.cu", "pairconv_spec_m.cu",
                     "pairconv_spec_l.cu")
 
 

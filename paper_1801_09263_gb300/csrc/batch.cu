@@ -163,6 +163,7 @@ lace_status prepare(lace_batch* b) {
     size_t need_pool = 0, max_ng = 0, min_ng = SIZE_MAX;
     int max_n1 = 0, max_n2 = 0, max_n3 = 0;
     std::vector<MultiInst> hi(b->n);
+    size_t spec_smem = 0;
     for (int q = 0; q < b->n; ++q) {
         lace_ctx* c = b->ctx[q];
         const size_t ng = c->g.ng;
@@ -199,12 +200,14 @@ lace_status prepare(lace_batch* b) {
         I.E = c->m(MS_E);
         I.n1 = c->g.n[0];
         I.n2 = c->g.n[1];
+        I.spec = multi_spec_size(c->g.n[0], c->g.n[1], c->g.n[2]);
+        spec_smem = std::max(spec_smem, multi_spec_smem(I.spec));
     }
     size_t cap = kPoolCap;
     if (const char* env = getenv("LACE_BATCH_POOL_MB")) cap = (size_t)std::max(1, atoi(env)) << 20;  // testing chunking
     b->pool_elems = std::max(std::min(need_pool, cap / sizeof(cplx<float>)), max_ng);
     b->epart_elems = 2 * (size_t)max_n1 * (b->pool_elems / min_ng + 1);
-    b->smem = pairconv_multi_smem(max_n1, max_n2, max_n3);
+    b->smem = std::max(pairconv_multi_smem(max_n1, max_n2, max_n3), spec_smem);
     BCK(b->inst.ensure(sizeof(MultiInst) * b->n), "batch tables");
     BCK(b->ngrids.ensure(sizeof(int) * b->n), "batch tables");
     BCK(b->pool.ensure(b->pool_elems * sizeof(cplx<float>)), "batch scratch");

@@ -503,10 +503,7 @@ lace_status apply_impl(lace_ctx* c) {
         c->s_thr = 0.0;
     }
     const long long n_grids = (c->n_pairs + 1) / 2;
-    // complex grids the scratch holds: the chunk size, even (the paired FFT
-    // passes take two grids per CTA)
-    int batch = (int)std::min<long long>(batch_for(c), std::max<long long>(n_grids, 1));
-    batch += batch & 1;
+    const int batch = (int)std::min<long long>(batch_for(c), std::max<long long>(n_grids, 1));
     CK(c->scratch.ensure((size_t)batch * ng * 2 * sizeof(T)), "alloc FFT scratch");
     CK(c->epart.ensure((size_t)batch * c->g.n[0] * 2 * sizeof(double)), "alloc energies");
     CK(cudaMemsetAsync(c->W.p, 0, (size_t)c->n_p * ng * sizeof(T), c->stream), "zero W");
@@ -534,8 +531,7 @@ lace_status exchange_prepare_f(lace_ctx* c, MergedSys<float>* m, int* n_grids_ou
         c->s_thr = 0.0;
     }
     const long long n_grids = (c->n_pairs + 1) / 2;
-    int batch = (int)std::min<long long>(batch_for(c), std::max<long long>(n_grids, 1));
-    batch += batch & 1;
+    const int batch = (int)std::min<long long>(batch_for(c), std::max<long long>(n_grids, 1));
     CK(c->scratch.ensure((size_t)batch * ng * 2 * sizeof(float)), "alloc FFT scratch");
     CK(c->epart.ensure((size_t)batch * c->g.n[0] * 2 * sizeof(double)), "alloc energies");
     CK(cudaMemsetAsync(c->W.p, 0, (size_t)c->n_p * ng * sizeof(float), c->stream), "zero W");

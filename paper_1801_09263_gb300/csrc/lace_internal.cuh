@@ -80,11 +80,9 @@ template <typename T> struct ConvArgs {
 
 // Size-specialised FP32 passes for cubic grids (pairconv_spec_*.cu): launch
 // pass 0/1/2 (A/B/C) for grid size n if a specialisation exists.
-// allow_pair: the scratch holds nb rounded up to even grids, so the passes
-// that take two complex grids per CTA may run.
-bool spec_launch_s(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s, bool allow_pair);
-bool spec_launch_m(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s, bool allow_pair);
-bool spec_launch_l(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s, bool allow_pair);
+bool spec_launch_s(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
+bool spec_launch_m(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
+bool spec_launch_l(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
 
 // Grid sizes whose size-specialised passes take merged launches (one grid
 // per CTA, out of place) (pairconv_spec_*.cu).
@@ -107,6 +105,7 @@ struct MultiInst {
     ConvArgs<float> P;  // per-instance arguments (P.scratch, P.epart unused)
     double* E;          // pair-energy matrix [n_occ][n_occ]
     int n1, n2;         // planes of passes A/C, slabs of pass B
+    int spec;           // cubic size with size-specialised pass bodies (multi_spec_size), else 0
 };
 struct MultiArgs {
     const MultiInst* inst;  // device array [n_inst]
@@ -119,6 +118,12 @@ struct MultiArgs {
     unsigned* bar;          // 4 unsigned: barrier counters and the timeout flag bar[2]
 };
 size_t pairconv_multi_smem(int n1, int n2, int n3);
+// Cubic sizes whose size-specialised pass bodies the persistent kernel runs
+// (with 256 or 512 threads a CTA): n, else 0; their shared memory.
+int multi_spec_size(int n1, int n2, int n3);
+size_t multi_spec_smem(int n);
+const void* multi_kernel_256();  // pairconv_multi_256.cu
+const void* multi_kernel_512();  // pairconv_multi_512.cu
 int pairconv_multi_occupancy(int threads, size_t smem);  // CTAs per SM (0: unsupported)
 // n_chunks cooperative launches (chunk c in launch c; see pairconv_multi_chunks).
 cudaError_t pairconv_multi_run(const MultiArgs& A, int n_chunks, size_t smem, int threads, int ctas_per_sm,

@@ -204,21 +204,15 @@ cudaError_t pairconv_run(const GridGeom& g, const FFTTables<T>& tb, const T* psi
     // size-specialised FP32 kernels for cubic grids with n % 4 == 0 (or LACE_GENERIC_FFT=1 to disable)
     const char* gen = getenv("LACE_GENERIC_FFT");
     const bool spec_ok = !(gen && gen[0] == '1') && g.n[0] == g.n[1] && g.n[1] == g.n[2] && g.n[0] % 4 == 0;
-    // The size-specialised passes may take two complex grids per CTA; their
-    // last pair of an odd chunk then writes one grid past the chunk, so the
-    // chunks hold an even number of grids (the scratch holds `batch`).
-    const bool allow_pair = std::is_same<T, float>::value && spec_ok && batch >= 2;
-    const int step = allow_pair ? (batch & ~1) : batch;
     if (ev0) cudaEventRecord(ev0, s);
-    for (int g0 = 0; g0 < n_grids; g0 += step) {
-        const int nb = std::min(step, n_grids - g0);
+    for (int g0 = 0; g0 < n_grids; g0 += batch) {
+        const int nb = std::min(batch, n_grids - g0);
         bool done = false;
         if constexpr (std::is_same<T, float>::value) {
             if (spec_ok) {
                 for (int pass = 0; pass < 3; ++pass)
-                    done = spec_launch_s(pass, g.n[0], nb, P, g0, s, allow_pair) ||
-                           spec_launch_m(pass, g.n[0], nb, P, g0, s, allow_pair) ||
-                           spec_launch_l(pass, g.n[0], nb, P, g0, s, allow_pair);
+                    done = spec_launch_s(pass, g.n[0], nb, P, g0, s) || spec_launch_m(pass, g.n[0], nb, P, g0, s) ||
+                           spec_launch_l(pass, g.n[0], nb, P, g0, s);
             }
         }
         if (!done) {
@@ -295,8 +289,8 @@ cudaError_t pairconv_run_merged(int n, const FFTTables<float>& tb, const std::ve
         const int g0 = start[r], nb = start[r + 1] - start[r];
         P.msys = d_sys + (size_t)r * nsys;
         for (int pass = 0; pass < 3; ++pass) {
-            const bool ok = spec_launch_s(pass, n, nb, P, g0, s, false) || spec_launch_m(pass, n, nb, P, g0, s, false) ||
-                            spec_launch_l(pass, n, nb, P, g0, s, false);
+            const bool ok = spec_launch_s(pass, n, nb, P, g0, s) || spec_launch_m(pass, n, nb, P, g0, s) ||
+                            spec_launch_l(pass, n, nb, P, g0, s);
             if (!ok) return cudaErrorInvalidValue;
         }
         energy_collect_merged_kernel<<<(nb + 127) / 128, 128, 0, s>>>(d_refs, P.msys, g0, nb, n);

@@ -1,0 +1,217 @@
+// Persistent multi-instance pair-convolution kernel (template), shared by
+// the translation units that instantiate it for each block size
+// (pairconv_multi*.cu).  See pairconv_multi.cu for the design.
+#pragma once
+
+#include <algorithm>
+#include <cstring>
+
+#include "grid_sync.cuh"
+#include "lace_internal.cuh"
+#include "pairconv_generic.cuh"
+#include "pairconv_spec2.cuh"
+
+namespace lace {
+namespace multi {
+
+constexpr int kMaxEntries = 256;  // instance pieces per chunk
+
+struct ChunkTable {
+    int n;                       // entries
+    int q[kMaxEntries];          // instance
+    int g0[kMaxEntries];         // first grid (instance-local index)
+    int cnt[kMaxEntries];        // grids
+    size_t pool[kMaxEntries];    // pool offset of the first grid (complex elements)
+    size_t ep[kMaxEntries];      // epart offset (doubles)
+    int item[kMaxEntries + 1];   // item prefix of the current phase
+    // where the next chunk starts
+    int next_q, next_g;
+};
+
+// Thread 0: the chunk starting at grid g of instance q.
+static __device__ void build_chunk(const MultiArgs& A, int q, int g, ChunkTable& t) {
+    size_t pool_used = 0, ep_used = 0;
+    int n = 0;
+    while (q < A.n_inst && n < kMaxEntries) {
+        const int total = A.n_grids[q];
+        const int rem = total - g;
+        if (rem <= 0) {
+            ++q;
+            g = 0;
+            continue;
+        }
+        const MultiInst& I = A.inst[q];
+        const size_t ng = I.P.ng;
+        const size_t per_ep = 2 * (size_t)I.n1;
+        const size_t fit_pool = (A.pool_elems - pool_used) / ng;
+        const size_t fit_ep = (A.epart_elems - ep_used) / per_ep;
+        const int fit = (int)std::min<size_t>((size_t)rem, std::min(fit_pool, fit_ep));
+        if (fit <= 0) break;
+        t.q[n] = q;
+        t.g0[n] = g;
+        t.cnt[n] = fit;
+        t.pool[n] = pool_used;
+        t.ep[n] = ep_used;
+        pool_used += (size_t)fit * ng;
+        ep_used += (size_t)fit * per_ep;
+        ++n;
+        g += fit;
+        if (g >= total) {
+            ++q;
+            g = 0;
+        }
+    }
+    t.n = n;
+    t.next_q = q;
+    t.next_g = g;
+}
+
+// Thread 0: item prefix for a phase (0: planes n1, 1: slabs n2, 2: grids).
+static __device__ void build_items(const MultiArgs& A, ChunkTable& t, int phase) {
+    int acc = 0;
+    for (int e = 0; e < t.n; ++e) {
+        t.item[e] = acc;
+        const MultiInst& I = A.inst[t.q[e]];
+        const int per = phase == 0 ? I.n1 : (phase == 1 ? I.n2 : 1);
+        acc += t.cnt[e] * per;
+    }
+    t.item[t.n] = acc;
+}
+
+static __device__ __forceinline__ int find_entry(const ChunkTable& t, int it) {
+    int lo = 0, hi = t.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (t.item[mid] <= it) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One work item through the size-specialised pass bodies of
+// pairconv_spec2.cuh (the instance's cubic size; NT threads).  phase 0: pass
+// A of plane `w`, 1: pass B of slab `w`, 2: pass C of plane `w` (a constant
+// at every call site, so each phase loop inlines only its own bodies).
+template <int NT>
+__device__ __forceinline__ void spec_item(int phase, const MultiInst& I, const PairGrid& d, cplx<float>* scr,
+                                          double* ep, int w, float4* smem, double* red) {
+    spec2::GridView V;
+    V.psi = I.P.psi;
+    V.W = I.P.W;
+    V.ktab = I.P.ktab;
+    V.scr = scr;
+    V.ep = ep;
+    V.d = d;
+    V.n_occ = I.P.n_occ;
+    V.dv = I.P.dv;
+#define LACE_SPEC_ITEM(NN)                                                \
+    case NN:                                                              \
+        if (phase == 0) spec2::body_a<NN, NT>(I.P, V, w, smem, nullptr);  \
+        else if (phase == 1) spec2::body_b<NN, NT>(I.P, V, w, smem);      \
+        else spec2::body_c<NN, NT>(I.P, V, w, smem, red);                 \
+        break;
+    switch (I.spec) {
+        LACE_SPEC_ITEM(24)
+        LACE_SPEC_ITEM(32)
+        LACE_SPEC_ITEM(36)
+        LACE_SPEC_ITEM(40)
+        LACE_SPEC_ITEM(48)
+        LACE_SPEC_ITEM(60)
+        LACE_SPEC_ITEM(64)
+        default: break;
+    }
+#undef LACE_SPEC_ITEM
+}
+
+// SPEC: instances with I.spec run the size-specialised bodies (the others,
+// and every instance without SPEC, the generic-radix bodies).  Planes and
+// slabs are taken plane-major within each run of grids of one instance, so
+// the CTAs in flight share the orbital planes of one x.
+template <int NT, bool SPEC>
+__global__ void __launch_bounds__(NT, 512 / NT > 0 ? 512 / NT : 1) pairconv_multi_kernel(MultiArgs A, int chunk) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx<float>* work = reinterpret_cast<cplx<float>*>(smem_raw);
+    float4* smem4 = reinterpret_cast<float4*>(smem_raw);
+    __shared__ ChunkTable t;
+    __shared__ double red[2 * 32];
+    __shared__ int abort_sh;
+    unsigned gen = 0;
+    if (threadIdx.x == 0) {
+        int q = 0, g = 0;
+        for (int c = 0;; ++c) {
+            build_chunk(A, q, g, t);
+            if (c == chunk || t.n == 0) break;
+            q = t.next_q;
+            g = t.next_g;
+        }
+    }
+    __syncthreads();
+    if (t.n == 0) return;
+    // A: planes
+    if (threadIdx.x == 0) build_items(A, t, 0);
+    __syncthreads();
+    for (int it = blockIdx.x; it < t.item[t.n]; it += gridDim.x) {
+        const int e = find_entry(t, it);
+        const MultiInst& I = A.inst[t.q[e]];
+        const int loc = it - t.item[e], x = loc / t.cnt[e], k = loc - x * t.cnt[e];
+        cplx<float>* scr = A.pool + t.pool[e] + (size_t)k * I.P.ng;
+        __syncthreads();  // the previous item's shared memory is free
+        if (SPEC && I.spec) spec_item<NT>(0, I, I.P.grids[t.g0[e] + k], scr, nullptr, x, smem4, red);
+        else gen::pass_a_plane<float>(I.P, I.P.grids[t.g0[e] + k], scr, x, work);
+    }
+    if (!grid_barrier(A.bar, gen, &abort_sh)) return;
+    // B: slabs
+    if (threadIdx.x == 0) build_items(A, t, 1);
+    __syncthreads();
+    for (int it = blockIdx.x; it < t.item[t.n]; it += gridDim.x) {
+        const int e = find_entry(t, it);
+        const MultiInst& I = A.inst[t.q[e]];
+        const int loc = it - t.item[e], k = loc / I.n2, ky = loc - k * I.n2;
+        cplx<float>* scr = A.pool + t.pool[e] + (size_t)k * I.P.ng;
+        __syncthreads();
+        if (SPEC && I.spec) spec_item<NT>(1, I, I.P.grids[t.g0[e] + k], scr, nullptr, ky, smem4, red);
+        else gen::pass_b_slab<float>(I.P, scr, ky, work);
+    }
+    if (!grid_barrier(A.bar, gen, &abort_sh)) return;
+    // C: planes
+    if (threadIdx.x == 0) build_items(A, t, 0);
+    __syncthreads();
+    for (int it = blockIdx.x; it < t.item[t.n]; it += gridDim.x) {
+        const int e = find_entry(t, it);
+        const MultiInst& I = A.inst[t.q[e]];
+        const int loc = it - t.item[e], x = loc / t.cnt[e], k = loc - x * t.cnt[e];
+        cplx<float>* scr = A.pool + t.pool[e] + (size_t)k * I.P.ng;
+        double* ep = A.epart + t.ep[e] + (size_t)k * I.n1 * 2;
+        __syncthreads();
+        if (SPEC && I.spec) spec_item<NT>(2, I, I.P.grids[t.g0[e] + k], scr, ep, x, smem4, red);
+        else gen::pass_c_plane<float>(I.P, I.P.grids[t.g0[e] + k], scr, x, work, red, ep + (size_t)x * 2);
+    }
+    if (!grid_barrier(A.bar, gen, &abort_sh)) return;
+    // D: per grid, the plane energies in a fixed order -> E[i][j] = E[j][i]
+    if (threadIdx.x == 0) build_items(A, t, 2);
+    __syncthreads();
+    for (int it = blockIdx.x * NT + threadIdx.x; it < t.item[t.n]; it += gridDim.x * NT) {
+        const int e = find_entry(t, it);
+        const MultiInst& I = A.inst[t.q[e]];
+        const int k = it - t.item[e];
+        const PairGrid d = I.P.grids[t.g0[e] + k];
+        const double* ep = A.epart + t.ep[e] + (size_t)k * I.n1 * 2;
+        double sa = 0.0, sb = 0.0;
+        for (int x = 0; x < I.n1; ++x) {
+            sa += ep[2 * x];
+            sb += ep[2 * x + 1];
+        }
+        const int no = I.P.n_occ;
+        if (d.j1 < no) {
+            I.E[(size_t)d.i1 * no + d.j1] = sa;
+            I.E[(size_t)d.j1 * no + d.i1] = sa;
+        }
+        if (d.j2 >= 0 && d.j2 < no) {
+            I.E[(size_t)d.i2 * no + d.j2] = sb;
+            I.E[(size_t)d.j2 * no + d.i2] = sb;
+        }
+    }
+}
+
+}  // namespace multi
+}  // namespace lace

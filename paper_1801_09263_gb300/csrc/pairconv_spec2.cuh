@@ -218,20 +218,19 @@ __device__ __forceinline__ void stage(const C* __restrict__ tw, Ld ld, St st) {
     }
 }
 
-// Pass A: rho of plane x, forward FFT along z then y.
-template <int N>
-__global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_a(ConvArgs<float> P, int g0) {
-    constexpr int NT = threads_for(N);
+// Pass A, one plane: rho of plane x of grid V, forward FFT along z then y,
+// on NT threads (the thread block).  pf_plane: an orbital plane to fetch into
+// L2 at the end (or null).
+template <int N, int NT>
+__device__ __forceinline__ void body_a(const ConvArgs<float>& P, const GridView& V, int x, float4* smem_v4,
+                                       const float* pf_plane) {
     constexpr int NP = N * N;
     constexpr Plan2 pl = plan2(N);
-    extern __shared__ float4 smem_v4[];
     constexpr int LP = N + 1;  // buffer rows hold up to n + 1 complex values
     constexpr int P01 = pitch(N, 0), P12 = pitch(N, 1), P23 = pitch(N, 2);
     C* b0 = reinterpret_cast<C*>(smem_v4);
     C* b1 = b0 + N * LP;
     C* tw = b1 + N * LP;
-    const int g = blockIdx.x, x = blockIdx.y;  // plane-major: the CTAs in flight share plane x
-    const GridView V = grid_view(P, g0, g, N);
     const PairGrid d = V.d;
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = P.tw[2][i];
     const size_t off = (size_t)x * NP;
@@ -240,14 +239,6 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     const float* c1 = V.psi + (size_t)d.j1 * P.ng + off;
     const float* a2 = V.psi + (size_t)(two ? d.i2 : d.i1) * P.ng + off;
     const float* c2 = V.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off;
-    int xa = 0, ga = 0;
-    const bool pf = threadIdx.x < 4 && ahead_cta(P.pf_ahead, ga, xa);
-    const float* pf_plane = nullptr;  // orbital plane of the CTA ahead that this thread prefetches
-    if (pf) {
-        const GridView A = grid_view(P, g0, ga, N);
-        const int o = threadIdx.x == 0 ? A.d.i1 : threadIdx.x == 1 ? A.d.j1 : threadIdx.x == 2 ? A.d.i2 : A.d.j2;
-        if (o >= 0) pf_plane = A.psi + (size_t)o * P.ng + (size_t)xa * NP;  // (j2 < 0: one pair)
-    }
     // z lines (line = y): rho straight from the orbitals
     stage<N, pl.r1, 1, -1, N, false, NT>(
         tw,
@@ -272,24 +263,37 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
     if (pf_plane) prefetch_l2(pf_plane, NP * sizeof(float));
 }
 
-// Pass B: slab ky: forward x-FFT (decimation in time), * K(G)/Ng, inverse
-// x-FFT (decimation in frequency); the middle three steps share registers.
+// Pass A: rho of plane x, forward FFT along z then y.
 template <int N>
-__global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_b(ConvArgs<float> P, int g0) {
-    constexpr int NT = threads_for(N);
+__global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_a(ConvArgs<float> P, int g0) {
+    extern __shared__ float4 smem_v4[];
+    const int g = blockIdx.x, x = blockIdx.y;  // plane-major: the CTAs in flight share plane x
+    const GridView V = grid_view(P, g0, g, N);
+    int xa = 0, ga = 0;
+    const float* pf_plane = nullptr;  // orbital plane of the CTA ahead that this thread prefetches
+    if (threadIdx.x < 4 && ahead_cta(P.pf_ahead, ga, xa)) {
+        const GridView A = grid_view(P, g0, ga, N);
+        const int o = threadIdx.x == 0 ? A.d.i1 : threadIdx.x == 1 ? A.d.j1 : threadIdx.x == 2 ? A.d.i2 : A.d.j2;
+        if (o >= 0) pf_plane = A.psi + (size_t)o * P.ng + (size_t)xa * N * N;  // (j2 < 0: one pair)
+    }
+    body_a<N, threads_for(N)>(P, V, x, smem_v4, pf_plane);
+}
+
+// Pass B, one slab: slab ky of grid V: forward x-FFT (decimation in time),
+// * K(G)/Ng, inverse x-FFT (decimation in frequency); the middle three steps
+// share registers.  NT threads.
+template <int N, int NT>
+__device__ __forceinline__ void body_b(const ConvArgs<float>& P, const GridView& V, int ky, float4* smem_v4) {
     constexpr int NP = N * N;
     constexpr Plan2 pl = plan2(N);
     constexpr int RB = pl.r2, RA = pl.r1;  // N = RA * RB; the middle (the heaviest step) takes the stage with fewer butterflies
     constexpr bool KS = kslab_fits(N);
-    extern __shared__ float4 smem_v4[];
     C* b0 = reinterpret_cast<C*>(smem_v4);
     C* b1 = b0 + NP;
     float* ks = reinterpret_cast<float*>(b1 + NP);  // K(G)/Ng of this slab, [x][z] (KS)
     C* tw = reinterpret_cast<C*>(ks + (KS ? NP : 0));
     float* gx2 = reinterpret_cast<float*>(tw + N);
     float* gz2 = gx2 + N;
-    const int g = blockIdx.y, ky = blockIdx.x;
-    const GridView V = grid_view(P, g0, g, N);
     const float* ktab = V.ktab;
     const bool kstage = KS && ktab != nullptr;
     if (kstage) {
@@ -308,11 +312,6 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
         gz2[i] = P.g2[2][i];
     }
     C* base = V.scr + (size_t)ky * N;
-    {
-        int ka = 0, ga = 0;
-        if (threadIdx.x < N && ahead_cta(P.pf_ahead, ka, ga))
-            prefetch_l2(grid_view(P, g0, ga, N).scr + (size_t)threadIdx.x * NP + (size_t)ka * N, N * sizeof(C));
-    }
     // forward stage 1 (line = z): DFT_RB over n2 of x[n1 + RA n2], to y[n1 RB + k2]
     stage<N, RB, 1, -1, N, true, NT>(
         tw, [&](int z, int xx) { return base[(size_t)xx * NP + z]; },
@@ -374,34 +373,40 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
             for (int s = 0; s < RB; ++s) base[(size_t)(n1 + RA * s) * NP + z] = v[s];
         }
     }
-    (void)g0;
 }
 
-// Pass C: inverse FFT along y then z of plane x, then the W updates
-// (16-byte vector reductions) and the real-space pair energies.
+// Pass B: slab ky: forward x-FFT, * K(G)/Ng, inverse x-FFT.
 template <int N>
-__global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_c(ConvArgs<float> P, int g0) {
-    constexpr int NT = threads_for(N);
+__global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_b(ConvArgs<float> P, int g0) {
+    extern __shared__ float4 smem_v4[];
+    const int g = blockIdx.y, ky = blockIdx.x;
+    const GridView V = grid_view(P, g0, g, N);
+    {
+        int ka = 0, ga = 0;
+        if (threadIdx.x < N && ahead_cta(P.pf_ahead, ka, ga))
+            prefetch_l2(grid_view(P, g0, ga, N).scr + (size_t)threadIdx.x * N * N + (size_t)ka * N, N * sizeof(C));
+    }
+    body_b<N, threads_for(N)>(P, V, ky, smem_v4);
+}
+
+// Pass C, one plane: inverse FFT along y then z of plane x of grid V, then
+// the W updates (16-byte vector reductions) and the real-space pair
+// energies.  NT threads; red: 2 x (NT / 32) doubles of shared memory.
+template <int N, int NT>
+__device__ __forceinline__ void body_c(const ConvArgs<float>& P, const GridView& V, int x, float4* smem_v4,
+                                       double* red) {
     constexpr int NP = N * N;
     constexpr Plan2 pl = plan2(N);
-    extern __shared__ float4 smem_v4[];
     constexpr int LP = N + 1;  // buffer rows hold up to n + 1 complex values (the last stage writes pitch n)
     constexpr int P01 = pitch(N, 3), P12 = pitch(N, 4), P23 = pitch(N, 5);
     C* b0 = reinterpret_cast<C*>(smem_v4);
     C* b1 = b0 + N * LP;
     C* tw = b1 + N * LP;
-    __shared__ double red[2][(NT + 31) / 32];
-    const int g = blockIdx.x, x = blockIdx.y;  // plane-major: the CTAs in flight share plane x
-    const GridView V = grid_view(P, g0, g, N);
+    constexpr int NW = (NT + 31) / 32;
     const PairGrid d = V.d;
     for (int i = threadIdx.x; i < N; i += NT) tw[i] = P.tw[2][i];
     const size_t off = (size_t)x * NP;
     const C* in = V.scr + off;
-    {
-        int xa = 0, ga = 0;
-        if (threadIdx.x == 32 && ahead_cta(P.pf_ahead, ga, xa))
-            prefetch_l2(grid_view(P, g0, ga, N).scr + (size_t)xa * NP, NP * sizeof(C));
-    }
     stage<N, pl.r1, 1, +1, N, true, NT>(
         tw, [&](int z, int y) { return in[y * N + z]; }, [&](int z, int y, C v) { b0[y * P01 + z] = v; });
     if (P.pf_ahead > 0 && threadIdx.x < 8) {
@@ -476,15 +481,30 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
         sb += __shfl_xor_sync(0xffffffffu, sb, o);
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) { red[0][warp] = (double)sa; red[1][warp] = (double)sb; }
+    if (lane == 0) { red[warp] = (double)sa; red[NW + warp] = (double)sb; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double ta = 0.0, tbb = 0.0;
-        for (int w = 0; w < (NT + 31) / 32; ++w) { ta += red[0][w]; tbb += red[1][w]; }
+        for (int w = 0; w < NW; ++w) { ta += red[w]; tbb += red[NW + w]; }
         double* ep = V.ep + (size_t)x * 2;
         ep[0] = ta * V.dv;
         ep[1] = tbb * V.dv;
     }
+}
+
+// Pass C: inverse FFT along y then z of plane x, W updates and pair energies.
+template <int N>
+__global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_c(ConvArgs<float> P, int g0) {
+    extern __shared__ float4 smem_v4[];
+    __shared__ double red[2 * ((threads_for(N) + 31) / 32)];
+    const int g = blockIdx.x, x = blockIdx.y;  // plane-major: the CTAs in flight share plane x
+    const GridView V = grid_view(P, g0, g, N);
+    {
+        int xa = 0, ga = 0;
+        if (threadIdx.x == 32 && ahead_cta(P.pf_ahead, ga, xa))
+            prefetch_l2(grid_view(P, g0, ga, N).scr + (size_t)xa * N * N, N * N * sizeof(C));
+    }
+    body_c<N, threads_for(N)>(P, V, x, smem_v4, red);
 }
 
 // Launch pass 0/1/2 of a batch of nb complex grids.
@@ -522,4 +542,20 @@ inline bool enabled() {
 
 }  // namespace spec2
 
+namespace spec {
+
+// The out-of-place passes where two planes fit in shared memory, else the
+// in-place ones.  A merged launch (several systems, P.refs) takes the
+// out-of-place passes or none.
+template <int N>
+bool launch_any(int pass, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s) {
+    if constexpr (spec2::smem_max(N) <= 200 * 1024) {
+        // merged launches (P.refs) exist only in the one-grid out-of-place passes
+        if (spec2::enabled() || P.refs) return spec2::launch_one<N>(pass, nb, P, g0, s);
+    }
+    if (P.refs) return false;
+    return spec_launch_one<N>(pass, nb, P, g0, s);
+}
+
+}  // namespace spec
 }  // namespace lace

@@ -1,12 +1,11 @@
-// Host-only checks of the launch plans of the out-of-place FFT passes, one
-// grid per CTA (pairconv_spec2.cuh) and two grids per CTA
-// (pairconv_pair.cuh), for every size-specialised cubic grid: a two-radix
+// Host-only checks of the launch plans of the out-of-place FFT passes
+// (pairconv_spec2.cuh) for every size-specialised cubic grid: a two-radix
 // plan, thread counts, register caps and shared memory that fit one SM at
-// the planned number of CTAs.  Prints one line per size and kind; exit code
-// = number of failed checks.
+// the planned number of CTAs.  Prints one line per size; exit code = number
+// of failed checks.
 #include <cstdio>
 
-#include "pairconv_pair.cuh"
+#include "pairconv_spec2.cuh"
 
 int main() {
     using namespace lace::spec2;
@@ -31,26 +30,6 @@ int main() {
             if (smem_bytes(n, pass) + 1024 > 227u * 1024u) ++fails;
         std::printf("n=%d plan=%dx%d threads=%d ctas=%d regs=%d smem_max=%zu kslab=%d %s\n", n, p.r1, p.r2, nt, m,
                     regs, smem_max(n), (int)kslab_fits(n), fails ? "FAIL" : "ok");
-        bad += fails;
-    }
-    for (int n : sizes) {
-        if (!lace::pair2::fits(n)) continue;
-        namespace q = lace::pair2;
-        const Plan2 p = plan2(n);
-        const int nt = q::threads_for(n), m = q::blocks_at(n, nt), regs = q::max_regs(n);
-        const int warps = (nt + 31) / 32;
-        const int a = n * (n / p.r1), b = n * (n / p.r2);
-        const int lo = ((a < b ? a : b) + 31) / 32 * 32;
-        int fails = 0;
-        if (nt % 32 || nt > 1024 || nt < (lo < 1024 ? lo : 1024)) ++fails;
-        if (m < 1 || m * nt > 2048) ++fails;
-        if (regs < 64 || regs > 255 || regs % 8) ++fails;
-        if ((m * warps + 3) / 4 * 32 * regs > 16384) ++fails;
-        if ((size_t)m * (q::smem_max(n) + 1024) > 227u * 1024u) ++fails;
-        for (int pass = 0; pass < 3; ++pass)
-            if (q::smem_bytes(n, pass) + 1024 > 227u * 1024u) ++fails;
-        std::printf("pair n=%d plan=%dx%d threads=%d ctas=%d regs=%d smem_max=%zu kslab=%d %s\n", n, p.r1, p.r2, nt, m,
-                    regs, q::smem_max(n), (int)q::kslab_fits(n), fails ? "FAIL" : "ok");
         bad += fails;
     }
     return bad;
