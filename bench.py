@@ -16,6 +16,7 @@ no collective on the data path); rank 0 prints one JSON line.
 from __future__ import annotations
 
 import argparse
+from concurrent.futures import ThreadPoolExecutor
 import json
 import os
 import statistics
@@ -441,7 +442,8 @@ SERVE_RATE = 200.0        # offered requests per second over all systems
 SERVE_MAX_INNER = 8       # inner-loop K_ACE applications per ACE rebuild at most
 SERVE_BLOCK = 32          # functions per application (a block of trial vectors)
 SERVE_EPS = 1e-3          # SCF-like drift of the orbitals between rebuilds
-SERVE_INNER_DECAY = 0.3   # the inner loop's block moves by SERVE_EPS x decay^k at its k-th step
+SERVE_INNER_EPS = 1e-2    # the inner loop's block moves by SERVE_INNER_EPS x decay^k at its k-th step
+SERVE_INNER_DECAY = 0.5
 SERVE_CADENCE_TOL = 1e-5  # rebuild once the block's ACE energy moves by less than this (relative)
 
 
@@ -451,18 +453,20 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
     the double loop of the paper (Sec. 2): an outer iteration is a REBUILD
     (orthonormalise, SCDM, screen, pair convolutions, ACE build); its inner
     loop applies that ACE projector (APPLY: K_ACE on a block of SERVE_BLOCK
-    functions) to a block that moves by SERVE_EPS x SERVE_INNER_DECAY^k at
-    step k, until the server reports the block's ACE energy converged
+    functions) to a block that moves by SERVE_INNER_EPS x SERVE_INNER_DECAY^k
+    at step k, until the server reports the block's ACE energy converged
     (relative change below SERVE_CADENCE_TOL; at most SERVE_MAX_INNER
     applies); then the orbitals drift by SERVE_EPS and the next REBUILD
     follows, for `iters` outer iterations.  Request k of a system arrives at
     its Poisson time (rate SERVE_RATE / n_systems per system, seeded) and is
-    submitted at max(arrival, completion of request k-1): a client sends its
-    next request only after the previous result.  Latency = submission to
+    submitted at max(arrival, completion of request k-1, the client's own
+    host work for it): a client sends its next request only after the
+    previous result, and prepares it (drift, next block) on a host thread.  Latency = submission to
     completion (the server's), response = arrival to completion.  Mixed
     precision (or plain FP64 with fp64=True); memory admission with the
-    default budget (90% of free device memory); REBUILDs on one grid size
-    share pass launches (merged pair convolutions)."""
+    default budget (90% of free device memory); queued REBUILDs on one grid
+    size are admitted in groups and share pass launches (merged pair
+    convolutions)."""
     import synth
     import torch
 
@@ -500,6 +504,28 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
     inner_counts, due_count = [], 0
     peak_running, peak_bytes = 0, 0
     fails = []
+
+    def prep_rebuild(k, drift):
+        # SCF-like drift of the orbitals; the inner loop's block starts from them
+        t = time.perf_counter()
+        if drift:
+            synth.perturb_in_place(phis[k], SERVE_EPS)
+        blocks[k][...] = phis[k][: len(blocks[k])]
+        return time.perf_counter() - t
+
+    def prep_apply(k, i):
+        # the inner loop's block moves less at every step
+        t = time.perf_counter()
+        if i > 0:
+            synth.perturb_in_place(blocks[k], SERVE_INNER_EPS * SERVE_INNER_DECAY ** i)
+        return time.perf_counter() - t
+
+    # the clients' host work (drift of up to 4 GB of orbitals a system) runs
+    # on a thread pool so that one client's preparation does not hold up the
+    # others' submissions
+    pool = ThreadPoolExecutor(max_workers=max(1, min(16, os.cpu_count() or 1)))
+    prep = [None] * n_systems
+    prep_s = 0.0
     t_start = time.perf_counter()
     done_all = 0
     finished = [False] * n_systems
@@ -535,17 +561,20 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
                     finished[k] = True
                     done_all += 1
                     continue
-            if outstanding[k] is None and now >= arrivals[k][step[k]]:
+            if outstanding[k] is None and prep[k] is None:
+                # the client's own work before its next request, on a host thread
                 if next_kind[k] == "rebuild":
-                    if outer[k] > 0:
-                        synth.perturb_in_place(phis[k], SERVE_EPS)
+                    prep[k] = pool.submit(prep_rebuild, k, outer[k] > 0)
+                else:
+                    prep[k] = pool.submit(prep_apply, k, inner[k])
+            if outstanding[k] is None and prep[k].done() and now >= arrivals[k][step[k]]:
+                prep_s += prep[k].result()
+                prep[k] = None
+                if next_kind[k] == "rebuild":
                     outstanding[k] = (srv.submit_rebuild(sids[k], phis[k]), "rebuild")
                     outer[k] += 1
                     inner[k] = 0
-                    blocks[k][...] = phis[k][: len(blocks[k])]
                 else:
-                    if inner[k] > 0:  # the inner loop's block moves less at every step
-                        synth.perturb_in_place(blocks[k], SERVE_EPS * SERVE_INNER_DECAY ** inner[k])
                     outstanding[k] = (srv.submit_apply(sids[k], blocks[k], outs[k]), "apply")
                     inner[k] += 1
                 step[k] += 1
@@ -554,6 +583,7 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
         peak_bytes = max(peak_bytes, st["bytes_resident"])
         time.sleep(0.0005)
     makespan = time.perf_counter() - t_start
+    pool.shutdown()
     merge = srv.merge_stats()
     srv.close()
     # accuracy: the last rebuild of the smallest systems against the plain FP64 GPU form
@@ -597,6 +627,7 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
         "peak_resident_GB": round(peak_bytes / 1e9, 2),
         "dE_x_vs_fp64_gpu_Ha": {"max": max(dex) if dex else None, "systems": len(dex)},
         "orbital_generation_s": round(gen_s, 1),
+        "client_host_prep_s": round(prep_s, 1),
     }
 
 

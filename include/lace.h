@@ -358,16 +358,21 @@ lace_status lace_server_apply_info(lace_server* srv, long long request_id, doubl
  * (blocks until then); later requests for it fail with LACE_ERR_ARG. */
 lace_status lace_server_remove_system(lace_server* srv, int system_id);
 
-/* Merged pair convolutions across requests (on by default, window 5 ms).
+/* Merged pair convolutions across requests (on by default, window 50 ms).
  * The REBUILDs of systems on one cubic grid size with size-specialised
  * passes (n in {24, 32, 36, 40, 48, 60, 64, 72, 80, 96, 100}, mixed
  * precision) that reach their exchange step together share every launch of
  * the FFT passes: one launch per pass covers the next chunk of complex grids
  * of every such system, each grid resolving its own system's orbitals, W,
- * kernel table and scratch.  The first REBUILD to arrive waits at most
- * window_ms (0..10000) for the others of its size still on their way there.
- * Results are those of the REBUILDs run alone (the same arithmetic per
- * grid).  Call while no request is queued or running (LACE_ERR_STATE
+ * kernel table and scratch.  The scheduler admits such REBUILDs in groups:
+ * when one starts, up to 3 queued REBUILDs of other idle systems on the same
+ * grid (each its system's oldest queued request, within the memory budget)
+ * start with it, the group taking one rebuild slot and going ahead of
+ * requests queued before its companions.  The first REBUILD of a size to
+ * reach its exchange step waits at most window_ms (0..10000) for the others
+ * of that size already started.  Results are those of the REBUILDs run alone
+ * (the same arithmetic per grid).  enable = 0 turns off both the merging and
+ * the groups.  Call while no request is queued or running (LACE_ERR_STATE
  * otherwise). */
 lace_status lace_server_set_pair_merging(lace_server* srv, int enable, double window_ms);
 

@@ -414,7 +414,7 @@ class Server:
         self._check(self.lib.lace_server_set_rebuild_tolerance(self.h, int(system), float(tol)),
                     "lace_server_set_rebuild_tolerance")
 
-    def set_pair_merging(self, enable: bool = True, window_ms: float = 5.0):
+    def set_pair_merging(self, enable: bool = True, window_ms: float = 50.0):
         self._check(self.lib.lace_server_set_pair_merging(self.h, int(bool(enable)), float(window_ms)),
                     "lace_server_set_pair_merging")
 

@@ -5,9 +5,10 @@
 //   * every radix stage reads one shared-memory plane and writes the other
 //     (ping-pong), so a thread keeps one butterfly live and a stage ends in
 //     one barrier instead of two;
-//   * the first stage of a pass loads its butterfly straight from global
-//     memory (pass A forms rho = w_i psi_j there) and the last stage of
-//     passes A and B stores straight to global memory;
+//   * pass A forms rho = w_i psi_j with 16-byte loads into the second
+//     plane buffer; the first stage of pass B loads its butterflies straight
+//     from global memory, and the last stage of passes A and B stores
+//     straight to global memory;
 //   * pass B runs the forward x-FFT as decimation in time and the inverse as
 //     decimation in frequency, so the second forward stage, the product
 //     with K(G)/Ng and the first inverse stage act on the same registers:
@@ -224,6 +225,7 @@ __device__ __forceinline__ void stage(const C* __restrict__ tw, Ld ld, St st) {
 template <int N, int NT>
 __device__ __forceinline__ void body_a(const ConvArgs<float>& P, const GridView& V, int x, float4* smem_v4,
                                        const float* pf_plane) {
+    static_assert(N % 2 == 0, "pass A reads orbital planes as 16-byte vectors");
     constexpr int NP = N * N;
     constexpr Plan2 pl = plan2(N);
     constexpr int LP = N + 1;  // buffer rows hold up to n + 1 complex values
@@ -239,16 +241,29 @@ __device__ __forceinline__ void body_a(const ConvArgs<float>& P, const GridView&
     const float* c1 = V.psi + (size_t)d.j1 * P.ng + off;
     const float* a2 = V.psi + (size_t)(two ? d.i2 : d.i1) * P.ng + off;
     const float* c2 = V.psi + (size_t)(two ? d.j2 : d.j1) * P.ng + off;
-    // z lines (line = y): rho straight from the orbitals
+    // rho of the plane into b1 (pitch n) with 16-byte loads, four points a
+    // thread (one load instruction per orbital per four points; n is even, so
+    // every plane starts on a 16-byte boundary), then the z lines (line = y)
+    {
+        const float4* A1 = reinterpret_cast<const float4*>(a1);
+        const float4* C1 = reinterpret_cast<const float4*>(c1);
+        const float4* A2 = reinterpret_cast<const float4*>(a2);
+        const float4* C2 = reinterpret_cast<const float4*>(c2);
+        float4* r4 = reinterpret_cast<float4*>(b1);
+        for (int e = threadIdx.x; e < NP / 4; e += NT) {
+            const float4 x1 = __ldg(A1 + e), y1 = __ldg(C1 + e);
+            float4 x2 = make_float4(0.f, 0.f, 0.f, 0.f), y2 = x2;
+            if (two) {
+                x2 = __ldg(A2 + e);
+                y2 = __ldg(C2 + e);
+            }
+            r4[2 * e] = make_float4(x1.x * y1.x, x2.x * y2.x, x1.y * y1.y, x2.y * y2.y);
+            r4[2 * e + 1] = make_float4(x1.z * y1.z, x2.z * y2.z, x1.w * y1.w, x2.w * y2.w);
+        }
+    }
+    __syncthreads();
     stage<N, pl.r1, 1, -1, N, false, NT>(
-        tw,
-        [&](int y, int z) {
-            const int q = y * N + z;
-            const float u = __ldg(a1 + q) * __ldg(c1 + q);
-            const float v = two ? __ldg(a2 + q) * __ldg(c2 + q) : 0.f;
-            return C{u, v};
-        },
-        [&](int y, int z, C v) { b0[y * P01 + z] = v; });
+        tw, [&](int y, int z) { return b1[y * N + z]; }, [&](int y, int z, C v) { b0[y * P01 + z] = v; });
     __syncthreads();
     stage<N, pl.r2, pl.r1, -1, N, false, NT>(
         tw, [&](int y, int z) { return b0[y * P01 + z]; }, [&](int y, int z, C v) { b1[y * P12 + z] = v; });

@@ -52,7 +52,7 @@ class PairMerger {
     };
 
     bool enabled = true;
-    double window_ms = 5.0;
+    double window_ms = 50.0;
     int device = 0;
 
     ~PairMerger() {
@@ -292,6 +292,9 @@ struct GpuExec {
 
 }  // namespace
 
+// REBUILDs of one grid size admitted together when pair merging is on.
+constexpr int kRebuildGroup = 4;
+
 struct lace_server {
     GpuExec exec;
     PairMerger merger;
@@ -325,6 +328,7 @@ lace_status lace_server_create(lace_server** out, int device, int precision, int
     s->merger.device = device;
     s->exec.merger = &s->merger;
     s->sched = new lace_serve::Scheduler<GpuExec>(s->exec, slots, rebuild_slots, (size_t)mem_bytes);
+    s->sched->set_rebuild_group(kRebuildGroup);
     *out = s;
     return LACE_OK;
 }
@@ -387,6 +391,7 @@ lace_status lace_server_set_pair_merging(lace_server* s, int enable, double wind
     if (running || queued) return LACE_ERR_STATE;
     s->merger.enabled = enable != 0;
     s->merger.window_ms = window_ms;
+    s->sched->set_rebuild_group(enable ? kRebuildGroup : 1);
     return LACE_OK;
 }
 

@@ -16,6 +16,8 @@
 //   int run(const SystemDesc&, Handle&, Request&);        // status code (0 = ok); fills ex / n_pairs /
 //                                                         // e_block (APPLY) / err
 //   void release(Handle&);                                // free the system's memory
+//   int merge_key(const SystemDesc&);                     // REBUILDs of systems with one nonzero key can
+//                                                         // share their pair-convolution launches (0: never)
 #pragma once
 
 #include <algorithm>
@@ -173,6 +175,12 @@ class Scheduler {
         return S_OK;
     }
 
+    // Largest group of REBUILDs admitted together (see pick); 1: none.
+    void set_rebuild_group(int max_group) {
+        std::lock_guard<std::mutex> lk(mu_);
+        group_max_ = std::max(1, std::min(max_group, kMaxGroup));
+    }
+
     // Relative tolerance of a system's rebuild cadence (0: off).
     int set_rebuild_tolerance(int sys, double tol) {
         std::lock_guard<std::mutex> lk(mu_);
@@ -203,6 +211,13 @@ class Scheduler {
         return S_OK;
     }
 
+    // REBUILD groups admitted so far (more than one request) and their requests.
+    void group_stats(long long* groups, long long* requests) {
+        std::lock_guard<std::mutex> lk(mu_);
+        if (groups) *groups = groups_;
+        if (requests) *requests = grouped_;
+    }
+
     void stats(size_t* held, int* running, int* queued) {
         std::lock_guard<std::mutex> lk(mu_);
         size_t h = 0;
@@ -225,6 +240,13 @@ class Scheduler {
 
     bool valid(int sys) const { return sys >= 0 && sys < (int)systems_.size() && systems_[sys]->alive; }
 
+    static constexpr int kMaxGroup = 8;
+
+    struct Pick {
+        std::shared_ptr<Request> r;
+        size_t growth;
+    };
+
     size_t committed() const {
         size_t b = 0;
         for (auto& s : systems_) b += s->held + (s->busy ? s->growth : 0);
@@ -234,8 +256,14 @@ class Scheduler {
     // Under mu_: the earliest pending request whose system is idle, that is
     // its system's oldest pending request, whose growth fits the budget and,
     // for a REBUILD, for which a rebuild slot is free.  A request that cannot
-    // fit even with nothing running completes with S_ERR_OOM.
-    std::shared_ptr<Request> pick(size_t* growth_out) {
+    // fit even with nothing running completes with S_ERR_OOM (growth -1).
+    // A REBUILD whose system has a merge key takes with it, as one group in
+    // one rebuild slot, up to group_max_ - 1 REBUILDs of other idle systems
+    // with the same key that are their systems' oldest pending requests and
+    // fit the budget beside it: the group runs at once, so its members reach
+    // their pair convolutions together and the executor can merge their
+    // launches.  Companions go ahead of requests queued before them.
+    std::vector<Pick> pick() {
         std::vector<char> seen(systems_.size(), 0);
         const size_t used = committed();
         for (auto it = pending_.begin(); it != pending_.end(); ++it) {
@@ -248,53 +276,105 @@ class Scheduler {
             const size_t after = exec_.predict(s.d, s.h, r->kind, r->n);
             const size_t growth = after > s.held ? after - s.held : 0;
             if (used + growth <= budget_) {
+                std::vector<Pick> group{{r, growth}};
                 pending_.erase(it);
-                *growth_out = growth;
-                return r;
+                const int key = r->kind == REQ_REBUILD && group_max_ > 1 ? exec_.merge_key(s.d) : 0;
+                if (key) add_companions(r->sys, key, used + growth, group);
+                return group;
             }
             // nothing else can release memory: this request never fits
             if (running_ == 0 && used - s.held + after > budget_) {
                 pending_.erase(it);
-                *growth_out = (size_t)-1;
-                return r;
+                return {{r, (size_t)-1}};
             }
         }
-        return nullptr;
+        return {};
+    }
+
+    void add_companions(int first_sys, int key, size_t used, std::vector<Pick>& group) {
+        std::vector<char> seen(systems_.size(), 0);
+        seen[first_sys] = 1;
+        for (auto it = pending_.begin(); it != pending_.end() && (int)group.size() < group_max_;) {
+            auto r = *it;
+            Sys& s = *systems_[r->sys];
+            if (seen[r->sys]) {
+                ++it;
+                continue;
+            }
+            seen[r->sys] = 1;  // only a system's oldest pending request may run
+            if (s.busy || r->kind != REQ_REBUILD || exec_.merge_key(s.d) != key) {
+                ++it;
+                continue;
+            }
+            const size_t after = exec_.predict(s.d, s.h, r->kind, r->n);
+            const size_t growth = after > s.held ? after - s.held : 0;
+            if (used + growth > budget_) {
+                ++it;
+                continue;
+            }
+            used += growth;
+            group.push_back({r, growth});
+            it = pending_.erase(it);
+        }
     }
 
     void work() {
         std::unique_lock<std::mutex> lk(mu_);
         for (;;) {
-            size_t growth = 0;
-            std::shared_ptr<Request> r;
-            work_cv_.wait(lk, [&] { return stop_ || (r = pick(&growth)) != nullptr; });
-            if (!r) return;  // stop_ with nothing runnable
-            Sys& s = *systems_[r->sys];
-            if (growth == (size_t)-1) {
-                r->err = "the request does not fit the device-memory budget beside the resident systems";
-                finish(s, *r, S_ERR_OOM);
+            std::vector<Pick> group;
+            work_cv_.wait(lk, [&] { return stop_ || !(group = pick()).empty(); });
+            if (group.empty()) return;  // stop_ with nothing runnable
+            if (group[0].growth == (size_t)-1) {
+                Request& r = *group[0].r;
+                r.err = "the request does not fit the device-memory budget beside the resident systems";
+                finish(*systems_[r.sys], r, S_ERR_OOM);
                 continue;
             }
-            const bool rebuild = r->kind == REQ_REBUILD;
-            s.busy = true;
-            s.growth = growth;
-            running_++;
-            rebuilds_running_ += rebuild;
-            lk.unlock();
-            const int st = exec_.run(s.d, s.h, *r);
-            const size_t held = exec_.held(s.h);
-            lk.lock();
-            s.held = held;
-            s.busy = false;
-            s.growth = 0;
-            running_--;
-            rebuilds_running_ -= rebuild;
-            if (st == S_OK) {
-                if (rebuild) s.cadence.rebuilt();
-                else r->rebuild_due = s.cadence.applied(r->n, r->e_block);
+            const bool rebuild = group[0].r->kind == REQ_REBUILD;
+            std::vector<Sys*> sys;  // taken under mu_ (add_system may grow systems_)
+            for (auto& g : group) {
+                Sys* s = systems_[g.r->sys].get();
+                s->busy = true;
+                s->growth = g.growth;
+                sys.push_back(s);
             }
-            finish(s, *r, st);
-            work_cv_.notify_all();  // memory and the system are free again
+            running_ += (int)group.size();
+            rebuilds_running_ += rebuild;  // a group takes one rebuild slot
+            if (group.size() > 1) groups_++, grouped_ += (long long)group.size();
+            lk.unlock();
+            // the companions on threads of their own, the first request here
+            std::vector<int> st(group.size(), S_OK);
+            std::vector<size_t> held(group.size(), 0);
+            auto run_one = [&](size_t k) {
+                st[k] = exec_.run(sys[k]->d, sys[k]->h, *group[k].r);
+                held[k] = exec_.held(sys[k]->h);
+            };
+            std::vector<std::thread> helpers;
+            for (size_t k = 1; k < group.size(); ++k) {
+                try {
+                    helpers.emplace_back(run_one, k);
+                } catch (...) {
+                    run_one(k);  // no thread to be had: one after the other (the merge is then skipped)
+                }
+            }
+            run_one(0);
+            for (auto& t : helpers) t.join();
+            lk.lock();
+            for (size_t k = 0; k < group.size(); ++k) {
+                Request& r = *group[k].r;
+                Sys& s = *sys[k];
+                s.held = held[k];
+                s.busy = false;
+                s.growth = 0;
+                if (st[k] == S_OK) {
+                    if (rebuild) s.cadence.rebuilt();
+                    else r.rebuild_due = s.cadence.applied(r.n, r.e_block);
+                }
+            }
+            running_ -= (int)group.size();
+            rebuilds_running_ -= rebuild;
+            for (size_t k = 0; k < group.size(); ++k) finish(*sys[k], *group[k].r, st[k]);
+            work_cv_.notify_all();  // memory and the systems are free again
         }
     }
 
@@ -319,6 +399,8 @@ class Scheduler {
     long long next_id_ = 1;
     int running_ = 0, rebuilds_running_ = 0;
     bool stop_ = false;
+    int group_max_ = 4;
+    long long groups_ = 0, grouped_ = 0;
 };
 
 }  // namespace lace_serve

@@ -15,6 +15,8 @@
 
 using namespace lace_serve;
 
+constexpr int kMergeable = 1 << 8;  // a flag of the fake executor's systems
+
 struct FakeExec {
     // a system holds n_occ units once built; a REBUILD needs n_occ + n_extra
     // units while it runs; s_thr is the request's duration in seconds.
@@ -73,11 +75,13 @@ struct FakeExec {
         return st;
     }
     void release(Handle& h) { h = Handle{}; }
+    // systems flagged kMergeable share a key per grid size
+    int merge_key(const SystemDesc& d) const { return (d.flags & kMergeable) ? d.n[0] : 0; }
     double ms() { return std::chrono::duration<double, std::milli>(Clock::now() - t0).count(); }
 };
 
-static SystemDesc sys_desc(int base, int transient, double seconds) {
-    return SystemDesc{{10, 10, 10}, {16, 16, 16}, 10.0, base, transient, seconds, 0};
+static SystemDesc sys_desc(int base, int transient, double seconds, int grid = 16, bool mergeable = false) {
+    return SystemDesc{{10, 10, 10}, {grid, grid, grid}, 10.0, base, transient, seconds, mergeable ? kMergeable : 0};
 }
 
 struct Sub {
@@ -190,6 +194,23 @@ int main() {
         std::vector<SystemDesc> sys{sys_desc(10, 10, 0.03), sys_desc(10, 10, 0.1), sys_desc(10, 10, 0.1)};
         std::vector<Sub> subs{{0, REQ_REBUILD}, {1, REQ_REBUILD}, {2, REQ_REBUILD}, {0, REQ_APPLY}, {0, REQ_APPLY}};
         scenario("rebuild_slots", 4, 1000, sys, subs, -1, -1, /*rebuild_slots=*/1);
+    }
+    // REBUILD groups: one rebuild slot, first held by system 3 (another grid)
+    // while the others queue; systems 0 and 2 share a grid and can merge,
+    // system 1 is on another grid.  When the slot frees, 0 and 2 start
+    // together as one group ahead of 1, which waits for the group's slot.
+    {
+        std::vector<SystemDesc> sys{sys_desc(10, 10, T, 16, true), sys_desc(10, 10, T, 24, true),
+                                    sys_desc(10, 10, T, 16, true), sys_desc(10, 10, T, 32, false)};
+        std::vector<Sub> subs{{3, REQ_REBUILD}, {0, REQ_REBUILD}, {1, REQ_REBUILD}, {2, REQ_REBUILD}};
+        scenario("group", 4, 1000, sys, subs, -1, -1, /*rebuild_slots=*/1);
+    }
+    // a group only within the memory budget: each rebuild needs 70 of 100
+    // while it runs, so 0 and 1 (same grid) run one after the other
+    {
+        std::vector<SystemDesc> sys{sys_desc(30, 40, T, 16, true), sys_desc(30, 40, T, 16, true)};
+        std::vector<Sub> subs{{0, REQ_REBUILD}, {1, REQ_REBUILD}};
+        scenario("group_memory", 4, 100, sys, subs);
     }
     // rebuild cadence: the inputs of an inner loop converge geometrically
     // (factor 1 + 0.5^k); a REBUILD resets the comparison

@@ -8,8 +8,11 @@ count; one system's requests run in submission order; an apply before the
 first rebuild fails with the state error; memory admission makes a request
 wait while its growth does not fit and fails it with the out-of-memory status
 when it can never fit; removing a system frees its memory; a rebuild-slot
-limit keeps slots free for applies; the rebuild cadence reports a rebuild as
-due once the block energy of consecutive applies has converged.
+limit keeps slots free for applies; a REBUILD starts together with a queued
+REBUILD on the same grid as one group in one rebuild slot (so that the two
+can share pass launches), but only within the memory budget; the
+rebuild cadence reports a rebuild as due once the block energy of
+consecutive applies has converged.
 """
 import json
 import os
@@ -112,3 +115,26 @@ def test_rebuild_is_due_once_the_inner_loop_has_converged(runs):
     assert 9 <= first_due <= 12 and all(expect[first_due:])
     assert q[15]["kind"] == REBUILD
     assert [bool(x["rebuild_due"]) for x in q[16:]] == [False, True]  # the same block twice after the rebuild
+
+
+def test_rebuilds_on_one_grid_start_together_as_one_group(runs):
+    """REBUILD groups: with one rebuild slot, system 2 (system 0's grid)
+    starts with system 0 as one group once the slot frees, ahead of system 1
+    submitted before it, and 1 waits for the group's slot.  Every request
+    runs once and succeeds."""
+    run = runs["group"]
+    q = {x["sys"]: x for x in run["requests"]}
+    assert all(x["status"] == OK for x in q.values())
+    assert q[0]["start"] >= q[3]["end"] - 1e-3
+    assert abs(q[2]["start"] - q[0]["start"]) < 20
+    assert q[1]["start"] >= max(q[0]["end"], q[2]["end"]) - 1e-3
+    assert run["max_rebuilding"] == 2  # the group ran at once in one slot
+
+
+def test_rebuild_group_stays_within_the_memory_budget(runs):
+    """Two REBUILDs on one grid that do not fit the budget together run one
+    after the other, not as a group."""
+    q = {x["sys"]: x for x in runs["group_memory"]["requests"]}
+    assert all(x["status"] == OK for x in q.values())
+    first, second = sorted(q.values(), key=lambda x: x["start"])
+    assert second["start"] >= first["end"] - 1e-3
