@@ -360,7 +360,7 @@ lace_status lace_server_remove_system(lace_server* srv, int system_id);
 
 /* Merged pair convolutions across requests (on by default, window 50 ms).
  * The REBUILDs of systems on one cubic grid size with size-specialised
- * passes (n in {24, 32, 36, 40, 48, 60, 64, 72, 80, 96, 100}, mixed
+ * passes (n in {24, 32, 36, 40, 48, 50, 54, 60, 64, 72, 80, 96, 100}, mixed
  * precision) that reach their exchange step together share every launch of
  * the FFT passes: one launch per pass covers the next chunk of complex grids
  * of every such system, each grid resolving its own system's orbitals, W,
@@ -441,12 +441,19 @@ lace_ctx* lace_batch_context(lace_batch* batch, int inst);
  * milliseconds of the last run ([0] setup, host; [1] pair convolutions,
  * device, of the last eager run or of the autotuned shape; [2] pair
  * convolutions + energies + ACE builds, device; [3] the whole call, host) and the timed candidates
- * (-1: did not fit; seven persistent launch shapes 128x1, 128x2, 128x3,
- * 128x4, 256x1, 256x2, 512x1, then the per-instance mode).  The shape
+ * (-1: did not fit; eight persistent launch shapes 128x1, 128x2, 128x3,
+ * 128x4, 256x1, 256x2, 512x1, 512x2, then the per-instance mode).  The shape
  * outputs name the best persistent shape even when the per-instance mode
- * was kept (it was when its time is the smallest).  Any output may be NULL. */
+ * was kept (it was when its time is the smallest).  The environment variable
+ * LACE_BATCH_SHAPE=<threads>x<ctas> restricts the persistent kernel to one
+ * shape and keeps it (for tests).  Any output may be NULL. */
 lace_status lace_batch_info(lace_batch* batch, int* threads, int* ctas_per_sm, int* chunks, long long* graph_replays,
                             long long* launches, double* ms_out, double* tune_ms_out, int tune_count);
+
+/* The mode the batch runs its pair convolutions in: *per_instance = 1 for
+ * the per-instance single-system passes, 0 for the persistent kernel (before
+ * the first run: 0).  LACE_ERR_ARG for a null argument. */
+lace_status lace_batch_mode(lace_batch* batch, int* per_instance);
 
 /* Message of the last failed batch call. */
 const char* lace_batch_last_error(lace_batch* batch);

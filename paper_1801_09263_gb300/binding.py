@@ -99,6 +99,7 @@ def load_library(build_if_missing: bool = False):
         "lace_batch_run": ([P, P, P], I),
         "lace_batch_context": ([P, I], P),
         "lace_batch_info": ([P, P, P, P, P, P, P, P, I], I),
+        "lace_batch_mode": ([P, P], I),
         "lace_batch_last_error": ([P], C.c_char_p),
         "lace_server_stats": ([P, P, P, P], I),
         "lace_server_set_pair_merging": ([P, I, D], I),
@@ -430,7 +431,7 @@ class _Instance(C.Structure):
                 ("ecut_ha", C.c_double), ("n_occ", C.c_int), ("s_thr", C.c_double)]
 
 
-TUNE_SHAPES = ((128, 1), (128, 2), (128, 3), (128, 4), (256, 1), (256, 2), (512, 1))
+TUNE_SHAPES = ((128, 1), (128, 2), (128, 3), (128, 4), (256, 1), (256, 2), (512, 1), (512, 2))
 
 
 class Batch:
@@ -511,8 +512,9 @@ class Batch:
         tune = np.zeros(len(TUNE_SHAPES) + 1, dtype=np.float64)
         self._check(self.lib.lace_batch_info(self.h, C.byref(th), C.byref(ct), C.byref(ch), C.byref(rp), C.byref(ln),
                                              _ptr(ms), _ptr(tune), len(tune)), "lace_batch_info")
-        shapes = [t for t in tune[:-1] if t >= 0]
-        per_instance = tune[-1] > 0 and (not shapes or tune[-1] < min(shapes))
+        pi = C.c_int(0)
+        self._check(self.lib.lace_batch_mode(self.h, C.byref(pi)), "lace_batch_mode")
+        per_instance = pi.value != 0
         tune_ms = {f"{a}x{b}": round(float(t), 3) for (a, b), t in zip(TUNE_SHAPES, tune)}
         tune_ms["per_instance"] = round(float(tune[-1]), 3)
         return dict(threads=th.value, ctas_per_sm=ct.value, chunks=ch.value, graph_replays=rp.value,

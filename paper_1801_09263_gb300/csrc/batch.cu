@@ -26,6 +26,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <thread>
@@ -99,7 +100,8 @@ struct lace_batch {
     std::vector<cudaEvent_t> ev_ready;
     DevBuf inst, ngrids, pool, epart, bar;
     int* h_ngrids = nullptr;  // pinned
-    size_t pool_elems = 0, epart_elems = 0, smem = 0;
+    size_t pool_elems = 0, epart_elems = 0, smem = 0;  // smem: what one item needs
+    size_t smem_run = 0;                                 // dynamic shared memory of the chosen launch shape
     int threads = 0, ctas = 0, chunks = 0;
     int mode = 0;  // 0: one persistent multi-instance launch per chunk; 1: per-instance specialised passes
     bool prepared = false;
@@ -287,21 +289,27 @@ lace_status pairconv_per_instance(lace_batch* b, cudaStream_t s, int* launches) 
 // Time every launch shape once on the real batch, and the per-instance mode
 // (W and E are zeroed by the hot part afterwards).
 lace_status autotune(lace_batch* b) {
-    const int cand[][2] = {{128, 1}, {128, 2}, {128, 3}, {128, 4}, {256, 1}, {256, 2}, {512, 1}};
+    const int cand[][2] = {{128, 1}, {128, 2}, {128, 3}, {128, 4}, {256, 1}, {256, 2}, {512, 1}, {512, 2}};
     const MultiArgs A = multi_args(b);
     const int chunks = std::max(1, chunks_for(b));
     float best = 1e30f;
     b->tune.clear();
+    // LACE_BATCH_SHAPE=<threads>x<ctas per SM> keeps only that persistent shape
+    int force_t = 0, force_c = 0;
+    if (const char* fs = getenv("LACE_BATCH_SHAPE")) {
+        if (sscanf(fs, "%dx%d", &force_t, &force_c) != 2) force_t = force_c = 0;
+    }
     for (const auto& cd : cand) {
-        const int occ = pairconv_multi_occupancy(cd[0], b->smem);
-        if (occ < cd[1]) {
+        const bool skip = force_t && (cd[0] != force_t || cd[1] != force_c);
+        const size_t smem = skip ? 0 : pairconv_multi_cta_smem(cd[0], cd[1], b->smem);
+        if (!smem) {
             b->tune.push_back(-1.0);
             continue;
         }
         int l = 0;
-        BCK(pairconv_multi_run(A, chunks, b->smem, cd[0], cd[1], b->main, &l), "autotune");  // warm-up
+        BCK(pairconv_multi_run(A, chunks, smem, cd[0], cd[1], b->main, &l), "autotune");  // warm-up
         BCK(cudaEventRecord(b->ev_pc0, b->main), "autotune");
-        BCK(pairconv_multi_run(A, chunks, b->smem, cd[0], cd[1], b->main, &l), "autotune");
+        BCK(pairconv_multi_run(A, chunks, smem, cd[0], cd[1], b->main, &l), "autotune");
         BCK(cudaEventRecord(b->ev_pc1, b->main), "autotune");
         BCK(cudaEventSynchronize(b->ev_pc1), "autotune");
         float ms = 0.f;
@@ -312,6 +320,7 @@ lace_status autotune(lace_batch* b) {
             best = ms;
             b->threads = cd[0];
             b->ctas = cd[1];
+            b->smem_run = smem;
         }
     }
     if (!b->threads) return bfail(b, LACE_ERR_UNSUPPORTED, "no launch shape of the batched pair convolutions fits");
@@ -330,7 +339,7 @@ lace_status autotune(lace_batch* b) {
         b->mode = ms < best ? 1 : 0;
         // LACE_BATCH_MODE=persistent | per_instance overrides the timing
         const char* fm = getenv("LACE_BATCH_MODE");
-        if (fm && !strcmp(fm, "persistent")) b->mode = 0;
+        if ((fm && !strcmp(fm, "persistent")) || force_t) b->mode = 0;
         if (fm && !strcmp(fm, "per_instance")) b->mode = 1;
         if (b->mode == 1) best = ms;
     }
@@ -353,7 +362,7 @@ lace_status enqueue_hot(lace_batch* b, bool capturing) {
         lace_status st = pairconv_per_instance(b, b->main, &l);
         if (st) return st;
     } else {
-        BCK(pairconv_multi_run(multi_args(b), b->chunks, b->smem, b->threads, b->ctas, b->main, &l),
+        BCK(pairconv_multi_run(multi_args(b), b->chunks, b->smem_run, b->threads, b->ctas, b->main, &l),
             "batched pair convolutions");
     }
     if (!capturing) BCK(cudaEventRecord(b->ev_pc1, b->main), "batch");
@@ -611,6 +620,12 @@ lace_status lace_batch_info(lace_batch* b, int* threads, int* ctas_per_sm, int* 
     if (ms_out) std::copy(b->ms, b->ms + 4, ms_out);
     if (tune_ms_out)
         for (int k = 0; k < tune_count; ++k) tune_ms_out[k] = k < (int)b->tune.size() ? b->tune[k] : -1.0;
+    return LACE_OK;
+}
+
+lace_status lace_batch_mode(lace_batch* b, int* per_instance) {
+    if (!b || !per_instance) return LACE_ERR_ARG;
+    *per_instance = b->mode == 1 ? 1 : 0;
     return LACE_OK;
 }
 

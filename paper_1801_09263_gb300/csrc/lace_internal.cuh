@@ -83,6 +83,7 @@ template <typename T> struct ConvArgs {
 bool spec_launch_s(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
 bool spec_launch_m(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
 bool spec_launch_l(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
+bool spec_launch_x(int pass, int n, int nb, const ConvArgs<float>& P, int g0, cudaStream_t s);
 
 // Grid sizes whose size-specialised passes take merged launches (one grid
 // per CTA, out of place) (pairconv_spec_*.cu).
@@ -116,15 +117,20 @@ struct MultiArgs {
     double* epart;          // plane energies, epart_elems doubles (>= 2 n1 of any instance)
     size_t epart_elems;
     unsigned* bar;          // 4 unsigned: barrier counters and the timeout flag bar[2]
+    size_t smem_cta;        // dynamic shared memory of a CTA (set by pairconv_multi_run)
 };
 size_t pairconv_multi_smem(int n1, int n2, int n3);
 // Cubic sizes whose size-specialised pass bodies the persistent kernel runs
 // (with 256 or 512 threads a CTA): n, else 0; their shared memory.
 int multi_spec_size(int n1, int n2, int n3);
 size_t multi_spec_smem(int n);
-const void* multi_kernel_256();  // pairconv_multi_256.cu
-const void* multi_kernel_512();  // pairconv_multi_512.cu
-int pairconv_multi_occupancy(int threads, size_t smem);  // CTAs per SM (0: unsupported)
+const void* multi_kernel_256();    // pairconv_multi_256.cu (two CTAs an SM)
+const void* multi_kernel_512();    // pairconv_multi_512.cu (one CTA an SM)
+const void* multi_kernel_512x2();  // pairconv_multi_512x2.cu (two CTAs an SM, 64 registers)
+// Dynamic shared memory for ctas_per_sm CTAs of `threads` an SM: all that
+// the SM shares out to each (at least need), or 0 when that launch shape
+// does not fit.
+size_t pairconv_multi_cta_smem(int threads, int ctas_per_sm, size_t need);
 // n_chunks cooperative launches (chunk c in launch c; see pairconv_multi_chunks).
 cudaError_t pairconv_multi_run(const MultiArgs& A, int n_chunks, size_t smem, int threads, int ctas_per_sm,
                                cudaStream_t s, int* launches);

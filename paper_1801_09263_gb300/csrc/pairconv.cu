@@ -201,9 +201,10 @@ cudaError_t pairconv_run(const GridGeom& g, const FFTTables<T>& tb, const T* psi
         P.pf_ahead = per_sm * nsm;
     }
     if (sm_plane > (size_t)INT32_MAX || sm_slab > (size_t)INT32_MAX) return cudaErrorInvalidValue;
-    // size-specialised FP32 kernels for cubic grids with n % 4 == 0 (or LACE_GENERIC_FFT=1 to disable)
+    // size-specialised FP32 kernels for even cubic grids of the specialised
+    // sizes (their planes start on 16-byte boundaries; LACE_GENERIC_FFT=1 to disable)
     const char* gen = getenv("LACE_GENERIC_FFT");
-    const bool spec_ok = !(gen && gen[0] == '1') && g.n[0] == g.n[1] && g.n[1] == g.n[2] && g.n[0] % 4 == 0;
+    const bool spec_ok = !(gen && gen[0] == '1') && g.n[0] == g.n[1] && g.n[1] == g.n[2] && g.n[0] % 2 == 0;
     if (ev0) cudaEventRecord(ev0, s);
     for (int g0 = 0; g0 < n_grids; g0 += batch) {
         const int nb = std::min(batch, n_grids - g0);
@@ -212,7 +213,7 @@ cudaError_t pairconv_run(const GridGeom& g, const FFTTables<T>& tb, const T* psi
             if (spec_ok) {
                 for (int pass = 0; pass < 3; ++pass)
                     done = spec_launch_s(pass, g.n[0], nb, P, g0, s) || spec_launch_m(pass, g.n[0], nb, P, g0, s) ||
-                           spec_launch_l(pass, g.n[0], nb, P, g0, s);
+                           spec_launch_l(pass, g.n[0], nb, P, g0, s) || spec_launch_x(pass, g.n[0], nb, P, g0, s);
             }
         }
         if (!done) {
@@ -290,7 +291,7 @@ cudaError_t pairconv_run_merged(int n, const FFTTables<float>& tb, const std::ve
         P.msys = d_sys + (size_t)r * nsys;
         for (int pass = 0; pass < 3; ++pass) {
             const bool ok = spec_launch_s(pass, n, nb, P, g0, s) || spec_launch_m(pass, n, nb, P, g0, s) ||
-                            spec_launch_l(pass, n, nb, P, g0, s);
+                            spec_launch_l(pass, n, nb, P, g0, s) || spec_launch_x(pass, n, nb, P, g0, s);
             if (!ok) return cudaErrorInvalidValue;
         }
         energy_collect_merged_kernel<<<(nb + 127) / 128, 128, 0, s>>>(d_refs, P.msys, g0, nb, n);

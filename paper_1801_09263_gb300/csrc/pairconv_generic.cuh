@@ -152,11 +152,19 @@ __device__ __forceinline__ void pass_c_plane(const ConvArgs<T>& P, const PairGri
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) { red[warp] = (double)sa; red[32 + warp] = (double)sb; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double ta = 0.0, tbb = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { ta += red[w]; tbb += red[32 + w]; }
-        ep[0] = ta * P.dv;
-        ep[1] = tbb * P.dv;
+    if (warp == 0) {
+        // the warp partials in FP64 across the lanes of one warp (short chain)
+        const int nw = (int)(blockDim.x >> 5);
+        double ta = lane < nw ? red[lane] : 0.0, tbb = lane < nw ? red[32 + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ta += __shfl_xor_sync(0xffffffffu, ta, o);
+            tbb += __shfl_xor_sync(0xffffffffu, tbb, o);
+        }
+        if (lane == 0) {
+            ep[0] = ta * P.dv;
+            ep[1] = tbb * P.dv;
+        }
     }
     __syncthreads();
 }

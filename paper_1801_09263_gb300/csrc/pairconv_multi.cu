@@ -14,7 +14,12 @@
 // with every work item (plane, slab, grid) taken round-robin by the CTAs.
 // With 256 or 512 threads a CTA, instances on a cubic grid with
 // size-specialised passes (24 ... 64) run their items through those pass
-// bodies (pairconv_spec2.cuh), the others through the generic-radix ones.
+// bodies (pairconv_spec2.cuh) in thread groups: a CTA splits into as many
+// groups of the size's thread count as its threads and shared memory hold
+// (four of 128 threads at 24^3, two of 256 at 32^3-48^3, one of 512 at 60^3
+// and 64^3 in a 512-thread CTA), each on its own plane or slab with its own
+// named barrier; the other instances run the generic-radix bodies on the
+// whole CTA.  Each launch gets all the shared memory its CTAs per SM leave.
 // The number of grids of each instance is read from device memory at run
 // time, so a captured graph of these launches serves any pair counts that
 // need no more chunks than it has launches (a launch without a chunk exits).
@@ -30,11 +35,11 @@ namespace {
 
 using multi::kMaxEntries;
 
-const void* fn_for(int threads) {
+const void* fn_for(int threads, int ctas_per_sm) {
     switch (threads) {
         case 128: return (const void*)multi::pairconv_multi_kernel<128, false>;
         case 256: return multi_kernel_256();
-        case 512: return multi_kernel_512();
+        case 512: return ctas_per_sm >= 2 ? multi_kernel_512x2() : multi_kernel_512();
         default: return nullptr;
     }
 }
@@ -85,7 +90,7 @@ size_t pairconv_multi_smem(int n1, int n2, int n3) {
 int multi_spec_size(int n1, int n2, int n3) {
     if (n1 != n2 || n2 != n3) return 0;
     switch (n1) {
-        case 24: case 32: case 36: case 40: case 48: case 60: case 64: return n1;
+        case 24: case 32: case 36: case 40: case 48: case 50: case 54: case 60: case 64: return n1;
         default: return 0;
     }
 }
@@ -97,40 +102,47 @@ size_t multi_spec_smem(int n) {
         case 36: return spec2::smem_max(36);
         case 40: return spec2::smem_max(40);
         case 48: return spec2::smem_max(48);
+        case 50: return spec2::smem_max(50);
+        case 54: return spec2::smem_max(54);
         case 60: return spec2::smem_max(60);
         case 64: return spec2::smem_max(64);
         default: return 0;
     }
 }
 
-int pairconv_multi_occupancy(int threads, size_t smem) {
-    const void* fn = fn_for(threads);
-    if (!fn) return 0;
-    int dev = 0, per_sm = 0, optin = 0;
+size_t pairconv_multi_cta_smem(int threads, int ctas_per_sm, size_t need) {
+    const void* fn = fn_for(threads, ctas_per_sm);
+    if (!fn || ctas_per_sm < 1) return 0;
+    int dev = 0, optin = 0, per_sm = 0, occ = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaFuncAttributes fa{};
     if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    // the limit is shared by every caller of this kernel: the opt-in maximum
-    if (smem + fa.sharedSizeBytes > (size_t)optin ||
-        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes) !=
-            cudaSuccess) {
+    // the SM's shared memory split evenly (1 KB reserved per CTA), within
+    // the per-CTA opt-in limit; the limit of the kernel is shared by every
+    // caller: the opt-in maximum
+    const long long share = (long long)per_sm / ctas_per_sm - 1024 - (long long)fa.sharedSizeBytes;
+    const long long cap = (long long)optin - (long long)fa.sharedSizeBytes;
+    const long long smem = (std::min(share, cap) / 16) * 16;
+    if (smem < (long long)need ||
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cap) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, threads, (size_t)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
     }
-    return per_sm;
+    return occ >= ctas_per_sm ? (size_t)smem : 0;
 }
 
 cudaError_t pairconv_multi_run(const MultiArgs& A, int n_chunks, size_t smem, int threads, int ctas_per_sm,
                                cudaStream_t s, int* launches) {
-    const void* fn = fn_for(threads);
+    const void* fn = fn_for(threads, ctas_per_sm);
     if (!fn || ctas_per_sm < 1) return cudaErrorInvalidValue;
     int dev = 0, sms = 0, coop = 0;
     cudaError_t e;
@@ -140,6 +152,7 @@ cudaError_t pairconv_multi_run(const MultiArgs& A, int n_chunks, size_t smem, in
     if (!coop) return cudaErrorNotSupported;
     if ((e = cudaMemsetAsync(A.bar, 0, 4 * sizeof(unsigned), s))) return e;
     MultiArgs a = A;
+    a.smem_cta = smem;
     for (int c = 0; c < n_chunks; ++c) {
         // fresh barrier counters per launch; the timeout flag bar[2] stays set
         if (c > 0 && (e = cudaMemsetAsync(A.bar, 0, 2 * sizeof(unsigned), s))) return e;

@@ -23,7 +23,8 @@ struct ChunkTable {
     int cnt[kMaxEntries];        // grids
     size_t pool[kMaxEntries];    // pool offset of the first grid (complex elements)
     size_t ep[kMaxEntries];      // epart offset (doubles)
-    int item[kMaxEntries + 1];   // item prefix of the current phase
+    int grp[kMaxEntries];        // thread groups a CTA runs at once on the entry's items (1: the whole CTA)
+    int item[kMaxEntries + 1];   // prefix of the current phase's work units (one unit = grp items)
     // where the next chunk starts
     int next_q, next_g;
 };
@@ -66,14 +67,40 @@ static __device__ void build_chunk(const MultiArgs& A, int q, int g, ChunkTable&
     t.next_g = g;
 }
 
-// Thread 0: item prefix for a phase (0: planes n1, 1: slabs n2, 2: grids).
+// Threads of one group for the size-specialised bodies of cubic size n in a
+// CTA of nt threads: about one butterfly a thread in the larger radix stage
+// of a plane (24: 144 butterflies, 32-48: 256-384, 60 and 64: 600, 512).
+__host__ __device__ constexpr int group_threads(int n, int nt) {
+    const int g = n <= 24 ? 128 : (n <= 48 ? 256 : 512);
+    return g < nt ? g : nt;
+}
+// Shared memory of one group of size n (16-byte multiple).
+__host__ __device__ inline size_t group_smem(int n) { return (spec2::smem_max(n) + 15) / 16 * 16; }
+// Groups a CTA of nt threads with smem_cta bytes of dynamic shared memory
+// runs at once on items of size n (named barriers 1..15); 0 if none fits.
+__host__ __device__ inline int groups_for(int n, int nt, size_t smem_cta) {
+    const int by_threads = nt / group_threads(n, nt);
+    const int by_smem = (int)(smem_cta / group_smem(n));
+    const int g = by_threads < by_smem ? by_threads : by_smem;
+    return g < 15 ? g : 15;
+}
+
+// Thread 0: unit prefix for a phase (0: planes n1, 1: slabs n2, 2: grids).
+// In phases 0 and 1 a unit is grp items of one entry, taken by one CTA at once.
+template <int NT, bool SPEC>
 static __device__ void build_items(const MultiArgs& A, ChunkTable& t, int phase) {
     int acc = 0;
     for (int e = 0; e < t.n; ++e) {
         t.item[e] = acc;
         const MultiInst& I = A.inst[t.q[e]];
         const int per = phase == 0 ? I.n1 : (phase == 1 ? I.n2 : 1);
-        acc += t.cnt[e] * per;
+        int g = 1;
+        if (SPEC && I.spec && phase < 2) {
+            g = groups_for(I.spec, NT, A.smem_cta);
+            if (g < 1) g = 1;  // the host sizes smem_cta for one group of every size
+        }
+        t.grp[e] = g;
+        acc += (t.cnt[e] * per + g - 1) / g;
     }
     t.item[t.n] = acc;
 }
@@ -88,50 +115,74 @@ static __device__ __forceinline__ int find_entry(const ChunkTable& t, int it) {
     return lo;
 }
 
-// One work item through the size-specialised pass bodies of
-// pairconv_spec2.cuh (the instance's cubic size; NT threads).  phase 0: pass
-// A of plane `w`, 1: pass B of slab `w`, 2: pass C of plane `w` (a constant
-// at every call site, so each phase loop inlines only its own bodies).
+// One work unit through the size-specialised pass bodies of
+// pairconv_spec2.cuh (the instance's cubic size): the CTA's threads split
+// into G groups of group_threads(n, NT), group gi taking item loc0 + gi of
+// entry e with its own shared memory, energy scratch and named barrier 1 + gi.
+// phase 0: pass A of a plane, 1: pass B of a slab, 2: pass C of a plane (a
+// constant at every call site, so each phase loop inlines only its bodies).
+// Planes are taken plane-major within each entry (the groups and CTAs in
+// flight share the orbital planes of one x).
 template <int NT>
-__device__ __forceinline__ void spec_item(int phase, const MultiInst& I, const PairGrid& d, cplx<float>* scr,
-                                          double* ep, int w, float4* smem, double* red) {
-    spec2::GridView V;
-    V.psi = I.P.psi;
-    V.W = I.P.W;
-    V.ktab = I.P.ktab;
-    V.scr = scr;
-    V.ep = ep;
-    V.d = d;
-    V.n_occ = I.P.n_occ;
-    V.dv = I.P.dv;
-#define LACE_SPEC_ITEM(NN)                                                \
-    case NN:                                                              \
-        if (phase == 0) spec2::body_a<NN, NT>(I.P, V, w, smem, nullptr);  \
-        else if (phase == 1) spec2::body_b<NN, NT>(I.P, V, w, smem);      \
-        else spec2::body_c<NN, NT>(I.P, V, w, smem, red);                 \
-        break;
+__device__ __forceinline__ void spec_unit(int phase, const MultiArgs& A, const ChunkTable& t, int e,
+                                          const MultiInst& I, int loc0, unsigned char* smem, double* red) {
+    const int G = t.grp[e];
+    const int cnt = t.cnt[e];
+    const int items = cnt * (phase == 1 ? I.n2 : I.n1);
+#define LACE_SPEC_UNIT(NN)                                                                 \
+    case NN: {                                                                             \
+        constexpr int T = group_threads(NN, NT);                                           \
+        const int gi = (int)threadIdx.x / T;                                               \
+        const int loc = loc0 + gi;                                                         \
+        if (gi < G && loc < items) {                                                       \
+            int k, w;                                                                      \
+            if (phase == 1) {                                                              \
+                k = loc / I.n2;                                                            \
+                w = loc - k * I.n2;                                                        \
+            } else {                                                                       \
+                w = loc / cnt;                                                             \
+                k = loc - w * cnt;                                                         \
+            }                                                                              \
+            spec2::GridView V;                                                             \
+            V.psi = I.P.psi;                                                               \
+            V.W = I.P.W;                                                                   \
+            V.ktab = I.P.ktab;                                                             \
+            V.scr = A.pool + t.pool[e] + (size_t)k * I.P.ng;                               \
+            V.ep = A.epart + t.ep[e] + (size_t)k * I.n1 * 2;                               \
+            V.d = I.P.grids[t.g0[e] + k];                                                  \
+            V.n_occ = I.P.n_occ;                                                           \
+            V.dv = I.P.dv;                                                                 \
+            const spec2::Sub<T> grp{(int)threadIdx.x - gi * T, 1 + gi};                    \
+            float4* sm = reinterpret_cast<float4*>(smem + (size_t)gi * group_smem(NN));    \
+            if (phase == 0) spec2::body_a<NN, T>(I.P, V, w, sm, nullptr, grp);             \
+            else if (phase == 1) spec2::body_b<NN, T>(I.P, V, w, sm, grp);                 \
+            else spec2::body_c<NN, T>(I.P, V, w, sm, red + gi * 2 * (T / 32), grp);        \
+        }                                                                                  \
+    } break;
     switch (I.spec) {
-        LACE_SPEC_ITEM(24)
-        LACE_SPEC_ITEM(32)
-        LACE_SPEC_ITEM(36)
-        LACE_SPEC_ITEM(40)
-        LACE_SPEC_ITEM(48)
-        LACE_SPEC_ITEM(60)
-        LACE_SPEC_ITEM(64)
+        LACE_SPEC_UNIT(24)
+        LACE_SPEC_UNIT(32)
+        LACE_SPEC_UNIT(36)
+        LACE_SPEC_UNIT(40)
+        LACE_SPEC_UNIT(48)
+        LACE_SPEC_UNIT(50)
+        LACE_SPEC_UNIT(54)
+        LACE_SPEC_UNIT(60)
+        LACE_SPEC_UNIT(64)
         default: break;
     }
-#undef LACE_SPEC_ITEM
+#undef LACE_SPEC_UNIT
 }
 
-// SPEC: instances with I.spec run the size-specialised bodies (the others,
-// and every instance without SPEC, the generic-radix bodies).  Planes and
-// slabs are taken plane-major within each run of grids of one instance, so
-// the CTAs in flight share the orbital planes of one x.
-template <int NT, bool SPEC>
-__global__ void __launch_bounds__(NT, 512 / NT > 0 ? 512 / NT : 1) pairconv_multi_kernel(MultiArgs A, int chunk) {
+// SPEC: instances with I.spec run the size-specialised bodies in thread
+// groups (spec_unit); the others, and every instance without SPEC, the
+// generic-radix bodies on the whole CTA.  Planes are taken plane-major within
+// each run of grids of one instance, so the CTAs in flight share the orbital
+// planes of one x.
+template <int NT, bool SPEC, int MINB = (512 / NT > 0 ? 512 / NT : 1)>
+__global__ void __launch_bounds__(NT, MINB) pairconv_multi_kernel(MultiArgs A, int chunk) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx<float>* work = reinterpret_cast<cplx<float>*>(smem_raw);
-    float4* smem4 = reinterpret_cast<float4*>(smem_raw);
     __shared__ ChunkTable t;
     __shared__ double red[2 * 32];
     __shared__ int abort_sh;
@@ -148,47 +199,56 @@ __global__ void __launch_bounds__(NT, 512 / NT > 0 ? 512 / NT : 1) pairconv_mult
     __syncthreads();
     if (t.n == 0) return;
     // A: planes
-    if (threadIdx.x == 0) build_items(A, t, 0);
+    if (threadIdx.x == 0) build_items<NT, SPEC>(A, t, 0);
     __syncthreads();
-    for (int it = blockIdx.x; it < t.item[t.n]; it += gridDim.x) {
-        const int e = find_entry(t, it);
+    for (int u = blockIdx.x; u < t.item[t.n]; u += gridDim.x) {
+        const int e = find_entry(t, u);
         const MultiInst& I = A.inst[t.q[e]];
-        const int loc = it - t.item[e], x = loc / t.cnt[e], k = loc - x * t.cnt[e];
-        cplx<float>* scr = A.pool + t.pool[e] + (size_t)k * I.P.ng;
-        __syncthreads();  // the previous item's shared memory is free
-        if (SPEC && I.spec) spec_item<NT>(0, I, I.P.grids[t.g0[e] + k], scr, nullptr, x, smem4, red);
-        else gen::pass_a_plane<float>(I.P, I.P.grids[t.g0[e] + k], scr, x, work);
+        __syncthreads();  // the previous unit's shared memory is free
+        if (SPEC && I.spec) {
+            spec_unit<NT>(0, A, t, e, I, (u - t.item[e]) * t.grp[e], smem_raw, red);
+        } else {
+            const int loc = u - t.item[e], x = loc / t.cnt[e], k = loc - x * t.cnt[e];
+            cplx<float>* scr = A.pool + t.pool[e] + (size_t)k * I.P.ng;
+            gen::pass_a_plane<float>(I.P, I.P.grids[t.g0[e] + k], scr, x, work);
+        }
     }
     if (!grid_barrier(A.bar, gen, &abort_sh)) return;
     // B: slabs
-    if (threadIdx.x == 0) build_items(A, t, 1);
+    if (threadIdx.x == 0) build_items<NT, SPEC>(A, t, 1);
     __syncthreads();
-    for (int it = blockIdx.x; it < t.item[t.n]; it += gridDim.x) {
-        const int e = find_entry(t, it);
+    for (int u = blockIdx.x; u < t.item[t.n]; u += gridDim.x) {
+        const int e = find_entry(t, u);
         const MultiInst& I = A.inst[t.q[e]];
-        const int loc = it - t.item[e], k = loc / I.n2, ky = loc - k * I.n2;
-        cplx<float>* scr = A.pool + t.pool[e] + (size_t)k * I.P.ng;
         __syncthreads();
-        if (SPEC && I.spec) spec_item<NT>(1, I, I.P.grids[t.g0[e] + k], scr, nullptr, ky, smem4, red);
-        else gen::pass_b_slab<float>(I.P, scr, ky, work);
+        if (SPEC && I.spec) {
+            spec_unit<NT>(1, A, t, e, I, (u - t.item[e]) * t.grp[e], smem_raw, red);
+        } else {
+            const int loc = u - t.item[e], k = loc / I.n2, ky = loc - k * I.n2;
+            cplx<float>* scr = A.pool + t.pool[e] + (size_t)k * I.P.ng;
+            gen::pass_b_slab<float>(I.P, scr, ky, work);
+        }
     }
     if (!grid_barrier(A.bar, gen, &abort_sh)) return;
     // C: planes
-    if (threadIdx.x == 0) build_items(A, t, 0);
+    if (threadIdx.x == 0) build_items<NT, SPEC>(A, t, 0);
     __syncthreads();
-    for (int it = blockIdx.x; it < t.item[t.n]; it += gridDim.x) {
-        const int e = find_entry(t, it);
+    for (int u = blockIdx.x; u < t.item[t.n]; u += gridDim.x) {
+        const int e = find_entry(t, u);
         const MultiInst& I = A.inst[t.q[e]];
-        const int loc = it - t.item[e], x = loc / t.cnt[e], k = loc - x * t.cnt[e];
-        cplx<float>* scr = A.pool + t.pool[e] + (size_t)k * I.P.ng;
-        double* ep = A.epart + t.ep[e] + (size_t)k * I.n1 * 2;
         __syncthreads();
-        if (SPEC && I.spec) spec_item<NT>(2, I, I.P.grids[t.g0[e] + k], scr, ep, x, smem4, red);
-        else gen::pass_c_plane<float>(I.P, I.P.grids[t.g0[e] + k], scr, x, work, red, ep + (size_t)x * 2);
+        if (SPEC && I.spec) {
+            spec_unit<NT>(2, A, t, e, I, (u - t.item[e]) * t.grp[e], smem_raw, red);
+        } else {
+            const int loc = u - t.item[e], x = loc / t.cnt[e], k = loc - x * t.cnt[e];
+            cplx<float>* scr = A.pool + t.pool[e] + (size_t)k * I.P.ng;
+            double* ep = A.epart + t.ep[e] + (size_t)k * I.n1 * 2;
+            gen::pass_c_plane<float>(I.P, I.P.grids[t.g0[e] + k], scr, x, work, red, ep + (size_t)x * 2);
+        }
     }
     if (!grid_barrier(A.bar, gen, &abort_sh)) return;
     // D: per grid, the plane energies in a fixed order -> E[i][j] = E[j][i]
-    if (threadIdx.x == 0) build_items(A, t, 2);
+    if (threadIdx.x == 0) build_items<NT, SPEC>(A, t, 2);
     __syncthreads();
     for (int it = blockIdx.x * NT + threadIdx.x; it < t.item[t.n]; it += gridDim.x * NT) {
         const int e = find_entry(t, it);

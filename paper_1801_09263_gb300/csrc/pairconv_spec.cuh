@@ -258,12 +258,20 @@ __global__ void __launch_bounds__(threads_for(N)) spec_pass_c(ConvArgs<float> P,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) { red[0][warp] = (double)sa; red[1][warp] = (double)sb; }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double ta = 0.0, tbb = 0.0;
-        for (int w = 0; w < NT / 32; ++w) { ta += red[0][w]; tbb += red[1][w]; }
-        double* ep = P.epart + ((size_t)g * gridDim.x + x) * 2;
-        ep[0] = ta * P.dv;
-        ep[1] = tbb * P.dv;
+    static_assert(NT / 32 <= 32, "one warp sums the warp partials");
+    if (warp == 0) {
+        // the warp partials in FP64 across the lanes of one warp (short chain)
+        double ta = lane < NT / 32 ? red[0][lane] : 0.0, tbb = lane < NT / 32 ? red[1][lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ta += __shfl_xor_sync(0xffffffffu, ta, o);
+            tbb += __shfl_xor_sync(0xffffffffu, tbb, o);
+        }
+        if (lane == 0) {
+            double* ep = P.epart + ((size_t)g * gridDim.x + x) * 2;
+            ep[0] = ta * P.dv;
+            ep[1] = tbb * P.dv;
+        }
     }
 }
 

@@ -51,10 +51,11 @@ using spec::Plan2;
 __host__ __device__ constexpr size_t smem_bytes_b(int n, bool kslab) {
     return sizeof(C) * (2 * (size_t)n * n + n) + 2 * sizeof(float) * n + (kslab ? sizeof(float) * n * n : 0);
 }
-// Pass B stages its slab of the K(G)/Ng table in shared memory when two
-// CTAs an SM still fit, or when the planes leave room for one CTA only and
-// the slab fits beside them.
+// Pass B stages its slab of the K(G)/Ng table in shared memory (16-byte
+// copies of table rows: n % 4 == 0) when two CTAs an SM still fit, or when
+// the planes leave room for one CTA only and the slab fits beside them.
 __host__ __device__ constexpr bool kslab_fits(int n) {
+    if (n % 4 != 0) return false;
     const size_t plane_ac = sizeof(C) * (2 * (size_t)n * (n + 1) + n);
     const size_t without = plane_ac > smem_bytes_b(n, false) ? plane_ac : smem_bytes_b(n, false);
     const bool one_cta = 2 * (without + 1024) > 227 * 1024;
@@ -121,13 +122,31 @@ __host__ __device__ constexpr int max_regs(int n) { return regs_at(threads_for(n
 // the plain one.
 __host__ __device__ constexpr int pad_mask(int n) {
     switch (n) {
-        case 24: case 36: case 60: return (1 << 4) | (1 << 5);
+        case 24: case 36: case 50: case 54: case 60: return (1 << 4) | (1 << 5);
         case 72: return (1 << 1) | (1 << 4) | (1 << 5);
         case 100: return (1 << 0) | (1 << 1) | (1 << 4) | (1 << 5);
         default: return (1 << 0) | (1 << 4) | (1 << 5);  // 32, 40, 48, 64, 80, 96
     }
 }
 __host__ __device__ constexpr int pitch(int n, int h) { return (pad_mask(n) >> h) & 1 ? n + 1 : n; }
+
+// The threads that run one pass body: the whole CTA (barrier 0), or one
+// group of NT consecutive threads (whole warps) of a larger CTA with a named
+// barrier of its own, so that several groups of one CTA work on different
+// planes or slabs at once.  Every thread of a group takes the same sequence
+// of barriers: the bodies' control flow around sync() is uniform.
+struct Cta {
+    __device__ __forceinline__ int tid() const { return (int)threadIdx.x; }
+    __device__ __forceinline__ void sync() const { __syncthreads(); }
+};
+template <int NT>
+struct Sub {
+    static_assert(NT % 32 == 0, "a group is whole warps");
+    int t;   // thread index in the group
+    int id;  // named barrier, 1..15
+    __device__ __forceinline__ int tid() const { return t; }
+    __device__ __forceinline__ void sync() const { asm volatile("bar.sync %0, %1;" ::"r"(id), "n"(NT) : "memory"); }
+};
 
 // Hint: fetch bytes (a multiple of 16, 16-byte aligned) at p into L2.
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
@@ -183,19 +202,20 @@ __device__ __forceinline__ GridView grid_view(const ConvArgs<float>& P, int g0, 
     return v;
 }
 
-// One radix-R Stockham stage over LINES lines of length N, out of place:
-// butterfly i of a line reads elements i + t N/R through ld(line, e),
-// multiplies by w_{P R}^{t k} (k = i mod P), runs DFT_R and writes element
-// (i - k) R + k + s P through st(line, e, v).  LF: consecutive threads take
-// consecutive lines (else consecutive butterflies of one line).
+// One radix-R Stockham stage over LINES lines of length N, out of place, on
+// NT threads (tid: this thread's index among them): butterfly i of a line
+// reads elements i + t N/R through ld(line, e), multiplies by w_{P R}^{t k}
+// (k = i mod P), runs DFT_R and writes element (i - k) R + k + s P through
+// st(line, e, v).  LF: consecutive threads take consecutive lines (else
+// consecutive butterflies of one line).
 template <int N, int R, int P, int DIR, int LINES, bool LF, int NT, class Ld, class St>
-__device__ __forceinline__ void stage(const C* __restrict__ tw, Ld ld, St st) {
+__device__ __forceinline__ void stage(int tid, const C* __restrict__ tw, Ld ld, St st) {
     constexpr int TN = N / R;
     constexpr int ITEMS = LINES * TN;
     constexpr int TWSTEP = N / (P * R);
 #pragma unroll
     for (int item0 = 0; item0 < ITEMS; item0 += NT) {
-        const int item = item0 + (int)threadIdx.x;
+        const int item = item0 + tid;
         if (item0 + NT <= ITEMS || item < ITEMS) {
             const int line = LF ? item % LINES : item / TN;
             const int i = LF ? item / LINES : item % TN;
@@ -220,11 +240,12 @@ __device__ __forceinline__ void stage(const C* __restrict__ tw, Ld ld, St st) {
 }
 
 // Pass A, one plane: rho of plane x of grid V, forward FFT along z then y,
-// on NT threads (the thread block).  pf_plane: an orbital plane to fetch into
+// on the NT threads of grp (the thread block, or a group of it).  pf_plane: an orbital plane to fetch into
 // L2 at the end (or null).
-template <int N, int NT>
+template <int N, int NT, class G = Cta>
 __device__ __forceinline__ void body_a(const ConvArgs<float>& P, const GridView& V, int x, float4* smem_v4,
-                                       const float* pf_plane) {
+                                       const float* pf_plane, G grp = G()) {
+    const int tid = grp.tid();
     static_assert(N % 2 == 0, "pass A reads orbital planes as 16-byte vectors");
     constexpr int NP = N * N;
     constexpr Plan2 pl = plan2(N);
@@ -234,7 +255,7 @@ __device__ __forceinline__ void body_a(const ConvArgs<float>& P, const GridView&
     C* b1 = b0 + N * LP;
     C* tw = b1 + N * LP;
     const PairGrid d = V.d;
-    for (int i = threadIdx.x; i < N; i += NT) tw[i] = P.tw[2][i];
+    for (int i = tid; i < N; i += NT) tw[i] = P.tw[2][i];
     const size_t off = (size_t)x * NP;
     const bool two = d.j2 >= 0;
     const float* a1 = V.psi + (size_t)d.i1 * P.ng + off;
@@ -250,7 +271,7 @@ __device__ __forceinline__ void body_a(const ConvArgs<float>& P, const GridView&
         const float4* A2 = reinterpret_cast<const float4*>(a2);
         const float4* C2 = reinterpret_cast<const float4*>(c2);
         float4* r4 = reinterpret_cast<float4*>(b1);
-        for (int e = threadIdx.x; e < NP / 4; e += NT) {
+        for (int e = tid; e < NP / 4; e += NT) {
             const float4 x1 = __ldg(A1 + e), y1 = __ldg(C1 + e);
             float4 x2 = make_float4(0.f, 0.f, 0.f, 0.f), y2 = x2;
             if (two) {
@@ -261,20 +282,20 @@ __device__ __forceinline__ void body_a(const ConvArgs<float>& P, const GridView&
             r4[2 * e + 1] = make_float4(x1.z * y1.z, x2.z * y2.z, x1.w * y1.w, x2.w * y2.w);
         }
     }
-    __syncthreads();
+    grp.sync();
     stage<N, pl.r1, 1, -1, N, false, NT>(
-        tw, [&](int y, int z) { return b1[y * N + z]; }, [&](int y, int z, C v) { b0[y * P01 + z] = v; });
-    __syncthreads();
+        tid, tw, [&](int y, int z) { return b1[y * N + z]; }, [&](int y, int z, C v) { b0[y * P01 + z] = v; });
+    grp.sync();
     stage<N, pl.r2, pl.r1, -1, N, false, NT>(
-        tw, [&](int y, int z) { return b0[y * P01 + z]; }, [&](int y, int z, C v) { b1[y * P12 + z] = v; });
-    __syncthreads();
+        tid, tw, [&](int y, int z) { return b0[y * P01 + z]; }, [&](int y, int z, C v) { b1[y * P12 + z] = v; });
+    grp.sync();
     // y lines (line = z)
     stage<N, pl.r1, 1, -1, N, true, NT>(
-        tw, [&](int z, int y) { return b1[y * P12 + z]; }, [&](int z, int y, C v) { b0[y * P23 + z] = v; });
-    __syncthreads();
+        tid, tw, [&](int z, int y) { return b1[y * P12 + z]; }, [&](int z, int y, C v) { b0[y * P23 + z] = v; });
+    grp.sync();
     C* out = V.scr + off;
     stage<N, pl.r2, pl.r1, -1, N, true, NT>(
-        tw, [&](int z, int y) { return b0[y * P23 + z]; }, [&](int z, int y, C v) { out[y * N + z] = v; });
+        tid, tw, [&](int z, int y) { return b0[y * P23 + z]; }, [&](int z, int y, C v) { out[y * N + z] = v; });
     if (pf_plane) prefetch_l2(pf_plane, NP * sizeof(float));
 }
 
@@ -296,9 +317,11 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
 
 // Pass B, one slab: slab ky of grid V: forward x-FFT (decimation in time),
 // * K(G)/Ng, inverse x-FFT (decimation in frequency); the middle three steps
-// share registers.  NT threads.
-template <int N, int NT>
-__device__ __forceinline__ void body_b(const ConvArgs<float>& P, const GridView& V, int ky, float4* smem_v4) {
+// share registers.  The NT threads of grp.
+template <int N, int NT, class G = Cta>
+__device__ __forceinline__ void body_b(const ConvArgs<float>& P, const GridView& V, int ky, float4* smem_v4,
+                                       G grp = G()) {
+    const int tid = grp.tid();
     constexpr int NP = N * N;
     constexpr Plan2 pl = plan2(N);
     constexpr int RB = pl.r2, RA = pl.r1;  // N = RA * RB; the middle (the heaviest step) takes the stage with fewer butterflies
@@ -314,14 +337,14 @@ __device__ __forceinline__ void body_b(const ConvArgs<float>& P, const GridView&
     if (kstage) {
         // asynchronous 16-byte copies, waited for before the middle
         const unsigned ks_s = (unsigned)__cvta_generic_to_shared(ks);
-        for (int q = threadIdx.x; q < NP / 4; q += NT) {
+        for (int q = tid; q < NP / 4; q += NT) {
             const int xx = q / (N / 4), z4 = q % (N / 4);
             const float* src = ktab + ((size_t)xx * N + ky) * N + 4 * z4;
             asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(ks_s + 16u * q), "l"(src) : "memory");
         }
         asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    for (int i = threadIdx.x; i < N; i += NT) {
+    for (int i = tid; i < N; i += NT) {
         tw[i] = P.tw[0][i];
         gx2[i] = P.g2[0][i];
         gz2[i] = P.g2[2][i];
@@ -329,17 +352,17 @@ __device__ __forceinline__ void body_b(const ConvArgs<float>& P, const GridView&
     C* base = V.scr + (size_t)ky * N;
     // forward stage 1 (line = z): DFT_RB over n2 of x[n1 + RA n2], to y[n1 RB + k2]
     stage<N, RB, 1, -1, N, true, NT>(
-        tw, [&](int z, int xx) { return base[(size_t)xx * NP + z]; },
+        tid, tw, [&](int z, int xx) { return base[(size_t)xx * NP + z]; },
         [&](int z, int xx, C v) { b0[xx * N + z] = v; });
     if (kstage) asm volatile("cp.async.wait_group 0;" ::: "memory");
-    __syncthreads();
+    grp.sync();
     const float gy2 = P.g2[1][ky];
     // middle: for each (z, k2): twiddle, DFT_RA -> X[k2 + RB k1], * K, inverse
     // DFT_RA -> z[k2][n1], twiddle w_N^{-n1 k2}, stored at n1 RB + k2
     constexpr int MID = N * RB;
 #pragma unroll
     for (int item0 = 0; item0 < MID; item0 += NT) {
-        const int item = item0 + (int)threadIdx.x;
+        const int item = item0 + tid;
         if (item0 + NT <= MID || item < MID) {
             const int z = item % N, k2 = item / N;
             C v[RA];
@@ -372,12 +395,12 @@ __device__ __forceinline__ void body_b(const ConvArgs<float>& P, const GridView&
             }
         }
     }
-    __syncthreads();
+    grp.sync();
     // inverse stage 2 (line = z): for each n1, DFT_RB over k2 -> x[n1 + RA n2]
     constexpr int LAST = N * RA;
 #pragma unroll
     for (int item0 = 0; item0 < LAST; item0 += NT) {
-        const int item = item0 + (int)threadIdx.x;
+        const int item = item0 + tid;
         if (item0 + NT <= LAST || item < LAST) {
             const int z = item % N, n1 = item / N;
             C v[RB];
@@ -406,10 +429,12 @@ __global__ void __launch_bounds__(threads_for(N)) __maxnreg__(max_regs(N)) pass_
 
 // Pass C, one plane: inverse FFT along y then z of plane x of grid V, then
 // the W updates (16-byte vector reductions) and the real-space pair
-// energies.  NT threads; red: 2 x (NT / 32) doubles of shared memory.
-template <int N, int NT>
+// energies.  The NT threads of grp; red: 2 x (NT / 32) doubles of shared
+// memory of its own.
+template <int N, int NT, class G = Cta>
 __device__ __forceinline__ void body_c(const ConvArgs<float>& P, const GridView& V, int x, float4* smem_v4,
-                                       double* red) {
+                                       double* red, G grp = G()) {
+    const int tid = grp.tid();
     constexpr int NP = N * N;
     constexpr Plan2 pl = plan2(N);
     constexpr int LP = N + 1;  // buffer rows hold up to n + 1 complex values (the last stage writes pitch n)
@@ -419,32 +444,32 @@ __device__ __forceinline__ void body_c(const ConvArgs<float>& P, const GridView&
     C* tw = b1 + N * LP;
     constexpr int NW = (NT + 31) / 32;
     const PairGrid d = V.d;
-    for (int i = threadIdx.x; i < N; i += NT) tw[i] = P.tw[2][i];
+    for (int i = tid; i < N; i += NT) tw[i] = P.tw[2][i];
     const size_t off = (size_t)x * NP;
     const C* in = V.scr + off;
     stage<N, pl.r1, 1, +1, N, true, NT>(
-        tw, [&](int z, int y) { return in[y * N + z]; }, [&](int z, int y, C v) { b0[y * P01 + z] = v; });
-    if (P.pf_ahead > 0 && threadIdx.x < 8) {
+        tid, tw, [&](int z, int y) { return in[y * N + z]; }, [&](int z, int y, C v) { b0[y * P01 + z] = v; });
+    if (P.pf_ahead > 0 && tid < 8) {
         // the epilogue's orbital planes and W planes, fetched into L2 while
         // the FFT stages run
-        const int q = threadIdx.x & 3;
+        const int q = tid & 3;
         const int o = q == 0 ? d.i1 : q == 1 ? d.j1 : q == 2 ? d.i2 : d.j2;
         if (o >= 0) {
-            const float* src = (threadIdx.x < 4 ? V.psi : V.W) + (size_t)o * P.ng + off;
+            const float* src = (tid < 4 ? V.psi : V.W) + (size_t)o * P.ng + off;
             prefetch_l2(src, NP * sizeof(float));
         }
     }
-    __syncthreads();
+    grp.sync();
     stage<N, pl.r2, pl.r1, +1, N, true, NT>(
-        tw, [&](int z, int y) { return b0[y * P01 + z]; }, [&](int z, int y, C v) { b1[y * P12 + z] = v; });
-    __syncthreads();
+        tid, tw, [&](int z, int y) { return b0[y * P01 + z]; }, [&](int z, int y, C v) { b1[y * P12 + z] = v; });
+    grp.sync();
     // z lines (line = y)
     stage<N, pl.r1, 1, +1, N, true, NT>(
-        tw, [&](int y, int z) { return b1[y * P12 + z]; }, [&](int y, int z, C v) { b0[y * P23 + z] = v; });
-    __syncthreads();
+        tid, tw, [&](int y, int z) { return b1[y * P12 + z]; }, [&](int y, int z, C v) { b0[y * P23 + z] = v; });
+    grp.sync();
     stage<N, pl.r2, pl.r1, +1, N, false, NT>(
-        tw, [&](int y, int z) { return b0[y * P23 + z]; }, [&](int y, int z, C v) { b1[y * N + z] = v; });
-    __syncthreads();
+        tid, tw, [&](int y, int z) { return b0[y * P23 + z]; }, [&](int y, int z, C v) { b1[y * N + z] = v; });
+    grp.sync();
     const bool two = d.j2 >= 0;
     const bool a_occ = d.j1 < V.n_occ, a_sym = a_occ && d.j1 != d.i1;
     const bool b_occ = two && d.j2 < V.n_occ, b_sym = b_occ && d.j2 != d.i2;
@@ -461,7 +486,7 @@ __device__ __forceinline__ void body_c(const ConvArgs<float>& P, const GridView&
     float sa = 0.f, ca = 0.f, sb = 0.f, cb = 0.f;
 #pragma unroll
     for (int e0 = 0; e0 < NP / 4; e0 += NT) {
-        const int e = e0 + (int)threadIdx.x;
+        const int e = e0 + tid;
         if (e0 + NT <= NP / 4 || e < NP / 4) {
             const float4 v01 = pl4[2 * e], v23 = pl4[2 * e + 1];
             const float4 x1 = __ldg(wi1 + e), y1 = __ldg(pj1 + e);
@@ -495,15 +520,25 @@ __device__ __forceinline__ void body_c(const ConvArgs<float>& P, const GridView&
         sa += __shfl_xor_sync(0xffffffffu, sa, o);
         sb += __shfl_xor_sync(0xffffffffu, sb, o);
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = tid >> 5, lane = tid & 31;
     if (lane == 0) { red[warp] = (double)sa; red[NW + warp] = (double)sb; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double ta = 0.0, tbb = 0.0;
-        for (int w = 0; w < NW; ++w) { ta += red[w]; tbb += red[NW + w]; }
-        double* ep = V.ep + (size_t)x * 2;
-        ep[0] = ta * V.dv;
-        ep[1] = tbb * V.dv;
+    grp.sync();
+    static_assert(NW <= 32, "one warp sums the warp partials");
+    if (warp == 0) {
+        // the warp partials in FP64 across the lanes of one warp (a short
+        // chain: FP64 issues slowly, and one thread summing them serially
+        // held the CTA's slot)
+        double ta = lane < NW ? red[lane] : 0.0, tbb = lane < NW ? red[NW + lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ta += __shfl_xor_sync(0xffffffffu, ta, o);
+            tbb += __shfl_xor_sync(0xffffffffu, tbb, o);
+        }
+        if (lane == 0) {
+            double* ep = V.ep + (size_t)x * 2;
+            ep[0] = ta * V.dv;
+            ep[1] = tbb * V.dv;
+        }
     }
 }
 
@@ -569,7 +604,9 @@ bool launch_any(int pass, int nb, const ConvArgs<float>& P, int g0, cudaStream_t
         if (spec2::enabled() || P.refs) return spec2::launch_one<N>(pass, nb, P, g0, s);
     }
     if (P.refs) return false;
-    return spec_launch_one<N>(pass, nb, P, g0, s);
+    // the in-place passes read rows as 16-byte vectors: n % 4 == 0 only
+    if constexpr (N % 4 == 0) return spec_launch_one<N>(pass, nb, P, g0, s);
+    return false;
 }
 
 }  // namespace spec

@@ -22,6 +22,8 @@ bool spec_merge_ok(int n) {
         case 36: return spec2::smem_max(36) <= 200 * 1024;
         case 40: return spec2::smem_max(40) <= 200 * 1024;
         case 48: return spec2::smem_max(48) <= 200 * 1024;
+        case 50: return spec2::smem_max(50) <= 200 * 1024;
+        case 54: return spec2::smem_max(54) <= 200 * 1024;
         case 60: return spec2::smem_max(60) <= 200 * 1024;
         case 64: return spec2::smem_max(64) <= 200 * 1024;
         case 72: return spec2::smem_max(72) <= 200 * 1024;

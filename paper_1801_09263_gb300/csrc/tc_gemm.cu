@@ -15,6 +15,7 @@
 // loads of one step overlap the MMAs of the previous one.  Every mbarrier
 // wait is bounded; on timeout the CTA records an error and stops issuing.
 #include <atomic>
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -267,6 +268,359 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same contraction with the FP32 rows brought in by the Tensor Memory
+// Accelerator: thread 0 keeps TG_STAGES steps of 128 x 64 FP32 tiles of A and
+// B in flight (cp.async.bulk.tensor into plain row-major shared memory,
+// completion counted on the stage's mbarrier; rows past M and columns past K
+// arrive as zeros), all 512 threads split the current step from shared memory
+// into the BF16 hi/lo tiles, and thread 0 hands them to the tensor cores and
+// refills the FP32 stage just read with the step TG_STAGES ahead.  One BF16
+// stage: the split of a step waits for the MMAs of the step before.  Every
+// wait is bounded; on a timeout the CTA records an error, waits (bounded)
+// for its copies and MMAs in flight, frees its tensor memory and returns.
+constexpr int TG_STAGES = 2;
+constexpr int TG_F32_TILE = TC_M * TC_BK * 4;  // 32 KB: 128 rows x 64 FP32
+constexpr int TG_F32_STAGE = 2 * TG_F32_TILE;  // A and B
+constexpr int TG_SMEM_BYTES = TG_STAGES * TG_F32_STAGE + TC_STAGE_BYTES + 1024;
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// 2D tile load: box at element coordinates (x = column, y = row) of the map.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Split this thread's share of a row-major 128 x 64 FP32 tile in shared
+// memory into the swizzled BF16 hi/lo tiles.
+__device__ __forceinline__ void split_tile(const unsigned char* f32, unsigned char* hi_tile, unsigned char* lo_tile) {
+    float4 v[TC_VPT];
+#pragma unroll
+    for (int j = 0; j < TC_VPT; ++j) {
+        const int e = threadIdx.x + j * TC_THREADS;
+        v[j] = *reinterpret_cast<const float4*>(f32 + (size_t)(e >> 4) * (TC_BK * 4) + (e & 15) * 16);
+    }
+    store_tile(v, hi_tile, lo_tile);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gram_tma_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M,
+                       int N, size_t K, size_t kchunk, double* __restrict__ work, int* __restrict__ err) {
+    extern __shared__ unsigned char tc_smem_raw[];
+    __shared__ uint64_t full[TG_STAGES];
+    __shared__ uint64_t mma_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* f32 = smem;                             // [stage][A | B] 128 x 64 FP32, row-major
+    unsigned char* bf = smem + TG_STAGES * TG_F32_STAGE;  // A_hi, A_lo, B_hi, B_lo (swizzled)
+    const int warp = threadIdx.x >> 5;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * TC_N;
+    const size_t k_begin = (size_t)blockIdx.z * kchunk;
+    const size_t k_end = min(K, k_begin + kchunk);
+    const int nsteps = (int)((k_end - k_begin + TC_BK - 1) / TC_BK);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TG_STAGES; ++s) mbar_init(&full[s], 1);
+        mbar_init(&mma_bar, 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+
+    // thread 0: step t of this chunk into FP32 stage t % TG_STAGES
+    int issued = 0;
+    auto issue = [&](int t) {
+        const int s = t % TG_STAGES;
+        const int x = (int)(k_begin + (size_t)t * TC_BK);
+        mbar_expect_tx(&full[s], TG_F32_STAGE);
+        tma_load_2d(f32 + s * TG_F32_STAGE, &map_a, x, m0, &full[s]);
+        tma_load_2d(f32 + s * TG_F32_STAGE + TG_F32_TILE, &map_b, x, n0, &full[s]);
+    };
+    if (threadIdx.x == 0)
+        for (; issued < TG_STAGES && issued < nsteps; ++issued) issue(issued);
+    int step = 0, committed = 0;
+    for (; step < nsteps; ++step) {
+        const int s = step % TG_STAGES;
+        bool ok = mbar_wait(&full[s], (uint32_t)(step / TG_STAGES) & 1);
+        // the BF16 stage is free once the previous step's MMAs are done
+        if (step > 0) ok = ok && mbar_wait(&mma_bar, (uint32_t)(step - 1) & 1);
+        if (!ok) abort_sh = 1;
+        __syncthreads();
+        if (abort_sh) break;
+        const unsigned char* fs = f32 + s * TG_F32_STAGE;
+        split_tile(fs, bf, bf + TC_TILE_BYTES);
+        split_tile(fs + TG_F32_TILE, bf + 2 * TC_TILE_BYTES, bf + 3 * TC_TILE_BYTES);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_hi = smem_u32(bf), a_lo = a_hi + TC_TILE_BYTES;
+            const uint32_t b_hi = a_hi + 2 * TC_TILE_BYTES, b_lo = a_hi + 3 * TC_TILE_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                const uint32_t ko = kk * 32;
+                const uint32_t first = (step == 0 && kk == 0) ? 0u : 1u;
+                mma_bf16(tmem, sw128_desc(a_hi + ko), sw128_desc(b_hi + ko), first);
+                mma_bf16(tmem, sw128_desc(a_hi + ko), sw128_desc(b_lo + ko), 1u);
+                mma_bf16(tmem, sw128_desc(a_lo + ko), sw128_desc(b_hi + ko), 1u);
+            }
+            mma_commit(&mma_bar);
+            // every thread has read FP32 stage s (the barrier above): refill it
+            if (issued < nsteps) issue(issued++);
+        }
+        committed = step + 1;
+    }
+    if (threadIdx.x == 0) {
+        if (abort_sh) {
+            // bounded waits for what is still in flight, so that nothing lands
+            // in shared or tensor memory after the CTA has gone
+            for (int t = step; t < issued; ++t) mbar_wait(&full[t % TG_STAGES], (uint32_t)(t / TG_STAGES) & 1);
+            if (committed > 0) mbar_wait(&mma_bar, (uint32_t)(committed - 1) & 1);
+        } else if (nsteps > 0 && !mbar_wait(&mma_bar, (uint32_t)(nsteps - 1) & 1)) {
+            abort_sh = 1;
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (abort_sh) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+    } else if (warp < 4) {
+        const int row = m0 + warp * 32 + (threadIdx.x & 31);
+        double* out = work + (size_t)blockIdx.z * M * N;
+        if (nsteps == 0) {
+            if (row < M)
+                for (int j = 0; j < TC_N; ++j)
+                    if (n0 + j < N) out[(size_t)row * N + n0 + j] = 0.0;
+        } else {
+#pragma unroll 1
+            for (int c0 = 0; c0 < TC_N; c0 += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < M) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col < N) out[(size_t)row * N + col] = (double)__uint_as_float(v[j]);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+    }
+}
+
+// The TMA-fed Gram in 32-wide K steps, so that two BF16 stages fit beside a
+// deep FP32 pipeline: TG2_STAGES steps of 128 x 32 FP32 tiles of A and B in
+// flight (plain row-major, 16 KB each), and two BF16 stages of the four
+// split tiles (64-byte swizzled K-major, 8 KB each), so the split of step t
+// overlaps the MMAs of step t - 1 and waits only for those of step t - 2.
+// An FP32 stage is refilled as soon as its step is split.
+constexpr int TG2_BK = 32;
+constexpr int TG2_STAGES = 4;
+constexpr int TG2_F32_TILE = TC_M * TG2_BK * 4;       // 16 KB
+constexpr int TG2_F32_STAGE = 2 * TG2_F32_TILE;       // A and B
+constexpr int TG2_BF_TILE = TC_M * TG2_BK * 2;        // 8 KB
+constexpr int TG2_BF_STAGE = 4 * TG2_BF_TILE;         // A_hi, A_lo, B_hi, B_lo
+constexpr int TG2_SMEM_BYTES = TG2_STAGES * TG2_F32_STAGE + 2 * TG2_BF_STAGE + 1024;
+constexpr int TG2_VPT = (TC_M * TG2_BK / 4) / TC_THREADS;  // float4 per thread per tile
+
+// 64-byte swizzled K-major shared-memory descriptor (SBO = 512 B between
+// 8-row groups, version 1, layout type 4 = SWIZZLE_64B).
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(512 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)4 << 61;
+    return d;
+}
+
+// Byte offset of BF16 element (row r, k) in a 64-byte swizzled K-major tile
+// of 32 columns (16-byte chunk c of row r at chunk c ^ ((r / 2) mod 4)).
+__device__ __forceinline__ uint32_t sw64_off(int r, int k) {
+    return (uint32_t)(r * 64 + ((((k >> 3) ^ (r >> 1)) & 3) << 4) + (k & 7) * 2);
+}
+
+__device__ __forceinline__ void split_tile32(const unsigned char* f32, unsigned char* hi_tile, unsigned char* lo_tile) {
+#pragma unroll
+    for (int j = 0; j < TG2_VPT; ++j) {
+        const int e = threadIdx.x + j * TC_THREADS;
+        const int r = e >> 3, kv = (e & 7) * 4;
+        const float4 v = *reinterpret_cast<const float4*>(f32 + (size_t)r * (TG2_BK * 4) + kv * 4);
+        uint2 h, l;
+        split4(v, h, l);
+        const uint32_t off = sw64_off(r, kv);
+        *reinterpret_cast<uint2*>(hi_tile + off) = h;
+        *reinterpret_cast<uint2*>(lo_tile + off) = l;
+    }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_gram_tma2_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M,
+                        int N, size_t K, size_t kchunk, double* __restrict__ work, int* __restrict__ err) {
+    extern __shared__ unsigned char tc_smem_raw[];
+    __shared__ uint64_t full[TG2_STAGES];
+    __shared__ uint64_t mma_bar[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* f32 = smem;                               // [stage][A | B] 128 x 32 FP32, row-major
+    unsigned char* bf = smem + TG2_STAGES * TG2_F32_STAGE;  // [2][A_hi, A_lo, B_hi, B_lo]
+    const int warp = threadIdx.x >> 5;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * TC_N;
+    const size_t k_begin = (size_t)blockIdx.z * kchunk;
+    const size_t k_end = min(K, k_begin + kchunk);
+    const int nsteps = (int)((k_end - k_begin + TG2_BK - 1) / TG2_BK);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TG2_STAGES; ++s) mbar_init(&full[s], 1);
+        mbar_init(&mma_bar[0], 1);
+        mbar_init(&mma_bar[1], 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+
+    int issued = 0;
+    auto issue = [&](int t) {
+        const int s = t % TG2_STAGES;
+        const int x = (int)(k_begin + (size_t)t * TG2_BK);
+        mbar_expect_tx(&full[s], TG2_F32_STAGE);
+        tma_load_2d(f32 + s * TG2_F32_STAGE, &map_a, x, m0, &full[s]);
+        tma_load_2d(f32 + s * TG2_F32_STAGE + TG2_F32_TILE, &map_b, x, n0, &full[s]);
+    };
+    if (threadIdx.x == 0)
+        for (; issued < TG2_STAGES && issued < nsteps; ++issued) issue(issued);
+    int step = 0, committed = 0;
+    for (; step < nsteps; ++step) {
+        const int s = step % TG2_STAGES, b = step & 1;
+        bool ok = mbar_wait(&full[s], (uint32_t)(step / TG2_STAGES) & 1);
+        // BF16 stage b is free once the MMAs of step - 2 (its last user) are done
+        if (step >= 2) ok = ok && mbar_wait(&mma_bar[b], (uint32_t)((step >> 1) - 1) & 1);
+        if (!ok) abort_sh = 1;
+        __syncthreads();
+        if (abort_sh) break;
+        const unsigned char* fs = f32 + s * TG2_F32_STAGE;
+        unsigned char* bs = bf + b * TG2_BF_STAGE;
+        split_tile32(fs, bs, bs + TG2_BF_TILE);
+        split_tile32(fs + TG2_F32_TILE, bs + 2 * TG2_BF_TILE, bs + 3 * TG2_BF_TILE);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_hi = smem_u32(bs), a_lo = a_hi + TG2_BF_TILE;
+            const uint32_t b_hi = a_hi + 2 * TG2_BF_TILE, b_lo = a_hi + 3 * TG2_BF_TILE;
+#pragma unroll
+            for (int kk = 0; kk < TG2_BK / 16; ++kk) {
+                const uint32_t ko = kk * 32;  // 16 BF16 = 32 bytes along K inside the 64-byte row
+                const uint32_t first = (step == 0 && kk == 0) ? 0u : 1u;
+                mma_bf16(tmem, sw64_desc(a_hi + ko), sw64_desc(b_hi + ko), first);
+                mma_bf16(tmem, sw64_desc(a_hi + ko), sw64_desc(b_lo + ko), 1u);
+                mma_bf16(tmem, sw64_desc(a_lo + ko), sw64_desc(b_hi + ko), 1u);
+            }
+            mma_commit(&mma_bar[b]);
+            // every thread has split FP32 stage s (the barrier above): refill it
+            if (issued < nsteps) issue(issued++);
+        }
+        committed = step + 1;
+    }
+    if (threadIdx.x == 0) {
+        if (abort_sh) {
+            for (int t = step; t < issued; ++t) mbar_wait(&full[t % TG2_STAGES], (uint32_t)(t / TG2_STAGES) & 1);
+            for (int t = committed - 2 > 0 ? committed - 2 : 0; t < committed; ++t)
+                mbar_wait(&mma_bar[t & 1], (uint32_t)(t >> 1) & 1);
+        } else {
+            // the last commit of each BF16 stage (commits complete in issue order)
+            for (int t = nsteps - 2 > 0 ? nsteps - 2 : 0; t < nsteps; ++t)
+                if (!mbar_wait(&mma_bar[t & 1], (uint32_t)(t >> 1) & 1)) abort_sh = 1;
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (abort_sh) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+    } else if (warp < 4) {
+        const int row = m0 + warp * 32 + (threadIdx.x & 31);
+        double* out = work + (size_t)blockIdx.z * M * N;
+        if (nsteps == 0) {
+            if (row < M)
+                for (int j = 0; j < TC_N; ++j)
+                    if (n0 + j < N) out[(size_t)row * N + n0 + j] = 0.0;
+        } else {
+#pragma unroll 1
+            for (int c0 = 0; c0 < TC_N; c0 += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < M) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col < N) out[(size_t)row * N + col] = (double)__uint_as_float(v[j]);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+    }
+}
+
 __global__ void tc_reduce_kernel(int M, int N, int nchunk, const double* __restrict__ work, double alpha,
                                  double* __restrict__ C, int ldc) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -451,6 +805,264 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+// The combination with its operands brought in by the Tensor Memory
+// Accelerator, persistent over output tiles: each CTA takes tiles (128 grid
+// points x 256 targets) round-robin and runs their 64-orbital steps as one
+// pipeline of TC_STAGES-deep copies: per step, the FP32 A tile [64 k][128 r]
+// (row-major, rows past Kc and columns past K arrive as zeros) and the
+// pre-split Coef^T hi/lo tiles [256 n][64 k], which TMA writes directly in
+// the 128-byte swizzled K-major layout the MMA reads.  All 512 threads
+// transpose-split A into the BF16 hi/lo tiles (one BF16 stage: the split of a
+// step waits for the MMAs of the step before, and a stage's copies are
+// replaced only after its MMAs are done); after a tile's last MMA all 16
+// warps read the accumulators (warp w: lanes 32 (w % 4).., columns 64 (w / 4)..)
+// and write Out.  Bounded waits throughout; on a timeout the CTA records an
+// error, waits (bounded) for its copies and MMAs in flight, frees its tensor
+// memory and returns.
+constexpr int CT_STAGES = 2;
+constexpr int CT_A32_BYTES = TC_BK * TC_M * 4;                 // 32 KB: 64 k x 128 r FP32
+constexpr int CT_STAGE_BYTES = CT_A32_BYTES + 2 * CB_B_BYTES;  // + Coef^T hi, lo (32 KB each)
+constexpr int CT_SMEM_BYTES = CT_STAGES * CT_STAGE_BYTES + 2 * CB_A_BYTES + 1024;
+
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    tc_combine_tma_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_hi,
+                          const __grid_constant__ CUtensorMap map_lo, int N, size_t K, int kpad, float beta,
+                          float* __restrict__ Out, size_t ldo, int* __restrict__ err) {
+    extern __shared__ unsigned char tc_smem_raw[];
+    __shared__ uint64_t full[CT_STAGES];
+    __shared__ uint64_t mma_bar;
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ int abort_sh;
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* abf = smem + CT_STAGES * CT_STAGE_BYTES;  // A^T hi, lo (swizzled K-major, 128 rows r)
+    const int warp = threadIdx.x >> 5;
+    const int nsteps = kpad / TC_BK;
+    const int rtiles = (int)((K + TC_M - 1) / TC_M), ntiles = (N + CB_N - 1) / CB_N;
+    const int tiles = rtiles * ntiles;
+    const int my_tiles = blockIdx.x < tiles ? (tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int total = my_tiles * nsteps;  // this CTA's steps over all its tiles
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < CT_STAGES; ++s) mbar_init(&full[s], 1);
+        mbar_init(&mma_bar, 1);
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_hi)) : "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_lo)) : "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(CB_N)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+
+    // thread 0: global step g (tile g / nsteps of this CTA, orbital step g % nsteps) into stage g % CT_STAGES
+    int issued = 0;
+    auto issue = [&](int g) {
+        const int s = g % CT_STAGES;
+        const int tile = (int)blockIdx.x + (g / nsteps) * (int)gridDim.x;
+        const int rt = tile % rtiles, nt = tile / rtiles;
+        const int k0 = (g % nsteps) * TC_BK;
+        unsigned char* st = smem + s * CT_STAGE_BYTES;
+        mbar_expect_tx(&full[s], CT_STAGE_BYTES);
+        tma_load_2d(st, &map_a, rt * TC_M, k0, &full[s]);
+        tma_load_2d(st + CT_A32_BYTES, &map_hi, k0, nt * CB_N, &full[s]);
+        tma_load_2d(st + CT_A32_BYTES + CB_B_BYTES, &map_lo, k0, nt * CB_N, &full[s]);
+    };
+    if (threadIdx.x == 0)
+        for (; issued < CT_STAGES && issued < total; ++issued) issue(issued);
+    // this thread's transpose-split share: grid point ar, k quads aq + 4j
+    const int ar = threadIdx.x & (TC_M - 1), aq = threadIdx.x >> 7;
+    int g = 0, committed = 0;
+    for (; g < total; ++g) {
+        const int s = g % CT_STAGES, step = g % nsteps;
+        bool ok = mbar_wait(&full[s], (uint32_t)(g / CT_STAGES) & 1);
+        if (g > 0) ok = ok && mbar_wait(&mma_bar, (uint32_t)(g - 1) & 1);
+        if (!ok) abort_sh = 1;
+        __syncthreads();
+        if (abort_sh) break;
+        // the MMAs of step g - 1 are done: its stage may be refilled
+        if (threadIdx.x == 0 && g > 0 && issued < total) issue(issued++);
+        if (g > 0 && step == 0) {
+            // the previous tile is complete: accumulators -> Out
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const int tile = (int)blockIdx.x + ((g - 1) / nsteps) * (int)gridDim.x;
+            const int rt = tile % rtiles, nt = tile / rtiles;
+            const size_t r = (size_t)rt * TC_M + (warp & 3) * 32 + (threadIdx.x & 31);
+            const int cb = (warp >> 2) * 64;
+#pragma unroll 1
+            for (int c0 = cb; c0 < cb + 64; c0 += 16) {
+                if (nt * CB_N + c0 >= N) break;
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (r < K) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int n = nt * CB_N + c0 + j;
+                        if (n < N) {
+                            float* o = Out + (size_t)n * ldo + r;
+                            *o = beta == 0.f ? __uint_as_float(v[j]) : beta * *o + __uint_as_float(v[j]);
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        }
+        // A^T: FP32 [64 k][128 r] -> BF16 hi/lo, K-major rows r
+        const float* a32 = reinterpret_cast<const float*>(smem + s * CT_STAGE_BYTES);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int kq = (aq + 4 * j) * 4;
+            const float4 v = make_float4(a32[(kq + 0) * TC_M + ar], a32[(kq + 1) * TC_M + ar],
+                                         a32[(kq + 2) * TC_M + ar], a32[(kq + 3) * TC_M + ar]);
+            uint2 h, l;
+            split4(v, h, l);
+            const uint32_t off = sw128_off(ar, kq);
+            *reinterpret_cast<uint2*>(abf + off) = h;
+            *reinterpret_cast<uint2*>(abf + CB_A_BYTES + off) = l;
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_hi = smem_u32(abf), a_lo = a_hi + CB_A_BYTES;
+            const uint32_t b_hi = smem_u32(smem + s * CT_STAGE_BYTES + CT_A32_BYTES), b_lo = b_hi + CB_B_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < TC_BK / 16; ++kk) {
+                const uint32_t ko = kk * 32;
+                const uint32_t first = (step == 0 && kk == 0) ? 0u : 1u;
+                mma_bf16_n256(tmem, sw128_desc(a_hi + ko), sw128_desc(b_hi + ko), first);
+                mma_bf16_n256(tmem, sw128_desc(a_hi + ko), sw128_desc(b_lo + ko), 1u);
+                mma_bf16_n256(tmem, sw128_desc(a_lo + ko), sw128_desc(b_hi + ko), 1u);
+            }
+            mma_commit(&mma_bar);
+        }
+        committed = g + 1;
+    }
+    if (threadIdx.x == 0) {
+        if (abort_sh) {
+            for (int t = g; t < issued; ++t) mbar_wait(&full[t % CT_STAGES], (uint32_t)(t / CT_STAGES) & 1);
+            if (committed > 0) mbar_wait(&mma_bar, (uint32_t)(committed - 1) & 1);
+        } else if (total > 0 && !mbar_wait(&mma_bar, (uint32_t)(total - 1) & 1)) {
+            abort_sh = 1;
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (abort_sh) {
+        if (threadIdx.x == 0) atomicExch(err, 1);
+    } else if (total > 0) {
+        // the last tile
+        const int tile = (int)blockIdx.x + ((total - 1) / nsteps) * (int)gridDim.x;
+        const int rt = tile % rtiles, nt = tile / rtiles;
+        const size_t r = (size_t)rt * TC_M + (warp & 3) * 32 + (threadIdx.x & 31);
+        const int cb = (warp >> 2) * 64;
+#pragma unroll 1
+        for (int c0 = cb; c0 < cb + 64; c0 += 16) {
+            if (nt * CB_N + c0 >= N) break;
+            uint32_t v[16];
+            const uint32_t taddr = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                  "=r"(v[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            if (r < K) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = nt * CB_N + c0 + j;
+                    if (n < N) {
+                        float* o = Out + (size_t)n * ldo + r;
+                        *o = beta == 0.f ? __uint_as_float(v[j]) : beta * *o + __uint_as_float(v[j]);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(CB_N) : "memory");
+    }
+}
+
+}  // namespace
+
+namespace {
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// The driver's tensor-map encoder (through the runtime's entry-point query,
+// so no link against the driver library), or null.  LACE_TC_TMA=0 turns the
+// TMA-fed Gram kernel off (tuning: the register-staged kernel then runs).
+EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = []() -> EncodeTiledFn {
+        const char* e = getenv("LACE_TC_TMA");
+        if (e && e[0] == '0') return nullptr;
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(f);
+    }();
+    return fn;
+}
+
+// Tensor map of a row-major matrix [rows][cols] (row pitch ld elements of
+// esize bytes; 16-byte aligned base and pitch) in boxes of box_rows x
+// box_cols; reads outside the matrix return zeros.
+bool make_map(CUtensorMap* m, CUtensorMapDataType type, size_t esize, const void* base, size_t rows, size_t cols,
+              size_t ld, int box_cols, int box_rows, CUtensorMapSwizzle swz) {
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc || rows == 0 || cols == 0 || rows > 0xffffffffull || cols > 0xffffffffull) return false;
+    if (((uintptr_t)base % 16) || ((ld * esize) % 16)) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)(ld * esize)};
+    const cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, type, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// FP32 [rows][cols] in boxes of 128 rows x bk columns (the Gram's A and B tiles).
+bool make_tile_map(CUtensorMap* m, const float* base, size_t rows, size_t cols, size_t ld, int bk) {
+    return make_map(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), base, rows, cols, ld, bk, TC_M,
+                    CU_TENSOR_MAP_SWIZZLE_NONE);
+}
+
+// LACE_TC_GRAM=32 selects the 32-wide double-buffered TMA Gram kernel
+// (tuning; default: the 64-wide one with a single BF16 stage).
+bool gram_wide() {
+    static const bool w = [] {
+        const char* e = getenv("LACE_TC_GRAM");
+        return !(e && atoi(e) == 32);
+    }();
+    return w;
+}
+
 }  // namespace
 
 size_t tc_combine_scratch_bytes(int N, int Kc) {
@@ -473,15 +1085,38 @@ cudaError_t tc_combine(int N, size_t K, int Kc, const float* A, size_t lda, cons
     if (dev < 64 && !(attr_done.load() & (1ull << dev))) {
         cudaError_t e =
             cudaFuncSetAttribute(tc_combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB_SMEM_BYTES);
+        if (!e)
+            e = cudaFuncSetAttribute(tc_combine_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     CT_SMEM_BYTES);
         if (e) return e;
         attr_done.fetch_or(1ull << dev);
     }
     cudaMemsetAsync(d_err, 0, sizeof(int), s);
     const int tot = kpad * npad;
     coef_split_kernel<<<(tot + 255) / 256, 256, 0, s>>>(Kc, N, Coef, ldcoef, kpad, npad, hiT, loT);
-    dim3 grid((unsigned)((K + TC_M - 1) / TC_M), npad / CB_N);
-    tc_combine_kernel<<<grid, TC_THREADS, CB_SMEM_BYTES, s>>>(N, K, Kc, kpad, A, lda, hiT, loT, (float)beta, Out,
-                                                              ldo, d_err);
+    // TMA-fed persistent kernel: A as [Kc][K] FP32 in boxes of 64 k x 128 r;
+    // Coef^T hi/lo as [npad][kpad] BF16 in boxes of 256 n x 64 k, written by
+    // the copy in the 128-byte swizzled layout
+    CUtensorMap map_a, map_hi, map_lo;
+    const bool tma = K <= 0x7fffffffull &&
+                     make_map(&map_a, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, sizeof(float), A, (size_t)Kc, K, lda, TC_M,
+                              TC_BK, CU_TENSOR_MAP_SWIZZLE_NONE) &&
+                     make_map(&map_hi, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, hiT, (size_t)npad, (size_t)kpad,
+                              (size_t)kpad, TC_BK, CB_N, CU_TENSOR_MAP_SWIZZLE_128B) &&
+                     make_map(&map_lo, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, loT, (size_t)npad, (size_t)kpad,
+                              (size_t)kpad, TC_BK, CB_N, CU_TENSOR_MAP_SWIZZLE_128B);
+    if (tma) {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const long long tiles = (long long)((K + TC_M - 1) / TC_M) * (npad / CB_N);
+        const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, sms));
+        tc_combine_tma_kernel<<<grid, TC_THREADS, CT_SMEM_BYTES, s>>>(map_a, map_hi, map_lo, N, K, kpad, (float)beta,
+                                                                      Out, ldo, d_err);
+    } else {
+        dim3 grid((unsigned)((K + TC_M - 1) / TC_M), npad / CB_N);
+        tc_combine_kernel<<<grid, TC_THREADS, CB_SMEM_BYTES, s>>>(N, K, Kc, kpad, A, lda, hiT, loT, (float)beta,
+                                                                  Out, ldo, d_err);
+    }
     *launches += 2;
     if (h_err) {
         cudaMemcpyAsync(h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
@@ -490,6 +1125,7 @@ cudaError_t tc_combine(int N, size_t K, int Kc, const float* A, size_t lda, cons
     }
     return cudaGetLastError();
 }
+
 
 size_t tc_gram_work_elems(int M, int N, size_t K) {
     const size_t tiles = (size_t)((M + TC_M - 1) / TC_M) * ((N + TC_N - 1) / TC_N);
@@ -516,12 +1152,27 @@ cudaError_t tc_gram(int M, int N, size_t K, const float* A, size_t lda, const fl
     cudaGetDevice(&dev);
     if (dev < 64 && !(attr_done.load() & (1ull << dev))) {
         cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+        if (!e)
+            e = cudaFuncSetAttribute(tc_gram_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TG_SMEM_BYTES);
+        if (!e)
+            e = cudaFuncSetAttribute(tc_gram_tma2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     TG2_SMEM_BYTES);
         if (e) return e;
         attr_done.fetch_or(1ull << dev);
     }
     cudaMemsetAsync(d_err, 0, sizeof(int), s);
     dim3 grid((M + TC_M - 1) / TC_M, (N + TC_N - 1) / TC_N, (unsigned)nch_eff);
-    tc_gram_kernel<<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(M, N, K, A, lda, B, ldb, kchunk, work, d_err);
+    CUtensorMap map_a, map_b;
+    const int bk = gram_wide() ? TC_BK : TG2_BK;
+    if (K <= 0x7fffffffull && make_tile_map(&map_a, A, (size_t)M, K, lda, bk) &&
+        make_tile_map(&map_b, B, (size_t)N, K, ldb, bk)) {
+        if (bk == TC_BK)
+            tc_gram_tma_kernel<<<grid, TC_THREADS, TG_SMEM_BYTES, s>>>(map_a, map_b, M, N, K, kchunk, work, d_err);
+        else
+            tc_gram_tma2_kernel<<<grid, TC_THREADS, TG2_SMEM_BYTES, s>>>(map_a, map_b, M, N, K, kchunk, work, d_err);
+    } else {
+        tc_gram_kernel<<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(M, N, K, A, lda, B, ldb, kchunk, work, d_err);
+    }
     const size_t tot = (size_t)M * N;
     tc_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, N, (int)nch_eff, work, alpha, C, ldc);
     *launches += 2;

@@ -18,7 +18,7 @@ import numpy as np
 import pytest
 
 RADICES = (2, 3, 4, 5, 6, 8, 9, 10, 12, 16)
-SIZES = (24, 32, 36, 40, 48, 60, 64, 72, 80, 96, 100)
+SIZES = (24, 32, 36, 40, 48, 50, 54, 60, 64, 72, 80, 96, 100)
 
 
 def plan2(n):

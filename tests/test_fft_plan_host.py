@@ -29,6 +29,6 @@ def test_out_of_place_pass_plans_fit_one_sm(tmp_path):
     out = subprocess.run([str(exe)], capture_output=True, text=True)
     assert out.returncode == 0, out.stdout
     lines = out.stdout.strip().splitlines()
-    assert len(lines) == 11 and all(line.endswith("ok") for line in lines), out.stdout
+    assert len(lines) == 13 and all(line.endswith("ok") for line in lines), out.stdout
     # the 72^3 workload: radix 9 x 8, 576 threads, two CTAs per SM
     assert "n=72 plan=9x8 threads=576 ctas=2" in out.stdout

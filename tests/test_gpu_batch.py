@@ -199,3 +199,27 @@ def test_per_instance_mode_matches_the_persistent_kernel(batch_runs, monkeypatch
             s, thr, _ = sy[q]
             assert len(b.context(q).get_pairs()) == len(single(s, thr, phis[q])["pairs"])
             assert abs(ex2[q] - single(s, thr, phis[q])["ex"]) <= 1e-5
+
+
+@pytest.mark.parametrize("shape", ["256x2", "512x1", "512x2"])
+def test_every_persistent_launch_shape_matches(batch_runs, monkeypatch, shape):
+    """The persistent kernel in each of its shapes with size-specialised
+    bodies (thread groups of 128-512 threads sharing a CTA, each on its own
+    plane or slab): E_x, W and xi against the first run of the batch (which
+    the autotuner may have given to either mode)."""
+    sy, out = batch_runs
+    monkeypatch.setenv("LACE_BATCH_SHAPE", shape)
+    with Batch([(s.cell, s.shape, s.ecut, s.n_occ, thr) for s, thr, _ in sy]) as b:
+        for q, (_, _, p) in enumerate(sy):
+            b.set_orbitals(q, p)
+        for _ in range(2):  # eager, capture
+            ex, st = b.run()
+            assert (st == 0).all(), st
+            assert np.max(np.abs(ex - out["runs"][0][0])) <= 1e-5
+        info = b.info()
+        assert info["mode"] == "persistent"
+        assert f'{info["threads"]}x{info["ctas_per_sm"]}' == shape
+        for q in range(len(sy)):
+            v = b.context(q)
+            assert relerr(v.get_orbitals(B.ORB_W), out["W"][q]) <= 2e-5
+            assert relerr(v.get_orbitals(B.ORB_XI), out["xi"][q]) <= 2e-5

@@ -117,7 +117,7 @@ def test_single_orbital_and_odd_pair_count(prec):
 # out-of-place passes (24 ... 100) and the in-place ones (128, whose two planes
 # do not fit on chip).  3 occupied + 1 extra orbital: 6 occupied pairs and 3
 # occupied-extra pairs, 5 complex grids of which the last holds one pair.
-SPEC_SIZES = [24, 32, 36, 40, 48, 60, 64, 72, 80, 96, 100, 128]
+SPEC_SIZES = [24, 32, 36, 40, 48, 50, 54, 60, 64, 72, 80, 96, 100, 128]
 
 
 @pytest.mark.parametrize("n", SPEC_SIZES)
