@@ -86,6 +86,8 @@ def parse():
     p.add_argument("--serve-slots", type=int, default=8)
     p.add_argument("--serve-rebuild-slots", type=int, default=4)
     p.add_argument("--serve-fp64", action="store_true", help="serve in the plain FP64 form (for comparison)")
+    p.add_argument("--serve-no-merge", action="store_true",
+                   help="serve without merged pair convolutions and REBUILD groups (for comparison)")
     p.add_argument("--no-serving", action="store_true", help="skip the serving sample of the default run")
     p.add_argument("--batched", action="store_true",
                    help="only the batched uneven instances (48 systems, persistent launch in a CUDA graph)")
@@ -447,7 +449,7 @@ SERVE_INNER_DECAY = 0.5
 SERVE_CADENCE_TOL = 1e-5  # rebuild once the block's ACE energy moves by less than this (relative)
 
 
-def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp64=False):
+def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp64=False, merging=True):
     """The serving stream: resident systems (N log-uniform in [32, 512],
     2/3/5-smooth cubic grids in [48, 128]), each an SCF-like client running
     the double loop of the paper (Sec. 2): an outer iteration is a REBUILD
@@ -489,6 +491,8 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
     gaps = rng.exponential(n_systems / SERVE_RATE, size=(n_systems, nreq_max))
     arrivals = np.cumsum(gaps, axis=1)
     srv = lace.Server(local, lace.LACE_FP64 if fp64 else lace.LACE_MIXED, slots=slots, rebuild_slots=rebuild_slots)
+    if not merging:
+        srv.set_pair_merging(False, 0.0)
     sids = [srv.add_system(s.cell, s.shape, s.ecut, s.n_occ, 0, S_THR) for s in systems]
     for sid in sids:
         srv.set_rebuild_tolerance(sid, SERVE_CADENCE_TOL)
@@ -610,7 +614,8 @@ def run_serving(local, n_systems, iters, slots, rebuild_slots, fp64_sample=4, fp
                     f"block's ACE energy moves by < {SERVE_CADENCE_TOL:g} relative, at most {SERVE_MAX_INNER}), "
                     f"Poisson arrivals {SERVE_RATE:g} req/s offered, closed loop per system, {slots} slots "
                     f"({rebuild_slots} for rebuilds), "
-                    f"S_thr={S_THR:g}, {'plain FP64' if fp64 else 'mixed precision'}",
+                    f"S_thr={S_THR:g}, {'plain FP64' if fp64 else 'mixed precision'}, "
+                    f"{'merged pair convolutions of same-grid REBUILD groups' if merging else 'no merging'}",
         "requests": len(all_lat), "failed": fails[:8], "n_failed": len(fails),
         "latency_ms": {"p50": pct(all_lat, 50), "p99": pct(all_lat, 99),
                        "rebuild_p50": pct(lat["rebuild"], 50), "rebuild_p99": pct(lat["rebuild"], 99),
@@ -797,7 +802,8 @@ def main():
 
         build()
         print(json.dumps({"serving": run_serving(local, args.serve_systems, args.serve_iters, args.serve_slots,
-                                                 args.serve_rebuild_slots, fp64=args.serve_fp64)}), flush=True)
+                                                 args.serve_rebuild_slots, fp64=args.serve_fp64,
+                                                 merging=not args.serve_no_merge)}), flush=True)
     elif args.impl == "reference":
         run_reference(args, rank, world)
     else:

@@ -369,7 +369,8 @@ lace_status enqueue_hot(lace_batch* b, bool capturing) {
     for (int q = 0; q < b->n; ++q) {
         if (!b->in_graph[q]) continue;
         lace_ctx* c = b->ctx[q];
-        BCK(exchange_energy_sum(c->n_occ, c->m(MS_E), c->exd.as<double>(), b->main, &l), "energy");
+        BCK(exchange_energy_sum(c->n_occ, c->m(MS_E), c->exd.as<double>() + 8, c->exd.as<double>(), b->main, &l),
+            "energy");
     }
     BCK(cudaEventRecord(b->ev_fork, b->main), "batch");
     for (int k = 0; k < kBranches; ++k) BCK(cudaStreamWaitEvent(b->branch[k], b->ev_fork, 0), "batch");

@@ -160,7 +160,7 @@ lace_status ensure_orbital_buffers(lace_ctx* c, int n_occ, int n_extra) {
     const size_t wk = std::max(gemm_rows_work_elems(n_p, n_p, ng), (size_t)1);
     CK(c->work.ensure(wk * sizeof(double)), "alloc work");
     CK(c->flag.ensure(64), "alloc flag");
-    CK(c->exd.ensure(64), "alloc exd");
+    CK(c->exd.ensure((8 + 2 * kSumBlocks) * sizeof(double)), "alloc exd");  // [0] E_x, [1] ACE energy, sum scratch
     CK(c->counts.ensure(sizeof(int) * (2 * (size_t)n_occ + 2)), "alloc counts");
     return LACE_OK;
 }
@@ -513,7 +513,8 @@ lace_status apply_impl(lace_ctx* c) {
                        &L.n, c->ev[2 * ST_PAIRCONV], c->ev[2 * ST_PAIRCONV + 1]),
        "pair convolutions");
     c->ev_used[ST_PAIRCONV] = true;
-    CK(exchange_energy_sum(c->n_occ, c->m(MS_E), c->exd.as<double>(), c->stream, &L.n), "energy");
+    CK(exchange_energy_sum(c->n_occ, c->m(MS_E), c->exd.as<double>() + 8, c->exd.as<double>(), c->stream, &L.n),
+       "energy");
     return LACE_OK;
 }
 
@@ -553,7 +554,8 @@ lace_status exchange_prepare_f(lace_ctx* c, MergedSys<float>* m, int* n_grids_ou
 
 lace_status exchange_finish(lace_ctx* c) {
     Launch L{c};
-    CK(exchange_energy_sum(c->n_occ, c->m(MS_E), c->exd.as<double>(), c->stream, &L.n), "energy");
+    CK(exchange_energy_sum(c->n_occ, c->m(MS_E), c->exd.as<double>() + 8, c->exd.as<double>(), c->stream, &L.n),
+       "energy");
     return LACE_OK;
 }
 
@@ -658,7 +660,9 @@ lace_status apply_ace_impl(lace_ctx* c, const double* d_psi64, int nf, double* d
         if (st) return st;
     }
     // the block's ACE energy sum_j <psi_j|K_ACE|psi_j> = dV psi^T xi X = -|X|^2
-    CK(neg_sum_squares((size_t)n * nf, X, c->exd.as<double>() + 1, c->stream, &L.n), "ace energy");
+    CK(neg_sum_squares((size_t)n * nf, X, c->exd.as<double>() + 8 + kSumBlocks, c->exd.as<double>() + 1, c->stream,
+                       &L.n),
+       "ace energy");
     T* dst = sizeof(T) == 8 ? reinterpret_cast<T*>(d_out64) : out;
     {
         lace_status st = ace_combine<T>(c, nf, n, c->xi.as<T>(), X, dst, L);

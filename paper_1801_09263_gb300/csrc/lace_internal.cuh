@@ -231,10 +231,15 @@ cudaError_t build_pair_list(int n_occ, int n_extra, const double* d_S, double th
                             int* d_counts, long long* n_pairs, cudaStream_t s, int* launches);
 // Pack pairs two by two into complex FFT grids.
 cudaError_t pack_pair_grids(const int2* d_pairs, long long n_pairs, PairGrid* d_grids, cudaStream_t s, int* launches);
+// Fixed-order FP64 sums over up to kSumBlocks blocks; part: kSumBlocks
+// doubles of scratch (one caller at a time per scratch).
+constexpr int kSumBlocks = 128;
 // out[0] = -sum of the squares of the m entries of X (fixed order).
-cudaError_t neg_sum_squares(size_t m, const double* d_X, double* d_out, cudaStream_t s, int* launches);
+cudaError_t neg_sum_squares(size_t m, const double* d_X, double* d_part, double* d_out, cudaStream_t s,
+                            int* launches);
 // E_x = -1/2 sum_ij E[i][j] over the n_occ x n_occ pair-energy matrix.
-cudaError_t exchange_energy_sum(int n_occ, const double* d_E, double* d_ex, cudaStream_t s, int* launches);
+cudaError_t exchange_energy_sum(int n_occ, const double* d_E, double* d_part, double* d_ex, cudaStream_t s,
+                                int* launches);
 
 // Precision conversions and small helpers (linalg.cu)
 template <typename Tin, typename Tout>

@@ -91,39 +91,60 @@ __global__ void pack_kernel(const int2* __restrict__ pairs, long long n_pairs, P
     grids[g] = d;
 }
 
-__global__ void energy_sum_kernel(int n, const double* __restrict__ E, double* __restrict__ ex) {
+// Fixed-order FP64 sums over many blocks (FP64 issues slowly: a one-block
+// sum of 65,536 values took ~120 us).  Block b sums the contiguous range b
+// of m values (x, or x^2 with SQUARE) into part[b]; a second one-block
+// kernel adds the partials in order and scales them.
+template <bool SQUARE>
+__global__ void partial_sum_kernel(size_t m, size_t chunk, const double* __restrict__ x, double* __restrict__ part) {
     __shared__ double sh[SC_THREADS];
-    double s = 0.0;
-    for (size_t idx = threadIdx.x; idx < (size_t)n * n; idx += blockDim.x) s += E[idx];
-    sh[threadIdx.x] = s;
+    const size_t lo = (size_t)blockIdx.x * chunk, hi = lo + chunk < m ? lo + chunk : m;
+    double s0 = 0.0, s1 = 0.0;
+    size_t i = lo + threadIdx.x;
+    for (; i + SC_THREADS < hi; i += 2 * SC_THREADS) {
+        const double a = x[i], b = x[i + SC_THREADS];
+        s0 += SQUARE ? a * a : a;
+        s1 += SQUARE ? b * b : b;
+    }
+    if (i < hi) s0 += SQUARE ? x[i] * x[i] : x[i];
+    sh[threadIdx.x] = s0 + s1;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    for (int o = SC_THREADS / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) ex[0] = -0.5 * sh[0];
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
 }
 
-// out[0] = -sum of squares of X (m entries), one block, fixed order.
-__global__ void neg_sum_sq_kernel(size_t m, const double* __restrict__ X, double* __restrict__ out) {
+__global__ void finish_sum_kernel(int nb, const double* __restrict__ part, double scale, double* __restrict__ out) {
     __shared__ double sh[SC_THREADS];
     double s = 0.0;
-    for (size_t idx = threadIdx.x; idx < m; idx += blockDim.x) s += X[idx] * X[idx];
+    for (int b = threadIdx.x; b < nb; b += SC_THREADS) s += part[b];
     sh[threadIdx.x] = s;
     __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    for (int o = SC_THREADS / 2; o > 0; o >>= 1) {
         if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[0] = -sh[0];
+    if (threadIdx.x == 0) out[0] = scale * sh[0];
+}
+
+cudaError_t fixed_sum(size_t m, const double* d_x, bool square, double scale, double* d_part, double* d_out,
+                      cudaStream_t s, int* launches) {
+    const int nb = (int)std::max<size_t>(1, std::min<size_t>(kSumBlocks, (m + 2047) / 2048));
+    const size_t chunk = (m + nb - 1) / nb;
+    if (square) partial_sum_kernel<true><<<nb, SC_THREADS, 0, s>>>(m, chunk, d_x, d_part);
+    else partial_sum_kernel<false><<<nb, SC_THREADS, 0, s>>>(m, chunk, d_x, d_part);
+    finish_sum_kernel<<<1, SC_THREADS, 0, s>>>(nb, d_part, scale, d_out);
+    *launches += 2;
+    return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t neg_sum_squares(size_t m, const double* d_X, double* d_out, cudaStream_t s, int* launches) {
-    neg_sum_sq_kernel<<<1, SC_THREADS, 0, s>>>(m, d_X, d_out);
-    *launches += 1;
-    return cudaGetLastError();
+cudaError_t neg_sum_squares(size_t m, const double* d_X, double* d_part, double* d_out, cudaStream_t s,
+                            int* launches) {
+    return fixed_sum(m, d_X, true, -1.0, d_part, d_out, s, launches);
 }
 
 cudaError_t build_pair_list(int n_occ, int n_extra, const double* d_S, double thr, bool use_S, int2* d_pairs,
@@ -149,10 +170,9 @@ cudaError_t pack_pair_grids(const int2* d_pairs, long long n_pairs, PairGrid* d_
     return cudaGetLastError();
 }
 
-cudaError_t exchange_energy_sum(int n_occ, const double* d_E, double* d_ex, cudaStream_t s, int* launches) {
-    energy_sum_kernel<<<1, SC_THREADS, 0, s>>>(n_occ, d_E, d_ex);
-    *launches += 1;
-    return cudaGetLastError();
+cudaError_t exchange_energy_sum(int n_occ, const double* d_E, double* d_part, double* d_ex, cudaStream_t s,
+                                int* launches) {
+    return fixed_sum((size_t)n_occ * n_occ, d_E, false, -0.5, d_part, d_ex, s, launches);
 }
 
 }  // namespace lace

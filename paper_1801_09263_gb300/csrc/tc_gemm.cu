@@ -94,17 +94,24 @@ __device__ __forceinline__ uint32_t sw128_off(int r, int k) {
     return (uint32_t)(r * 128 + ((((k >> 3) ^ (r & 7)) & 7) << 4) + (k & 7) * 2);
 }
 
+// Two FP32 values rounded to BF16 (round to nearest even) and packed: x0 in
+// the low half (the lower address), x1 in the high half.
+__device__ __forceinline__ uint32_t bf16x2_rn(float x0, float x1) {
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(x1), "f"(x0));
+    return r;
+}
+
+// hi = bf16(x), lo = bf16(x - hi) for four values, packed in element order
+// (one conversion instruction per two values; a BF16 value widens to FP32
+// exactly by placing its bits in the upper half).
 __device__ __forceinline__ void split4(float4 v, uint2& hi, uint2& lo) {
-    const __nv_bfloat16 h0 = __float2bfloat16_rn(v.x), h1 = __float2bfloat16_rn(v.y);
-    const __nv_bfloat16 h2 = __float2bfloat16_rn(v.z), h3 = __float2bfloat16_rn(v.w);
-    const __nv_bfloat16 l0 = __float2bfloat16_rn(v.x - __bfloat162float(h0));
-    const __nv_bfloat16 l1 = __float2bfloat16_rn(v.y - __bfloat162float(h1));
-    const __nv_bfloat16 l2 = __float2bfloat16_rn(v.z - __bfloat162float(h2));
-    const __nv_bfloat16 l3 = __float2bfloat16_rn(v.w - __bfloat162float(h3));
-    hi.x = (uint32_t)__bfloat16_as_ushort(h0) | ((uint32_t)__bfloat16_as_ushort(h1) << 16);
-    hi.y = (uint32_t)__bfloat16_as_ushort(h2) | ((uint32_t)__bfloat16_as_ushort(h3) << 16);
-    lo.x = (uint32_t)__bfloat16_as_ushort(l0) | ((uint32_t)__bfloat16_as_ushort(l1) << 16);
-    lo.y = (uint32_t)__bfloat16_as_ushort(l2) | ((uint32_t)__bfloat16_as_ushort(l3) << 16);
+    hi.x = bf16x2_rn(v.x, v.y);
+    hi.y = bf16x2_rn(v.z, v.w);
+    const float r0 = v.x - __uint_as_float(hi.x << 16), r1 = v.y - __uint_as_float(hi.x & 0xffff0000u);
+    const float r2 = v.z - __uint_as_float(hi.y << 16), r3 = v.w - __uint_as_float(hi.y & 0xffff0000u);
+    lo.x = bf16x2_rn(r0, r1);
+    lo.y = bf16x2_rn(r2, r3);
 }
 
 // Load this thread's share of a 128 x 64 FP32 tile (rows row0.., columns
@@ -621,6 +628,195 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     }
 }
 
+// The 32-wide TMA-fed Gram with warp roles instead of CTA-wide barriers:
+// warps 0-15 split (and later read the accumulators), warp 16 (lane 0)
+// issues the TMA copies, warp 17 (lane 0) issues the MMAs.  They hand off
+// through mbarriers only: full[s] (copies landed), empty[s] (stage s split,
+// one arrival per splitting warp), split[b] (BF16 stage b written, one
+// arrival per splitting warp) and mma[b] (the MMAs that read BF16 stage b
+// are done; tcgen05.commit).  So the copies run TG2_STAGES steps ahead, the
+// split of step t overlaps the MMAs of step t - 1, and no role waits for
+// another except on data.  Every wait is bounded and also gives up once
+// another role has recorded a timeout; the roles then drain what they
+// started (bounded) and the CTA reports the error.
+constexpr int TW_SPLIT_WARPS = 16;
+constexpr int TW_THREADS = (TW_SPLIT_WARPS + 2) * 32;
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait that also gives up when *abort is set.
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    const uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < TC_WAIT_LIMIT; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n.reg .pred p;\n"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            "selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if ((it & 63) == 63 && *abort) return false;
+    }
+    *abort = 1;
+    return false;
+}
+
+__global__ void __launch_bounds__(TW_THREADS, 1)
+    tc_gram_ws_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M,
+                      int N, size_t K, size_t kchunk, double* __restrict__ work, int* __restrict__ err) {
+    extern __shared__ unsigned char tc_smem_raw[];
+    __shared__ uint64_t full[TG2_STAGES], empty[TG2_STAGES], split_bar[2], mma_bar[2];
+    __shared__ uint32_t tmem_base_sh;
+    __shared__ volatile int abort_sh;
+    __shared__ int last_issued[TG2_STAGES];
+    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* f32 = smem;
+    unsigned char* bf = smem + TG2_STAGES * TG2_F32_STAGE;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * TC_N;
+    const size_t k_begin = (size_t)blockIdx.z * kchunk;
+    const size_t k_end = min(K, k_begin + kchunk);
+    const int nsteps = (int)((k_end - k_begin + TG2_BK - 1) / TG2_BK);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < TG2_STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], TW_SPLIT_WARPS);
+            last_issued[s] = -1;
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&split_bar[b], TW_SPLIT_WARPS);
+            mbar_init(&mma_bar[b], 1);
+        }
+        abort_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base_sh)),
+                     "r"(128)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = tmem_base_sh;
+    int committed = 0;  // MMA thread: steps committed
+
+    if (warp == TW_SPLIT_WARPS) {
+        // producer: step t into FP32 stage t % TG2_STAGES once its previous step was split
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
+            for (int t = 0; t < nsteps; ++t) {
+                const int s = t % TG2_STAGES;
+                if (t >= TG2_STAGES &&
+                    !mbar_wait_or_abort(&empty[s], (uint32_t)(t / TG2_STAGES - 1) & 1, &abort_sh))
+                    break;
+                const int x = (int)(k_begin + (size_t)t * TG2_BK);
+                mbar_expect_tx(&full[s], TG2_F32_STAGE);
+                tma_load_2d(f32 + s * TG2_F32_STAGE, &map_a, x, m0, &full[s]);
+                tma_load_2d(f32 + s * TG2_F32_STAGE + TG2_F32_TILE, &map_b, x, n0, &full[s]);
+                last_issued[s] = t;
+            }
+        }
+    } else if (warp == TW_SPLIT_WARPS + 1) {
+        // MMA issuer
+        if (lane == 0) {
+            for (int t = 0; t < nsteps; ++t) {
+                const int b = t & 1;
+                if (!mbar_wait_or_abort(&split_bar[b], (uint32_t)(t >> 1) & 1, &abort_sh)) break;
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t a_hi = smem_u32(bf + b * TG2_BF_STAGE), a_lo = a_hi + TG2_BF_TILE;
+                const uint32_t b_hi = a_hi + 2 * TG2_BF_TILE, b_lo = a_hi + 3 * TG2_BF_TILE;
+#pragma unroll
+                for (int kk = 0; kk < TG2_BK / 16; ++kk) {
+                    const uint32_t ko = kk * 32;
+                    const uint32_t first = (t == 0 && kk == 0) ? 0u : 1u;
+                    mma_bf16(tmem, sw64_desc(a_hi + ko), sw64_desc(b_hi + ko), first);
+                    mma_bf16(tmem, sw64_desc(a_hi + ko), sw64_desc(b_lo + ko), 1u);
+                    mma_bf16(tmem, sw64_desc(a_lo + ko), sw64_desc(b_hi + ko), 1u);
+                }
+                mma_commit(&mma_bar[b]);
+                committed = t + 1;
+            }
+        }
+    } else {
+        // splitters: 512 threads, TG2_VPT vectors per tile each
+        for (int t = 0; t < nsteps; ++t) {
+            const int s = t % TG2_STAGES, b = t & 1;
+            if (!mbar_wait_or_abort(&full[s], (uint32_t)(t / TG2_STAGES) & 1, &abort_sh)) break;
+            // BF16 stage b: the MMAs of step t - 2 are done with it
+            if (t >= 2 && !mbar_wait_or_abort(&mma_bar[b], (uint32_t)((t >> 1) - 1) & 1, &abort_sh)) break;
+            const unsigned char* fs = f32 + s * TG2_F32_STAGE;
+            unsigned char* bs = bf + b * TG2_BF_STAGE;
+            split_tile32(fs, bs, bs + TG2_BF_TILE);
+            split_tile32(fs + TG2_F32_TILE, bs + 2 * TG2_BF_TILE, bs + 3 * TG2_BF_TILE);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&empty[s]);
+                mbar_arrive(&split_bar[b]);
+            }
+        }
+    }
+    __syncthreads();
+    if (abort_sh) {
+        // drain: copies still landing, MMAs still running (bounded waits)
+        if (warp == TW_SPLIT_WARPS && lane == 0)
+            for (int s = 0; s < TG2_STAGES; ++s)
+                if (last_issued[s] >= 0) mbar_wait(&full[s], (uint32_t)(last_issued[s] / TG2_STAGES) & 1);
+        if (warp == TW_SPLIT_WARPS + 1 && lane == 0 && committed > 0)
+            mbar_wait(&mma_bar[(committed - 1) & 1], (uint32_t)((committed - 1) >> 1) & 1);
+        if (threadIdx.x == 0) atomicExch(err, 1);
+    } else if (warp < 4) {
+        const int row = m0 + warp * 32 + lane;
+        double* out = work + (size_t)blockIdx.z * M * N;
+        bool ok = true;
+        // the last step's commit: every MMA of this CTA is done (commits complete in issue order)
+        if (nsteps > 0) ok = mbar_wait(&mma_bar[(nsteps - 1) & 1], (uint32_t)((nsteps - 1) >> 1) & 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (!ok) {
+            if (lane == 0) atomicExch(err, 1);
+        } else if (nsteps == 0) {
+            if (row < M)
+                for (int j = 0; j < TC_N; ++j)
+                    if (n0 + j < N) out[(size_t)row * N + n0 + j] = 0.0;
+        } else {
+#pragma unroll 1
+            for (int c0 = 0; c0 < TC_N; c0 += 16) {
+                uint32_t v[16];
+                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                      "=r"(v[14]), "=r"(v[15])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                if (row < M) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = n0 + c0 + j;
+                        if (col < N) out[(size_t)row * N + col] = (double)__uint_as_float(v[j]);
+                    }
+                }
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+    }
+}
+
 __global__ void tc_reduce_kernel(int M, int N, int nchunk, const double* __restrict__ work, double alpha,
                                  double* __restrict__ C, int ldc) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1053,14 +1249,16 @@ bool make_tile_map(CUtensorMap* m, const float* base, size_t rows, size_t cols, 
                     CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
-// LACE_TC_GRAM=32 selects the 32-wide double-buffered TMA Gram kernel
-// (tuning; default: the 64-wide one with a single BF16 stage).
-bool gram_wide() {
-    static const bool w = [] {
+// TMA-fed Gram variant (tuning): LACE_TC_GRAM=64 the 64-wide kernel with
+// one BF16 stage, =32 the 32-wide double-buffered one with CTA barriers;
+// default (0) the 32-wide one with warp roles.
+int gram_variant() {
+    static const int v = [] {
         const char* e = getenv("LACE_TC_GRAM");
-        return !(e && atoi(e) == 32);
+        const int k = e ? atoi(e) : 0;
+        return k == 64 || k == 32 ? k : 0;
     }();
-    return w;
+    return v;
 }
 
 }  // namespace
@@ -1157,19 +1355,24 @@ cudaError_t tc_gram(int M, int N, size_t K, const float* A, size_t lda, const fl
         if (!e)
             e = cudaFuncSetAttribute(tc_gram_tma2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      TG2_SMEM_BYTES);
+        if (!e)
+            e = cudaFuncSetAttribute(tc_gram_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TG2_SMEM_BYTES);
         if (e) return e;
         attr_done.fetch_or(1ull << dev);
     }
     cudaMemsetAsync(d_err, 0, sizeof(int), s);
     dim3 grid((M + TC_M - 1) / TC_M, (N + TC_N - 1) / TC_N, (unsigned)nch_eff);
     CUtensorMap map_a, map_b;
-    const int bk = gram_wide() ? TC_BK : TG2_BK;
+    const int variant = gram_variant();
+    const int bk = variant == 64 ? TC_BK : TG2_BK;
     if (K <= 0x7fffffffull && make_tile_map(&map_a, A, (size_t)M, K, lda, bk) &&
         make_tile_map(&map_b, B, (size_t)N, K, ldb, bk)) {
-        if (bk == TC_BK)
+        if (variant == 64)
             tc_gram_tma_kernel<<<grid, TC_THREADS, TG_SMEM_BYTES, s>>>(map_a, map_b, M, N, K, kchunk, work, d_err);
-        else
+        else if (variant == 32)
             tc_gram_tma2_kernel<<<grid, TC_THREADS, TG2_SMEM_BYTES, s>>>(map_a, map_b, M, N, K, kchunk, work, d_err);
+        else
+            tc_gram_ws_kernel<<<grid, TW_THREADS, TG2_SMEM_BYTES, s>>>(map_a, map_b, M, N, K, kchunk, work, d_err);
     } else {
         tc_gram_kernel<<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(M, N, K, A, lda, B, ldb, kchunk, work, d_err);
     }
