@@ -487,9 +487,9 @@ const char* lace_batch_last_error(lace_batch* batch);
  * Set-up: the first call on a device, and the first call after a
  * cudaDeviceReset of it, looks up the array's device address with that
  * device current (the reset gives the device code a new context, where the
- * array can sit at another address); make that first call before any
- * stream capture.  Each call synchronises `stream` once, after checking the
- * pair list on the device and before queueing the FFT passes.
+ * array can sit at another address).  Each call synchronises `stream` once,
+ * after checking the pair list on the device and before queueing the FFT
+ * passes.
  * Returns LACE_ERR_ARG for null pointers, bad counts, a pair outside the
  * ranges above or a pair listed twice; LACE_ERR_UNSUPPORTED for a grid size
  * outside the list above or when one complex FFT grid (16 n1 n2 n3 bytes)

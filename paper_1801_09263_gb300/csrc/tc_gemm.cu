@@ -6,14 +6,20 @@
 // accumulated in FP32 in tensor memory (the lo.lo term, ~2^-16 relative, is
 // dropped).  Chunks of K are reduced in FP64 by the caller in a fixed order.
 //
-// CTA: 512 threads, one 128 x 128 output tile, one K chunk.  Per 64-wide K
-// step all threads load the FP32 rows (16-byte vectors, one step ahead in
-// registers), split them and
-// store four 128 x 64 BF16 tiles (A_hi, A_lo, B_hi, B_lo) in the 128-byte
-// swizzled K-major layout; thread 0 issues 3 x 4 tcgen05.mma (M128 N128 K16)
-// and commits them to the stage's mbarrier.  Two stages alternate so the
-// loads of one step overlap the MMAs of the previous one.  Every mbarrier
-// wait is bounded; on timeout the CTA records an error and stops issuing.
+// Kernels:
+// * tc_gram_ws_kernel (the Gram, default): one 128 x 128 output tile and one
+//   K chunk per CTA; the FP32 rows arrive by TMA (cp.async.bulk.tensor) four
+//   32-wide steps ahead, 16 warps split them into BF16 hi/lo tiles (64-byte
+//   swizzled K-major, two stages), one thread issues the tcgen05.mma (M128
+//   N128 K16) and one the copies; the roles hand off through mbarriers.
+// * tc_combine_tma_kernel (the combination, default): persistent over output
+//   tiles of 128 grid points x 256 targets; the FP32 A tiles and the pre-split
+//   coefficient tiles arrive by TMA (the latter directly in the 128-byte
+//   swizzled layout), the threads transpose-split A.
+// * tc_gram_kernel / tc_combine_kernel: the same contractions with the
+//   operands loaded through registers (used when no tensor map can be made).
+// Every mbarrier wait is bounded; on a timeout the CTA records an error,
+// drains what it started and returns.
 #include <atomic>
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -276,21 +282,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 }
 
 // ---------------------------------------------------------------------------
-// The same contraction with the FP32 rows brought in by the Tensor Memory
-// Accelerator: thread 0 keeps TG_STAGES steps of 128 x 64 FP32 tiles of A and
-// B in flight (cp.async.bulk.tensor into plain row-major shared memory,
-// completion counted on the stage's mbarrier; rows past M and columns past K
-// arrive as zeros), all 512 threads split the current step from shared memory
-// into the BF16 hi/lo tiles, and thread 0 hands them to the tensor cores and
-// refills the FP32 stage just read with the step TG_STAGES ahead.  One BF16
-// stage: the split of a step waits for the MMAs of the step before.  Every
-// wait is bounded; on a timeout the CTA records an error, waits (bounded)
-// for its copies and MMAs in flight, frees its tensor memory and returns.
-constexpr int TG_STAGES = 2;
-constexpr int TG_F32_TILE = TC_M * TC_BK * 4;  // 32 KB: 128 rows x 64 FP32
-constexpr int TG_F32_STAGE = 2 * TG_F32_TILE;  // A and B
-constexpr int TG_SMEM_BYTES = TG_STAGES * TG_F32_STAGE + TC_STAGE_BYTES + 1024;
-
+// TMA helpers.
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
@@ -305,155 +297,12 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
-// Split this thread's share of a row-major 128 x 64 FP32 tile in shared
-// memory into the swizzled BF16 hi/lo tiles.
-__device__ __forceinline__ void split_tile(const unsigned char* f32, unsigned char* hi_tile, unsigned char* lo_tile) {
-    float4 v[TC_VPT];
-#pragma unroll
-    for (int j = 0; j < TC_VPT; ++j) {
-        const int e = threadIdx.x + j * TC_THREADS;
-        v[j] = *reinterpret_cast<const float4*>(f32 + (size_t)(e >> 4) * (TC_BK * 4) + (e & 15) * 16);
-    }
-    store_tile(v, hi_tile, lo_tile);
-}
-
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    tc_gram_tma_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M,
-                       int N, size_t K, size_t kchunk, double* __restrict__ work, int* __restrict__ err) {
-    extern __shared__ unsigned char tc_smem_raw[];
-    __shared__ uint64_t full[TG_STAGES];
-    __shared__ uint64_t mma_bar;
-    __shared__ uint32_t tmem_base_sh;
-    __shared__ int abort_sh;
-    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* f32 = smem;                             // [stage][A | B] 128 x 64 FP32, row-major
-    unsigned char* bf = smem + TG_STAGES * TG_F32_STAGE;  // A_hi, A_lo, B_hi, B_lo (swizzled)
-    const int warp = threadIdx.x >> 5;
-    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * TC_N;
-    const size_t k_begin = (size_t)blockIdx.z * kchunk;
-    const size_t k_end = min(K, k_begin + kchunk);
-    const int nsteps = (int)((k_end - k_begin + TC_BK - 1) / TC_BK);
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < TG_STAGES; ++s) mbar_init(&full[s], 1);
-        mbar_init(&mma_bar, 1);
-        abort_sh = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&tmem_base_sh)),
-                     "r"(128)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base_sh;
-
-    // thread 0: step t of this chunk into FP32 stage t % TG_STAGES
-    int issued = 0;
-    auto issue = [&](int t) {
-        const int s = t % TG_STAGES;
-        const int x = (int)(k_begin + (size_t)t * TC_BK);
-        mbar_expect_tx(&full[s], TG_F32_STAGE);
-        tma_load_2d(f32 + s * TG_F32_STAGE, &map_a, x, m0, &full[s]);
-        tma_load_2d(f32 + s * TG_F32_STAGE + TG_F32_TILE, &map_b, x, n0, &full[s]);
-    };
-    if (threadIdx.x == 0)
-        for (; issued < TG_STAGES && issued < nsteps; ++issued) issue(issued);
-    int step = 0, committed = 0;
-    for (; step < nsteps; ++step) {
-        const int s = step % TG_STAGES;
-        bool ok = mbar_wait(&full[s], (uint32_t)(step / TG_STAGES) & 1);
-        // the BF16 stage is free once the previous step's MMAs are done
-        if (step > 0) ok = ok && mbar_wait(&mma_bar, (uint32_t)(step - 1) & 1);
-        if (!ok) abort_sh = 1;
-        __syncthreads();
-        if (abort_sh) break;
-        const unsigned char* fs = f32 + s * TG_F32_STAGE;
-        split_tile(fs, bf, bf + TC_TILE_BYTES);
-        split_tile(fs + TG_F32_TILE, bf + 2 * TC_TILE_BYTES, bf + 3 * TC_TILE_BYTES);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a_hi = smem_u32(bf), a_lo = a_hi + TC_TILE_BYTES;
-            const uint32_t b_hi = a_hi + 2 * TC_TILE_BYTES, b_lo = a_hi + 3 * TC_TILE_BYTES;
-#pragma unroll
-            for (int kk = 0; kk < TC_BK / 16; ++kk) {
-                const uint32_t ko = kk * 32;
-                const uint32_t first = (step == 0 && kk == 0) ? 0u : 1u;
-                mma_bf16(tmem, sw128_desc(a_hi + ko), sw128_desc(b_hi + ko), first);
-                mma_bf16(tmem, sw128_desc(a_hi + ko), sw128_desc(b_lo + ko), 1u);
-                mma_bf16(tmem, sw128_desc(a_lo + ko), sw128_desc(b_hi + ko), 1u);
-            }
-            mma_commit(&mma_bar);
-            // every thread has read FP32 stage s (the barrier above): refill it
-            if (issued < nsteps) issue(issued++);
-        }
-        committed = step + 1;
-    }
-    if (threadIdx.x == 0) {
-        if (abort_sh) {
-            // bounded waits for what is still in flight, so that nothing lands
-            // in shared or tensor memory after the CTA has gone
-            for (int t = step; t < issued; ++t) mbar_wait(&full[t % TG_STAGES], (uint32_t)(t / TG_STAGES) & 1);
-            if (committed > 0) mbar_wait(&mma_bar, (uint32_t)(committed - 1) & 1);
-        } else if (nsteps > 0 && !mbar_wait(&mma_bar, (uint32_t)(nsteps - 1) & 1)) {
-            abort_sh = 1;
-        }
-    }
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (abort_sh) {
-        if (threadIdx.x == 0) atomicExch(err, 1);
-    } else if (warp < 4) {
-        const int row = m0 + warp * 32 + (threadIdx.x & 31);
-        double* out = work + (size_t)blockIdx.z * M * N;
-        if (nsteps == 0) {
-            if (row < M)
-                for (int j = 0; j < TC_N; ++j)
-                    if (n0 + j < N) out[(size_t)row * N + n0 + j] = 0.0;
-        } else {
-#pragma unroll 1
-            for (int c0 = 0; c0 < TC_N; c0 += 16) {
-                uint32_t v[16];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (row < M) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int col = n0 + c0 + j;
-                        if (col < N) out[(size_t)row * N + col] = (double)__uint_as_float(v[j]);
-                    }
-                }
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
-    }
-}
-
-// The TMA-fed Gram in 32-wide K steps, so that two BF16 stages fit beside a
-// deep FP32 pipeline: TG2_STAGES steps of 128 x 32 FP32 tiles of A and B in
-// flight (plain row-major, 16 KB each), and two BF16 stages of the four
-// split tiles (64-byte swizzled K-major, 8 KB each), so the split of step t
-// overlaps the MMAs of step t - 1 and waits only for those of step t - 2.
-// An FP32 stage is refilled as soon as its step is split.
+// Geometry of the TMA-fed Gram (tc_gram_ws_kernel): 32-wide K steps, so that
+// two BF16 stages fit beside a deep FP32 pipeline: TG2_STAGES steps of 128 x
+// 32 FP32 tiles of A and B in flight (plain row-major, 16 KB each), and two
+// BF16 stages of the four split tiles (64-byte swizzled K-major, 8 KB each),
+// so the split of step t overlaps the MMAs of step t - 1 and waits only for
+// those of step t - 2.  An FP32 stage is refilled as soon as its step is split.
 constexpr int TG2_BK = 32;
 constexpr int TG2_STAGES = 4;
 constexpr int TG2_F32_TILE = TC_M * TG2_BK * 4;       // 16 KB
@@ -492,139 +341,6 @@ __device__ __forceinline__ void split_tile32(const unsigned char* f32, unsigned 
         const uint32_t off = sw64_off(r, kv);
         *reinterpret_cast<uint2*>(hi_tile + off) = h;
         *reinterpret_cast<uint2*>(lo_tile + off) = l;
-    }
-}
-
-__global__ void __launch_bounds__(TC_THREADS, 1)
-    tc_gram_tma2_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M,
-                        int N, size_t K, size_t kchunk, double* __restrict__ work, int* __restrict__ err) {
-    extern __shared__ unsigned char tc_smem_raw[];
-    __shared__ uint64_t full[TG2_STAGES];
-    __shared__ uint64_t mma_bar[2];
-    __shared__ uint32_t tmem_base_sh;
-    __shared__ int abort_sh;
-    unsigned char* smem = reinterpret_cast<unsigned char*>(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* f32 = smem;                               // [stage][A | B] 128 x 32 FP32, row-major
-    unsigned char* bf = smem + TG2_STAGES * TG2_F32_STAGE;  // [2][A_hi, A_lo, B_hi, B_lo]
-    const int warp = threadIdx.x >> 5;
-    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * TC_N;
-    const size_t k_begin = (size_t)blockIdx.z * kchunk;
-    const size_t k_end = min(K, k_begin + kchunk);
-    const int nsteps = (int)((k_end - k_begin + TG2_BK - 1) / TG2_BK);
-
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < TG2_STAGES; ++s) mbar_init(&full[s], 1);
-        mbar_init(&mma_bar[0], 1);
-        mbar_init(&mma_bar[1], 1);
-        abort_sh = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_a)) : "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&map_b)) : "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(&tmem_base_sh)),
-                     "r"(128)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const uint32_t tmem = tmem_base_sh;
-
-    int issued = 0;
-    auto issue = [&](int t) {
-        const int s = t % TG2_STAGES;
-        const int x = (int)(k_begin + (size_t)t * TG2_BK);
-        mbar_expect_tx(&full[s], TG2_F32_STAGE);
-        tma_load_2d(f32 + s * TG2_F32_STAGE, &map_a, x, m0, &full[s]);
-        tma_load_2d(f32 + s * TG2_F32_STAGE + TG2_F32_TILE, &map_b, x, n0, &full[s]);
-    };
-    if (threadIdx.x == 0)
-        for (; issued < TG2_STAGES && issued < nsteps; ++issued) issue(issued);
-    int step = 0, committed = 0;
-    for (; step < nsteps; ++step) {
-        const int s = step % TG2_STAGES, b = step & 1;
-        bool ok = mbar_wait(&full[s], (uint32_t)(step / TG2_STAGES) & 1);
-        // BF16 stage b is free once the MMAs of step - 2 (its last user) are done
-        if (step >= 2) ok = ok && mbar_wait(&mma_bar[b], (uint32_t)((step >> 1) - 1) & 1);
-        if (!ok) abort_sh = 1;
-        __syncthreads();
-        if (abort_sh) break;
-        const unsigned char* fs = f32 + s * TG2_F32_STAGE;
-        unsigned char* bs = bf + b * TG2_BF_STAGE;
-        split_tile32(fs, bs, bs + TG2_BF_TILE);
-        split_tile32(fs + TG2_F32_TILE, bs + 2 * TG2_BF_TILE, bs + 3 * TG2_BF_TILE);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a_hi = smem_u32(bs), a_lo = a_hi + TG2_BF_TILE;
-            const uint32_t b_hi = a_hi + 2 * TG2_BF_TILE, b_lo = a_hi + 3 * TG2_BF_TILE;
-#pragma unroll
-            for (int kk = 0; kk < TG2_BK / 16; ++kk) {
-                const uint32_t ko = kk * 32;  // 16 BF16 = 32 bytes along K inside the 64-byte row
-                const uint32_t first = (step == 0 && kk == 0) ? 0u : 1u;
-                mma_bf16(tmem, sw64_desc(a_hi + ko), sw64_desc(b_hi + ko), first);
-                mma_bf16(tmem, sw64_desc(a_hi + ko), sw64_desc(b_lo + ko), 1u);
-                mma_bf16(tmem, sw64_desc(a_lo + ko), sw64_desc(b_hi + ko), 1u);
-            }
-            mma_commit(&mma_bar[b]);
-            // every thread has split FP32 stage s (the barrier above): refill it
-            if (issued < nsteps) issue(issued++);
-        }
-        committed = step + 1;
-    }
-    if (threadIdx.x == 0) {
-        if (abort_sh) {
-            for (int t = step; t < issued; ++t) mbar_wait(&full[t % TG2_STAGES], (uint32_t)(t / TG2_STAGES) & 1);
-            for (int t = committed - 2 > 0 ? committed - 2 : 0; t < committed; ++t)
-                mbar_wait(&mma_bar[t & 1], (uint32_t)(t >> 1) & 1);
-        } else {
-            // the last commit of each BF16 stage (commits complete in issue order)
-            for (int t = nsteps - 2 > 0 ? nsteps - 2 : 0; t < nsteps; ++t)
-                if (!mbar_wait(&mma_bar[t & 1], (uint32_t)(t >> 1) & 1)) abort_sh = 1;
-        }
-    }
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (abort_sh) {
-        if (threadIdx.x == 0) atomicExch(err, 1);
-    } else if (warp < 4) {
-        const int row = m0 + warp * 32 + (threadIdx.x & 31);
-        double* out = work + (size_t)blockIdx.z * M * N;
-        if (nsteps == 0) {
-            if (row < M)
-                for (int j = 0; j < TC_N; ++j)
-                    if (n0 + j < N) out[(size_t)row * N + n0 + j] = 0.0;
-        } else {
-#pragma unroll 1
-            for (int c0 = 0; c0 < TC_N; c0 += 16) {
-                uint32_t v[16];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (row < M) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int col = n0 + c0 + j;
-                        if (col < N) out[(size_t)row * N + col] = (double)__uint_as_float(v[j]);
-                    }
-                }
-            }
-        }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-    __syncthreads();
-    if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
     }
 }
 
@@ -1249,17 +965,6 @@ bool make_tile_map(CUtensorMap* m, const float* base, size_t rows, size_t cols, 
                     CU_TENSOR_MAP_SWIZZLE_NONE);
 }
 
-// TMA-fed Gram variant (tuning): LACE_TC_GRAM=64 the 64-wide kernel with
-// one BF16 stage, =32 the 32-wide double-buffered one with CTA barriers;
-// default (0) the 32-wide one with warp roles.
-int gram_variant() {
-    static const int v = [] {
-        const char* e = getenv("LACE_TC_GRAM");
-        const int k = e ? atoi(e) : 0;
-        return k == 64 || k == 32 ? k : 0;
-    }();
-    return v;
-}
 
 }  // namespace
 
@@ -1351,11 +1056,6 @@ cudaError_t tc_gram(int M, int N, size_t K, const float* A, size_t lda, const fl
     if (dev < 64 && !(attr_done.load() & (1ull << dev))) {
         cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
         if (!e)
-            e = cudaFuncSetAttribute(tc_gram_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TG_SMEM_BYTES);
-        if (!e)
-            e = cudaFuncSetAttribute(tc_gram_tma2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     TG2_SMEM_BYTES);
-        if (!e)
             e = cudaFuncSetAttribute(tc_gram_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TG2_SMEM_BYTES);
         if (e) return e;
         attr_done.fetch_or(1ull << dev);
@@ -1363,16 +1063,9 @@ cudaError_t tc_gram(int M, int N, size_t K, const float* A, size_t lda, const fl
     cudaMemsetAsync(d_err, 0, sizeof(int), s);
     dim3 grid((M + TC_M - 1) / TC_M, (N + TC_N - 1) / TC_N, (unsigned)nch_eff);
     CUtensorMap map_a, map_b;
-    const int variant = gram_variant();
-    const int bk = variant == 64 ? TC_BK : TG2_BK;
-    if (K <= 0x7fffffffull && make_tile_map(&map_a, A, (size_t)M, K, lda, bk) &&
-        make_tile_map(&map_b, B, (size_t)N, K, ldb, bk)) {
-        if (variant == 64)
-            tc_gram_tma_kernel<<<grid, TC_THREADS, TG_SMEM_BYTES, s>>>(map_a, map_b, M, N, K, kchunk, work, d_err);
-        else if (variant == 32)
-            tc_gram_tma2_kernel<<<grid, TC_THREADS, TG2_SMEM_BYTES, s>>>(map_a, map_b, M, N, K, kchunk, work, d_err);
-        else
-            tc_gram_ws_kernel<<<grid, TW_THREADS, TG2_SMEM_BYTES, s>>>(map_a, map_b, M, N, K, kchunk, work, d_err);
+    if (K <= 0x7fffffffull && make_tile_map(&map_a, A, (size_t)M, K, lda, TG2_BK) &&
+        make_tile_map(&map_b, B, (size_t)N, K, ldb, TG2_BK)) {
+        tc_gram_ws_kernel<<<grid, TW_THREADS, TG2_SMEM_BYTES, s>>>(map_a, map_b, M, N, K, kchunk, work, d_err);
     } else {
         tc_gram_kernel<<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(M, N, K, A, lda, B, ldb, kchunk, work, d_err);
     }
