@@ -278,8 +278,14 @@ __device__ __forceinline__ void body_a(const ConvArgs<float>& P, const GridView&
                 x2 = __ldg(A2 + e);
                 y2 = __ldg(C2 + e);
             }
-            r4[2 * e] = make_float4(x1.x * y1.x, x2.x * y2.x, x1.y * y1.y, x2.y * y2.y);
-            r4[2 * e + 1] = make_float4(x1.z * y1.z, x2.z * y2.z, x1.w * y1.w, x2.w * y2.w);
+            const float4 lo = make_float4(x1.x * y1.x, x2.x * y2.x, x1.y * y1.y, x2.y * y2.y);
+            const float4 hi = make_float4(x1.z * y1.z, x2.z * y2.z, x1.w * y1.w, x2.w * y2.w);
+            // each thread writes 32 bytes; threads 4-7 of every 8 write their
+            // upper half first, so each store instruction's 8-thread phases
+            // cover all eight 16-byte bank groups
+            const bool sw = (tid >> 2) & 1;
+            r4[2 * e + sw] = sw ? hi : lo;
+            r4[2 * e + 1 - sw] = sw ? lo : hi;
         }
     }
     grp.sync();
@@ -488,7 +494,10 @@ __device__ __forceinline__ void body_c(const ConvArgs<float>& P, const GridView&
     for (int e0 = 0; e0 < NP / 4; e0 += NT) {
         const int e = e0 + tid;
         if (e0 + NT <= NP / 4 || e < NP / 4) {
-            const float4 v01 = pl4[2 * e], v23 = pl4[2 * e + 1];
+            // 32 bytes a thread, read in the bank-group order of pass A's rho stores
+            const bool sw = (tid >> 2) & 1;
+            const float4 p0 = pl4[2 * e + sw], p1 = pl4[2 * e + 1 - sw];
+            const float4 v01 = sw ? p1 : p0, v23 = sw ? p0 : p1;
             const float4 x1 = __ldg(wi1 + e), y1 = __ldg(pj1 + e);
             atomicAdd(Wj1 + e, make_float4(-x1.x * v01.x, -x1.y * v01.z, -x1.z * v23.x, -x1.w * v23.z));
             const float4 wi_acc = make_float4(-y1.x * v01.x, -y1.y * v01.z, -y1.z * v23.x, -y1.w * v23.z);

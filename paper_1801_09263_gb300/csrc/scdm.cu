@@ -503,15 +503,13 @@ __global__ void gather_columns_kernel(const T* __restrict__ psi, size_t ldpsi, i
 // columns of a CTA that do not fit in registers live in shared memory with a
 // padded row pitch (16-byte accesses free of bank conflicts).  The row work
 // runs on packed FP32 pairs.  Per step each warp publishes its best column
-// to global memory; each CTA then writes its best key (the FP32 squared
-// norm's bits above the complemented column index: the largest norm, then
-// the lowest index) with release semantics into its own slot of the step's
-// row of slots, and one warp of every CTA polls that row until every slot is
-// set, taking the maximum as it reads: the row is the grid barrier and the
-// argmax in one (no atomics, no second read for the winner); every CTA then
-// reads the winner's published column and scales it by the inverse norm
-// taken from the key (no FP64 sums on the step's critical path: FP64 runs at
-// a small fraction of the FP32 rate on this GPU).
+// to global memory; the CTAs then agree on the global winner through one
+// 64-bit atomicMax per CTA (key = the FP32 squared norm's bits above the
+// complemented column index: the largest norm, then the lowest index) and a
+// grid barrier on a monotone arrival counter; every CTA reads the winner's
+// published column and scales it by the inverse norm taken from the key
+// (no FP64 sums on the step's critical path: FP64 runs at a small fraction
+// of the FP32 rate on this GPU).
 constexpr int QR2_THREADS = 512, QR2_WARPS = QR2_THREADS / 32;
 
 __device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) {
@@ -643,7 +641,7 @@ __device__ __forceinline__ unsigned long long col_key(float nrm, int col) {
 template <int RPL, int LPC>
 __global__ void __launch_bounds__(QR2_THREADS, 1)
     qr_resident_kernel(int nrow, int ncol, const float* __restrict__ R, int npiv, int cpb, float* __restrict__ pub,
-                       unsigned long long* __restrict__ slots, int* __restrict__ piv, unsigned* bar,
+                       unsigned long long* __restrict__ keys, int* __restrict__ piv, unsigned* bar,
                        unsigned long long limit_ns) {
     constexpr int G = QR2_THREADS / LPC;
     constexpr int NPAD = RPL * LPC;     // padded rows
@@ -652,7 +650,6 @@ __global__ void __launch_bounds__(QR2_THREADS, 1)
     float* qs = qr2_smem;                // [LPC][PITCH] q of the current step
     float* sc = qr2_smem + LPC * PITCH;  // [SC][LPC][PITCH] shared-memory columns
     __shared__ unsigned long long wkey[QR2_WARPS];
-    __shared__ unsigned long long key_sh;
     __shared__ int abort_sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = tid / LPC, l = tid % LPC;
@@ -738,56 +735,41 @@ __global__ void __launch_bounds__(QR2_THREADS, 1)
             }
         }
         if (lane == 0) wkey[warp] = wb;
+        // grid barrier: arrive with this CTA's best key, wait for every CTA.
+        // The key goes in first (a relaxed reduction, ordered before the
+        // arrival by its release); waiting CTAs poll with relaxed loads and
+        // a short back-off, then take one acquire fence.
         __syncthreads();
-        if (warp == 0) {
-            // this CTA's best key into its slot of the step's row (release:
-            // the published columns go first; 1 = no candidate here), then
-            // poll the row until every slot is set, keeping the maximum
-            unsigned long long kb = lane < QR2_WARPS ? wkey[lane] : 0ull;
+        if (tid == 0) {
+            unsigned long long kb = 0ull;
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long x = __shfl_xor_sync(0xffffffffu, kb, o);
-                kb = x > kb ? x : kb;
-            }
-            unsigned long long* row = slots + (size_t)step * gridDim.x;
-            if (lane == 0)
-                asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(row + blockIdx.x), "l"(kb ? kb : 1ull)
-                             : "memory");
-            const unsigned long long t0 = global_ns();
-            unsigned long long m = 0ull;
+            for (int w = 0; w < QR2_WARPS; ++w) kb = wkey[w] > kb ? wkey[w] : kb;
+            if (kb) asm volatile("red.relaxed.gpu.global.max.u64 [%0], %1;" ::"l"(keys + step), "l"(kb) : "memory");
+            const unsigned target = (unsigned)(step + 1) * gridDim.x;
+            unsigned cnt;
+            asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(cnt) : "l"(bar) : "memory");
             int timed_out = 0;
-            for (;;) {
-                bool all = true;
-                m = 0ull;
-                for (int c = lane; c < (int)gridDim.x; c += 32) {
-                    unsigned long long v;
-                    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(row + c) : "memory");
-                    all = all && v != 0ull;
-                    m = v > m ? v : m;
+            if (cnt + 1 < target) {
+                const unsigned long long t0 = global_ns();
+                for (;;) {
+                    unsigned v;
+                    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
+                    if (v >= target) break;
+                    if (global_ns() - t0 > limit_ns) {
+                        atomicExch(bar + 2, 1u);
+                        timed_out = 1;
+                        break;
+                    }
+                    __nanosleep(40);
                 }
-                if (__all_sync(0xffffffffu, all)) break;
-                if (__any_sync(0xffffffffu, global_ns() - t0 > limit_ns)) {
-                    timed_out = 1;
-                    break;
-                }
-                __nanosleep(40);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-                const unsigned long long x = __shfl_xor_sync(0xffffffffu, m, o);
-                m = x > m ? x : m;
             }
             asm volatile("fence.acq_rel.gpu;" ::: "memory");
-            if (lane == 0) {
-                key_sh = m;
-                abort_sh = timed_out;
-                if (timed_out) atomicExch(bar + 2, 1u);
-            }
+            abort_sh = timed_out;
         }
         __syncthreads();
         if (abort_sh) return;
-        const unsigned long long key = key_sh;
-        if (key <= 1ull) {  // no live column left: cannot happen for npiv <= ncol
+        const unsigned long long key = ld_cg_u64(keys + step);
+        if (key == 0ull) {  // no live column left: cannot happen for npiv <= ncol
             if (tid == 0) atomicExch(bar + 2, 2u);
             return;
         }
@@ -834,14 +816,10 @@ static size_t pub_bytes(int nrow) {
     return align256(std::max(old, res));
 }
 
-// Step slots of the register-resident kernel: one row of up to 304 CTA keys
-// per pivot step (at most nrow steps).
-static size_t slot_bytes(int nrow) { return align256((size_t)nrow * 304 * sizeof(unsigned long long)); }
-
 size_t qrcp_aux_bytes(int nrow, int ncol) {
     const int nblocks = nblocks_cap(ncol);
     return align256(sizeof(Best) * nblocks) + align256((size_t)ncol) + align256(sizeof(double) * nrow) + 256 +
-           pub_bytes(nrow) + slot_bytes(nrow);
+           pub_bytes(nrow);
 }
 
 // The persistent kernel for one (T, RPW, NREG); *ran = false when the rows
@@ -901,7 +879,7 @@ static cudaError_t qr_persistent_launch(int nrow, int ncol, T* R, int npiv, Best
 // matrix does not fit on chip (registers of 256 threads an SM plus shared
 // memory) or the device cannot co-schedule the CTAs.
 template <int RPL, int LPC>
-static cudaError_t qr_resident_launch(int nrow, int ncol, const float* R, int npiv, unsigned long long* slots,
+static cudaError_t qr_resident_launch(int nrow, int ncol, const float* R, int npiv, unsigned long long* keys,
                                       float* pub, int* d_piv, unsigned* bar, unsigned long long limit_ns,
                                       cudaStream_t s, int* launches, bool* ran) {
     *ran = false;
@@ -911,7 +889,7 @@ static cudaError_t qr_resident_launch(int nrow, int ncol, const float* R, int np
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     constexpr int G = QR2_THREADS / LPC, NPAD = RPL * LPC, PITCH = RPL + 4;
-    if (!coop || nrow > NPAD || sms > 304 || npiv > nrow) return cudaSuccess;  // slots: nrow rows of 304
+    if (!coop || nrow > NPAD || sms > 304 || npiv > 4864) return cudaSuccess;
     int ctas = std::min(sms, (ncol + G - 1) / G);
     const int cpb = (ncol + ctas - 1) / ctas;
     ctas = (ncol + cpb - 1) / cpb;
@@ -930,10 +908,10 @@ static cudaError_t qr_resident_launch(int nrow, int ncol, const float* R, int np
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, QR2_THREADS, dyn))) return e;
     if (per_sm < 1 || ctas > per_sm * sms) return cudaSuccess;
     if ((e = cudaMemsetAsync(bar, 0, 4 * sizeof(unsigned), s))) return e;
-    if ((e = cudaMemsetAsync(slots, 0, (size_t)npiv * ctas * sizeof(unsigned long long), s))) return e;
+    if ((e = cudaMemsetAsync(keys, 0, (size_t)npiv * sizeof(unsigned long long), s))) return e;
     int cpb_arg = cpb;
-    void* args[] = {(void*)&nrow, (void*)&ncol,  (void*)&R,     (void*)&npiv, (void*)&cpb_arg,
-                    (void*)&pub,  (void*)&slots, (void*)&d_piv, (void*)&bar,  (void*)&limit_ns};
+    void* args[] = {(void*)&nrow, (void*)&ncol, (void*)&R,     (void*)&npiv,     (void*)&cpb_arg,
+                    (void*)&pub,  (void*)&keys, (void*)&d_piv, (void*)&bar, (void*)&limit_ns};
     if ((e = cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(QR2_THREADS), args, dyn, s))) return e;
     *launches += 1;
     *ran = true;
@@ -974,10 +952,9 @@ cudaError_t qrcp_pivots(int nrow, int ncol, T* R, int npiv, int* d_piv, void* au
         if (qr_resident_enabled()) {
             int rpl = 0, lpc = 0;
             qr2_layout(nrow, &rpl, &lpc);
-            unsigned long long* slots =
-                reinterpret_cast<unsigned long long*>(reinterpret_cast<unsigned char*>(pub) + pub_bytes(nrow));
+            unsigned long long* keys = reinterpret_cast<unsigned long long*>(best);
             auto go = [&](auto launch) {
-                return launch(nrow, ncol, R, npiv, slots, pub, d_piv, bar, wait_limit_ns, s, launches, &ran);
+                return launch(nrow, ncol, R, npiv, keys, pub, d_piv, bar, wait_limit_ns, s, launches, &ran);
             };
             if (rpl == 32) e = go(qr_resident_launch<32, 1>);
             else if (lpc == 1) e = go(qr_resident_launch<64, 1>);
