@@ -349,7 +349,7 @@ const char* lace_server_request_error(lace_server* srv, long long request_id);
 lace_status lace_server_set_rebuild_tolerance(lace_server* srv, int system_id, double tol);
 
 /* APPLY results of a completed request: *e_block_out its block's ACE energy
- * (lace_get_ace_energy) and *rebuild_due_out the cadence's verdict.  Any
+ * (lace_get_ace_energy) and *rebuild_due_out the cadence's decision.  Any
  * output may be NULL; LACE_ERR_ARG for an unknown or unfinished request. */
 lace_status lace_server_apply_info(lace_server* srv, long long request_id, double* e_block_out,
                                    int* rebuild_due_out);

@@ -322,19 +322,11 @@ __global__ void small_gemm_f32_staged_kernel(int N, const float* __restrict__ A0
     }
     __syncthreads();
     const int m = m0 + ty, n = n0 + tx;
-    // four independent partial sums (k mod 4): a quarter of the dependent FMA chain
-    float acc0 = 0.f, acc1 = 0.f, acc2 = 0.f, acc3 = 0.f;
+    float acc = 0.f;
     const float* ar = As + ty * lp;
-    int k = 0;
-#pragma unroll 2
-    for (; k + 4 <= N; k += 4) {
-        acc0 = fmaf(ar[k], Bs[k * SG + tx], acc0);
-        acc1 = fmaf(ar[k + 1], Bs[(k + 1) * SG + tx], acc1);
-        acc2 = fmaf(ar[k + 2], Bs[(k + 2) * SG + tx], acc2);
-        acc3 = fmaf(ar[k + 3], Bs[(k + 3) * SG + tx], acc3);
-    }
-    for (; k < N; ++k) acc0 = fmaf(ar[k], Bs[k * SG + tx], acc0);
-    if (m < N && n < N) C[(size_t)m * N + n] = (acc0 + acc1) + (acc2 + acc3);
+#pragma unroll 8
+    for (int k = 0; k < N; ++k) acc = fmaf(ar[k], Bs[k * SG + tx], acc);
+    if (m < N && n < N) C[(size_t)m * N + n] = acc;
 }
 
 void sgemm_f32_square(int N, const float* A, const float* B, float* C, cudaStream_t s) {

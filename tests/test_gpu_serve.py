@@ -150,8 +150,8 @@ MERGE_SYSTEMS = [  # three systems on the 48^3 grid: different cells, band sizes
 
 def test_rebuilds_on_one_grid_size_share_pass_launches():
     """The pair convolutions of REBUILDs of three systems on the 48^3 grid
-    run in shared launches of the FFT passes (spec serving pattern:
-    pair convolutions batched across requests), and every result is the same
+    run in shared launches of the FFT passes (pair convolutions batched
+    across requests), and every result is the same
     as the system's REBUILD alone: E_x to 1e-9 Ha (the pair energies are
     summed in a fixed order per grid), K_ACE on probes to 1e-5 relative (W
     is accumulated with atomics, whose order varies)."""
