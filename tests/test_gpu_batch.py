@@ -1,8 +1,9 @@
 """Batched uneven instances on the device.
 
-Six systems with different cells, grids (one odd size on the generic FFT
-radices, one size with a specialised single-system kernel) and orbital
-counts run through one lace_batch: the first run is eager, the second
+Eight systems with different cells, grids (one odd size on the generic FFT
+radices, the others with specialised passes, among them 50^3 and 54^3 whose
+rows are not 16-byte multiples) and orbital counts run through one
+lace_batch: the first run is eager, the second
 captures the CUDA graph, later runs replay it.  Each instance's E_x, W and
 xi must match a single-system context on the same orbitals (the same method
 on the single-system kernels) within the mixed-precision tolerances
@@ -28,6 +29,8 @@ INST = [  # L, n, ecut, n_occ, s_thr
     (14.0, 48, 20.0, 24, 1e-3),
     (13.0, 36, 16.0, 16, 1e-3),
     (15.0, 32, 10.0, 30, 1e-3),
+    (14.0, 50, 22.0, 18, 1e-3),
+    (15.0, 54, 22.0, 14, 1e-3),
 ]
 
 
