@@ -778,11 +778,13 @@ __global__ void __launch_bounds__(QR2_THREADS, 1)
         const int wg = li < G ? li : (li - G) % G;
         const size_t slot = ((size_t)(step & 1) * gridDim.x + wcta) * QR2_WARPS + (wg * LPC) / 32;
         // the winner's squared norm is the key's upper half (the FP32 value the
-        // argmax compared)
-        const double nn = (double)__uint_as_float((unsigned)(key >> 32));
-        const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+        // argmax compared); its inverse square root in FP32 (correctly rounded
+        // square root and division: FP64 arithmetic in every thread of every
+        // CTA cost ~5 us a step on this GPU's FP64 rate)
+        const float nn = __uint_as_float((unsigned)(key >> 32));
+        const float inv = nn > 0.f ? 1.f / sqrtf(nn) : 0.f;
         for (int j = tid; j < NPAD; j += QR2_THREADS)
-            qs[(j / RPL) * PITCH + j % RPL] = (float)((double)__ldcg(pub + slot * NPAD + j) * inv);
+            qs[(j / RPL) * PITCH + j % RPL] = __ldcg(pub + slot * NPAD + j) * inv;
         if (wcta == (int)blockIdx.x && wg == g) {
             if (li < G) chosen |= 1u;
             else chosen |= 1u << (1 + (li - G) / G);
