@@ -8,7 +8,7 @@
 //
 // Kernels:
 // * tc_gram_ws_kernel (the Gram, default): one 128 x 128 output tile and one
-//   K chunk per CTA; the FP32 rows arrive by TMA (cp.async.bulk.tensor) four
+//   K chunk per CTA; the FP32 rows arrive by TMA (cp.async.bulk.tensor) five
 //   32-wide steps ahead, 16 warps split them into BF16 hi/lo tiles (64-byte
 //   swizzled K-major, two stages), one thread issues the tcgen05.mma (M128
 //   N128 K16) and one the copies; the roles hand off through mbarriers.
@@ -304,7 +304,7 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 // so the split of step t overlaps the MMAs of step t - 1 and waits only for
 // those of step t - 2.  An FP32 stage is refilled as soon as its step is split.
 constexpr int TG2_BK = 32;
-constexpr int TG2_STAGES = 4;
+constexpr int TG2_STAGES = 5;
 constexpr int TG2_F32_TILE = TC_M * TG2_BK * 4;       // 16 KB
 constexpr int TG2_F32_STAGE = 2 * TG2_F32_TILE;       // A and B
 constexpr int TG2_BF_TILE = TC_M * TG2_BK * 2;        // 8 KB
