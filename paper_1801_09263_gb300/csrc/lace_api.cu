@@ -420,13 +420,31 @@ lace_status align_impl(lace_ctx* c) {
 }
 
 // ------------------------------------------------------------------ screening
+// S_ik = dV sum_r |psi_i(r)| |psi_k(r)| (Eq. 4).  Mixed path: tcgen05 3xBF16
+// (S only decides which pairs pass the threshold; the Gram's periodic
+// compensated drains keep it ~1e-7 relative), symmetric tiles only; FP64 and
+// grids whose point count is not a multiple of 4: the CUDA-core kernel.
 template <typename T>
 lace_status screen_impl(lace_ctx* c, double thr) {
     Launch L{c};
     const size_t ng = c->g.ng;
     const int n = c->n_occ;
-    CK(gemm_rows<T>(n, n, ng, c->psi.as<T>(), ng, c->psi.as<T>(), ng, c->g.dv, true, c->m(MS_S), n,
-                    c->work.as<double>(), c->work.bytes / sizeof(double), c->stream, &L.n),
+    const T* psi = c->psi.as<T>();
+    if constexpr (std::is_same<T, float>::value) {
+        const char* notc = getenv("LACE_NO_TC");
+        if (!(notc && notc[0] == '1') && ng % 4 == 0 && (uintptr_t)psi % 16 == 0) {
+            CK(c->work.ensure(std::max(c->work.bytes, tc_gram_work_elems(n, n, ng, true) * sizeof(double))),
+               "alloc work");
+            int herr = 0;
+            CK(tc_gram(n, n, ng, psi, ng, psi, ng, c->g.dv, c->m(MS_S), n, c->work.as<double>(),
+                       c->work.bytes / sizeof(double), c->flag.as<int>(), &herr, c->stream, &L.n, true, true),
+               "overlap of moduli");
+            if (herr) return fail(c, LACE_ERR_TIMEOUT, "overlap of moduli: an mbarrier wait timed out");
+            return LACE_OK;
+        }
+    }
+    CK(gemm_rows<T>(n, n, ng, psi, ng, psi, ng, c->g.dv, true, c->m(MS_S), n, c->work.as<double>(),
+                    c->work.bytes / sizeof(double), c->stream, &L.n),
        "overlap of moduli");
     return LACE_OK;
 }
@@ -766,6 +784,7 @@ size_t predict_ctx_bytes(int prec, const int n[3], int n_occ, int n_extra, int n
     work = std::max(work, (size_t)n_occ * ncol * eb);
     if (prec != LACE_FP64) {
         work = std::max(work, tc_gram_work_elems((int)n_p, (int)n_p, ng) * sizeof(double));
+        work = std::max(work, tc_gram_work_elems(n_occ, n_occ, ng, true) * sizeof(double));
         work = std::max(work, tc_combine_scratch_bytes((int)n_p, (int)n_p));
         if (na) {
             work = std::max(work, tc_gram_work_elems((int)n_p, (int)na, ng) * sizeof(double));

@@ -164,13 +164,14 @@ template <typename T>
 cudaError_t gemm_combine(int N, size_t K, int Kc, const T* A, size_t lda, const double* Coef, int ldcoef, double beta,
                          T* Out, size_t ldo, cudaStream_t s, int* launches);
 
-// Tensor-core (tcgen05) 3xBF16 contraction C = alpha * sum_r A[m][r] B[n][r]
-// (FP32 operands, rows 16-byte aligned); h_err (nullable) receives 1 if a
-// bounded mbarrier wait gave up (the call then synchronises s).
+// Tensor-core (tcgen05) 3xBF16 contraction C = alpha * sum_r op(A[m][r]) op(B[n][r])
+// (FP32 operands, rows 16-byte aligned; op = |.| if absval); sym: A = B and
+// only the tiles on and above the diagonal are computed.  h_err (nullable)
+// receives 1 if a bounded mbarrier wait gave up (the call then synchronises s).
 cudaError_t tc_gram(int M, int N, size_t K, const float* A, size_t lda, const float* B, size_t ldb, double alpha,
                     double* C, int ldc, double* work, size_t work_elems, int* d_err, int* h_err, cudaStream_t s,
-                    int* launches);
-size_t tc_gram_work_elems(int M, int N, size_t K);
+                    int* launches, bool absval = false, bool sym = false);
+size_t tc_gram_work_elems(int M, int N, size_t K, bool sym = false);
 // Tensor-core combination Out[n][r] = beta Out + sum_k Coef[k][n] A[k][r]
 // (FP32 A and Out, FP64 Coef, split 3xBF16); scratch of tc_combine_scratch_bytes.
 cudaError_t tc_combine(int N, size_t K, int Kc, const float* A, size_t lda, const double* Coef, int ldcoef,

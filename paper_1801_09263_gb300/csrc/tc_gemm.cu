@@ -1,14 +1,16 @@
 // Tensor-core (tcgen05, sm_103a) split-precision contraction over the grid:
-//   work[chunk][m][n] = sum_{r in chunk} A[m][r] * B[n][r]
+//   work[chunk][m][n] = sum_{r in chunk} op(A[m][r]) * op(B[n][r])
 // for the dense ACE contractions (Eq. 3: M = dV Psi^T W; K_ACE psi needs
-// X = dV xi^T psi).  Each FP32 operand is split in registers into BF16
-// hi = bf16(x), lo = bf16(x - hi); the products hi.hi + hi.lo + lo.hi are
-// accumulated in FP32 in tensor memory (the lo.lo term, ~2^-16 relative, is
-// dropped).  Chunks of K are reduced in FP64 by the caller in a fixed order.
+// X = dV xi^T psi) and the overlap of moduli (Eq. 4, op = |.|, A = B).  Each
+// FP32 operand is split in registers into BF16 hi = bf16(x), lo = bf16(x - hi);
+// the products hi.hi + hi.lo + lo.hi are accumulated in FP32 in tensor memory
+// (the lo.lo term, ~2^-16 relative and of random sign between different
+// operands, is dropped; the overlap of moduli keeps it).  Chunks of K are
+// reduced in FP64 by the caller in a fixed order.
 //
 // Kernels:
 // * tc_gram_ws_kernel (the Gram, default): one 128 x 128 output tile and one
-//   K chunk per CTA; the FP32 rows arrive by TMA (cp.async.bulk.tensor) five
+//   K chunk per CTA; the FP32 rows arrive by TMA (cp.async.bulk.tensor) four
 //   32-wide steps ahead, 16 warps split them into BF16 hi/lo tiles (64-byte
 //   swizzled K-major, two stages), one thread issues the tcgen05.mma (M128
 //   N128 K16) and one the copies; the roles hand off through mbarriers.
@@ -145,20 +147,24 @@ __device__ __forceinline__ void load_tile(const float* __restrict__ src, size_t 
     }
 }
 
-// Split the registers into BF16 hi/lo and store them in the swizzled tiles.
+// Split the registers (or their absolute values) into BF16 hi/lo and store
+// them in the swizzled tiles.
+template <bool ABS>
 __device__ __forceinline__ void store_tile(const float4* v, unsigned char* hi_tile, unsigned char* lo_tile) {
 #pragma unroll
     for (int j = 0; j < TC_VPT; ++j) {
         const int e = threadIdx.x + j * TC_THREADS;
         const int r = e >> 4, kv = (e & 15) * 4;
         uint2 h, l;
-        split4(v[j], h, l);
+        const float4 x = ABS ? make_float4(fabsf(v[j].x), fabsf(v[j].y), fabsf(v[j].z), fabsf(v[j].w)) : v[j];
+        split4(x, h, l);
         const uint32_t off = sw128_off(r, kv);
         *reinterpret_cast<uint2*>(hi_tile + off) = h;
         *reinterpret_cast<uint2*>(lo_tile + off) = l;
     }
 }
 
+template <bool ABS>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_gram_kernel(int M, int N, size_t K, const float* __restrict__ A, size_t lda, const float* __restrict__ B,
                    size_t ldb, size_t kchunk, double* __restrict__ work, int* __restrict__ err) {
@@ -209,8 +215,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             __syncthreads();
             if (abort_sh) break;
         }
-        store_tile(va, st, st + TC_TILE_BYTES);
-        store_tile(vb, st + 2 * TC_TILE_BYTES, st + 3 * TC_TILE_BYTES);
+        store_tile<ABS>(va, st, st + TC_TILE_BYTES);
+        store_tile<ABS>(vb, st + 2 * TC_TILE_BYTES, st + 3 * TC_TILE_BYTES);
         if (step + 1 < nsteps) {
             const size_t k1 = k_begin + (size_t)(step + 1) * TC_BK;
             load_tile(A, lda, m0, M, k1, k_end, va);
@@ -304,7 +310,7 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 // so the split of step t overlaps the MMAs of step t - 1 and waits only for
 // those of step t - 2.  An FP32 stage is refilled as soon as its step is split.
 constexpr int TG2_BK = 32;
-constexpr int TG2_STAGES = 5;
+constexpr int TG2_STAGES = 4;
 constexpr int TG2_F32_TILE = TC_M * TG2_BK * 4;       // 16 KB
 constexpr int TG2_F32_STAGE = 2 * TG2_F32_TILE;       // A and B
 constexpr int TG2_BF_TILE = TC_M * TG2_BK * 2;        // 8 KB
@@ -330,12 +336,14 @@ __device__ __forceinline__ uint32_t sw64_off(int r, int k) {
     return (uint32_t)(r * 64 + ((((k >> 3) ^ (r >> 1)) & 3) << 4) + (k & 7) * 2);
 }
 
+template <bool ABS>
 __device__ __forceinline__ void split_tile32(const unsigned char* f32, unsigned char* hi_tile, unsigned char* lo_tile) {
 #pragma unroll
     for (int j = 0; j < TG2_VPT; ++j) {
         const int e = threadIdx.x + j * TC_THREADS;
         const int r = e >> 3, kv = (e & 7) * 4;
-        const float4 v = *reinterpret_cast<const float4*>(f32 + (size_t)r * (TG2_BK * 4) + kv * 4);
+        float4 v = *reinterpret_cast<const float4*>(f32 + (size_t)r * (TG2_BK * 4) + kv * 4);
+        if (ABS) v = make_float4(fabsf(v.x), fabsf(v.y), fabsf(v.z), fabsf(v.w));
         uint2 h, l;
         split4(v, h, l);
         const uint32_t off = sw64_off(r, kv);
@@ -345,18 +353,31 @@ __device__ __forceinline__ void split_tile32(const unsigned char* f32, unsigned 
 }
 
 // The 32-wide TMA-fed Gram with warp roles instead of CTA-wide barriers:
-// warps 0-15 split (and later read the accumulators), warp 16 (lane 0)
-// issues the TMA copies, warp 17 (lane 0) issues the MMAs.  They hand off
-// through mbarriers only: full[s] (copies landed), empty[s] (stage s split,
-// one arrival per splitting warp), split[b] (BF16 stage b written, one
-// arrival per splitting warp) and mma[b] (the MMAs that read BF16 stage b
-// are done; tcgen05.commit).  So the copies run TG2_STAGES steps ahead, the
-// split of step t overlaps the MMAs of step t - 1, and no role waits for
-// another except on data.  Every wait is bounded and also gives up once
-// another role has recorded a timeout; the roles then drain what they
-// started (bounded) and the CTA reports the error.
+// warps 0-15 split (and drain the accumulators), warp 16 (lane 0) issues the
+// TMA copies, warp 17 (lane 0) issues the MMAs.  They hand off through
+// mbarriers only: full[s] (copies landed), empty[s] (stage s split, one
+// arrival per splitting warp), split[b] (BF16 stage b written, one arrival
+// per splitting warp) and mma[b] (the MMAs that read BF16 stage b are done;
+// tcgen05.commit).  So the copies run TG2_STAGES steps ahead, the split of
+// step t overlaps the MMAs of step t - 1, and no role waits for another
+// except on data.  Every wait is bounded and also gives up once another role
+// has recorded a timeout; the roles then drain what they started (bounded)
+// and the CTA reports the error.
+//
+// Accumulation: the tensor cores add each K16 product block into the FP32
+// accumulator with their own rounding, which over a K chunk of ~10^4 points
+// biased the 256 x 256 ACE matrix of the 72^3 workload by -5.6e-6 relative
+// (diagonal mean against FP64).  So the MMAs accumulate only TG2_DRAIN steps
+// (128 products) into one of two TMEM accumulators; the split warps then read
+// that period's sums (tcgen05.ld) and add them into compensated (Kahan) FP32
+// registers, while the MMAs of the next period fill the other accumulator
+// (measured bias: -2.1e-7 with 2-step periods, -6.1e-7 with 8-step periods).
+// Split warp w owns TMEM lanes 32 (w mod 4).. (the lanes its warp may read)
+// and columns 32 (w / 4)..
 constexpr int TW_SPLIT_WARPS = 16;
 constexpr int TW_THREADS = (TW_SPLIT_WARPS + 2) * 32;
+constexpr int TG2_DRAIN = 4;  // steps per accumulation period
+static_assert(TG2_DRAIN >= 2, "a period's drain follows the split of the next period's second step");
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
@@ -381,9 +402,61 @@ __device__ __forceinline__ bool mbar_wait_or_abort(uint64_t* bar, uint32_t parit
     return false;
 }
 
+// 16 FP32 accumulator columns of this warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* v) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+}
+
+// Add one period's accumulator (32 columns at taddr) into the Kahan sums.
+// The compensations are kept as BF16 pairs (comp2[j] holds columns 2j and
+// 2j + 1): a compensation is below half an ulp of its sum, so its own 8-bit
+// rounding costs ~2^-9 of that half ulp per period, and the 48 registers of
+// state (instead of 64) leave room for the split.
+__device__ __forceinline__ void drain_period(uint32_t taddr, float* fold, uint32_t* comp2) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        uint32_t v[16];
+        tmem_ld16(taddr + 16 * h, v);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 16; j += 2) {
+            const int q = 16 * h + j;
+            const uint32_t c = comp2[q >> 1];
+            const float y0 = __uint_as_float(v[j]) - __uint_as_float(c << 16);
+            const float y1 = __uint_as_float(v[j + 1]) - __uint_as_float(c & 0xffff0000u);
+            const float t0 = fold[q] + y0, t1 = fold[q + 1] + y1;
+            comp2[q >> 1] = bf16x2_rn((t0 - fold[q]) - y0, (t1 - fold[q + 1]) - y1);
+            fold[q] = t0;
+            fold[q + 1] = t1;
+        }
+    }
+}
+
+// Output tile of a CTA: tile_m fastest over all tiles, or, for a symmetric
+// product (A = B), the tiles on and above the diagonal only, column by column.
+__device__ __forceinline__ void gram_tile(int idx, int tiles_m, bool sym, int& tm, int& tn) {
+    if (!sym) {
+        tm = idx % tiles_m;
+        tn = idx / tiles_m;
+        return;
+    }
+    tn = 0;
+    while (idx > tn) {
+        idx -= tn + 1;
+        ++tn;
+    }
+    tm = idx;
+}
+
+template <bool ABS>
 __global__ void __launch_bounds__(TW_THREADS, 1)
     tc_gram_ws_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_b, int M,
-                      int N, size_t K, size_t kchunk, double* __restrict__ work, int* __restrict__ err) {
+                      int N, size_t K, size_t kchunk, int tiles_m, bool sym, double* __restrict__ work,
+                      int* __restrict__ err) {
     extern __shared__ unsigned char tc_smem_raw[];
     __shared__ uint64_t full[TG2_STAGES], empty[TG2_STAGES], split_bar[2], mma_bar[2];
     __shared__ uint32_t tmem_base_sh;
@@ -393,10 +466,13 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
     unsigned char* f32 = smem;
     unsigned char* bf = smem + TG2_STAGES * TG2_F32_STAGE;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * TC_M, n0 = blockIdx.y * TC_N;
+    int tm, tn;
+    gram_tile((int)blockIdx.x, tiles_m, sym, tm, tn);
+    const int m0 = tm * TC_M, n0 = tn * TC_N;
     const size_t k_begin = (size_t)blockIdx.z * kchunk;
     const size_t k_end = min(K, k_begin + kchunk);
     const int nsteps = (int)((k_end - k_begin + TG2_BK - 1) / TG2_BK);
+    const int nperiods = (nsteps + TG2_DRAIN - 1) / TG2_DRAIN;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < TG2_STAGES; ++s) {
@@ -412,9 +488,10 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
+        // two accumulators of 128 lanes x 128 FP32 columns
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(&tmem_base_sh)),
-                     "r"(128)
+                     "r"(256)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -442,7 +519,8 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
             }
         }
     } else if (warp == TW_SPLIT_WARPS + 1) {
-        // MMA issuer
+        // MMA issuer: step t accumulates into accumulator (t / TG2_DRAIN) mod 2,
+        // starting it afresh at the first step of each period
         if (lane == 0) {
             for (int t = 0; t < nsteps; ++t) {
                 const int b = t & 1;
@@ -450,37 +528,85 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t a_hi = smem_u32(bf + b * TG2_BF_STAGE), a_lo = a_hi + TG2_BF_TILE;
                 const uint32_t b_hi = a_hi + 2 * TG2_BF_TILE, b_lo = a_hi + 3 * TG2_BF_TILE;
+                const uint32_t acc = tmem + (uint32_t)(((t / TG2_DRAIN) & 1) * TC_N);
 #pragma unroll
                 for (int kk = 0; kk < TG2_BK / 16; ++kk) {
                     const uint32_t ko = kk * 32;
-                    const uint32_t first = (t == 0 && kk == 0) ? 0u : 1u;
-                    mma_bf16(tmem, sw64_desc(a_hi + ko), sw64_desc(b_hi + ko), first);
-                    mma_bf16(tmem, sw64_desc(a_hi + ko), sw64_desc(b_lo + ko), 1u);
-                    mma_bf16(tmem, sw64_desc(a_lo + ko), sw64_desc(b_hi + ko), 1u);
+                    const uint32_t first = (t % TG2_DRAIN == 0 && kk == 0) ? 0u : 1u;
+                    mma_bf16(acc, sw64_desc(a_hi + ko), sw64_desc(b_hi + ko), first);
+                    mma_bf16(acc, sw64_desc(a_hi + ko), sw64_desc(b_lo + ko), 1u);
+                    mma_bf16(acc, sw64_desc(a_lo + ko), sw64_desc(b_hi + ko), 1u);
+                    // |x| |x|: lo.lo >= 0 on the diagonal, so dropping it would bias it low
+                    if (ABS) mma_bf16(acc, sw64_desc(a_lo + ko), sw64_desc(b_lo + ko), 1u);
                 }
                 mma_commit(&mma_bar[b]);
                 committed = t + 1;
             }
         }
     } else {
-        // splitters: 512 threads, TG2_VPT vectors per tile each
+        // splitters: 512 threads, TG2_VPT vectors per tile each; they also
+        // drain period p once the MMAs of its last step, (p + 1) D - 1, are
+        // done, i.e. at step t = (p + 1) D + 1 after the wait on mma[b] of
+        // step t - 2, once step t is split.  The MMAs of period p + 2 (from
+        // step (p + 2) D >= t + 1 for D >= 2) wait for the split[b] arrival
+        // of that step, which follows the drain, so the accumulator is read
+        // before they start it afresh.
+        float fold[32];
+        uint32_t comp2[16];
+#pragma unroll
+        for (int q = 0; q < 32; ++q) fold[q] = 0.f;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) comp2[q] = 0u;
+        const uint32_t tlane = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)((warp >> 2) * 32);
+        int drained = 0;
+        bool ok = true;
         for (int t = 0; t < nsteps; ++t) {
             const int s = t % TG2_STAGES, b = t & 1;
-            if (!mbar_wait_or_abort(&full[s], (uint32_t)(t / TG2_STAGES) & 1, &abort_sh)) break;
+            if (!mbar_wait_or_abort(&full[s], (uint32_t)(t / TG2_STAGES) & 1, &abort_sh)) { ok = false; break; }
             // BF16 stage b: the MMAs of step t - 2 are done with it
-            if (t >= 2 && !mbar_wait_or_abort(&mma_bar[b], (uint32_t)((t >> 1) - 1) & 1, &abort_sh)) break;
+            if (t >= 2 && !mbar_wait_or_abort(&mma_bar[b], (uint32_t)((t >> 1) - 1) & 1, &abort_sh)) {
+                ok = false;
+                break;
+            }
             const unsigned char* fs = f32 + s * TG2_F32_STAGE;
             unsigned char* bs = bf + b * TG2_BF_STAGE;
-            split_tile32(fs, bs, bs + TG2_BF_TILE);
-            split_tile32(fs + TG2_F32_TILE, bs + 2 * TG2_BF_TILE, bs + 3 * TG2_BF_TILE);
+            split_tile32<ABS>(fs, bs, bs + TG2_BF_TILE);
+            split_tile32<ABS>(fs + TG2_F32_TILE, bs + 2 * TG2_BF_TILE, bs + 3 * TG2_BF_TILE);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(&empty[s]);
                 mbar_arrive(&split_bar[b]);
             }
+            // off the MMAs' path: the MMAs of step t (period p + 1) use the other accumulator
+            if (t >= TG2_DRAIN + 1 && (t - 1) % TG2_DRAIN == 0) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                drain_period(tlane + (uint32_t)((drained & 1) * TC_N), fold, comp2);
+                asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+                ++drained;
+            }
+        }
+        // the periods left: wait for the last step's commit (every MMA of this
+        // CTA is then done; commits complete in issue order)
+        if (ok && nsteps > 0 &&
+            !mbar_wait_or_abort(&mma_bar[(nsteps - 1) & 1], (uint32_t)((nsteps - 1) >> 1) & 1, &abort_sh))
+            ok = false;
+        if (ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            for (; drained < nperiods; ++drained) drain_period(tlane + (uint32_t)((drained & 1) * TC_N), fold, comp2);
+            const int row = m0 + (warp & 3) * 32 + lane;
+            const int c0 = n0 + (warp >> 2) * 32;
+            double* out = work + (size_t)blockIdx.z * M * N + (size_t)row * N;
+            if (row < M) {
+#pragma unroll
+                for (int q = 0; q < 32; ++q)
+                    if (c0 + q < N)
+                        out[c0 + q] = (double)fold[q] -
+                                      (double)__uint_as_float((q & 1) ? (comp2[q >> 1] & 0xffff0000u) : (comp2[q >> 1] << 16));
+            }
         }
     }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (abort_sh) {
         // drain: copies still landing, MMAs still running (bounded waits)
@@ -490,56 +616,23 @@ __global__ void __launch_bounds__(TW_THREADS, 1)
         if (warp == TW_SPLIT_WARPS + 1 && lane == 0 && committed > 0)
             mbar_wait(&mma_bar[(committed - 1) & 1], (uint32_t)((committed - 1) >> 1) & 1);
         if (threadIdx.x == 0) atomicExch(err, 1);
-    } else if (warp < 4) {
-        const int row = m0 + warp * 32 + lane;
-        double* out = work + (size_t)blockIdx.z * M * N;
-        bool ok = true;
-        // the last step's commit: every MMA of this CTA is done (commits complete in issue order)
-        if (nsteps > 0) ok = mbar_wait(&mma_bar[(nsteps - 1) & 1], (uint32_t)((nsteps - 1) >> 1) & 1);
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (!ok) {
-            if (lane == 0) atomicExch(err, 1);
-        } else if (nsteps == 0) {
-            if (row < M)
-                for (int j = 0; j < TC_N; ++j)
-                    if (n0 + j < N) out[(size_t)row * N + n0 + j] = 0.0;
-        } else {
-#pragma unroll 1
-            for (int c0 = 0; c0 < TC_N; c0 += 16) {
-                uint32_t v[16];
-                const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                    "[%16];"
-                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                      "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
-                      "=r"(v[14]), "=r"(v[15])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                if (row < M) {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int col = n0 + c0 + j;
-                        if (col < N) out[(size_t)row * N + col] = (double)__uint_as_float(v[j]);
-                    }
-                }
-            }
-        }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (warp == 0) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128) : "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256) : "memory");
     }
 }
 
-__global__ void tc_reduce_kernel(int M, int N, int nchunk, const double* __restrict__ work, double alpha,
+// Sum of the chunks in FP64 in a fixed order; for a symmetric product the
+// tiles below the diagonal were not computed and are read mirrored.
+__global__ void tc_reduce_kernel(int M, int N, int nchunk, const double* __restrict__ work, double alpha, bool sym,
                                  double* __restrict__ C, int ldc) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (idx >= (size_t)M * N) return;
-    double s = 0.0;
-    for (int c = 0; c < nchunk; ++c) s += work[(size_t)c * M * N + idx];
     const int m = (int)(idx / N), n = (int)(idx % N);
+    const size_t src = (sym && n / TC_N < m / TC_M) ? (size_t)n * N + m : idx;
+    double s = 0.0;
+    for (int c = 0; c < nchunk; ++c) s += work[(size_t)c * M * N + src];
     C[(size_t)m * ldc + n] = alpha * s;
 }
 
@@ -1030,22 +1123,32 @@ cudaError_t tc_combine(int N, size_t K, int Kc, const float* A, size_t lda, cons
 }
 
 
-size_t tc_gram_work_elems(int M, int N, size_t K) {
-    const size_t tiles = (size_t)((M + TC_M - 1) / TC_M) * ((N + TC_N - 1) / TC_N);
-    size_t want = (152 + tiles - 1) / tiles;
-    const size_t maxc = (K + 4095) / 4096;
-    want = std::max<size_t>(1, std::min(want, maxc));
-    return want * (size_t)M * N;
+namespace {
+// Output tiles of the Gram (only those on and above the diagonal when symmetric).
+size_t gram_tiles(int M, int N, bool sym) {
+    const size_t tm = (M + TC_M - 1) / TC_M, tn = (N + TC_N - 1) / TC_N;
+    return sym ? tm * (tm + 1) / 2 : tm * tn;
 }
+// K chunks: as many CTAs as fit one wave of 152 SMs (one CTA per SM), a
+// chunk at least 4096 points long.
+size_t gram_chunks(int M, int N, size_t K, bool sym) {
+    const size_t tiles = gram_tiles(M, N, sym);
+    const size_t want = std::max<size_t>(1, 152 / tiles);
+    const size_t maxc = (K + 4095) / 4096;
+    return std::max<size_t>(1, std::min(want, maxc));
+}
+}  // namespace
+
+size_t tc_gram_work_elems(int M, int N, size_t K, bool sym) { return gram_chunks(M, N, K, sym) * (size_t)M * N; }
 
 cudaError_t tc_gram(int M, int N, size_t K, const float* A, size_t lda, const float* B, size_t ldb, double alpha,
                     double* C, int ldc, double* work, size_t work_elems, int* d_err, int* h_err, cudaStream_t s,
-                    int* launches) {
+                    int* launches, bool absval, bool sym) {
     if (M <= 0 || N <= 0) return cudaSuccess;
     // 16-byte row alignment for the vector loads
     if ((lda % 4) || (ldb % 4) || ((uintptr_t)A % 16) || ((uintptr_t)B % 16)) return cudaErrorInvalidValue;
-    const size_t tiles = (size_t)((M + TC_M - 1) / TC_M) * ((N + TC_N - 1) / TC_N);
-    const size_t nch = tc_gram_work_elems(M, N, K) / ((size_t)M * N);
+    if (sym && (A != B || M != N || lda != ldb)) return cudaErrorInvalidValue;
+    const size_t nch = gram_chunks(M, N, K, sym);
     if (nch * (size_t)M * N > work_elems) return cudaErrorInvalidValue;
     size_t kchunk = (K + nch - 1) / nch;
     kchunk = (kchunk + TC_BK - 1) / TC_BK * TC_BK;
@@ -1054,25 +1157,32 @@ cudaError_t tc_gram(int M, int N, size_t K, const float* A, size_t lda, const fl
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !(attr_done.load() & (1ull << dev))) {
-        cudaError_t e = cudaFuncSetAttribute(tc_gram_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
-        if (!e)
-            e = cudaFuncSetAttribute(tc_gram_ws_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TG2_SMEM_BYTES);
+        cudaError_t e = cudaSuccess;
+        for (auto f : {tc_gram_kernel<false>, tc_gram_kernel<true>})
+            if (!e) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM_BYTES);
+        for (auto f : {tc_gram_ws_kernel<false>, tc_gram_ws_kernel<true>})
+            if (!e) e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, TG2_SMEM_BYTES);
         if (e) return e;
         attr_done.fetch_or(1ull << dev);
     }
     cudaMemsetAsync(d_err, 0, sizeof(int), s);
-    dim3 grid((M + TC_M - 1) / TC_M, (N + TC_N - 1) / TC_N, (unsigned)nch_eff);
+    const int tiles_m = (M + TC_M - 1) / TC_M;
     CUtensorMap map_a, map_b;
+    bool mirrored = false;
     if (K <= 0x7fffffffull && make_tile_map(&map_a, A, (size_t)M, K, lda, TG2_BK) &&
         make_tile_map(&map_b, B, (size_t)N, K, ldb, TG2_BK)) {
-        tc_gram_ws_kernel<<<grid, TW_THREADS, TG2_SMEM_BYTES, s>>>(map_a, map_b, M, N, K, kchunk, work, d_err);
+        dim3 grid((unsigned)gram_tiles(M, N, sym), 1, (unsigned)nch_eff);
+        auto kern = absval ? tc_gram_ws_kernel<true> : tc_gram_ws_kernel<false>;
+        kern<<<grid, TW_THREADS, TG2_SMEM_BYTES, s>>>(map_a, map_b, M, N, K, kchunk, tiles_m, sym, work, d_err);
+        mirrored = sym;
     } else {
-        tc_gram_kernel<<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(M, N, K, A, lda, B, ldb, kchunk, work, d_err);
+        dim3 grid(tiles_m, (N + TC_N - 1) / TC_N, (unsigned)nch_eff);
+        auto kern = absval ? tc_gram_kernel<true> : tc_gram_kernel<false>;
+        kern<<<grid, TC_THREADS, TC_SMEM_BYTES, s>>>(M, N, K, A, lda, B, ldb, kchunk, work, d_err);
     }
     const size_t tot = (size_t)M * N;
-    tc_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, N, (int)nch_eff, work, alpha, C, ldc);
+    tc_reduce_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, N, (int)nch_eff, work, alpha, mirrored, C, ldc);
     *launches += 2;
-    (void)tiles;
     if (h_err) {
         cudaMemcpyAsync(h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
         cudaError_t e = cudaStreamSynchronize(s);
