@@ -10,6 +10,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "f32x2.cuh"
 #include "lace_internal.cuh"
 
 namespace lace {
@@ -67,6 +68,15 @@ __global__ void __launch_bounds__(GR_THREADS) gemm_rows_kernel(int M, int N, siz
     for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) { acc[i][j] = T(0); fold[i][j] = T(0); comp[i][j] = T(0); }
+    // FP32: the same products and sums on packed pairs (columns 2jj, 2jj + 1),
+    // one instruction per two lanes, each lane rounded as the scalar one
+    f2 acc2[4][2], fold2[4][2], comp2[4][2];
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) { acc2[i][jj] = bc2(0.f); fold2[i][jj] = bc2(0.f); comp2[i][jj] = bc2(0.f); }
+    }
     int inner = 0;
     // each thread loads 4 consecutive k of one row of the A tile and of the B
     // tile per step; the next step's values are loaded while this one is used
@@ -90,22 +100,28 @@ __global__ void __launch_bounds__(GR_THREADS) gemm_rows_kernel(int M, int N, siz
         }
 #pragma unroll
         for (int kk = 0; kk < GR_BK; ++kk) {
-            T a[4], b[4];
             if constexpr (sizeof(T) == 4) {
                 const float4 a4 = *reinterpret_cast<const float4*>(&As[kk][ty * 4]);
                 const float4 b4 = *reinterpret_cast<const float4*>(&Bs[kk][tx * 4]);
-                a[0] = a4.x; a[1] = a4.y; a[2] = a4.z; a[3] = a4.w;
-                b[0] = b4.x; b[1] = b4.y; b[2] = b4.z; b[3] = b4.w;
+                const f2 b01 = mk2(b4.x, b4.y), b23 = mk2(b4.z, b4.w);
+                const float a[4] = {a4.x, a4.y, a4.z, a4.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const f2 ai = bc2(a[i]);
+                    acc2[i][0] = fma2(ai, b01, acc2[i][0]);
+                    acc2[i][1] = fma2(ai, b23, acc2[i][1]);
+                }
             } else {
+                T a[4], b[4];
 #pragma unroll
                 for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
 #pragma unroll
                 for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
             }
-#pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
         }
         __syncthreads();
         if constexpr (sizeof(T) == 4) {
@@ -114,15 +130,25 @@ __global__ void __launch_bounds__(GR_THREADS) gemm_rows_kernel(int M, int N, siz
 #pragma unroll
                 for (int i = 0; i < 4; ++i)
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        const T y = acc[i][j] - comp[i][j];
-                        const T t = fold[i][j] + y;
-                        comp[i][j] = (t - fold[i][j]) - y;
-                        fold[i][j] = t;
-                        acc[i][j] = T(0);
+                    for (int jj = 0; jj < 2; ++jj) {
+                        const f2 y = acc2[i][jj] - comp2[i][jj];
+                        const f2 t = fold2[i][jj] + y;
+                        comp2[i][jj] = (t - fold2[i][jj]) - y;
+                        fold2[i][jj] = t;
+                        acc2[i][jj] = bc2(0.f);
                     }
             }
         }
+    }
+    if constexpr (sizeof(T) == 4) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int jj = 0; jj < 2; ++jj) {
+                unpk2(acc2[i][jj], acc[i][2 * jj], acc[i][2 * jj + 1]);
+                unpk2(fold2[i][jj], fold[i][2 * jj], fold[i][2 * jj + 1]);
+                unpk2(comp2[i][jj], comp[i][2 * jj], comp[i][2 * jj + 1]);
+            }
     }
     double* out = work + (size_t)blockIdx.z * M * N;
 #pragma unroll
@@ -611,11 +637,13 @@ __global__ void __launch_bounds__(GC_THREADS) gemm_combine_f32_kernel(int N, siz
     const int tid = threadIdx.x;
     const int tr = tid % 32;  // 4 r each: r = r0 + tr + 32*i
     const int tn = tid / 32;  // 8 n each: n = n0 + tn*8 + j
-    float acc[4][8];
+    // packed accumulators: acc2[i][jj] holds targets 2jj and 2jj + 1 (the
+    // same FMAs in the same order as one scalar accumulator per target)
+    f2 acc2[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+        for (int jj = 0; jj < 4; ++jj) acc2[i][jj] = bc2(0.f);
     const unsigned as_s = (unsigned)__cvta_generic_to_shared(&As[0][0][0]);
     // A tile: 16 rows x 32 chunks of 4 floats, 2 chunks per thread
     auto issue_a = [&](int k0, int buf) {
@@ -669,19 +697,27 @@ __global__ void __launch_bounds__(GC_THREADS) gemm_combine_f32_kernel(int N, siz
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GC_BK; ++kk) {
-            float a[4], c[8];
+            float a[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) a[i] = As[buf][kk][tr + 32 * i];
+            const float4 c0 = *reinterpret_cast<const float4*>(&Cs[buf][kk][tn * 8]);
+            const float4 c1 = *reinterpret_cast<const float4*>(&Cs[buf][kk][tn * 8 + 4]);
+            const f2 cc[4] = {mk2(c0.x, c0.y), mk2(c0.z, c0.w), mk2(c1.x, c1.y), mk2(c1.z, c1.w)};
 #pragma unroll
-            for (int j = 0; j < 8; ++j) c[j] = Cs[buf][kk][tn * 8 + j];
+            for (int i = 0; i < 4; ++i) {
+                const f2 ai = bc2(a[i]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
-#pragma unroll
-                for (int j = 0; j < 8; ++j) acc[i][j] += a[i] * c[j];
+                for (int jj = 0; jj < 4; ++jj) acc2[i][jj] = fma2(ai, cc[jj], acc2[i][jj]);
+            }
         }
         if (more) store_c(buf ^ 1);
         __syncthreads();
     }
+    float acc[4][8];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) unpk2(acc2[i][jj], acc[i][2 * jj], acc[i][2 * jj + 1]);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const int n = n0 + tn * 8 + j;
