@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(GC_THREADS) gemm_combine_kernel(int N, size_t 
 // ------------------------------------------------------------------ small FP64
 constexpr int SG = 16;
 
+// C = alpha op(A) op(B) + beta C, SG x SG outputs a CTA, one a thread.
 __global__ void small_gemm_kernel(int M, int N, int K, const double* __restrict__ A, int lda, bool ta,
                                   const double* __restrict__ B, int ldb, bool tb, double alpha, double beta,
                                   double* __restrict__ C, int ldc) {
@@ -299,6 +300,51 @@ __global__ void small_gemm_kernel(int M, int N, int K, const double* __restrict_
     if (m < M && n < N) {
         double* c = C + (size_t)m * ldc + n;
         *c = alpha * acc + (beta == 0.0 ? 0.0 : beta * *c);
+    }
+}
+
+// The same product for small grids (FP64 throughput is per SM, ~2 FMAs a
+// clock here, so small products need more CTAs), 8 x 8 outputs a CTA: K in panels of
+// SGP_K, every load of a panel issued before any is used (one L2 round trip a
+// panel instead of one per 8-wide step), and four partial sums a thread to
+// shorten the dependent FMA chain.
+constexpr int SGP_K = 256;
+__global__ void __launch_bounds__(64) small_gemm_staged_f64_kernel(int M, int N, int K, const double* __restrict__ A,
+                                                                   int lda, bool ta, const double* __restrict__ B,
+                                                                   int ldb, bool tb, double alpha, double beta,
+                                                                   double* __restrict__ C, int ldc) {
+    __shared__ double As[8][SGP_K + 1];  // op(A)[m0 + r][k0 + k]
+    __shared__ double Bs[SGP_K][8];      // op(B)[k0 + k][n0 + c]
+    const int tx = threadIdx.x, ty = threadIdx.y, t = ty * 8 + tx;
+    const int m0 = blockIdx.y * 8, n0 = blockIdx.x * 8;
+    const int m = m0 + ty, n = n0 + tx;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int k0 = 0; k0 < K; k0 += SGP_K) {
+        const int kp = min(SGP_K, K - k0);
+        for (int q = t; q < 8 * kp; q += 64) {
+            // A: ta reads along m (consecutive q -> consecutive r), else along k
+            const int r = ta ? q % 8 : q / kp, k = ta ? q / 8 : q % kp;
+            const int mm = m0 + r, kk = k0 + k;
+            As[r][k] = mm < M ? (ta ? A[(size_t)kk * lda + mm] : A[(size_t)mm * lda + kk]) : 0.0;
+        }
+        for (int q = t; q < 8 * kp; q += 64) {
+            const int c = tb ? q / kp : q % 8, k = tb ? q % kp : q / 8;
+            const int nn = n0 + c, kk = k0 + k;
+            Bs[k][c] = nn < N ? (tb ? B[(size_t)nn * ldb + kk] : B[(size_t)kk * ldb + nn]) : 0.0;
+        }
+        __syncthreads();
+        int k = 0;
+        for (; k + 4 <= kp; k += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = fma(As[ty][k + u], Bs[k + u][tx], acc[u]);
+        }
+        for (; k < kp; ++k) acc[0] = fma(As[ty][k], Bs[k][tx], acc[0]);
+        __syncthreads();
+    }
+    if (m < M && n < N) {
+        double* c = C + (size_t)m * ldc + n;
+        const double v = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+        *c = alpha * v + (beta == 0.0 ? 0.0 : beta * *c);
     }
 }
 
@@ -444,7 +490,7 @@ __global__ void frob_rows_kernel(int N, const TA* __restrict__ A, int mode, doub
     for (int c = threadIdx.x; c < N; c += blockDim.x) {
         double v = (double)A[(size_t)r * N + c];
         if (mode == 1) v = (r == c ? 1.0 : 0.0) - v;
-        s += v * v;
+        s += mode == 2 ? fabs(v) : v * v;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
@@ -469,6 +515,29 @@ __global__ void sum_rows_kernel(int N, const double* __restrict__ part, double* 
     if (threadIdx.x == 0) out[0] = sh[0];
 }
 
+__global__ void max_rows_kernel(int N, const double* __restrict__ part, double* __restrict__ out) {
+    __shared__ double sh[256];
+    double m = 0.0;
+    for (int r = threadIdx.x; r < N; r += blockDim.x) m = fmax(m, part[r]);
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = sh[0];
+}
+
+// scal[0] = ||A||_inf = max_i sum_j |a_ij|, an upper bound of the largest
+// eigenvalue of a symmetric A (Gershgorin) and usually far tighter than the
+// Frobenius norm: the Newton-Schulz iterations start with A's spectrum
+// scaled into (0, 1] close to 1 and need fewer steps.
+void norm_inf(int N, const double* A, double* scal, cudaStream_t s, int* launches) {
+    frob_rows_kernel<double><<<N, 128, 0, s>>>(N, A, 2, scal + 8);
+    max_rows_kernel<<<1, 256, 0, s>>>(N, scal + 8, scal);
+    *launches += 2;
+}
+
 template <typename TA>
 void frob(int N, const TA* A, int mode, double* scal, cudaStream_t s, int* launches) {
     frob_rows_kernel<TA><<<N, 128, 0, s>>>(N, A, mode, scal + 8);
@@ -478,54 +547,80 @@ void frob(int N, const TA* A, int mode, double* scal, cudaStream_t s, int* launc
 
 // ------------------------------------------------------------------ Cholesky
 constexpr int CH_NB = 32;
+static_assert(CH_NB == 32, "the block kernels map one block row or column to the lanes of a warp");
 
-// Unblocked Cholesky of the diagonal block at k0 (nb x nb) in shared memory.
-__global__ void potrf_diag_kernel(int N, double* A, int lda, int k0, int nb, int* flag) {
+// FP64 runs at ~2 FMAs per clock per SM on this GPU (1/64 of FP32), so the
+// factorisation kernels below keep FP64 operations off their serial chains
+// (reciprocal square roots and products instead of square roots and
+// divisions) and spread independent rows over many SMs.
+
+// Unblocked Cholesky of the diagonal block at k0 (nb x nb) in shared memory,
+// thread (r, c) of a 32 x 32 block owning element (r, c).  Per column j:
+// warp 0 scales column j by the pivot's reciprocal square root (lane 0 takes
+// it), then the threads of the trailing triangle (r >= c > j) do one FMA each.
+__global__ void __launch_bounds__(CH_NB * CH_NB) potrf_diag_kernel(int N, double* A, int lda, int k0, int nb,
+                                                                   int* flag) {
     __shared__ double D[CH_NB][CH_NB + 1];
-    const int tid = threadIdx.x;
-    for (int e = tid; e < nb * nb; e += blockDim.x) D[e / nb][e % nb] = A[(size_t)(k0 + e / nb) * lda + k0 + e % nb];
+    __shared__ double Lc[CH_NB];
+    const int tid = threadIdx.x, r = tid / CH_NB, c = tid % CH_NB;
+    if (r < nb && c < nb) D[r][c] = A[(size_t)(k0 + r) * lda + k0 + c];
     __syncthreads();
     for (int j = 0; j < nb; ++j) {
-        if (tid == 0) {
-            double d = D[j][j];
-            if (!(d > 0.0)) {
-                atomicExch(flag, 1);
-                d = 1.0;
+        if (tid < 32) {
+            double ri = 0.0;
+            if (tid == 0) {
+                double d = D[j][j];
+                if (!(d > 0.0)) {
+                    atomicExch(flag, 1);
+                    d = 1.0;
+                }
+                ri = rsqrt(d);
             }
-            D[j][j] = sqrt(d);
+            ri = __shfl_sync(0xffffffffu, ri, 0);
+            if (tid >= j && tid < nb) {
+                const double l = D[tid][j] * ri;  // L_jj = d / sqrt(d) for tid == j
+                Lc[tid] = l;
+                D[tid][j] = l;
+            }
         }
         __syncthreads();
-        const double piv = D[j][j];
-        for (int i = j + 1 + tid; i < nb; i += blockDim.x) D[i][j] /= piv;
-        __syncthreads();
-        // trailing update of the block (lower part)
-        for (int e = tid; e < nb * nb; e += blockDim.x) {
-            const int i = e / nb, k = e % nb;
-            if (i > j && k > j && k <= i) D[i][k] -= D[i][j] * D[k][j];
-        }
+        if (r < nb && c > j && c <= r) D[r][c] = fma(-Lc[r], Lc[c], D[r][c]);
         __syncthreads();
     }
-    for (int e = tid; e < nb * nb; e += blockDim.x) {
-        const int i = e / nb, k = e % nb;
-        A[(size_t)(k0 + i) * lda + k0 + k] = (k <= i) ? D[i][k] : 0.0;
-    }
+    if (r < nb && c < nb) A[(size_t)(k0 + r) * lda + k0 + c] = (c <= r) ? D[r][c] : 0.0;
 }
 
-// Rows below the diagonal block: L_ik = A_ik L_kk^{-T} (forward substitution per row).
-__global__ void trsm_panel_kernel(int N, double* A, int lda, int k0, int nb) {
+// Forward substitution across the lanes of one warp: lane l holds s_l of the
+// right-hand side on entry and x_l of L x = s on exit (lanes >= nb idle), L
+// the lower-triangular block in D with reciprocal diagonal dinv; steps from
+// j0 (the lanes below j0 must hold zeros).  At step j, x_j = s_j / L_jj
+// reaches every lane by a shuffle and lanes l > j subtract L_lj x_j.
+__device__ __forceinline__ double warp_forward_subst(double s, const double (*D)[CH_NB + 1], const double* dinv,
+                                                     int nb, int j0) {
+    const int lane = threadIdx.x & 31;
+    for (int j = j0; j < nb; ++j) {
+        const double x = __shfl_sync(0xffffffffu, s, j) * dinv[j];
+        if (lane == j) s = x;
+        else if (lane > j && lane < nb) s = fma(-D[lane][j], x, s);
+    }
+    return s;
+}
+
+// Rows below the diagonal block: L_ik = A_ik L_kk^{-T}, i.e. L_kk x = a for
+// each row a, one warp per row, four rows per CTA.
+__global__ void __launch_bounds__(128) trsm_panel_kernel(int N, double* A, int lda, int k0, int nb) {
     __shared__ double D[CH_NB][CH_NB + 1];
+    __shared__ double dinv[CH_NB];
     for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) D[e / nb][e % nb] = A[(size_t)(k0 + e / nb) * lda + k0 + e % nb];
     __syncthreads();
-    const int i = k0 + nb + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= N) return;
-    double x[CH_NB];
+    if (threadIdx.x < nb) dinv[threadIdx.x] = 1.0 / D[threadIdx.x][threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int i = k0 + nb + blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+    if (i >= N) return;  // whole warps
     double* row = A + (size_t)i * lda + k0;
-    for (int j = 0; j < nb; ++j) {
-        double s = row[j];
-        for (int l = 0; l < j; ++l) s -= x[l] * D[j][l];
-        x[j] = s / D[j][j];
-    }
-    for (int j = 0; j < nb; ++j) row[j] = x[j];
+    const double s = warp_forward_subst(lane < nb ? row[lane] : 0.0, D, dinv, nb, 0);
+    if (lane < nb) row[lane] = s;
 }
 
 __global__ void zero_upper_kernel(int N, double* A, int lda) {
@@ -535,25 +630,24 @@ __global__ void zero_upper_kernel(int N, double* A, int lda) {
     if (j > i) A[(size_t)i * lda + j] = 0.0;
 }
 
-// Inverse of the lower-triangular diagonal block at k0 (nb x nb), written to X.
-__global__ void trtri_diag_kernel(int N, const double* L, int ldl, double* X, int ldx) {
-    const int k0 = blockIdx.x * CH_NB;
+// Inverses of the lower-triangular diagonal blocks, written to X: column c of
+// block b solves L x = e_c (one warp per column, four columns per CTA, the
+// CH_NB / 4 CTAs of a block side by side).
+__global__ void __launch_bounds__(128) trtri_diag_kernel(int N, const double* L, int ldl, double* X, int ldx) {
+    constexpr int CPB = CH_NB / 4;  // CTAs per diagonal block
+    const int k0 = (blockIdx.x / CPB) * CH_NB;
     const int nb = min(CH_NB, N - k0);
     __shared__ double D[CH_NB][CH_NB + 1];
-    __shared__ double R[CH_NB][CH_NB + 1];
+    __shared__ double dinv[CH_NB];
     for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) D[e / nb][e % nb] = L[(size_t)(k0 + e / nb) * ldl + k0 + e % nb];
     __syncthreads();
-    // column c of the inverse by forward substitution (one thread per column)
-    const int c = threadIdx.x;
-    if (c < nb) {
-        for (int i = 0; i < nb; ++i) {
-            double s = (i == c) ? 1.0 : 0.0;
-            for (int l = c; l < i; ++l) s -= D[i][l] * R[l][c];
-            R[i][c] = (i < c) ? 0.0 : s / D[i][i];
-        }
-    }
+    if (threadIdx.x < nb) dinv[threadIdx.x] = 1.0 / D[threadIdx.x][threadIdx.x];
     __syncthreads();
-    for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) X[(size_t)(k0 + e / nb) * ldx + k0 + e % nb] = R[e / nb][e % nb];
+    const int lane = threadIdx.x & 31;
+    const int c = (blockIdx.x % CPB) * 4 + (threadIdx.x >> 5);
+    if (c >= nb) return;  // whole warps
+    const double s = warp_forward_subst(lane == c ? 1.0 : 0.0, D, dinv, nb, c);
+    if (lane < nb) X[(size_t)(k0 + lane) * ldx + k0 + c] = lane >= c ? s : 0.0;
 }
 
 __global__ void symmetrize_kernel(int N, const double* A, double* B, int mode, double sgn) {
@@ -794,8 +888,13 @@ cudaError_t gemm_combine(int N, size_t K, int Kc, const T* A, size_t lda, const 
 cudaError_t small_gemm_f64(int M, int N, int K, const double* A, int lda, bool ta, const double* B, int ldb, bool tb,
                            double alpha, double beta, double* C, int ldc, cudaStream_t s, int* launches) {
     if (M <= 0 || N <= 0) return cudaSuccess;
-    dim3 grid((N + SG - 1) / SG, (M + SG - 1) / SG);
-    small_gemm_kernel<<<grid, dim3(SG, SG), 0, s>>>(M, N, K, A, lda, ta, B, ldb, tb, alpha, beta, C, ldc);
+    const dim3 grid((N + SG - 1) / SG, (M + SG - 1) / SG);
+    if (grid.x * grid.y < 64) {  // few 16 x 16 tiles (the blocked factorisations): 8 x 8 tiles, K panels staged
+        const dim3 g8((N + 7) / 8, (M + 7) / 8);
+        small_gemm_staged_f64_kernel<<<g8, dim3(8, 8), 0, s>>>(M, N, K, A, lda, ta, B, ldb, tb, alpha, beta, C, ldc);
+    } else {
+        small_gemm_kernel<<<grid, dim3(SG, SG), 0, s>>>(M, N, K, A, lda, ta, B, ldb, tb, alpha, beta, C, ldc);
+    }
     *launches += 1;
     return cudaGetLastError();
 }
@@ -817,12 +916,12 @@ cudaError_t inv_sqrt_spd(int N, const double* A, double* X, double* work, int* d
     double* scal = work + 4 * nn;
     const int nb = (int)((nn + 255) / 256);
     double h_norm2 = 0.0;
-    frob<double>(N, A, 0, scal, s, launches);
+    norm_inf(N, A, scal, s, launches);
     cudaMemcpyAsync(&h_norm2, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e) return e;
     if (!(h_norm2 > 0.0) || !std::isfinite(h_norm2)) { *ok = 0; return cudaSuccess; }
-    const double c = std::sqrt(h_norm2);
+    const double c = h_norm2;  // ||A||_inf >= lambda_max
     scale_copy_kernel<<<nb, 256, 0, s>>>((int)nn, A, Y, 1.0 / c);
     set_identity_kernel<<<nb, 256, 0, s>>>(N, Z, 1.0);
     *launches += 2;
@@ -876,17 +975,22 @@ cudaError_t inv_sqrt_spd_mixed(int N, const double* A, double* X, double* work, 
     double* scal = work + 3 * nn;  // past the five FP32 matrices (2.5 nn doubles)
     const int nb = (int)((nn + 255) / 256);
     double h = 0.0;
-    frob<double>(N, A, 0, scal, s, launches);
+    norm_inf(N, A, scal, s, launches);
     cudaMemcpyAsync(&h, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e) return e;
     *ok = 0;
     if (!(h > 0.0) || !std::isfinite(h)) return cudaSuccess;
-    const double c = std::sqrt(h);
+    const double c = h;  // ||A||_inf >= lambda_max
     scale_to_f32_kernel<<<nb, 256, 0, s>>>((int)nn, A, Y, 1.0 / c);
     identity_f32_kernel<<<nb, 256, 0, s>>>(N, Z);
     *launches += 2;
+    // h = ||I - Z Y||_F^2 = sum_k (1 - x_k)^2 over the eigenvalues x_k of Z Y.
+    // Once h < 1e-6 N every |1 - x_k| < 0.016 and the iteration is in its
+    // quadratic regime (1 - x -> ~(3/4)(1 - x)^2): two more steps reach the
+    // FP32 rounding floor without another host-checked product.
     double prev = INFINITY;
+    int extra = -1;
     for (int it = 0; it < 160; ++it) {
         sgemm_f32_square(N, Z, Y, T, s);
         ns_t_f32_kernel<<<nb, 256, 0, s>>>(N, T);
@@ -894,7 +998,11 @@ cudaError_t inv_sqrt_spd_mixed(int N, const double* A, double* X, double* work, 
         std::swap(Y, Y2);
         std::swap(Z, Z2);
         *launches += 3;
-        if (it >= 5 && (it % 3 == 2)) {
+        if (extra > 0 && --extra == 0) {
+            *ok = 1;
+            break;
+        }
+        if (extra < 0 && it >= 3 && (it % 2 == 1)) {
             sgemm_f32_square(N, Z, Y, T, s);
             frob<float>(N, T, 1, scal, s, launches);
             cudaMemcpyAsync(&h, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -902,6 +1010,7 @@ cudaError_t inv_sqrt_spd_mixed(int N, const double* A, double* X, double* work, 
             if ((e = cudaStreamSynchronize(s))) return e;
             if (!std::isfinite(h)) break;
             if (h < 1e-11 * N || (h < 1e-6 * N && h > 0.25 * prev)) { *ok = 1; break; }
+            if (h < 1e-6 * N) extra = 2;
             prev = h;
         }
     }
@@ -948,11 +1057,11 @@ cudaError_t cholesky_lower(int N, double* A, int lda, int* d_flag, int* ok, cuda
     cudaMemsetAsync(d_flag, 0, sizeof(int), s);
     for (int k0 = 0; k0 < N; k0 += CH_NB) {
         const int nb = std::min(CH_NB, N - k0);
-        potrf_diag_kernel<<<1, 256, 0, s>>>(N, A, lda, k0, nb, d_flag);
+        potrf_diag_kernel<<<1, CH_NB * CH_NB, 0, s>>>(N, A, lda, k0, nb, d_flag);
         *launches += 1;
         const int rem = N - k0 - nb;
         if (rem > 0) {
-            trsm_panel_kernel<<<(rem + 127) / 128, 128, 0, s>>>(N, A, lda, k0, nb);
+            trsm_panel_kernel<<<(rem + 3) / 4, 128, 0, s>>>(N, A, lda, k0, nb);
             *launches += 1;
             // A22 -= L21 L21^T
             double* L21 = A + (size_t)(k0 + nb) * lda + k0;
@@ -974,7 +1083,7 @@ cudaError_t cholesky_lower(int N, double* A, int lda, int* d_flag, int* ok, cuda
 cudaError_t trtri_lower(int N, const double* L, int ldl, double* X, int ldx, cudaStream_t s, int* launches) {
     cudaMemsetAsync(X, 0, sizeof(double) * (size_t)N * ldx, s);
     const int nblk = (N + CH_NB - 1) / CH_NB;
-    trtri_diag_kernel<<<nblk, CH_NB, 0, s>>>(N, L, ldl, X, ldx);
+    trtri_diag_kernel<<<nblk * (CH_NB / 4), 128, 0, s>>>(N, L, ldl, X, ldx);
     *launches += 1;
     // temp rows: use the upper triangle of X?  No: need a separate buffer of nb x N.
     // Work in place: for block row i, compute T = L[i, 0:i] * X[0:i, 0:i] into X[i, 0:i]

@@ -496,20 +496,22 @@ __global__ void gather_columns_kernel(const T* __restrict__ psi, size_t ldpsi, i
 // ---------------------------------------------------------------------------
 // Register-resident pivoted QR (FP32): the same Businger-Golub steps as the
 // kernels above (take the live column with the largest residual norm, ties
-// to the lowest index; remove its direction from every column; recompute
-// every norm exactly from the updated values), laid out so that one step is
-// a short dependent chain.  LPC lanes hold one column (RPL rows each), so
-// the q.r dot products and the norms reduce with lane shuffles alone; the
-// columns of a CTA that do not fit in registers live in shared memory with a
-// padded row pitch (16-byte accesses free of bank conflicts).  The row work
-// runs on packed FP32 pairs.  Per step each warp publishes its best column
-// to global memory; the CTAs then agree on the global winner through one
-// 64-bit atomicMax per CTA (key = the FP32 squared norm's bits above the
-// complemented column index: the largest norm, then the lowest index) and a
-// grid barrier on a monotone arrival counter; every CTA reads the winner's
-// published column and scales it by the inverse norm taken from the key
-// (no FP64 sums on the step's critical path: FP64 runs at a small fraction
-// of the FP32 rate on this GPU).
+// to the lowest index; remove its direction from every column), laid out so
+// that one step is a short dependent chain.  LPC lanes hold one column (RPL
+// rows each), so the q.r dot products and the norms reduce with lane
+// shuffles alone; the columns of a CTA that do not fit in registers live in
+// shared memory with a padded row pitch (16-byte accesses free of bank
+// conflicts).  The row work runs on packed FP32 pairs.  A step makes one
+// pass over each column (the previous step's projection, this step's dot and
+// the squared norm before this step's projection: the residual norm is the
+// difference, |v|^2 - (q.v)^2).  Per step each warp publishes its best
+// column, projected, with its exact squared norm to global memory; the CTAs
+// then agree on the global winner through one 64-bit atomicMax per CTA
+// (key = the FP32 squared norm's bits above the complemented column index:
+// the largest norm, then the lowest index) and a grid barrier on a monotone
+// arrival counter; every CTA reads the winner's published column and scales
+// it by the inverse square root of its published norm (in FP32: FP64 runs
+// at a small fraction of the FP32 rate on this GPU).
 constexpr int QR2_THREADS = 512, QR2_WARPS = QR2_THREADS / 32;
 
 __device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) {
@@ -518,80 +520,59 @@ __device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long
     return v;
 }
 
-template <int RPL>
-__device__ __forceinline__ float qdot(const float* __restrict__ qs, const float* v) {
-    f2 a0 = bc2(0.f), a1 = bc2(0.f);
+// sum over the LPC lanes of one column (consecutive lanes)
+template <int LPC>
+__device__ __forceinline__ float lane_sum(float x) {
 #pragma unroll
-    for (int j = 0; j < RPL; j += 4) {
-        const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
-        a0 = fma2(mk2(q4.x, q4.y), mk2(v[j], v[j + 1]), a0);
-        a1 = fma2(mk2(q4.z, q4.w), mk2(v[j + 2], v[j + 3]), a1);
-    }
-    float x0, x1;
-    unpk2(a0 + a1, x0, x1);
-    return x0 + x1;
+    for (int o = 1; o < LPC; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
 }
 
-// v -= q d, and the squared norm of the result
+// One pass over a column chunk held in registers: v <- v - dp qp (the
+// previous step's projection, deferred to this pass), then the partial dot
+// q.v and squared norm v.v of the result.  The stored values and the dot are
+// those of the two-pass form (same products in the same order); only the
+// norm after this step's projection, |v|^2 - (q.v)^2, is formed differently.
 template <int RPL>
-__device__ __forceinline__ float qupdate(const float* __restrict__ qs, float* v, float d) {
-    const f2 nd = bc2(-d);
-    f2 n0 = bc2(0.f), n1 = bc2(0.f);
+__device__ __forceinline__ void qpass(const float* __restrict__ qp, const float* __restrict__ q, float* v, float dp,
+                                      float& dot, float& ss) {
+    const f2 nd = bc2(-dp);
+    f2 a0 = bc2(0.f), a1 = bc2(0.f), n0 = bc2(0.f), n1 = bc2(0.f);
 #pragma unroll
     for (int j = 0; j < RPL; j += 4) {
-        const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
-        const f2 u0 = fma2(mk2(q4.x, q4.y), nd, mk2(v[j], v[j + 1]));
-        const f2 u1 = fma2(mk2(q4.z, q4.w), nd, mk2(v[j + 2], v[j + 3]));
+        const float4 p4 = *reinterpret_cast<const float4*>(qp + j);
+        const float4 q4 = *reinterpret_cast<const float4*>(q + j);
+        const f2 u0 = fma2(mk2(p4.x, p4.y), nd, mk2(v[j], v[j + 1]));
+        const f2 u1 = fma2(mk2(p4.z, p4.w), nd, mk2(v[j + 2], v[j + 3]));
+        a0 = fma2(mk2(q4.x, q4.y), u0, a0);
+        a1 = fma2(mk2(q4.z, q4.w), u1, a1);
         n0 = fma2(u0, u0, n0);
         n1 = fma2(u1, u1, n1);
         unpk2(u0, v[j], v[j + 1]);
         unpk2(u1, v[j + 2], v[j + 3]);
     }
     float x0, x1;
-    unpk2(n0 + n1, x0, x1);
-    return x0 + x1;
-}
-
-template <int RPL>
-__device__ __forceinline__ float qnorm(const float* v) {
-    f2 n0 = bc2(0.f), n1 = bc2(0.f);
-#pragma unroll
-    for (int j = 0; j < RPL; j += 4) {
-        const f2 u0 = mk2(v[j], v[j + 1]), u1 = mk2(v[j + 2], v[j + 3]);
-        n0 = fma2(u0, u0, n0);
-        n1 = fma2(u1, u1, n1);
-    }
-    float x0, x1;
-    unpk2(n0 + n1, x0, x1);
-    return x0 + x1;
-}
-
-// The same three for a column chunk in shared memory (16-byte accesses,
-// nothing held in registers across the chunk).
-template <int RPL>
-__device__ __forceinline__ float sdot(const float* __restrict__ qs, const float* w) {
-    f2 a0 = bc2(0.f), a1 = bc2(0.f);
-#pragma unroll 4
-    for (int j = 0; j < RPL; j += 4) {
-        const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
-        const float4 x = *reinterpret_cast<const float4*>(w + j);
-        a0 = fma2(mk2(q4.x, q4.y), mk2(x.x, x.y), a0);
-        a1 = fma2(mk2(q4.z, q4.w), mk2(x.z, x.w), a1);
-    }
-    float x0, x1;
     unpk2(a0 + a1, x0, x1);
-    return x0 + x1;
+    dot = x0 + x1;
+    unpk2(n0 + n1, x0, x1);
+    ss = x0 + x1;
 }
+// The same pass over a column chunk in shared memory: one read and (store)
+// one write of the chunk per step.
 template <int RPL>
-__device__ __forceinline__ float supdate(const float* __restrict__ qs, float* w, float d, bool store) {
-    const f2 nd = bc2(-d);
-    f2 n0 = bc2(0.f), n1 = bc2(0.f);
+__device__ __forceinline__ void spass(const float* __restrict__ qp, const float* __restrict__ q, float* w, float dp,
+                                      bool store, float& dot, float& ss) {
+    const f2 nd = bc2(-dp);
+    f2 a0 = bc2(0.f), a1 = bc2(0.f), n0 = bc2(0.f), n1 = bc2(0.f);
 #pragma unroll 4
     for (int j = 0; j < RPL; j += 4) {
-        const float4 q4 = *reinterpret_cast<const float4*>(qs + j);
+        const float4 p4 = *reinterpret_cast<const float4*>(qp + j);
+        const float4 q4 = *reinterpret_cast<const float4*>(q + j);
         const float4 x = *reinterpret_cast<const float4*>(w + j);
-        const f2 u0 = fma2(mk2(q4.x, q4.y), nd, mk2(x.x, x.y));
-        const f2 u1 = fma2(mk2(q4.z, q4.w), nd, mk2(x.z, x.w));
+        const f2 u0 = fma2(mk2(p4.x, p4.y), nd, mk2(x.x, x.y));
+        const f2 u1 = fma2(mk2(p4.z, p4.w), nd, mk2(x.z, x.w));
+        a0 = fma2(mk2(q4.x, q4.y), u0, a0);
+        a1 = fma2(mk2(q4.z, q4.w), u1, a1);
         n0 = fma2(u0, u0, n0);
         n1 = fma2(u1, u1, n1);
         if (store) {
@@ -602,30 +583,10 @@ __device__ __forceinline__ float supdate(const float* __restrict__ qs, float* w,
         }
     }
     float x0, x1;
+    unpk2(a0 + a1, x0, x1);
+    dot = x0 + x1;
     unpk2(n0 + n1, x0, x1);
-    return x0 + x1;
-}
-template <int RPL>
-__device__ __forceinline__ float snorm(const float* w) {
-    f2 n0 = bc2(0.f), n1 = bc2(0.f);
-#pragma unroll 4
-    for (int j = 0; j < RPL; j += 4) {
-        const float4 x = *reinterpret_cast<const float4*>(w + j);
-        const f2 u0 = mk2(x.x, x.y), u1 = mk2(x.z, x.w);
-        n0 = fma2(u0, u0, n0);
-        n1 = fma2(u1, u1, n1);
-    }
-    float x0, x1;
-    unpk2(n0 + n1, x0, x1);
-    return x0 + x1;
-}
-
-// sum over the LPC lanes of one column (consecutive lanes)
-template <int LPC>
-__device__ __forceinline__ float lane_sum(float x) {
-#pragma unroll
-    for (int o = 1; o < LPC; o <<= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    return x;
+    ss = x0 + x1;
 }
 
 __device__ __forceinline__ unsigned long long col_key(float nrm, int col) {
@@ -637,7 +598,15 @@ __device__ __forceinline__ unsigned long long col_key(float nrm, int col) {
 // memory, handled by group s % G.  Rows: lane l of a group holds rows
 // [l RPL, (l + 1) RPL); q is kept as LPC row chunks of RPL + 4 floats, so
 // the LPC distinct chunks a warp reads at once fall on different banks.
-// keys[npiv] and bar[0] are zero at launch.
+//
+// Each step makes one pass over every column: it applies the previous step's
+// projection (v -= d_{k-1} q_{k-1}, deferred from that step), and forms
+// d_k = q_k.v and |v|^2, so the column's norm after step k's projection is
+// |v|^2 - d_k^2 (clamped at 0).  A shared-memory column is read and written
+// once per step instead of read twice and written once.  The published
+// candidate is the projected column v - d_k q_k with its exact squared norm
+// (pnorm), from which the next q is normalised.  keys[npiv] and bar[0] are
+// zero at launch.
 template <int RPL, int LPC>
 __global__ void __launch_bounds__(QR2_THREADS, 1)
     qr_resident_kernel(int nrow, int ncol, const float* __restrict__ R, int npiv, int cpb, float* __restrict__ pub,
@@ -647,10 +616,6 @@ __global__ void __launch_bounds__(QR2_THREADS, 1)
     constexpr int NPAD = RPL * LPC;     // padded rows
     constexpr int PITCH = RPL + 4;      // shared-memory row-chunk pitch (floats)
     extern __shared__ __align__(16) float qr2_smem[];
-    float* qs = qr2_smem;                // [LPC][PITCH] q of the current step
-    float* sc = qr2_smem + LPC * PITCH;  // [SC][LPC][PITCH] shared-memory columns
-    __shared__ unsigned long long wkey[QR2_WARPS];
-    __shared__ int abort_sh;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int g = tid / LPC, l = tid % LPC;
     const int c0 = blockIdx.x * cpb;
@@ -658,7 +623,14 @@ __global__ void __launch_bounds__(QR2_THREADS, 1)
     const int SC = max(0, ncta - G);       // of them in shared memory
     const int rounds = (SC + G - 1) / G;
     const int myreg = g < ncta ? c0 + g : -1;
+    float* qbuf = qr2_smem;                            // 2 x [LPC][PITCH]: q of steps k (k & 1) and k - 1
+    float* sc = qr2_smem + 2 * LPC * PITCH;            // [SC][LPC][PITCH] shared-memory columns
+    float* dsm = sc + (size_t)SC * LPC * PITCH;        // [SC] each shared column's last dot
+    float* pnorm = pub + (size_t)2 * gridDim.x * QR2_WARPS * NPAD;  // [2][CTAs][warps] exact squared norms
+    __shared__ unsigned long long wkey[QR2_WARPS];
+    __shared__ int abort_sh;
     float v[RPL];
+    float dreg = 0.f;      // the register column's last dot
     unsigned chosen = 0u;  // bit 0: the register column; bit 1 + r: shared column of round r
 #pragma unroll
     for (int j = 0; j < RPL; ++j) {
@@ -676,20 +648,21 @@ __global__ void __launch_bounds__(QR2_THREADS, 1)
             }
         }
     }
-    for (int j = tid; j < LPC * PITCH; j += QR2_THREADS) qs[j] = 0.f;
+    for (int j = tid; j < 2 * LPC * PITCH; j += QR2_THREADS) qbuf[j] = 0.f;
+    for (int j = tid; j < SC; j += QR2_THREADS) dsm[j] = 0.f;
     __syncthreads();
     for (int step = 0; step < npiv; ++step) {
-        const float* qrow = qs + l * PITCH;
+        const float* qrow = qbuf + (step & 1) * LPC * PITCH + l * PITCH;        // q_k (zero at step 0)
+        const float* prow = qbuf + ((step + 1) & 1) * LPC * PITCH + l * PITCH;  // q_{k-1}
         unsigned long long best = 0ull;
         // register column
         {
-            float nrm;
-            if (step > 0) {
-                const float d = lane_sum<LPC>(qdot<RPL>(qrow, v));
-                nrm = lane_sum<LPC>(qupdate<RPL>(qrow, v, d));
-            } else {
-                nrm = lane_sum<LPC>(qnorm<RPL>(v));
-            }
+            float d, ss;
+            qpass<RPL>(prow, qrow, v, dreg, d, ss);
+            d = lane_sum<LPC>(d);
+            ss = lane_sum<LPC>(ss);
+            dreg = d;
+            const float nrm = fmaxf(ss - d * d, 0.f);
             if (myreg >= 0 && !(chosen & 1u)) best = col_key(nrm, myreg);
         }
         // shared-memory columns
@@ -697,15 +670,14 @@ __global__ void __launch_bounds__(QR2_THREADS, 1)
             const int s = r * G + g;
             const bool has = s < SC;  // uniform over the LPC lanes of the group
             float* w = sc + ((size_t)(has ? s : 0) * LPC + l) * PITCH;
-            float nrm;
-            if (step > 0) {
-                const float d = lane_sum<LPC>(sdot<RPL>(qrow, w));
-                nrm = lane_sum<LPC>(supdate<RPL>(qrow, w, d, has));
-            } else {
-                nrm = lane_sum<LPC>(snorm<RPL>(w));
-            }
+            const float dp = has ? dsm[s] : 0.f;
+            float d, ss;
+            spass<RPL>(prow, qrow, w, dp, has, d, ss);
+            d = lane_sum<LPC>(d);
+            ss = lane_sum<LPC>(ss);
+            if (has && l == 0) dsm[s] = d;
             if (has && !((chosen >> (1 + r)) & 1u)) {
-                const unsigned long long k = col_key(nrm, c0 + G + s);
+                const unsigned long long k = col_key(fmaxf(ss - d * d, 0.f), c0 + G + s);
                 best = k > best ? k : best;
             }
         }
@@ -716,24 +688,32 @@ __global__ void __launch_bounds__(QR2_THREADS, 1)
             const unsigned long long x = __shfl_xor_sync(0xffffffffu, wb, o);
             wb = x > wb ? x : wb;
         }
-        // the lanes holding the warp's best column publish it
-        if (wb != 0ull) {
-            const int wcol = (int)(0xffffffffu - (unsigned)(wb & 0xffffffffu));
-            const size_t slot = ((size_t)(step & 1) * gridDim.x + blockIdx.x) * QR2_WARPS + warp;
+        // the lanes holding the warp's best column publish it projected
+        // (v - d q) with its exact squared norm
+        __syncwarp();  // this step's dsm writes are visible to the group's lanes
+        const size_t slot = ((size_t)(step & 1) * gridDim.x + blockIdx.x) * QR2_WARPS + warp;
+        const int wcol = (int)(0xffffffffu - (unsigned)(wb & 0xffffffffu));
+        const int ws = wcol - c0 - G;
+        const bool own_reg = wb != 0ull && wcol == myreg;
+        const bool own_sh = wb != 0ull && ws >= 0 && ws < SC && ws % G == g;
+        float pn = 0.f;
+        if (own_reg || own_sh) {
             float* out = pub + slot * NPAD + l * RPL;
-            if (wcol == myreg) {
+            const float* src = own_sh ? sc + ((size_t)ws * LPC + l) * PITCH : nullptr;
+            const float d = own_sh ? dsm[ws] : dreg;
 #pragma unroll
-                for (int j = 0; j < RPL; j += 4)
-                    *reinterpret_cast<float4*>(out + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-            } else {
-                const int s = wcol - c0 - G;
-                if (s >= 0 && s < SC && s % G == g) {
-                    const float* w = sc + ((size_t)s * LPC + l) * PITCH;
-                    for (int j = 0; j < RPL; j += 4)
-                        *reinterpret_cast<float4*>(out + j) = *reinterpret_cast<const float4*>(w + j);
-                }
+            for (int j = 0; j < RPL; j += 4) {
+                const float4 q4 = *reinterpret_cast<const float4*>(qrow + j);
+                const float4 x = own_sh ? *reinterpret_cast<const float4*>(src + j)
+                                        : make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+                const float4 o = make_float4(fmaf(-d, q4.x, x.x), fmaf(-d, q4.y, x.y), fmaf(-d, q4.z, x.z),
+                                             fmaf(-d, q4.w, x.w));
+                pn = fmaf(o.x, o.x, fmaf(o.y, o.y, fmaf(o.z, o.z, fmaf(o.w, o.w, pn))));
+                *reinterpret_cast<float4*>(out + j) = o;
             }
         }
+        pn = lane_sum<LPC>(pn);  // every lane takes part; the owner group's lanes get its norm
+        if ((own_reg || own_sh) && l == 0) pnorm[slot] = pn;
         if (lane == 0) wkey[warp] = wb;
         // grid barrier: arrive with this CTA's best key, wait for every CTA.
         // The key goes in first (a relaxed reduction, ordered before the
@@ -752,9 +732,9 @@ __global__ void __launch_bounds__(QR2_THREADS, 1)
             if (cnt + 1 < target) {
                 const unsigned long long t0 = global_ns();
                 for (;;) {
-                    unsigned v;
-                    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(bar) : "memory");
-                    if (v >= target) break;
+                    unsigned vv;
+                    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(vv) : "l"(bar) : "memory");
+                    if (vv >= target) break;
                     if (global_ns() - t0 > limit_ns) {
                         atomicExch(bar + 2, 1u);
                         timed_out = 1;
@@ -776,15 +756,15 @@ __global__ void __launch_bounds__(QR2_THREADS, 1)
         const int p = (int)(0xffffffffu - (unsigned)(key & 0xffffffffu));
         const int wcta = p / cpb, li = p - wcta * cpb;
         const int wg = li < G ? li : (li - G) % G;
-        const size_t slot = ((size_t)(step & 1) * gridDim.x + wcta) * QR2_WARPS + (wg * LPC) / 32;
-        // the winner's squared norm is the key's upper half (the FP32 value the
-        // argmax compared); its inverse square root in FP32 (correctly rounded
-        // square root and division: FP64 arithmetic in every thread of every
-        // CTA cost ~5 us a step on this GPU's FP64 rate)
-        const float nn = __uint_as_float((unsigned)(key >> 32));
+        const size_t wslot = ((size_t)(step & 1) * gridDim.x + wcta) * QR2_WARPS + (wg * LPC) / 32;
+        // the winner's exact squared norm, published with its column; the
+        // inverse square root in FP32 (FP64 arithmetic in every thread of
+        // every CTA cost ~5 us a step on this GPU's FP64 rate)
+        const float nn = __ldcg(pnorm + wslot);
         const float inv = nn > 0.f ? 1.f / sqrtf(nn) : 0.f;
+        float* qnext = qbuf + ((step + 1) & 1) * LPC * PITCH;  // q_{k-1} is no longer read
         for (int j = tid; j < NPAD; j += QR2_THREADS)
-            qs[(j / RPL) * PITCH + j % RPL] = __ldcg(pub + slot * NPAD + j) * inv;
+            qnext[(j / RPL) * PITCH + j % RPL] = __ldcg(pub + wslot * NPAD + j) * inv;
         if (wcta == (int)blockIdx.x && wg == g) {
             if (li < G) chosen |= 1u;
             else chosen |= 1u << (1 + (li - G) / G);
@@ -901,7 +881,9 @@ static cudaError_t qr_resident_launch(int nrow, int ncol, const float* R, int np
     cudaFuncAttributes fa{};
     cudaError_t e;
     if ((e = cudaFuncGetAttributes(&fa, fn))) return e;
-    const size_t dyn = ((size_t)LPC * PITCH + (size_t)sc * LPC * PITCH) * sizeof(float);
+    // two q buffers, the shared-memory columns and their last dots
+    const size_t dyn = (2 * (size_t)LPC * PITCH + (size_t)sc * LPC * PITCH + (((size_t)sc + 3) & ~(size_t)3)) *
+                       sizeof(float);
     if (dyn + fa.sharedSizeBytes + 1024 > (size_t)optin) return cudaSuccess;
     // one limit for every caller of this kernel: the opt-in maximum
     if ((e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes)))
