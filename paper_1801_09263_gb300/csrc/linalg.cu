@@ -164,6 +164,107 @@ __global__ void __launch_bounds__(GR_THREADS) gemm_rows_kernel(int M, int N, siz
     }
 }
 
+// The FP32 Gram of 16-byte aligned rows without |.|: the same 64 x 64 tiles,
+// chunks and compensated fold, with the A and B tiles brought in by cp.async
+// through a GA_STAGES-deep ring of row-major [row][k] tiles (the loads of
+// step t + 2 in flight while step t is computed), thread (tx, ty) owning
+// rows ty + 16 i and columns tx + 16 j (a warp's 16-byte reads of 16
+// consecutive rows fall on distinct bank groups with the 20-float pitch), and
+// the products paired along k on packed FMAs: each accumulator pair holds the
+// even- and odd-k sums of one output, added before the fold.
+constexpr int GA_BK = 16, GA_STAGES = 3, GA_PITCH = GA_BK + 4;
+static_assert(GA_BK == GR_BK, "the chunk length is a multiple of GR_BK");
+__global__ void __launch_bounds__(GR_THREADS) gemm_rows_f32_async_kernel(int M, int N, size_t K,
+                                                                         const float* __restrict__ A, size_t lda,
+                                                                         const float* __restrict__ B, size_t ldb,
+                                                                         bool sym, size_t kchunk,
+                                                                         double* __restrict__ work) {
+    __shared__ __align__(16) float As[GA_STAGES][GR_BM][GA_PITCH];
+    __shared__ __align__(16) float Bs[GA_STAGES][GR_BN][GA_PITCH];
+    if (sym && blockIdx.y < blockIdx.x) return;  // symmetric: upper tiles only
+    const int m0 = blockIdx.x * GR_BM, n0 = blockIdx.y * GR_BN;
+    const size_t k_begin = (size_t)blockIdx.z * kchunk;
+    const size_t k_end = min(K, k_begin + kchunk);
+    const int nsteps = k_begin < k_end ? (int)((k_end - k_begin + GA_BK - 1) / GA_BK) : 0;
+    const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
+    const int crow = tid / 4, cq = tid % 4;  // the 16-byte chunk this thread copies per tile
+    const unsigned as_s = (unsigned)__cvta_generic_to_shared(&As[0][crow][cq * 4]);
+    const unsigned bs_s = (unsigned)__cvta_generic_to_shared(&Bs[0][crow][cq * 4]);
+    constexpr unsigned kStageBytes = GR_BM * GA_PITCH * sizeof(float);
+    auto issue = [&](int t) {
+        if (t < nsteps) {
+            const size_t k = k_begin + (size_t)t * GA_BK + cq * 4;
+            const unsigned st = (unsigned)(t % GA_STAGES) * kStageBytes;
+            int ab = 0, bb = 0;
+            const float* pa = A;
+            const float* pb = B;
+            if (k < k_end) {
+                const int bytes = (int)(min((size_t)4, k_end - k) * sizeof(float));
+                if (m0 + crow < M) { ab = bytes; pa = A + (size_t)(m0 + crow) * lda + k; }
+                if (n0 + crow < N) { bb = bytes; pb = B + (size_t)(n0 + crow) * ldb + k; }
+            }
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(as_s + st), "l"(pa), "r"(ab) : "memory");
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(bs_s + st), "l"(pb), "r"(bb) : "memory");
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");  // one group per step, empty past the end
+    };
+    f2 acc[4][4];
+    float fold[4][4], comp[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) { acc[i][j] = bc2(0.f); fold[i][j] = 0.f; comp[i][j] = 0.f; }
+    issue(0);
+    issue(1);
+    for (int t = 0; t < nsteps; ++t) {
+        issue(t + 2);
+        asm volatile("cp.async.wait_group 2;" ::: "memory");  // step t's copies have landed
+        __syncthreads();
+        const int st = t % GA_STAGES;
+#pragma unroll
+        for (int kq = 0; kq < GA_BK; kq += 4) {
+            float4 b[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = *reinterpret_cast<const float4*>(&Bs[st][tx + 16 * j][kq]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float4 a = *reinterpret_cast<const float4*>(&As[st][ty + 16 * i][kq]);
+                const f2 a01 = mk2(a.x, a.y), a23 = mk2(a.z, a.w);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    acc[i][j] = fma2(a01, mk2(b[j].x, b[j].y), acc[i][j]);
+                    acc[i][j] = fma2(a23, mk2(b[j].z, b[j].w), acc[i][j]);
+                }
+            }
+        }
+        __syncthreads();  // stage t % GA_STAGES is refilled by issue(t + 3)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                float e, o;
+                unpk2(acc[i][j], e, o);
+                const float y = (e + o) - comp[i][j];
+                const float s = fold[i][j] + y;
+                comp[i][j] = (s - fold[i][j]) - y;
+                fold[i][j] = s;
+                acc[i][j] = bc2(0.f);
+            }
+    }
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    double* out = work + (size_t)blockIdx.z * M * N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int m = m0 + ty + 16 * i;
+        if (m >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n = n0 + tx + 16 * j;
+            if (n < N) out[(size_t)m * N + n] = (double)fold[i][j] - (double)comp[i][j];
+        }
+    }
+}
+
 __global__ void reduce_chunks_kernel(int M, int N, int nchunk, const double* __restrict__ work, double alpha,
                                      bool sym, double* __restrict__ C, int ldc) {
     const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -368,9 +469,11 @@ __global__ void small_gemm_f32_kernel(int N, const float* __restrict__ A, const 
 }
 
 // C = A B for N x N row-major, N <= 376: the block's 16 rows of A and 16
-// columns of B are staged in shared memory with all loads in flight at once
-// (the products are latency-bound at N ~ 256), then one output per thread
-// over the full K = N, in the same order as small_gemm_f32_kernel.
+// columns of B (transposed, so both are read along k) are staged in shared
+// memory with all loads in flight at once (the products are latency-bound at
+// N ~ 256), then one output per thread over the full K = N from 16-byte reads
+// (two shared-memory loads per four FMAs) into four partial sums.
+__host__ __device__ inline int sg_pitch(int N) { return ((N + 3) & ~3) + 4; }
 __global__ void small_gemm_f32_staged_kernel(int N, const float* __restrict__ A0, const float* __restrict__ B0,
                                              float* __restrict__ C0, const float* __restrict__ A1,
                                              const float* __restrict__ B1, float* __restrict__ C1) {
@@ -378,32 +481,41 @@ __global__ void small_gemm_f32_staged_kernel(int N, const float* __restrict__ A0
     const float* __restrict__ A = blockIdx.z ? A1 : A0;
     const float* __restrict__ B = blockIdx.z ? B1 : B0;
     float* __restrict__ C = blockIdx.z ? C1 : C0;
-    extern __shared__ float sg_smem[];
-    const int lp = N + 1;               // row pitch of As: the two rows a warp reads sit in different banks
-    float* As = sg_smem;                // [SG][N + 1]
-    float* Bs = sg_smem + SG * lp;      // [N][SG]
+    extern __shared__ __align__(16) float sg_smem[];
+    const int lp = sg_pitch(N);       // 16-byte aligned rows, the pitch offsetting rows by 4 banks
+    float* As = sg_smem;              // [SG][lp]: A[m0 + r][k]
+    float* Bs = sg_smem + SG * lp;    // [SG][lp]: B[k][n0 + c]
     const int tx = threadIdx.x, ty = threadIdx.y, t = ty * SG + tx;
     const int m0 = blockIdx.y * SG, n0 = blockIdx.x * SG;
-    for (int q = t; q < SG * N; q += SG * SG) {
-        const int r = q / N, k = q % N;
-        As[r * lp + k] = m0 + r < N ? __ldg(A + (size_t)(m0 + r) * N + k) : 0.f;
+    const int kpad = (N + 3) & ~3;
+    for (int q = t; q < SG * kpad; q += SG * SG) {
+        const int r = q / kpad, k = q % kpad;
+        As[r * lp + k] = (m0 + r < N && k < N) ? __ldg(A + (size_t)(m0 + r) * N + k) : 0.f;
     }
-    for (int q = t; q < SG * N; q += SG * SG) {
+    for (int q = t; q < SG * kpad; q += SG * SG) {
         const int k = q / SG, c = q % SG;
-        Bs[q] = n0 + c < N ? __ldg(B + (size_t)k * N + n0 + c) : 0.f;
+        Bs[c * lp + k] = (n0 + c < N && k < N) ? __ldg(B + (size_t)k * N + n0 + c) : 0.f;
     }
     __syncthreads();
     const int m = m0 + ty, n = n0 + tx;
-    float acc = 0.f;
     const float* ar = As + ty * lp;
-#pragma unroll 8
-    for (int k = 0; k < N; ++k) acc = fmaf(ar[k], Bs[k * SG + tx], acc);
-    if (m < N && n < N) C[(size_t)m * N + n] = acc;
+    const float* br = Bs + tx * lp;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < kpad; k += 4) {
+        const float4 x = *reinterpret_cast<const float4*>(ar + k);
+        const float4 y = *reinterpret_cast<const float4*>(br + k);
+        a0 = fmaf(x.x, y.x, a0);
+        a1 = fmaf(x.y, y.y, a1);
+        a2 = fmaf(x.z, y.z, a2);
+        a3 = fmaf(x.w, y.w, a3);
+    }
+    if (m < N && n < N) C[(size_t)m * N + n] = (a0 + a1) + (a2 + a3);
 }
 
 void sgemm_f32_square(int N, const float* A, const float* B, float* C, cudaStream_t s) {
     const dim3 gg((N + SG - 1) / SG, (N + SG - 1) / SG), bb(SG, SG);
-    const size_t smem = (size_t)SG * (2 * N + 1) * sizeof(float);  // <= 48 KB
+    const size_t smem = (size_t)2 * SG * sg_pitch(N) * sizeof(float);  // <= 48 KB for N <= 376
     if (N <= 376) small_gemm_f32_staged_kernel<<<gg, bb, smem, s>>>(N, A, B, C, A, B, C);
     else small_gemm_f32_kernel<<<gg, bb, 0, s>>>(N, A, B, C);
 }
@@ -413,7 +525,7 @@ void sgemm_f32_square_pair(int N, const float* A0, const float* B0, float* C0, c
                            float* C1, cudaStream_t s) {
     if (N <= 376) {
         const dim3 gg((N + SG - 1) / SG, (N + SG - 1) / SG, 2), bb(SG, SG);
-        const size_t smem = (size_t)SG * (2 * N + 1) * sizeof(float);
+        const size_t smem = (size_t)2 * SG * sg_pitch(N) * sizeof(float);
         small_gemm_f32_staged_kernel<<<gg, bb, smem, s>>>(N, A0, B0, C0, A1, B1, C1);
     } else {
         sgemm_f32_square(N, A0, B0, C0, s);
@@ -855,8 +967,16 @@ cudaError_t gemm_rows(int M, int N, size_t K, const T* A, size_t lda, const T* B
     dim3 grid((M + GR_BM - 1) / GR_BM, (N + GR_BN - 1) / GR_BN, (unsigned)nch_eff);
     const bool vec = sizeof(T) == 4 && lda % 4 == 0 && ldb % 4 == 0 && ((uintptr_t)A & 15) == 0 &&
                      ((uintptr_t)B & 15) == 0;
-    if (vec) gemm_rows_kernel<T, true><<<grid, GR_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, absval, sym, kchunk, work);
-    else gemm_rows_kernel<T, false><<<grid, GR_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, absval, sym, kchunk, work);
+    if constexpr (sizeof(T) == 4) {
+        if (vec && !absval)
+            gemm_rows_f32_async_kernel<<<grid, GR_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, sym, kchunk, work);
+        else if (vec)
+            gemm_rows_kernel<T, true><<<grid, GR_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, absval, sym, kchunk, work);
+        else
+            gemm_rows_kernel<T, false><<<grid, GR_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, absval, sym, kchunk, work);
+    } else {
+        gemm_rows_kernel<T, false><<<grid, GR_THREADS, 0, s>>>(M, N, K, A, lda, B, ldb, absval, sym, kchunk, work);
+    }
     const size_t tot = (size_t)M * N;
     reduce_chunks_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(M, N, (int)nch_eff, work, alpha, sym, C,
                                                                        ldc);
