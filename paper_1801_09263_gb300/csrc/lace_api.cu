@@ -607,8 +607,11 @@ lace_status ace_contract(lace_ctx* c, int M, int N, const T* A, const T* B, doub
 
 // Out[n] = sum_k Coef[k][n] A[k] over the grid for the ACE vectors: tcgen05
 // 3xBF16 on the mixed path (LACE_NO_TC=1: CUDA-core FP32), FP64 otherwise.
-template <typename T>
-lace_status ace_combine(lace_ctx* c, int N, int Kc, const T* A, const double* Coef, T* Out, Launch& L) {
+// Out may be FP64 on the mixed path (the ACE apply's result, written by the
+// tensor-core epilogue directly); the CUDA-core form then goes through an FP32
+// buffer and a conversion.
+template <typename T, typename TO>
+lace_status ace_combine(lace_ctx* c, int N, int Kc, const T* A, const double* Coef, TO* Out, Launch& L) {
     const size_t ng = c->g.ng;
     if constexpr (std::is_same<T, float>::value) {
         const char* notc = getenv("LACE_NO_TC");
@@ -622,7 +625,14 @@ lace_status ace_combine(lace_ctx* c, int N, int Kc, const T* A, const double* Co
             return LACE_OK;
         }
     }
-    CK(gemm_combine<T>(N, ng, Kc, A, ng, Coef, N, 0.0, Out, ng, c->stream, &L.n), "combination");
+    if constexpr (std::is_same<T, TO>::value) {
+        CK(gemm_combine<T>(N, ng, Kc, A, ng, Coef, N, 0.0, Out, ng, c->stream, &L.n), "combination");
+    } else {
+        CK(c->scratch.ensure((size_t)2 * N * ng * sizeof(T)), "alloc combination");
+        T* tmp = c->scratch.as<T>() + (size_t)N * ng;  // past the staged input of the ACE apply
+        CK(gemm_combine<T>(N, ng, Kc, A, ng, Coef, N, 0.0, tmp, ng, c->stream, &L.n), "combination");
+        CK(convert<T, TO>(tmp, Out, (size_t)N * ng, c->stream, &L.n), "convert out");
+    }
     return LACE_OK;
 }
 
@@ -649,7 +659,7 @@ lace_status build_ace_impl(lace_ctx* c, int sym) {
     CK(transpose_f64(n, Linv, LinvT, c->stream, &L.n), "transpose");
     // xi_k = sum_j W_j (L^{-T})_{jk} = sum_j W_j Linv[k][j]: Coef[j][k] = LinvT[j][k]
     {
-        lace_status st = ace_combine<T>(c, n, n, c->W.as<T>(), LinvT, c->xi.as<T>(), L);
+        lace_status st = ace_combine<T, T>(c, n, n, c->W.as<T>(), LinvT, c->xi.as<T>(), L);
         if (st) return st;
     }
     return LACE_OK;
@@ -663,7 +673,6 @@ lace_status apply_ace_impl(lace_ctx* c, const double* d_psi64, int nf, double* d
     // staging for psi and result in working precision: use the FFT scratch
     CK(c->scratch.ensure((size_t)2 * nf * ng * sizeof(T)), "alloc ace apply");
     T* f = c->scratch.as<T>();
-    T* out = f + (size_t)nf * ng;
     const T* in = nullptr;
     if (sizeof(T) == 8) {
         in = reinterpret_cast<const T*>(d_psi64);
@@ -681,13 +690,9 @@ lace_status apply_ace_impl(lace_ctx* c, const double* d_psi64, int nf, double* d
     CK(neg_sum_squares((size_t)n * nf, X, c->exd.as<double>() + 8 + kSumBlocks, c->exd.as<double>() + 1, c->stream,
                        &L.n),
        "ace energy");
-    T* dst = sizeof(T) == 8 ? reinterpret_cast<T*>(d_out64) : out;
-    {
-        lace_status st = ace_combine<T>(c, nf, n, c->xi.as<T>(), X, dst, L);
-        if (st) return st;
-    }
-    if (sizeof(T) != 8) CK(convert<T, double>(out, d_out64, (size_t)nf * ng, c->stream, &L.n), "convert out");
-    return LACE_OK;
+    // K_ACE psi straight into the FP64 result (mixed path: the tensor-core
+    // epilogue widens its FP32 accumulators as it stores them)
+    return ace_combine<T, double>(c, nf, n, c->xi.as<T>(), X, d_out64, L);
 }
 
 template <typename T>

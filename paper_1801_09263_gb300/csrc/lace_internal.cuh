@@ -173,9 +173,11 @@ cudaError_t tc_gram(int M, int N, size_t K, const float* A, size_t lda, const fl
                     int* launches, bool absval = false, bool sym = false);
 size_t tc_gram_work_elems(int M, int N, size_t K, bool sym = false);
 // Tensor-core combination Out[n][r] = beta Out + sum_k Coef[k][n] A[k][r]
-// (FP32 A and Out, FP64 Coef, split 3xBF16); scratch of tc_combine_scratch_bytes.
+// (FP32 A, FP64 Coef, split 3xBF16, FP32 accumulation; Out FP32 or FP64);
+// scratch of tc_combine_scratch_bytes.
+template <typename TO>
 cudaError_t tc_combine(int N, size_t K, int Kc, const float* A, size_t lda, const double* Coef, int ldcoef,
-                       double beta, float* Out, size_t ldo, void* scratch, int* d_err, int* h_err, cudaStream_t s,
+                       double beta, TO* Out, size_t ldo, void* scratch, int* d_err, int* h_err, cudaStream_t s,
                        int* launches);
 size_t tc_combine_scratch_bytes(int N, int Kc);
 

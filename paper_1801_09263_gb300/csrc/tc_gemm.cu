@@ -672,10 +672,11 @@ __global__ void coef_split_kernel(int Kc, int N, const double* __restrict__ coef
     loT[idx] = __float2bfloat16_rn(x - __bfloat162float(h));
 }
 
+template <typename TO>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_combine_kernel(int N, size_t K, int Kc, int kpad, const float* __restrict__ A, size_t lda,
                       const __nv_bfloat16* __restrict__ hiT, const __nv_bfloat16* __restrict__ loT, float beta,
-                      float* __restrict__ Out, size_t ldo, int* __restrict__ err) {
+                      TO* __restrict__ Out, size_t ldo, int* __restrict__ err) {
     extern __shared__ unsigned char tc_smem_raw[];
     __shared__ uint64_t bars[2];
     __shared__ uint32_t tmem_base_sh;
@@ -796,8 +797,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int j = 0; j < 16; ++j) {
                     const int n = n0 + c0 + j;
                     if (n < N) {
-                        float* o = Out + (size_t)n * ldo + r;
-                        *o = beta == 0.f ? __uint_as_float(v[j]) : beta * *o + __uint_as_float(v[j]);
+                        TO* o = Out + (size_t)n * ldo + r;
+                        *o = beta == 0.f ? (TO)__uint_as_float(v[j]) : (TO)(beta * (float)*o + __uint_as_float(v[j]));
                     }
                 }
             }
@@ -829,10 +830,11 @@ constexpr int CT_A32_BYTES = TC_BK * TC_M * 4;                 // 32 KB: 64 k x 
 constexpr int CT_STAGE_BYTES = CT_A32_BYTES + 2 * CB_B_BYTES;  // + Coef^T hi, lo (32 KB each)
 constexpr int CT_SMEM_BYTES = CT_STAGES * CT_STAGE_BYTES + 2 * CB_A_BYTES + 1024;
 
+template <typename TO>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     tc_combine_tma_kernel(const __grid_constant__ CUtensorMap map_a, const __grid_constant__ CUtensorMap map_hi,
                           const __grid_constant__ CUtensorMap map_lo, int N, size_t K, int kpad, float beta,
-                          float* __restrict__ Out, size_t ldo, int* __restrict__ err) {
+                          TO* __restrict__ Out, size_t ldo, int* __restrict__ err) {
     extern __shared__ unsigned char tc_smem_raw[];
     __shared__ uint64_t full[CT_STAGES];
     __shared__ uint64_t mma_bar;
@@ -919,8 +921,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     for (int j = 0; j < 16; ++j) {
                         const int n = nt * CB_N + c0 + j;
                         if (n < N) {
-                            float* o = Out + (size_t)n * ldo + r;
-                            *o = beta == 0.f ? __uint_as_float(v[j]) : beta * *o + __uint_as_float(v[j]);
+                            TO* o = Out + (size_t)n * ldo + r;
+                            *o = beta == 0.f ? (TO)__uint_as_float(v[j]) : (TO)(beta * (float)*o + __uint_as_float(v[j]));
                         }
                     }
                 }
@@ -994,8 +996,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                 for (int j = 0; j < 16; ++j) {
                     const int n = nt * CB_N + c0 + j;
                     if (n < N) {
-                        float* o = Out + (size_t)n * ldo + r;
-                        *o = beta == 0.f ? __uint_as_float(v[j]) : beta * *o + __uint_as_float(v[j]);
+                        TO* o = Out + (size_t)n * ldo + r;
+                        *o = beta == 0.f ? (TO)__uint_as_float(v[j]) : (TO)(beta * (float)*o + __uint_as_float(v[j]));
                     }
                 }
             }
@@ -1067,22 +1069,23 @@ size_t tc_combine_scratch_bytes(int N, int Kc) {
     return 2 * kpad * npad * sizeof(__nv_bfloat16);
 }
 
+template <typename TO>
 cudaError_t tc_combine(int N, size_t K, int Kc, const float* A, size_t lda, const double* Coef, int ldcoef,
-                       double beta, float* Out, size_t ldo, void* scratch, int* d_err, int* h_err, cudaStream_t s,
+                       double beta, TO* Out, size_t ldo, void* scratch, int* d_err, int* h_err, cudaStream_t s,
                        int* launches) {
     if (N <= 0 || K == 0) return cudaSuccess;
     const int kpad = (Kc + TC_BK - 1) / TC_BK * TC_BK;
     const int npad = (N + CB_N - 1) / CB_N * CB_N;
     __nv_bfloat16* hiT = static_cast<__nv_bfloat16*>(scratch);
     __nv_bfloat16* loT = hiT + (size_t)kpad * npad;
-    static std::atomic<unsigned long long> attr_done{0};
+    static std::atomic<unsigned long long> attr_done{0};  // one per output type
     int dev = 0;
     cudaGetDevice(&dev);
     if (dev < 64 && !(attr_done.load() & (1ull << dev))) {
         cudaError_t e =
-            cudaFuncSetAttribute(tc_combine_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, CB_SMEM_BYTES);
+            cudaFuncSetAttribute(tc_combine_kernel<TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, CB_SMEM_BYTES);
         if (!e)
-            e = cudaFuncSetAttribute(tc_combine_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+            e = cudaFuncSetAttribute(tc_combine_tma_kernel<TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      CT_SMEM_BYTES);
         if (e) return e;
         attr_done.fetch_or(1ull << dev);
@@ -1106,12 +1109,12 @@ cudaError_t tc_combine(int N, size_t K, int Kc, const float* A, size_t lda, cons
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         const long long tiles = (long long)((K + TC_M - 1) / TC_M) * (npad / CB_N);
         const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(tiles, sms));
-        tc_combine_tma_kernel<<<grid, TC_THREADS, CT_SMEM_BYTES, s>>>(map_a, map_hi, map_lo, N, K, kpad, (float)beta,
-                                                                      Out, ldo, d_err);
+        tc_combine_tma_kernel<TO><<<grid, TC_THREADS, CT_SMEM_BYTES, s>>>(map_a, map_hi, map_lo, N, K, kpad,
+                                                                          (float)beta, Out, ldo, d_err);
     } else {
         dim3 grid((unsigned)((K + TC_M - 1) / TC_M), npad / CB_N);
-        tc_combine_kernel<<<grid, TC_THREADS, CB_SMEM_BYTES, s>>>(N, K, Kc, kpad, A, lda, hiT, loT, (float)beta,
-                                                                  Out, ldo, d_err);
+        tc_combine_kernel<TO><<<grid, TC_THREADS, CB_SMEM_BYTES, s>>>(N, K, Kc, kpad, A, lda, hiT, loT,
+                                                                      (float)beta, Out, ldo, d_err);
     }
     *launches += 2;
     if (h_err) {
@@ -1190,5 +1193,10 @@ cudaError_t tc_gram(int M, int N, size_t K, const float* A, size_t lda, const fl
     }
     return cudaGetLastError();
 }
+
+template cudaError_t tc_combine<float>(int, size_t, int, const float*, size_t, const double*, int, double, float*,
+                                       size_t, void*, int*, int*, cudaStream_t, int*);
+template cudaError_t tc_combine<double>(int, size_t, int, const float*, size_t, const double*, int, double, double*,
+                                        size_t, void*, int*, int*, cudaStream_t, int*);
 
 }  // namespace lace
