@@ -665,8 +665,10 @@ lace_status build_ace_impl(lace_ctx* c, int sym) {
     return LACE_OK;
 }
 
+// chunk >= 0: one chunk of a pipelined host apply; its share of the ACE
+// energy goes to exd[2 + chunk] (summed into exd[1] after the last chunk).
 template <typename T>
-lace_status apply_ace_impl(lace_ctx* c, const double* d_psi64, int nf, double* d_out64) {
+lace_status apply_ace_impl(lace_ctx* c, const double* d_psi64, int nf, double* d_out64, int chunk = -1) {
     Launch L{c};
     const size_t ng = c->g.ng;
     const int n = c->n_p;
@@ -687,8 +689,8 @@ lace_status apply_ace_impl(lace_ctx* c, const double* d_psi64, int nf, double* d
         if (st) return st;
     }
     // the block's ACE energy sum_j <psi_j|K_ACE|psi_j> = dV psi^T xi X = -|X|^2
-    CK(neg_sum_squares((size_t)n * nf, X, c->exd.as<double>() + 8 + kSumBlocks, c->exd.as<double>() + 1, c->stream,
-                       &L.n),
+    CK(neg_sum_squares((size_t)n * nf, X, c->exd.as<double>() + 8 + kSumBlocks,
+                       c->exd.as<double>() + (chunk < 0 ? 1 : 2 + chunk), c->stream, &L.n),
        "ace energy");
     // K_ACE psi straight into the FP64 result (mixed path: the tensor-core
     // epilogue widens its FP32 accumulators as it stores them)
@@ -866,6 +868,13 @@ lace_status lace_destroy(lace_ctx* c) {
     c->ktab_f.release();
     c->ktab_d.release();
     for (auto& e : c->ev) if (e) cudaEventDestroy(e);
+    if (c->io_in) {
+        cudaStreamSynchronize(c->io_in);
+        cudaStreamSynchronize(c->io_out);
+        cudaStreamDestroy(c->io_in);
+        cudaStreamDestroy(c->io_out);
+    }
+    for (auto& e : c->io_ev) if (e) cudaEventDestroy(e);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
     return LACE_OK;
@@ -1068,11 +1077,72 @@ lace_status lace_build_ace(lace_ctx* c, int sym) {
     return LACE_OK;
 }
 
+__global__ void sum_chunks_kernel(int n, const double* __restrict__ in, double* __restrict__ out) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += in[i];  // fixed order
+    *out = s;
+}
+
+// Mixed-precision ACE apply of host arrays in chunks of functions: chunk k's
+// upload (io_in), its application (the context's stream) and chunk k - 1's
+// download (io_out) overlap, so the two directions of the host link and the
+// GPU work at once instead of one after the other.
+static lace_status apply_ace_pipelined(lace_ctx* c, const double* psi, int n, double* out) {
+    const size_t ng = c->g.ng, cnt = (size_t)n * ng;
+    CK(c->aceio.ensure(2 * cnt * sizeof(double)), "alloc ace io");
+    if (!c->io_in) {
+        CK(cudaStreamCreateWithFlags(&c->io_in, cudaStreamNonBlocking), "streams");
+        CK(cudaStreamCreateWithFlags(&c->io_out, cudaStreamNonBlocking), "streams");
+        for (auto& e : c->io_ev) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "events");
+    }
+    double* din = c->aceio.as<double>();
+    double* dout = din + cnt;
+    const int nch = std::min(kApplyChunks, n);
+    const int per = (n + nch - 1) / nch;
+    // uploads after whatever the context's stream holds
+    CK(cudaEventRecord(c->io_ev[0], c->stream), "events");
+    CK(cudaStreamWaitEvent(c->io_in, c->io_ev[0], 0), "events");
+    for (int k = 0; k < nch; ++k) {
+        const size_t off = (size_t)k * per * ng, m = (size_t)std::max(0, std::min(per, n - k * per));
+        if (m) CK(cudaMemcpyAsync(din + off, psi + off, m * ng * sizeof(double), cudaMemcpyHostToDevice, c->io_in),
+                  "upload");
+        CK(cudaEventRecord(c->io_ev[1 + k], c->io_in), "events");
+    }
+    ev_begin(c, ST_ACE_APPLY);
+    lace_status st = LACE_OK;
+    for (int k = 0; k < nch && !st; ++k) {
+        const int m = std::max(0, std::min(per, n - k * per));
+        const size_t off = (size_t)k * per * ng;
+        CK(cudaStreamWaitEvent(c->stream, c->io_ev[1 + k], 0), "events");
+        if (m) st = apply_ace_impl<float>(c, din + off, m, dout + off, k);
+        else CK(cudaMemsetAsync(c->exd.as<double>() + 2 + k, 0, sizeof(double), c->stream), "energy");
+        if (st) break;
+        CK(cudaEventRecord(c->io_ev[1 + kApplyChunks + k], c->stream), "events");
+        CK(cudaStreamWaitEvent(c->io_out, c->io_ev[1 + kApplyChunks + k], 0), "events");
+        if (m) CK(cudaMemcpyAsync(out + off, dout + off, (size_t)m * ng * sizeof(double), cudaMemcpyDeviceToHost,
+                                  c->io_out),
+                  "download");
+    }
+    if (!st) {
+        sum_chunks_kernel<<<1, 1, 0, c->stream>>>(nch, c->exd.as<double>() + 2, c->exd.as<double>() + 1);
+        c->launches += 1;
+    }
+    ev_end(c, ST_ACE_APPLY);
+    cudaError_t e1 = cudaStreamSynchronize(c->io_out), e2 = cudaStreamSynchronize(c->stream),
+                e3 = cudaStreamSynchronize(c->io_in);
+    if (st) return st;
+    if (e1 || e2 || e3) return cuda_fail(c, e1 ? e1 : e2 ? e2 : e3, "apply ace");
+    CK(cudaGetLastError(), "apply ace");
+    c->ace_applied = true;
+    return LACE_OK;
+}
+
 static lace_status apply_ace_common(lace_ctx* c, const double* psi, int n, double* out, bool dev) {
     if (!c) return LACE_ERR_ARG;
     if (!c->ace) return fail(c, LACE_ERR_STATE, "build ACE before applying it");
     if (!psi || !out || n < 1) return fail(c, LACE_ERR_ARG, "bad pointers or count");
     cudaSetDevice(c->device);
+    if (!dev && c->prec != LACE_FP64 && (size_t)n * c->n_p <= c->mslot) return apply_ace_pipelined(c, psi, n, out);
     const size_t cnt = (size_t)n * c->g.ng;
     const double* din = psi;
     double* dout = out;

@@ -39,6 +39,8 @@ enum Stage { ST_LOAD = 0, ST_LOCALIZE, ST_SCREEN, ST_EXCHANGE, ST_ACE_BUILD, ST_
 enum MatSlot { MS_S = 0, MS_M, MS_MSYM, MS_L, MS_LINV, MS_LINVT, MS_E, MS_U, MS_A, MS_B, MS_X, MS_NSWORK, MS_COUNT_BASE };
 // MS_NSWORK takes 5 slots (Newton-Schulz work)
 constexpr int kMatSlots = MS_NSWORK + 5 + 1;
+// chunks of a host ACE apply (the chunk energies sit in exd[2 .. 2 + kApplyChunks))
+constexpr int kApplyChunks = 4;
 
 }  // namespace lace
 
@@ -91,6 +93,10 @@ struct lace_ctx {
 
     cudaEvent_t ev[2 * lace::ST_COUNT] = {};
     bool ev_used[lace::ST_COUNT] = {};
+    // a host ACE apply's chunks: uploads on io_in, downloads on io_out (both
+    // directions of the host link at once), made on first use
+    cudaStream_t io_in = nullptr, io_out = nullptr;
+    cudaEvent_t io_ev[1 + 2 * lace::kApplyChunks] = {};
 
     // small-matrix slots inside `mat` (each n_p*n_p doubles, plus staging)
     size_t mslot = 0;

@@ -255,6 +255,7 @@ def test_ace_build_and_apply(small_loc, prec, sym):
         psi = ctx.get_orbitals(B.ORB_PSI)
         k_on_psi = ctx.apply_ace(psi)
         k_probe = ctx.apply_ace(probe)
+        e_probe = ctx.ace_energy()  # the host apply runs in chunks (mixed path): their energies summed
     keep = keep_from_pairs(pairs, n, ne)
     W_ref, _, _ = O.apply_exchange(g, w, extra, keep)
     psi_ref = np.concatenate([w, extra])
@@ -267,6 +268,9 @@ def test_ace_build_and_apply(small_loc, prec, sym):
     # with truncation M' is not symmetric, so ACE is not exact on Psi: compare with the oracle's K_ACE
     assert relerr(k_on_psi, O.ace_apply(g, xi_ref, psi_ref)) < tol
     assert relerr(k_probe, O.ace_apply(g, xi_ref, probe)) < tol
+    # the block ACE energy sum_j <probe_j|K_ACE|probe_j> of the last application
+    e_ref = g.dv * float(np.sum(probe * O.ace_apply(g, xi_ref, probe)))
+    assert abs(e_probe - e_ref) <= tol * abs(e_ref), (e_probe, e_ref)
 
 
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
