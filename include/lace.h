@@ -189,7 +189,12 @@ lace_status lace_exchange_energy(lace_ctx* ctx, double f_spin, double* ex_out);
 lace_status lace_build_ace(lace_ctx* ctx, int sym);
 
 /* K_ACE psi = -xi (dV xi^T psi) for n functions psi (host FP64,
- * [n][n1][n2][n3]); kpsi_out (host FP64, same shape) receives the result. */
+ * [n][n1][n2][n3]); kpsi_out (host FP64, same shape) receives the result.
+ * In mixed precision the functions go in up to four chunks whose uploads,
+ * applications and downloads overlap (two extra streams of the context,
+ * made on first use); the call returns when all are done.  A tensor-core
+ * wait that gave up (LACE_ERR_TIMEOUT) is reported when the call returns;
+ * kpsi_out is then undefined. */
 lace_status lace_apply_ace(lace_ctx* ctx, const double* psi, int n, double* kpsi_out);
 
 /* The ACE energy of the block of the last lace_apply_ace(_dev):

@@ -420,6 +420,40 @@ lace_status align_impl(lace_ctx* c) {
 }
 
 // ------------------------------------------------------------------ screening
+// Timeout flags of the tensor-core calls (see lace_ctx::hflags): a call
+// takes slot s of the device flags (or, with none left, waits for its own,
+// h_err != nullptr), and tc_flag_copy queues the slot's copy to the pinned
+// host flags; tc_timed_out, after the API call's stream synchronisation,
+// reports whether any of them gave up.
+struct TcFlag {
+    int* d = nullptr;  // device slot
+    int* h = nullptr;  // host word to wait on (synchronous mode) or nullptr
+    int s = -1;
+    int herr = 0;
+};
+TcFlag tc_flag(lace_ctx* c) {
+    TcFlag f;
+    if (c->hflags && c->tc_next < kFlagSlots) {
+        f.s = c->tc_next++;
+        c->hflags[f.s] = 0;
+        f.d = c->flag.as<int>() + f.s;
+    } else {
+        f.d = c->flag.as<int>() + 1;
+        f.h = &f.herr;
+    }
+    return f;
+}
+cudaError_t tc_flag_copy(lace_ctx* c, const TcFlag& f) {
+    if (f.s < 0) return cudaSuccess;
+    return cudaMemcpyAsync(c->hflags + f.s, f.d, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+}
+bool tc_timed_out(lace_ctx* c) {
+    bool any = false;
+    for (int k = 2; k < c->tc_next; ++k) any |= c->hflags[k] != 0;
+    c->tc_next = 2;
+    return any;
+}
+
 // S_ik = dV sum_r |psi_i(r)| |psi_k(r)| (Eq. 4).  Mixed path: tcgen05 3xBF16
 // (S only decides which pairs pass the threshold; the Gram's periodic
 // compensated drains keep it ~1e-7 relative), symmetric tiles only; FP64 and
@@ -435,11 +469,12 @@ lace_status screen_impl(lace_ctx* c, double thr) {
         if (!(notc && notc[0] == '1') && ng % 4 == 0 && (uintptr_t)psi % 16 == 0) {
             CK(c->work.ensure(std::max(c->work.bytes, tc_gram_work_elems(n, n, ng, true) * sizeof(double))),
                "alloc work");
-            int herr = 0;
+            TcFlag f = tc_flag(c);
             CK(tc_gram(n, n, ng, psi, ng, psi, ng, c->g.dv, c->m(MS_S), n, c->work.as<double>(),
-                       c->work.bytes / sizeof(double), c->flag.as<int>(), &herr, c->stream, &L.n, true, true),
+                       c->work.bytes / sizeof(double), f.d, f.h, c->stream, &L.n, true, true),
                "overlap of moduli");
-            if (herr) return fail(c, LACE_ERR_TIMEOUT, "overlap of moduli: an mbarrier wait timed out");
+            if (f.herr) return fail(c, LACE_ERR_TIMEOUT, "overlap of moduli: an mbarrier wait timed out");
+            CK(tc_flag_copy(c, f), "flags");
             return LACE_OK;
         }
     }
@@ -590,11 +625,12 @@ lace_status ace_contract(lace_ctx* c, int M, int N, const T* A, const T* B, doub
         const bool aligned = ng % 4 == 0 && (uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0;
         if (!(notc && notc[0] == '1') && aligned) {
             CK(c->work.ensure(std::max(c->work.bytes, tc_gram_work_elems(M, N, ng) * sizeof(double))), "alloc work");
-            int herr = 0;
+            TcFlag f = tc_flag(c);
             CK(tc_gram(M, N, ng, A, ng, B, ng, alpha, C, N, c->work.as<double>(), c->work.bytes / sizeof(double),
-                       c->flag.as<int>(), &herr, c->stream, &L.n),
+                       f.d, f.h, c->stream, &L.n),
                "tensor-core contraction");
-            if (herr) return fail(c, LACE_ERR_TIMEOUT, "tensor-core contraction: an mbarrier wait timed out");
+            if (f.herr) return fail(c, LACE_ERR_TIMEOUT, "tensor-core contraction: an mbarrier wait timed out");
+            CK(tc_flag_copy(c, f), "flags");
             return LACE_OK;
         }
     }
@@ -617,11 +653,11 @@ lace_status ace_combine(lace_ctx* c, int N, int Kc, const T* A, const double* Co
         const char* notc = getenv("LACE_NO_TC");
         if (!(notc && notc[0] == '1')) {
             CK(c->work.ensure(std::max(c->work.bytes, tc_combine_scratch_bytes(N, Kc))), "alloc work");
-            int herr = 0;
-            CK(tc_combine(N, ng, Kc, A, ng, Coef, N, 0.0, Out, ng, c->work.p, c->flag.as<int>(), &herr, c->stream,
-                          &L.n),
+            TcFlag f = tc_flag(c);
+            CK(tc_combine(N, ng, Kc, A, ng, Coef, N, 0.0, Out, ng, c->work.p, f.d, f.h, c->stream, &L.n),
                "tensor-core combination");
-            if (herr) return fail(c, LACE_ERR_TIMEOUT, "tensor-core combination: an mbarrier wait timed out");
+            if (f.herr) return fail(c, LACE_ERR_TIMEOUT, "tensor-core combination: an mbarrier wait timed out");
+            CK(tc_flag_copy(c, f), "flags");
             return LACE_OK;
         }
     }
@@ -653,6 +689,9 @@ lace_status build_ace_impl(lace_ctx* c, int sym) {
     CK(symmetrize(n, M, A, sym, true, c->stream, &L.n), "symmetrize");
     int ok = 0;
     CK(cholesky_lower(n, A, n, c->flag.as<int>(), &ok, c->stream, &L.n), "cholesky");
+    // (the Cholesky's flag read synchronised the stream: the Gram's flag is in)
+    if (c->hflags && tc_timed_out(c))
+        return fail(c, LACE_ERR_TIMEOUT, "tensor-core contraction: an mbarrier wait timed out");
     if (!ok) return fail(c, LACE_ERR_NOT_PD, "-M' is not positive definite (Cholesky failed)");
     CK(cudaMemcpyAsync(c->m(MS_L), A, sizeof(double) * n * n, cudaMemcpyDeviceToDevice, c->stream), "copy L");
     CK(trtri_lower(n, A, n, Linv, n, c->stream, &L.n), "trtri");
@@ -852,6 +891,12 @@ lace_status lace_create(lace_ctx** out, int device, int precision) {
     }
     c->stream = c->own_stream;
     for (auto& e : c->ev) cudaEventCreate(&e);
+    void* hf = nullptr;  // pinned timeout flags (without them every tensor-core call waits for its own)
+    if (cudaHostAlloc(&hf, kFlagSlots * sizeof(int), cudaHostAllocDefault) == cudaSuccess) {
+        c->hflags = static_cast<int*>(hf);
+    } else {
+        cudaGetLastError();
+    }
     *out = c;
     return LACE_OK;
 }
@@ -875,6 +920,7 @@ lace_status lace_destroy(lace_ctx* c) {
         cudaStreamDestroy(c->io_out);
     }
     for (auto& e : c->io_ev) if (e) cudaEventDestroy(e);
+    if (c->hflags) cudaFreeHost(c->hflags);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
     return LACE_OK;
@@ -1010,11 +1056,14 @@ lace_status lace_screen(lace_ctx* c, double s_thr, long long* n_pairs_out) {
         if (st) return st;
     }
     ev_begin(c, ST_SCREEN);
+    c->tc_next = 2;
     lace_status st = c->prec == LACE_FP64 ? screen_impl<double>(c, s_thr) : screen_impl<float>(c, s_thr);
     if (st) return st;
     Launch L{c};
-    st = make_pairs(c, true, s_thr, L);
+    st = make_pairs(c, true, s_thr, L);  // reads the pair count back (stream synchronised)
     ev_end(c, ST_SCREEN);
+    if (c->hflags && tc_timed_out(c))
+        return fail(c, LACE_ERR_TIMEOUT, "overlap of moduli: an mbarrier wait timed out");
     if (st) return st;
     c->screened = true;
     c->s_thr = s_thr;
@@ -1064,6 +1113,7 @@ lace_status lace_build_ace(lace_ctx* c, int sym) {
     if (sym < 0 || sym > 2) return fail(c, LACE_ERR_ARG, "bad symmetrisation");
     cudaSetDevice(c->device);
     ev_begin(c, ST_ACE_BUILD);
+    c->tc_next = 2;
     lace_status st = c->prec == LACE_FP64 ? build_ace_impl<double>(c, sym) : build_ace_impl<float>(c, sym);
     ev_end(c, ST_ACE_BUILD);
     if (st) {
@@ -1073,6 +1123,10 @@ lace_status lace_build_ace(lace_ctx* c, int sym) {
         return st;
     }
     CK(cudaStreamSynchronize(c->stream), "build ace");
+    if (c->hflags && tc_timed_out(c)) {
+        c->ace = false;
+        return fail(c, LACE_ERR_TIMEOUT, "tensor-core combination: an mbarrier wait timed out");
+    }
     c->ace = true;
     return LACE_OK;
 }
@@ -1097,6 +1151,7 @@ static lace_status apply_ace_pipelined(lace_ctx* c, const double* psi, int n, do
     }
     double* din = c->aceio.as<double>();
     double* dout = din + cnt;
+    c->tc_next = 2;
     const int nch = std::min(kApplyChunks, n);
     const int per = (n + nch - 1) / nch;
     // uploads after whatever the context's stream holds
@@ -1130,9 +1185,11 @@ static lace_status apply_ace_pipelined(lace_ctx* c, const double* psi, int n, do
     ev_end(c, ST_ACE_APPLY);
     cudaError_t e1 = cudaStreamSynchronize(c->io_out), e2 = cudaStreamSynchronize(c->stream),
                 e3 = cudaStreamSynchronize(c->io_in);
+    const bool timed_out = c->hflags && tc_timed_out(c);
     if (st) return st;
     if (e1 || e2 || e3) return cuda_fail(c, e1 ? e1 : e2 ? e2 : e3, "apply ace");
     CK(cudaGetLastError(), "apply ace");
+    if (timed_out) return fail(c, LACE_ERR_TIMEOUT, "ACE apply: a tensor-core mbarrier wait timed out");
     c->ace_applied = true;
     return LACE_OK;
 }
@@ -1143,6 +1200,7 @@ static lace_status apply_ace_common(lace_ctx* c, const double* psi, int n, doubl
     if (!psi || !out || n < 1) return fail(c, LACE_ERR_ARG, "bad pointers or count");
     cudaSetDevice(c->device);
     if (!dev && c->prec != LACE_FP64 && (size_t)n * c->n_p <= c->mslot) return apply_ace_pipelined(c, psi, n, out);
+    c->tc_next = 2;
     const size_t cnt = (size_t)n * c->g.ng;
     const double* din = psi;
     double* dout = out;
@@ -1161,8 +1219,10 @@ static lace_status apply_ace_common(lace_ctx* c, const double* psi, int n, doubl
         if (e) st = cuda_fail(c, e, "download");
     }
     cudaError_t e = cudaStreamSynchronize(c->stream);
+    const bool timed_out = c->hflags && tc_timed_out(c);
     if (st) return st;
     if (e) return cuda_fail(c, e, "apply ace");
+    if (timed_out) return fail(c, LACE_ERR_TIMEOUT, "ACE apply: a tensor-core mbarrier wait timed out");
     c->ace_applied = true;
     return LACE_OK;
 }

@@ -41,6 +41,8 @@ enum MatSlot { MS_S = 0, MS_M, MS_MSYM, MS_L, MS_LINV, MS_LINVT, MS_E, MS_U, MS_
 constexpr int kMatSlots = MS_NSWORK + 5 + 1;
 // chunks of a host ACE apply (the chunk energies sit in exd[2 .. 2 + kApplyChunks))
 constexpr int kApplyChunks = 4;
+// int slots of a context's device flag buffer (64 bytes)
+constexpr int kFlagSlots = 16;
 
 }  // namespace lace
 
@@ -97,6 +99,11 @@ struct lace_ctx {
     // directions of the host link at once), made on first use
     cudaStream_t io_in = nullptr, io_out = nullptr;
     cudaEvent_t io_ev[1 + 2 * lace::kApplyChunks] = {};
+    // timeout flags of the tensor-core calls of one API call: device slots
+    // flag[2 .. tc_next), copied after each call into pinned hflags and read
+    // at the API call's next synchronisation instead of one wait per call
+    int* hflags = nullptr;  // pinned, kFlagSlots ints
+    int tc_next = 2;
 
     // small-matrix slots inside `mat` (each n_p*n_p doubles, plus staging)
     size_t mslot = 0;
