@@ -1109,29 +1109,30 @@ cudaError_t inv_sqrt_spd_mixed(int N, const double* A, double* X, double* work, 
     // Once h < 1e-6 N every |1 - x_k| < 0.016 and the iteration is in its
     // quadratic regime (1 - x -> ~(3/4)(1 - x)^2): two more steps reach the
     // FP32 rounding floor without another host-checked product.
+    // The check after every second step from the fourth on reads h from the
+    // next step's own first product P = Z Y, so it costs no product of its own.
     double prev = INFINITY;
     int extra = -1;
     for (int it = 0; it < 160; ++it) {
-        sgemm_f32_square(N, Z, Y, T, s);
-        ns_t_f32_kernel<<<nb, 256, 0, s>>>(N, T);
-        sgemm_f32_square_pair(N, Y, T, Y2, T, Z, Z2, s);
-        std::swap(Y, Y2);
-        std::swap(Z, Z2);
-        *launches += 3;
-        if (extra > 0 && --extra == 0) {
-            *ok = 1;
-            break;
-        }
-        if (extra < 0 && it >= 3 && (it % 2 == 1)) {
-            sgemm_f32_square(N, Z, Y, T, s);
+        sgemm_f32_square(N, Z, Y, T, s);  // P = Z Y of the current iterates
+        *launches += 1;
+        if (extra < 0 && it >= 4 && (it % 2 == 0)) {
             frob<float>(N, T, 1, scal, s, launches);
             cudaMemcpyAsync(&h, scal, sizeof(double), cudaMemcpyDeviceToHost, s);
-            *launches += 1;
             if ((e = cudaStreamSynchronize(s))) return e;
             if (!std::isfinite(h)) break;
             if (h < 1e-11 * N || (h < 1e-6 * N && h > 0.25 * prev)) { *ok = 1; break; }
             if (h < 1e-6 * N) extra = 2;
             prev = h;
+        }
+        ns_t_f32_kernel<<<nb, 256, 0, s>>>(N, T);
+        sgemm_f32_square_pair(N, Y, T, Y2, T, Z, Z2, s);
+        std::swap(Y, Y2);
+        std::swap(Z, Z2);
+        *launches += 2;
+        if (extra > 0 && --extra == 0) {
+            *ok = 1;
+            break;
         }
     }
     if (!*ok) return cudaGetLastError();
