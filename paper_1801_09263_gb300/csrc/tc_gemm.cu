@@ -10,14 +10,17 @@
 //
 // Kernels:
 // * tc_gram_ws_kernel (the Gram, default): one 128 x 128 output tile and one
-//   K chunk per CTA; the FP32 rows arrive by TMA (cp.async.bulk.tensor) four
-//   32-wide steps ahead, 16 warps split them into BF16 hi/lo tiles (64-byte
-//   swizzled K-major, two stages), one thread issues the tcgen05.mma (M128
-//   N128 K16) and one the copies; the roles hand off through mbarriers.
+//   K chunk per CTA (for A = B only the tiles on and above the diagonal); the
+//   FP32 rows arrive by TMA (cp.async.bulk.tensor) four 32-wide steps ahead,
+//   16 warps split them into BF16 hi/lo tiles (64-byte swizzled K-major, two
+//   stages), one thread issues the tcgen05.mma (M128 N128 K16) and one the
+//   copies; the roles hand off through mbarriers.  The MMAs accumulate a few
+//   steps per TMEM accumulator (two alternating), which the split warps drain
+//   into compensated FP32 sums.
 // * tc_combine_tma_kernel (the combination, default): persistent over output
 //   tiles of 128 grid points x 256 targets; the FP32 A tiles and the pre-split
 //   coefficient tiles arrive by TMA (the latter directly in the 128-byte
-//   swizzled layout), the threads transpose-split A.
+//   swizzled layout), the threads transpose-split A; FP32 or FP64 output.
 // * tc_gram_kernel / tc_combine_kernel: the same contractions with the
 //   operands loaded through registers (used when no tensor map can be made).
 // Every mbarrier wait is bounded; on a timeout the CTA records an error,
