@@ -86,6 +86,26 @@ def test_plain_exchange_24cubed_8_orbitals(cfg1, cfg1_ref, prec):
         assert abs(-0.5 * e.sum() - ex) <= 1e-12 * abs(ex)
 
 
+@pytest.mark.parametrize("n_occ,centres", [(100, 80), (300, 120)])
+def test_host_load_matches_the_device_load(n_occ, centres):
+    """Mixed precision, 100 and 300 orbitals (2 and 5 tiles of the Loewdin
+    overlap, the last one partial): orbitals loaded from host arrays are
+    bit-identical to those of lace_load_orbitals_dev, and close to the
+    oracle's symmetric orthonormalisation (overlap condition numbers ~200
+    and ~1,000 here)."""
+    torch = pytest.importorskip("torch")
+    sysm = synth.small_localized_system(91, (13.0, 13.0, 13.0), (36, 36, 36), 12.0, centres, n_occ, 0)
+    with make_ctx(sysm, LACE_MIXED) as ctx:
+        psi_host = ctx.get_orbitals(B.ORB_PSI)
+    with Lace(0, LACE_MIXED) as ctx:
+        ctx.set_cell(sysm.cell, sysm.shape, sysm.ecut)
+        ctx.load_orbitals_dev(torch.from_numpy(sysm.phi).cuda(), n_occ, 0, True)
+        psi_dev = ctx.get_orbitals(B.ORB_PSI)
+    assert np.array_equal(psi_host, psi_dev)
+    occ = O.lowdin(O.Grid(sysm.cell, sysm.shape), sysm.phi)
+    assert relerr(psi_host, occ) < 1e-4
+
+
 @pytest.mark.parametrize("shape,cell", [((45, 45, 45), (11.0, 11.0, 11.0)),
                                         ((24, 30, 20), (9.0, 11.0, 8.0)),
                                         ((25, 27, 32), (9.5, 10.0, 12.0))])
