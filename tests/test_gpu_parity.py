@@ -86,6 +86,28 @@ def test_plain_exchange_24cubed_8_orbitals(cfg1, cfg1_ref, prec):
         assert abs(-0.5 * e.sum() - ex) <= 1e-12 * abs(ex)
 
 
+@pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
+def test_overlap_of_moduli_with_partial_tiles(prec):
+    """150 orbitals: two 128-row tiles of the tensor-core Gram (the second
+    partial), the three symmetric tiles only, against the oracle's Eq. 4 on
+    the oracle's SCDM orbitals at the same pivots."""
+    sysm = synth.small_localized_system(93, (13.0, 13.0, 13.0), (36, 36, 36), 12.0, 120, 150, 0)
+    g, occ, _ = oracle_orbitals(sysm)
+    piv, _, w = O.scdm(g, occ, 2)
+    s_ref = O.overlap_moduli(g, w)
+    with make_ctx(sysm, prec) as ctx:
+        ctx.set_pivots(piv)
+        n = ctx.screen(1e-3)
+        s = ctx.get_matrix(B.MAT_OVERLAP_MODULI)
+        pairs = ctx.get_pairs()
+    assert relerr(s, s_ref) < (1e-10 if prec == LACE_FP64 else 1e-5)
+    keep = keep_from_pairs(pairs, 150, 0)
+    keep_ref = O.kept_pairs(s_ref, 1e-3, 150, 0)
+    band = np.abs(s_ref - 1e-3) <= 1e-4 * 1e-3
+    assert not ((keep != keep_ref) & ~band).any()
+    assert n == len(pairs) == int(np.triu(keep).sum())
+
+
 @pytest.mark.parametrize("n_occ,centres", [(100, 80), (300, 120)])
 def test_host_load_matches_the_device_load(n_occ, centres):
     """Mixed precision, 100 and 300 orbitals (2 and 5 tiles of the Loewdin
