@@ -315,6 +315,30 @@ def test_ace_build_and_apply(small_loc, prec, sym):
     assert abs(e_probe - e_ref) <= tol * abs(e_ref), (e_probe, e_ref)
 
 
+def test_host_ace_apply_in_uneven_chunks(small_loc):
+    """Mixed precision, 5 host functions: the chunked host apply runs chunks
+    of 2, 2 and 1 functions and an empty fourth; its result is bit-identical
+    to the device apply of the same functions (the same tiles and K chunks),
+    and the chunk energies sum to the device apply's block energy."""
+    torch = pytest.importorskip("torch")
+    g, occ, _ = oracle_orbitals(small_loc)
+    piv, _, _ = O.scdm(g, occ, 2)
+    probe = np.random.default_rng(11).standard_normal((5,) + g.shape)
+    with make_ctx(small_loc, LACE_MIXED) as ctx:
+        ctx.set_pivots(piv)
+        ctx.screen(1e-3)
+        ctx.apply_exchange()
+        ctx.build_ace()
+        k_host = ctx.apply_ace(probe)
+        e_host = ctx.ace_energy()
+        p_dev = torch.from_numpy(probe).cuda()
+        k_dev = torch.empty_like(p_dev)
+        ctx.apply_ace_dev(p_dev, k_dev)
+        e_dev = ctx.ace_energy()
+    assert np.array_equal(k_host, k_dev.cpu().numpy())
+    assert abs(e_host - e_dev) <= 1e-12 * abs(e_dev)
+
+
 @pytest.mark.parametrize("prec", PRECS, ids=PNAME.get)
 def test_ace_on_a_grid_with_an_odd_point_count(prec):
     # 25 x 27 x 45 points: rows of the orbital arrays are not 16-byte aligned
